@@ -1,0 +1,289 @@
+"""Benchmark: converged space-time DOF/s of the all-at-once BDF1 Newton solver.
+
+Workload (N = 1): viscous Burgers, 256 x 256 interior nodes on [0,1]^2, nu = 0.01,
+zero Dirichlet data, u0 = sin(2 pi x) sin(2 pi y), dt = 1e-3, M = 256 levels,
+FP64 throughout, plain initial guess u^n = u^0, Newton to ||R||_inf <= 1e-12.
+One step = one converged solve (plain guess -> residual/assembly/level chain per
+Newton iteration -> converged U), inputs resident in HBM. The working set
+(U, R, five Jacobian planes: ~0.94 GB) is larger than L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun, one rank per GPU) runs independent replicas of the workload
+(the single solve does not shard; weak scaling, no data-path collective).
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (its first levels: the system is block lower-triangular in time, so the
+first L levels form a closed problem).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "converged space-time DOF/s at ≤1e-10 rel. error; plain vs mixed/batched/learned"
+UNIT = "DOF/s"
+# FP64 peak of GB300: 1.25 TFLOP/s (152 SMs x 2 FP64 FMA/clk x 2 flop x ~2.07 GHz),
+# the dense FP64 rate the profiling recipe lists; measured MEASURED_PEAKS.json has
+# no FP64 entry.
+FP64_PEAK_TFLOPS = 1.25
+# Algorithmic FP64 flops (FMA = 2) per unknown: one red-black SOR update
+# (4 couplings, rhs, relaxation) and one BiCGStab iteration (2 SpMV + 6 axpy + 5 dots).
+FLOPS_PER_SOR_UPDATE = 11
+FLOPS_PER_BICGSTAB_ITER = 2 * 9 + 6 * 2 + 5 * 2
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2406_00878_gb300 import pit
+    from paper_2406_00878_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    p = W.burgers256(seed=0, M=args.levels)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = pit.context_for(p, stream=stream)
+        U = torch.empty(p.dof, dtype=torch.float64, device="cuda")
+
+        def step():
+            pit.pit_fill_plain_guess(ctx, U)
+            return pit.pit_solve(ctx, U)[1]
+
+        for _ in range(max(args.warmup, 0)):
+            info = step()
+        stream.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        infos = []
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                infos.append(step())
+            e1.record(stream)
+            e1.synchronize()
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        ms = e0.elapsed_time(e1) / args.steps
+        if ws > 1:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        # accuracy of the timed result against the oracle's first levels (rank 0)
+        Ug = U.cpu().numpy().reshape(p.M, -1)
+
+        # end to end through the host-buffer entry point: H2D u0 + solve + D2H U
+        u0_h = torch.from_numpy(np.ascontiguousarray(p.u0)).pin_memory()
+        U_h = torch.empty(p.dof, dtype=torch.float64).pin_memory()
+        for _ in range(2):
+            pit.pit_solve_host(ctx, u0_h, U_h)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pit.pit_solve_host(ctx, u0_h, U_h)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        if ws > 1:
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        ctx.close()
+
+    last = infos[-1]
+    k = last["newton_iters"]
+    steps = last["steps"]
+    ms_res = sum(s["ms_residual"] for s in steps)
+    ms_asm = sum(s["ms_assemble"] for s in steps)
+    ms_sol = sum(s["ms_solve"] for s in steps)
+    launches = 1 + 3 * k + 1  # plain guess + (residual, assembly, chain) per update + final residual
+    # dominant kernel: the level chain; its algorithmic FP64 flops per launch from the
+    # measured sweeps / iterations of each level
+    flops = 0.0
+    for s in steps:
+        n_sor = s["levels_sor"]
+        n_bcg = p.M - n_sor
+        it = s["lin_iters_mean"] * p.M
+        # split iterations between methods in proportion (all levels share a method here)
+        frac_sor = n_sor / p.M
+        flops += p.grid.ns * (it * frac_sor * FLOPS_PER_SOR_UPDATE + it * (1 - frac_sor) * FLOPS_PER_BICGSTAB_ITER)
+    flops_per_launch = flops / max(k, 1)
+    chain_ms_per_launch = ms_sol / max(k, 1)
+    achieved_tflops = flops_per_launch / (chain_ms_per_launch * 1e-3) / 1e12
+    out = None
+    if rank == 0:
+        value = ws * p.dof / (ms * 1e-3)
+        err = None
+        if args.check:
+            import oracle
+            L = 6
+            Uo, _, _, _ = oracle.solve(W.truncated(p, L), tol=1e-13)
+            err = float(np.abs(Ug[:L] - Uo).max() / np.abs(Uo).max())
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"burgers256: 2-D viscous Burgers 256x256 interior, nu=0.01, dt=1e-3, "
+                                   f"M={p.M}, u0=sin(2pi x)sin(2pi y), plain guess, Newton to ||R||_inf<=1e-12",
+                       "dof_per_solve": p.dof, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (U, R, 5 Jacobian planes ~0.94 GB); no flush",
+                       "newton_iters": k, "res_inf": last["res_inf"],
+                       "lin_iters_mean_per_level": [round(s["lin_iters_mean"], 2) for s in steps],
+                       "levels_sor": [s["levels_sor"] for s in steps],
+                       "stage_ms": {"residual": ms_res, "assemble": ms_asm, "level_chain": ms_sol},
+                       "max_rel_err_first_levels_vs_oracle": err},
+            "gpu_launches": launches * args.steps,
+            "e2e": {"value": ws * p.dof / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(p.grid.ns * 8),
+                    "d2h_bytes_per_step": int(p.dof * 8)},
+            "roofline": {"kernel": "chain_kernel (level chain, eq. 7 nested inverse)", "bound": "alu",
+                         "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "FP64 nominal 1.25 TFLOP/s (profiling recipe); FP64 not in MEASURED_PEAKS"},
+            "clocks": clk.summary(),
+        }
+        if args.cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def cpu_baseline(args, levels=None):
+    """The FP64 oracle (all-at-once Newton, banded/BiCGStab level solves, single thread)
+    on the first `levels` levels of the same workload."""
+    import oracle
+    from paper_2406_00878_gb300 import workloads as W
+    L = levels or args.cpu_levels
+    p = W.truncated(W.burgers256(seed=0, M=args.levels), L)
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.solve(p, tol=1e-12)
+    dt = time.perf_counter() - t0
+    return {"value": p.dof / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {L} of {args.levels} levels of burgers256 ({p.dof} DOF), all-at-once Newton "
+                      f"to 1e-12, {dt:.1f} s"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    vals = []
+    for _ in range(max(args.warmup, 0)):
+        cpu_baseline(args, levels=args.ref_levels)
+    t_total = 0.0
+    dof = 0
+    for _ in range(args.steps):
+        r = cpu_baseline(args, levels=args.ref_levels)
+        vals.append(r["value"])
+    value = statistics.median(vals)
+    cb = cpu_baseline.__doc__
+    from paper_2406_00878_gb300 import workloads as W
+    dof = args.ref_levels * W.Grid(256, 256).ns
+    ms = dof / value * 1e3
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"burgers256 (first {args.ref_levels} of {args.levels} levels per step)",
+                       "dof_per_step": dof},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {args.ref_levels} levels of burgers256 per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--levels", type=int, default=256)
+    ap.add_argument("--cpu-levels", type=int, default=48)
+    ap.add_argument("--ref-levels", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-check", dest="check", action="store_false")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+    else:
+        out = run_ours(args, ws, rank, local)
+    if out is not None and rank == 0:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

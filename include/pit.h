@@ -1,0 +1,190 @@
+/*
+ * pit.h -- C ABI of libpit.so: the all-at-once BDF1 Newton iteration of
+ * Yamaleev & Paudel, "A New Parallel-in-time Direct Inverse Method for
+ * Nonlinear Differential Equations" (arXiv 2406.00878), on one GB300 GPU.
+ *
+ * The method (paper Sec. 2-4):
+ *   eq. 1  u_t + f(u)_x + g(u)_y = (mu(u) u_x)_x + (mu(u) u_y)_y on a rectangle,
+ *          Dirichlet data b on the boundary (eq. 2), initial data u0;
+ *          nonlinear heat: f = g = 0, mu = mu_a + mu_b u^2;
+ *          viscous Burgers: f = g = u^2/2, mu = mu_a (+ mu_b u^2).
+ *   eq. 3  BDF1 in time, 2nd-order 3-point central differences in x and y,
+ *          mid-point viscosity mu_{i+1/2} = mu((u_i + u_{i+1})/2).
+ *   eq. 4  all time levels n = 1..M form one nonlinear system G(U) = 0.
+ *   eq. 5  Newton: A_n du^n - du^{n-1} = r^n with A_n = I + tau dF/du(u^n)
+ *          and r^n = -tau[(u^n - u^{n-1})/tau + F(u^n) - q^n].
+ *   eq. 6  the Jacobian is block bidiagonal (A_n on the diagonal, -I below).
+ *   eq. 7  its exact inverse, applied in nested form
+ *          du^n = A_n^{-1}(r^n + du^{n-1}), one level solve per time level.
+ *
+ * Conventions for every entry point:
+ *   - nx, ny count INTERIOR nodes; h_x = (xr - xl)/(nx + 1), node (j, i) sits at
+ *     x = xl + (i + 1) h_x, y = yl + (j + 1) h_y; Ns = nx * ny.
+ *   - All arrays are IEEE FP64 and C-contiguous with x fastest:
+ *       level vector  [ny][nx]
+ *       space-time    [M][ny][nx]       level n = 1..M at offset (n-1)*Ns
+ *       boundary data [M][2*nx + 2*ny]  per level: south row (j = -1, nx values),
+ *                                       north row (j = ny, nx), west column
+ *                                       (i = -1, ny), east column (i = nx, ny)
+ *       coefficients  [5][M][Ns]        C, W, E, S, N entries of each row of A_n
+ *   - Pointers named *_dev are device pointers on the context's device; they are
+ *     owned by the caller and must stay valid for the duration of the call.
+ *     Pointers named *_host are host pointers (pinned memory is fastest).
+ *   - Every call is ordered on the CUDA stream given to pit_create (NULL = the
+ *     legacy default stream). Calls that return norms or statistics synchronise
+ *     that stream before returning.
+ *   - Errors are returned as pit_status; the library never aborts and never
+ *     throws across the ABI. pit_last_error() gives a message for the last
+ *     failing call on a context. Device-side waits are bounded: a wait that runs
+ *     out of its budget ends the kernel with PIT_ETIMEOUT instead of hanging.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef PIT_H
+#define PIT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pit_ctx pit_ctx;
+
+typedef enum {
+    PIT_OK = 0,
+    PIT_EINVAL = 1,       /* invalid argument (sizes, NULL pointers, parameters) */
+    PIT_ECUDA = 2,        /* a CUDA runtime call failed */
+    PIT_ENOMEM = 3,       /* device allocation failed */
+    PIT_ENOCONV = 4,      /* Newton or a level solve hit its iteration cap */
+    PIT_EDIVERGED = 5,    /* NaN/Inf in the residual or the update */
+    PIT_ETIMEOUT = 6,     /* a bounded device-side wait ran out of budget */
+    PIT_EUNSUPPORTED = 7  /* the problem does not fit the kernels' limits */
+} pit_status;
+
+typedef enum { PIT_HEAT = 0, PIT_BURGERS = 1 } pit_equation;
+
+/* Level solver for the diagonal blocks A_n (eq. 7, one solve per level). */
+typedef enum {
+    PIT_LIN_AUTO = 0,     /* per level: SOR when the Jacobi-scaled Gershgorin bound of
+                             A_n is below sor_rho_max, else BiCGStab */
+    PIT_LIN_SOR = 1,      /* red-black SOR, omega from the Gershgorin bound */
+    PIT_LIN_BICGSTAB = 2  /* Jacobi-preconditioned BiCGStab */
+} pit_lin_solver;
+
+typedef struct {
+    int nx, ny;             /* interior nodes, >= 1 */
+    double xl, xr, yl, yr;  /* domain, xr > xl, yr > yl */
+} pit_grid;
+
+typedef struct {
+    int equation;           /* pit_equation */
+    double mu_a, mu_b;      /* mu(u) = mu_a + mu_b u^2, both >= 0 (mu >= 0, Sec. 2) */
+} pit_params;
+
+typedef struct {
+    int newton_max;         /* max Newton updates in pit_solve (default 30) */
+    double tol_res;         /* pit_solve stops when ||R||_inf <= tol_res, R the tau-scaled
+                               residual of eq. 5 (default 1e-12) */
+    int lin_solver;         /* pit_lin_solver (default PIT_LIN_AUTO) */
+    double eta_max;         /* inexact-Newton forcing: each level solve reduces its error
+                               estimate to eta * ||rhs||, eta = min(eta_max, eta_gamma*||R||_inf)
+                               (default 1e-2) */
+    double eta_gamma;       /* (default 1.0) */
+    double lin_atol;        /* absolute floor of the level-solve tolerance (default 1e-15) */
+    int lin_max_iter;       /* cap on sweeps / iterations per level solve (default 4000) */
+    double sor_rho_max;     /* AUTO uses SOR below this Gershgorin bound (default 0.95) */
+    int team_ctas;          /* CTAs that share one level in the chain kernel (0 = auto) */
+    long long wait_budget;  /* spin iterations before a device wait gives up (default 1<<26) */
+} pit_options;
+
+#define PIT_MAX_NEWTON 64
+
+typedef struct {
+    double res_inf;         /* ||R||_inf of the iterate the step started from */
+    double upd_rms;         /* sqrt(sum(dU^2) / (M Ns)), the update norm of Sec. 8 */
+    double lin_iters_mean;  /* mean sweeps (SOR) or iterations (BiCGStab) per level */
+    int lin_iters_max;
+    int levels_sor;         /* levels solved by SOR in this step */
+    int levels_capped;      /* levels that hit lin_max_iter */
+    float ms_residual, ms_assemble, ms_solve;  /* device time of the three stages */
+} pit_step_info;
+
+typedef struct {
+    int newton_iters;                      /* Newton updates applied */
+    int converged;                         /* 1 when ||R||_inf <= tol_res was reached */
+    double res_inf[PIT_MAX_NEWTON + 1];    /* ||R_k||_inf, k = 0..newton_iters */
+    pit_step_info steps[PIT_MAX_NEWTON];
+    double ms_total;                       /* device time of the whole solve */
+} pit_solve_info;
+
+/* Fill *opt with the defaults listed above. */
+void pit_default_options(pit_options* opt);
+
+/* Create a context for one problem: grid, M time levels of constant step dt
+ * (tau_n = dt, t^n = n dt), closure parameters; opt may be NULL (defaults).
+ * stream is a cudaStream_t (NULL = legacy default stream). Allocates every
+ * device workspace here (residual, Jacobian planes, team workspace, the iterate of
+ * pit_solve_host); only pit_set_data allocates later, once, for boundary data or
+ * sources. Dirichlet data and sources are zero and u0 is zero until pit_set_data.
+ * The chain kernel shares each level among a team of CTAs that must be co-resident
+ * (cooperative launch); PIT_EUNSUPPORTED when a grid row does not fit. */
+pit_status pit_create(const pit_grid* grid, int M, double dt, const pit_params* params, const pit_options* opt,
+                      void* stream, pit_ctx** out);
+
+/* Copy problem data into the context (device to device, stream ordered):
+ * u0_dev [Ns] initial data u^0 (required); bc_dev [M][2nx+2ny] Dirichlet data at
+ * t^n, or NULL for zero (eq. 2); q_dev [M][Ns] source q^n, or NULL for zero (eq. 4). */
+pit_status pit_set_data(pit_ctx* ctx, const double* u0_dev, const double* bc_dev, const double* q_dev);
+
+/* Write the plain initial iterate u^n = u^0, n = 1..M, into U_dev [M][Ns]. */
+pit_status pit_fill_plain_guess(pit_ctx* ctx, double* U_dev);
+
+/* Row (a1): the all-at-once residual of eq. 4-5 for all M levels at once,
+ * R_dev[n] = -tau[(u^n - u^{n-1})/tau + F(u^n) - q^n] with F of eq. 3.
+ * U_dev [M][Ns] in, R_dev [M][Ns] out (may not alias U_dev). If res_inf is not
+ * NULL it receives ||R||_inf (synchronises the stream). */
+pit_status pit_residual(pit_ctx* ctx, const double* U_dev, double* R_dev, double* res_inf);
+
+/* Row (a2): the Jacobian blocks A_n = I + tau dF/du(u^n) of eq. 5-6 for all M
+ * levels at once: coef_dev [5][M][Ns] receives the C, W, E, S, N entries of
+ * every row (couplings to boundary nodes are 0). */
+pit_status pit_assemble(pit_ctx* ctx, const double* U_dev, double* coef_dev);
+
+/* Row (a3): solve the block-bidiagonal system of eq. 6 whose diagonal blocks are
+ * the Jacobians A_n at U_dev, with right-hand side R_dev, by the exact block
+ * inverse of eq. 7 in nested form: du^1 = A_1^{-1} r^1, du^n = A_n^{-1}(r^n + du^{n-1}),
+ * one level solve per time level, chained. dU_dev [M][Ns] receives the solution;
+ * U_dev is not modified. Each level solve stops when its error estimate (SOR) or
+ * its preconditioned residual (BiCGStab) falls below max(eta * ||rhs||, lin_atol);
+ * pass a small eta (e.g. 1e-14) for a nearly exact solve. info (may be NULL)
+ * receives iteration statistics. PIT_ENOCONV: a level hit lin_max_iter (dU holds
+ * the capped result). */
+pit_status pit_block_solve(pit_ctx* ctx, const double* U_dev, const double* R_dev, double* dU_dev, double eta,
+                           pit_step_info* info);
+
+/* One Newton iteration in place on U_dev [M][Ns]: residual (a1), blocks (a2),
+ * nested block inverse (a3) with the inexact-Newton forcing of pit_options, and
+ * the update U += dU. info (may be NULL) receives norms and statistics. */
+pit_status pit_newton_step(pit_ctx* ctx, double* U_dev, pit_step_info* info);
+
+/* Row (a4): Newton from the iterate in U_dev until ||R||_inf <= tol_res or
+ * newton_max updates (PIT_ENOCONV; U_dev holds the last iterate). */
+pit_status pit_solve(pit_ctx* ctx, double* U_dev, pit_solve_info* info);
+
+/* pit_solve with host buffers: copies u0_host [Ns] to the device (replacing u^0),
+ * starts from the plain guess u^n = u^0, solves, and copies the solution to
+ * U_host [M][Ns]. Uses the context-owned device iterate allocated by pit_create;
+ * the boundary data and sources set by pit_set_data are kept. */
+pit_status pit_solve_host(pit_ctx* ctx, const double* u0_host, double* U_host, pit_solve_info* info);
+
+/* Message for the last failing call on ctx (never NULL). */
+const char* pit_last_error(const pit_ctx* ctx);
+
+/* Name of a status code (never NULL). */
+const char* pit_status_string(pit_status s);
+
+/* Release every device and host resource of ctx (NULL is ignored). */
+void pit_destroy(pit_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIT_H */

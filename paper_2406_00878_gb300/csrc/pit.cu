@@ -1,0 +1,529 @@
+// pit.cu -- host side of libpit.so: the C ABI declared in include/pit.h.
+//
+// A context owns the problem data (u^0, Dirichlet data, sources), the residual,
+// the Jacobi-scaled Jacobian planes of all levels and the chain kernel's team
+// workspace. Every entry point enqueues work on the context's stream; norms and
+// statistics are read back with small device-to-host copies.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "pit.h"
+#include "pit_kernels.cuh"
+
+using namespace pit;
+
+namespace {
+constexpr int kNT = 256;        // threads per CTA of every kernel
+constexpr int kMinLocal = 256;  // auto team size: at least this many unknowns per CTA
+}  // namespace
+
+struct pit_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    cudaStream_t stream = nullptr;
+    pit_grid grid{};
+    int M = 0;
+    double dt = 0.0;
+    pit_params params{};
+    pit_options opt{};
+    OpConst oc{};
+    bool conv = false, nlv = false;
+    long long Ns = 0, DOF = 0;
+    int nb = 0;  // boundary values per level
+
+    // problem data and workspaces (device)
+    double* u0 = nullptr;
+    double* bc = nullptr;    // nullptr = zero Dirichlet data
+    double* q = nullptr;     // nullptr = no source
+    bool has_bc = false, has_q = false;
+    double* R = nullptr;     // [M][Ns]
+    double* coef = nullptr;  // [5][M][Ns] scaled planes
+    double* Uh = nullptr;    // [M][Ns] iterate of pit_solve_host
+    unsigned long long* keys = nullptr;  // [0] ||R||_inf key, [1..M] Gershgorin keys
+
+    // chain team workspace
+    int G = 0, rows_base = 0, rows_rem = 0;
+    size_t chain_smem = 0;
+    double* pub = nullptr;
+    double* red_part = nullptr;
+    unsigned long long* sync_words = nullptr;  // flags[G], red_cnt[4]
+    int* ints = nullptr;                       // abort, status, level_iters[M], level_method[M]
+    double* cta_sumsq = nullptr;               // [G]
+
+    // host mirrors
+    std::vector<int> h_ints;
+    std::vector<double> h_sumsq;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+
+    char err[512] = "";
+};
+
+// ------------------------------------------------------------------- helpers
+
+static pit_status fail(pit_ctx* c, pit_status s, const char* fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? PIT_ENOMEM : PIT_ECUDA, "%s: %s (%s:%d)", #call, \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                               \
+    } while (0)
+
+#define CHECK_RET(expr)             \
+    do {                            \
+        pit_status s_ = (expr);     \
+        if (s_ != PIT_OK) return s_; \
+    } while (0)
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t count) {
+    return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+static double key_to_double(unsigned long long k) {
+    double d;
+    std::memcpy(&d, &k, sizeof(d));
+    return d;
+}
+
+extern "C" void pit_default_options(pit_options* o) {
+    if (!o) return;
+    o->newton_max = 30;
+    o->tol_res = 1e-12;
+    o->lin_solver = PIT_LIN_AUTO;
+    o->eta_max = 1e-2;
+    o->eta_gamma = 1.0;
+    o->lin_atol = 1e-15;
+    o->lin_max_iter = 4000;
+    o->sor_rho_max = 0.95;
+    o->team_ctas = 0;
+    o->wait_budget = 1ll << 26;
+}
+
+extern "C" const char* pit_status_string(pit_status s) {
+    switch (s) {
+        case PIT_OK: return "PIT_OK";
+        case PIT_EINVAL: return "PIT_EINVAL";
+        case PIT_ECUDA: return "PIT_ECUDA";
+        case PIT_ENOMEM: return "PIT_ENOMEM";
+        case PIT_ENOCONV: return "PIT_ENOCONV";
+        case PIT_EDIVERGED: return "PIT_EDIVERGED";
+        case PIT_ETIMEOUT: return "PIT_ETIMEOUT";
+        case PIT_EUNSUPPORTED: return "PIT_EUNSUPPORTED";
+    }
+    return "PIT_UNKNOWN";
+}
+
+extern "C" const char* pit_last_error(const pit_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+// ------------------------------------------------------------ kernel dispatch
+
+template <bool CONV, bool NLV>
+static void launch_residual(pit_ctx* c, const double* U, double* R) {
+    dim3 grid((unsigned)((c->Ns + kNT - 1) / kNT), (unsigned)c->M);
+    residual_kernel<CONV, NLV, kNT><<<grid, kNT, 0, c->stream>>>(c->oc, c->u0, U, c->has_bc ? c->bc : nullptr,
+                                                                 c->has_q ? c->q : nullptr, R, c->keys);
+}
+
+template <bool CONV, bool NLV, bool SCALED>
+static void launch_assemble(pit_ctx* c, const double* U, double* coef) {
+    dim3 grid((unsigned)((c->Ns + kNT - 1) / kNT), (unsigned)c->M);
+    assemble_kernel<CONV, NLV, SCALED, kNT><<<grid, kNT, 0, c->stream>>>(c->oc, U, c->has_bc ? c->bc : nullptr, coef,
+                                                                         c->keys + 1);
+}
+
+static pit_status enqueue_residual(pit_ctx* ctx, const double* U, double* R) {
+    CK(cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long), ctx->stream));
+    if (ctx->conv) {
+        if (ctx->nlv) launch_residual<true, true>(ctx, U, R);
+        else launch_residual<true, false>(ctx, U, R);
+    } else {
+        if (ctx->nlv) launch_residual<false, true>(ctx, U, R);
+        else launch_residual<false, false>(ctx, U, R);
+    }
+    CK(cudaGetLastError());
+    return PIT_OK;
+}
+
+static pit_status read_res_inf(pit_ctx* ctx, double* out) {
+    unsigned long long k = 0;
+    CK(cudaMemcpyAsync(&k, ctx->keys, sizeof(k), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *out = key_to_double(k);
+    return PIT_OK;
+}
+
+template <bool SCALED>
+static pit_status enqueue_assemble(pit_ctx* ctx, const double* U, double* coef) {
+    if (SCALED) CK(cudaMemsetAsync(ctx->keys + 1, 0, sizeof(unsigned long long) * ctx->M, ctx->stream));
+    if (ctx->conv) {
+        if (ctx->nlv) launch_assemble<true, true, SCALED>(ctx, U, coef);
+        else launch_assemble<true, false, SCALED>(ctx, U, coef);
+    } else {
+        if (ctx->nlv) launch_assemble<false, true, SCALED>(ctx, U, coef);
+        else launch_assemble<false, false, SCALED>(ctx, U, coef);
+    }
+    CK(cudaGetLastError());
+    return PIT_OK;
+}
+
+// Run the level chain on the scaled planes in ctx->coef with right-hand sides R.
+// update_U: U += dU; dU (may be null) receives the solution. Fills the statistics.
+static pit_status run_chain(pit_ctx* ctx, const double* R, double* U, double* dU, double eta, pit_step_info* info) {
+    const int G = ctx->G, M = ctx->M;
+    CK(cudaMemsetAsync(ctx->sync_words, 0, sizeof(unsigned long long) * (G + 4), ctx->stream));
+    CK(cudaMemsetAsync(ctx->ints, 0, sizeof(int) * (2 + 2 * (size_t)M), ctx->stream));
+    ChainArgs a{};
+    a.nx = ctx->grid.nx;
+    a.ny = ctx->grid.ny;
+    a.M = M;
+    a.G = G;
+    a.rows_base = ctx->rows_base;
+    a.rows_rem = ctx->rows_rem;
+    a.R = R;
+    a.coef = ctx->coef;
+    a.rho_key = ctx->keys + 1;
+    a.U = U;
+    a.dU = dU;
+    a.update_U = U != nullptr;
+    a.method = ctx->opt.lin_solver;
+    a.sor_rho_max = ctx->opt.sor_rho_max;
+    a.eta = eta;
+    a.atol = ctx->opt.lin_atol;
+    a.max_iter = ctx->opt.lin_max_iter;
+    a.wait_budget = ctx->opt.wait_budget;
+    a.pub = ctx->pub;
+    a.flags = ctx->sync_words;
+    a.red_cnt = ctx->sync_words + G;
+    a.red_part = ctx->red_part;
+    a.abort_flag = ctx->ints;
+    a.status = ctx->ints + 1;
+    a.level_iters = ctx->ints + 2;
+    a.level_method = ctx->ints + 2 + M;
+    a.cta_sumsq = ctx->cta_sumsq;
+    void* args[] = {&a};
+    CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+    CK(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(chain_kernel<kNT>), dim3(G), dim3(kNT), args,
+                                   ctx->chain_smem, ctx->stream));
+    CK(cudaEventRecord(ctx->ev[3], ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_ints.data(), ctx->ints, sizeof(int) * (2 + 2 * (size_t)M), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_sumsq.data(), ctx->cta_sumsq, sizeof(double) * G, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int status = ctx->h_ints[1];
+    if (info) {
+        long long tot = 0;
+        int mx = 0, nsor = 0, ncap = 0;
+        for (int n = 0; n < M; ++n) {
+            const int it = ctx->h_ints[2 + n];
+            tot += it;
+            mx = std::max(mx, it);
+            nsor += ctx->h_ints[2 + M + n] == 1;
+            ncap += it >= ctx->opt.lin_max_iter;
+        }
+        double ss = 0.0;
+        for (int b = 0; b < G; ++b) ss += ctx->h_sumsq[b];
+        info->upd_rms = std::sqrt(ss / (double)ctx->DOF);
+        info->lin_iters_mean = (double)tot / M;
+        info->lin_iters_max = mx;
+        info->levels_sor = nsor;
+        info->levels_capped = ncap;
+    }
+    if (status == ST_ETIMEOUT) return fail(ctx, PIT_ETIMEOUT, "chain kernel: a device wait ran out of budget");
+    if (status == ST_EDIVERGED) return fail(ctx, PIT_EDIVERGED, "chain kernel: NaN/Inf in a level solve");
+    if (status == ST_ENOCONV) return fail(ctx, PIT_ENOCONV, "chain kernel: a level solve hit lin_max_iter");
+    return PIT_OK;
+}
+
+static bool finite_positive(double v) { return std::isfinite(v) && v > 0.0; }
+
+// ------------------------------------------------------------------ the ABI
+
+extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const pit_params* params,
+                                 const pit_options* opt, void* stream, pit_ctx** out) {
+    pit_ctx* ctx = nullptr;
+    if (!out) return PIT_EINVAL;
+    *out = nullptr;
+    if (!grid || !params) return PIT_EINVAL;
+    if (grid->nx < 1 || grid->ny < 1 || M < 1 || M > 65535 || !finite_positive(dt)) return PIT_EINVAL;
+    if (!(grid->xr > grid->xl) || !(grid->yr > grid->yl) || !std::isfinite(grid->xr - grid->xl) ||
+        !std::isfinite(grid->yr - grid->yl))
+        return PIT_EINVAL;
+    if (params->equation != PIT_HEAT && params->equation != PIT_BURGERS) return PIT_EINVAL;
+    if (!(params->mu_a >= 0.0) || !(params->mu_b >= 0.0) || !std::isfinite(params->mu_a) ||
+        !std::isfinite(params->mu_b))
+        return PIT_EINVAL;
+    if ((long long)grid->nx * grid->ny > (1ll << 31)) return PIT_EUNSUPPORTED;
+
+    ctx = new (std::nothrow) pit_ctx();
+    if (!ctx) return PIT_ENOMEM;
+    pit_default_options(&ctx->opt);
+    if (opt) ctx->opt = *opt;
+    const pit_options& o = ctx->opt;
+    if (o.newton_max < 0 || o.newton_max > PIT_MAX_NEWTON || !(o.tol_res >= 0.0) || o.lin_solver < 0 ||
+        o.lin_solver > 2 || !(o.eta_max > 0.0) || !(o.eta_gamma >= 0.0) || !(o.lin_atol >= 0.0) ||
+        o.lin_max_iter < 1 || !(o.sor_rho_max > 0.0) || o.team_ctas < 0 || o.wait_budget < 1) {
+        delete ctx;
+        return PIT_EINVAL;
+    }
+    ctx->grid = *grid;
+    ctx->M = M;
+    ctx->dt = dt;
+    ctx->params = *params;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    ctx->Ns = (long long)grid->nx * grid->ny;
+    ctx->DOF = ctx->Ns * M;
+    ctx->nb = 2 * grid->nx + 2 * grid->ny;
+    ctx->conv = params->equation == PIT_BURGERS;
+    ctx->nlv = params->mu_b != 0.0;
+    const double hx = (grid->xr - grid->xl) / (grid->nx + 1), hy = (grid->yr - grid->yl) / (grid->ny + 1);
+    OpConst& c = ctx->oc;
+    c.nx = grid->nx;
+    c.ny = grid->ny;
+    c.M = M;
+    c.Ns = ctx->Ns;
+    c.dt = dt;
+    c.cx = dt / (4.0 * hx);
+    c.cy = dt / (4.0 * hy);
+    c.jx = dt / (2.0 * hx);
+    c.jy = dt / (2.0 * hy);
+    c.vx = dt / (hx * hx);
+    c.vy = dt / (hy * hy);
+    c.mu_a = params->mu_a;
+    c.mu_b = params->mu_b;
+
+    pit_status st = PIT_OK;
+    auto setup = [&]() -> pit_status {
+        CK(cudaGetDevice(&ctx->device));
+        CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+        int optin = 0, coop = 0;
+        CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+        CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
+        if (!coop) return fail(ctx, PIT_EUNSUPPORTED, "device lacks cooperative launch");
+        ctx->smem_optin = (size_t)optin;
+        // team of G CTAs per level: row strips of rows_per rows
+        const int nx = grid->nx, ny = grid->ny;
+        int rows_per;
+        if (o.team_ctas > 0) {
+            const int G = std::min(o.team_ctas, ny);
+            rows_per = (ny + G - 1) / G;
+        } else {
+            rows_per = std::max((ny + ctx->num_sms - 1) / ctx->num_sms, (kMinLocal + nx - 1) / nx);
+        }
+        rows_per = std::min(rows_per, ny);
+        for (;;) {
+            const size_t bytes = sizeof(double) * chain_smem_doubles(rows_per * nx, nx);
+            if (bytes <= ctx->smem_optin) {
+                ctx->chain_smem = bytes;
+                break;
+            }
+            if (rows_per == 1) return fail(ctx, PIT_EUNSUPPORTED, "one grid row (nx = %d) exceeds shared memory", nx);
+            rows_per = (rows_per + 1) / 2;  // more, thinner strips
+        }
+        ctx->G = (ny + rows_per - 1) / rows_per;
+        ctx->rows_base = ny / ctx->G;
+        ctx->rows_rem = ny % ctx->G;
+        CK(cudaFuncSetAttribute(reinterpret_cast<const void*>(chain_kernel<kNT>),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->chain_smem));
+        int per_sm = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chain_kernel<kNT>, kNT, ctx->chain_smem));
+        if ((long long)per_sm * ctx->num_sms < ctx->G)
+            return fail(ctx, PIT_EUNSUPPORTED, "team of %d CTAs cannot be co-resident (%d per SM x %d SMs)", ctx->G,
+                        per_sm, ctx->num_sms);
+        CK(dalloc(&ctx->u0, ctx->Ns));
+        CK(cudaMemsetAsync(ctx->u0, 0, sizeof(double) * ctx->Ns, ctx->stream));
+        CK(dalloc(&ctx->R, ctx->DOF));
+        CK(dalloc(&ctx->coef, 5 * (size_t)ctx->DOF));
+        CK(dalloc(&ctx->Uh, ctx->DOF));
+        CK(dalloc(&ctx->keys, (size_t)M + 1));
+        CK(dalloc(&ctx->pub, (size_t)2 * ctx->G * 2 * nx));
+        CK(dalloc(&ctx->red_part, (size_t)4 * ctx->G * 4));
+        CK(dalloc(&ctx->sync_words, (size_t)ctx->G + 4));
+        CK(dalloc(&ctx->ints, 2 + 2 * (size_t)M));
+        CK(dalloc(&ctx->cta_sumsq, (size_t)ctx->G));
+        ctx->h_ints.assign(2 + 2 * (size_t)M, 0);
+        ctx->h_sumsq.assign(ctx->G, 0.0);
+        for (auto& e : ctx->ev) CK(cudaEventCreate(&e));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return PIT_OK;
+    };
+    st = setup();
+    if (st != PIT_OK) {
+        fprintf(stderr, "pit_create: %s\n", ctx->err);
+        pit_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return PIT_OK;
+}
+
+extern "C" void pit_destroy(pit_ctx* ctx) {
+    if (!ctx) return;
+    cudaFree(ctx->u0);
+    cudaFree(ctx->bc);
+    cudaFree(ctx->q);
+    cudaFree(ctx->R);
+    cudaFree(ctx->coef);
+    cudaFree(ctx->Uh);
+    cudaFree(ctx->keys);
+    cudaFree(ctx->pub);
+    cudaFree(ctx->red_part);
+    cudaFree(ctx->sync_words);
+    cudaFree(ctx->ints);
+    cudaFree(ctx->cta_sumsq);
+    for (auto& e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    delete ctx;
+}
+
+extern "C" pit_status pit_set_data(pit_ctx* ctx, const double* u0_dev, const double* bc_dev, const double* q_dev) {
+    if (!ctx) return PIT_EINVAL;
+    if (!u0_dev) return fail(ctx, PIT_EINVAL, "pit_set_data: u0 is required");
+    CK(cudaMemcpyAsync(ctx->u0, u0_dev, sizeof(double) * ctx->Ns, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (bc_dev) {
+        if (!ctx->bc) CK(dalloc(&ctx->bc, (size_t)ctx->M * ctx->nb));
+        CK(cudaMemcpyAsync(ctx->bc, bc_dev, sizeof(double) * ctx->M * ctx->nb, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    ctx->has_bc = bc_dev != nullptr;
+    if (q_dev) {
+        if (!ctx->q) CK(dalloc(&ctx->q, (size_t)ctx->DOF));
+        CK(cudaMemcpyAsync(ctx->q, q_dev, sizeof(double) * ctx->DOF, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    ctx->has_q = q_dev != nullptr;
+    return PIT_OK;
+}
+
+extern "C" pit_status pit_fill_plain_guess(pit_ctx* ctx, double* U_dev) {
+    if (!ctx) return PIT_EINVAL;
+    if (!U_dev) return fail(ctx, PIT_EINVAL, "pit_fill_plain_guess: U is NULL");
+    const int blocks = std::max(1, std::min(ctx->num_sms * 8, (int)((ctx->DOF + kNT - 1) / kNT)));
+    plain_guess_kernel<<<blocks, kNT, 0, ctx->stream>>>(ctx->u0, U_dev, ctx->Ns, ctx->M);
+    CK(cudaGetLastError());
+    return PIT_OK;
+}
+
+extern "C" pit_status pit_residual(pit_ctx* ctx, const double* U_dev, double* R_dev, double* res_inf) {
+    if (!ctx) return PIT_EINVAL;
+    if (!U_dev || !R_dev || U_dev == R_dev) return fail(ctx, PIT_EINVAL, "pit_residual: bad U/R pointers");
+    CHECK_RET(enqueue_residual(ctx, U_dev, R_dev));
+    if (res_inf) CHECK_RET(read_res_inf(ctx, res_inf));
+    return PIT_OK;
+}
+
+extern "C" pit_status pit_assemble(pit_ctx* ctx, const double* U_dev, double* coef_dev) {
+    if (!ctx) return PIT_EINVAL;
+    if (!U_dev || !coef_dev) return fail(ctx, PIT_EINVAL, "pit_assemble: NULL pointer");
+    return enqueue_assemble<false>(ctx, U_dev, coef_dev);
+}
+
+extern "C" pit_status pit_block_solve(pit_ctx* ctx, const double* U_dev, const double* R_dev, double* dU_dev,
+                                      double eta, pit_step_info* info) {
+    if (!ctx) return PIT_EINVAL;
+    if (!U_dev || !R_dev || !dU_dev) return fail(ctx, PIT_EINVAL, "pit_block_solve: NULL pointer");
+    if (!(eta > 0.0)) return fail(ctx, PIT_EINVAL, "pit_block_solve: eta must be > 0");
+    if (info) std::memset(info, 0, sizeof(*info));
+    CHECK_RET(enqueue_assemble<true>(ctx, U_dev, ctx->coef));
+    return run_chain(ctx, R_dev, nullptr, dU_dev, eta, info);
+}
+
+// One Newton update given that ctx->R holds the residual of U and res its max norm.
+static pit_status newton_update(pit_ctx* ctx, double* U, double res, pit_step_info* info) {
+    const double eta = std::max(std::min(ctx->opt.eta_max, ctx->opt.eta_gamma * res), 1e-300);
+    CK(cudaEventRecord(ctx->ev[1], ctx->stream));
+    CHECK_RET(enqueue_assemble<true>(ctx, U, ctx->coef));
+    pit_status st = run_chain(ctx, ctx->R, U, nullptr, eta, info);  // records ev[2], ev[3] around the launch
+    if (info) {
+        CK(cudaEventSynchronize(ctx->ev[3]));
+        CK(cudaEventElapsedTime(&info->ms_residual, ctx->ev[0], ctx->ev[1]));
+        CK(cudaEventElapsedTime(&info->ms_assemble, ctx->ev[1], ctx->ev[2]));
+        CK(cudaEventElapsedTime(&info->ms_solve, ctx->ev[2], ctx->ev[3]));
+    }
+    return st;
+}
+
+extern "C" pit_status pit_newton_step(pit_ctx* ctx, double* U_dev, pit_step_info* info) {
+    if (!ctx) return PIT_EINVAL;
+    if (!U_dev) return fail(ctx, PIT_EINVAL, "pit_newton_step: U is NULL");
+    if (info) std::memset(info, 0, sizeof(*info));
+    CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+    CHECK_RET(enqueue_residual(ctx, U_dev, ctx->R));
+    double res = 0.0;
+    CHECK_RET(read_res_inf(ctx, &res));
+    if (info) info->res_inf = res;
+    if (!std::isfinite(res)) return fail(ctx, PIT_EDIVERGED, "pit_newton_step: residual is not finite");
+    return newton_update(ctx, U_dev, res, info);
+}
+
+extern "C" pit_status pit_solve(pit_ctx* ctx, double* U_dev, pit_solve_info* info) {
+    if (!ctx) return PIT_EINVAL;
+    if (!U_dev) return fail(ctx, PIT_EINVAL, "pit_solve: U is NULL");
+    pit_solve_info local;
+    pit_solve_info* inf = info ? info : &local;
+    std::memset(inf, 0, sizeof(*inf));
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    CK(cudaEventCreate(&t0));
+    CK(cudaEventCreate(&t1));
+    CK(cudaEventRecord(t0, ctx->stream));
+    pit_status st = PIT_OK;
+    for (int k = 0;; ++k) {
+        CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+        st = enqueue_residual(ctx, U_dev, ctx->R);
+        double res = 0.0;
+        if (st == PIT_OK) st = read_res_inf(ctx, &res);
+        if (st != PIT_OK) break;
+        inf->res_inf[k] = res;
+        if (!std::isfinite(res)) {
+            st = fail(ctx, PIT_EDIVERGED, "pit_solve: residual is not finite at Newton iteration %d", k);
+            break;
+        }
+        if (res <= ctx->opt.tol_res) {
+            inf->converged = 1;
+            break;
+        }
+        if (k >= ctx->opt.newton_max) {
+            st = fail(ctx, PIT_ENOCONV, "pit_solve: ||R||_inf = %.3e > %.3e after %d Newton updates", res,
+                      ctx->opt.tol_res, k);
+            break;
+        }
+        inf->steps[k].res_inf = res;
+        st = newton_update(ctx, U_dev, res, &inf->steps[k]);
+        inf->newton_iters = k + 1;
+        if (st == PIT_ENOCONV) st = PIT_OK;  // a capped level solve: Newton carries on
+        if (st != PIT_OK) break;
+    }
+    CK(cudaEventRecord(t1, ctx->stream));
+    CK(cudaEventSynchronize(t1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, t0, t1));
+    inf->ms_total = ms;
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    return st;
+}
+
+extern "C" pit_status pit_solve_host(pit_ctx* ctx, const double* u0_host, double* U_host, pit_solve_info* info) {
+    if (!ctx) return PIT_EINVAL;
+    if (!u0_host || !U_host) return fail(ctx, PIT_EINVAL, "pit_solve_host: NULL pointer");
+    CK(cudaMemcpyAsync(ctx->u0, u0_host, sizeof(double) * ctx->Ns, cudaMemcpyHostToDevice, ctx->stream));
+    CHECK_RET(pit_fill_plain_guess(ctx, ctx->Uh));
+    pit_status st = pit_solve(ctx, ctx->Uh, info);
+    CK(cudaMemcpyAsync(U_host, ctx->Uh, sizeof(double) * ctx->DOF, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return st;
+}

@@ -1,0 +1,687 @@
+// pit_kernels.cuh -- sm_103a kernels of the all-at-once BDF1 Newton iteration
+// (arXiv 2406.00878, eq. 3-7).
+//
+//   residual_kernel   row (a1): r^n for all M levels at once (eq. 3-5) + ||R||_inf
+//   assemble_kernel   row (a2): the 5 entries per row of A_n = I + tau dF/du for all
+//                     levels at once (eq. 5-6), raw or Jacobi-scaled, + per-level
+//                     Gershgorin bound of the scaled block
+//   chain_kernel      row (a3): the exact block inverse of eq. 7 in nested form,
+//                     du^n = A_n^{-1}(r^n + du^{n-1}), as one persistent cooperative
+//                     launch that walks the level chain; a team of G CTAs shares each
+//                     level (row strips), keeping the level's data in shared memory.
+//
+// Arithmetic is FP64 throughout. Closures: f = g = beta u^2/2 (CONV = Burgers),
+// mu(u) = mu_a + mu_b u^2 (NLV when mu_b != 0), mid-point viscosity
+// mu_{i+1/2} = mu((u_i + u_{i+1})/2).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pit {
+
+// ------------------------------------------------------------------ constants
+
+struct OpConst {
+    int nx, ny, M;
+    long long Ns;
+    double dt;
+    double cx, cy;    // dt / (4 h_x), dt / (4 h_y): tau * (f_E - f_W)/(2h) with f = u^2/2
+    double jx, jy;    // dt / (2 h_x), dt / (2 h_y): tau * f'(u)/(2h)
+    double vx, vy;    // dt / h_x^2, dt / h_y^2
+    double mu_a, mu_b;
+};
+
+// Status codes shared with the host (values of pit_status).
+enum : int { ST_OK = 0, ST_ENOCONV = 4, ST_EDIVERGED = 5, ST_ETIMEOUT = 6 };
+
+// --------------------------------------------------------- memory primitives
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_s32(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// |x| as an order-preserving key: non-negative doubles compare like their bits,
+// and NaN (after fabs, 0x7ff8...) sorts above +Inf so it propagates through max.
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+    return static_cast<unsigned long long>(__double_as_longlong(fabs(x)));
+}
+__device__ __forceinline__ double key_val(unsigned long long k) { return __longlong_as_double((long long)k); }
+
+template <int NT>
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < NT / 32 ? red[lane] : 0ull;
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = w > v ? w : v;
+        }
+        if (lane == 0) red[0] = v;
+    }
+    __syncthreads();
+    v = red[0];
+    __syncthreads();
+    return v;
+}
+
+// Sum of K doubles over the block in a fixed order (deterministic).
+template <int NT, int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* red) {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[wid * K + k] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double s = lane < NT / 32 ? red[lane * K + k] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) red[k] = s;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = red[k];
+    __syncthreads();
+}
+
+// ------------------------------------------------------------ stencil access
+
+// Value of level vector u at (j, i), j in [-1, ny], i in [-1, nx]; off-interior
+// nodes read the level's Dirichlet data (zero when bnd == nullptr).
+__device__ __forceinline__ double node_value(const double* __restrict__ u, const double* __restrict__ bnd,
+                                             int nx, int ny, int j, int i) {
+    if (i >= 0 && i < nx && j >= 0 && j < ny) return u[(long long)j * nx + i];
+    if (bnd == nullptr) return 0.0;
+    if (j < 0) return bnd[i];
+    if (j >= ny) return bnd[nx + i];
+    if (i < 0) return bnd[2 * nx + j];
+    return bnd[2 * nx + ny + j];
+}
+
+// tau * F(u) at one node (eq. 3 without the time term), from the five stencil values.
+template <bool CONV, bool NLV>
+__device__ __forceinline__ double tau_F(const OpConst& c, double uC, double uW, double uE, double uS, double uN) {
+    double t = 0.0;
+    if (CONV) t = c.cx * ((uE - uW) * (uE + uW)) + c.cy * ((uN - uS) * (uN + uS));
+    if (NLV) {
+        const double ae = 0.5 * (uC + uE), aw = 0.5 * (uC + uW), an = 0.5 * (uC + uN), as = 0.5 * (uC + uS);
+        const double me = fma(c.mu_b, ae * ae, c.mu_a), mw = fma(c.mu_b, aw * aw, c.mu_a);
+        const double mn = fma(c.mu_b, an * an, c.mu_a), ms = fma(c.mu_b, as * as, c.mu_a);
+        const double fx = me * (uE - uC) - mw * (uC - uW);
+        const double fy = mn * (uN - uC) - ms * (uC - uS);
+        t -= c.vx * fx + c.vy * fy;
+    } else {
+        t -= c.mu_a * (c.vx * ((uE - uC) - (uC - uW)) + c.vy * ((uN - uC) - (uC - uS)));
+    }
+    return t;
+}
+
+// The five entries of row C of A = I + tau dF/du (eq. 5-6).
+template <bool CONV, bool NLV>
+__device__ __forceinline__ void jac_row(const OpConst& c, double uC, double uW, double uE, double uS, double uN,
+                                        double& aC, double& aW, double& aE, double& aS, double& aN) {
+    if (NLV) {
+        const double ae = 0.5 * (uC + uE), aw = 0.5 * (uC + uW), an = 0.5 * (uC + uN), as = 0.5 * (uC + uS);
+        const double me = fma(c.mu_b, ae * ae, c.mu_a), mw = fma(c.mu_b, aw * aw, c.mu_a);
+        const double mn = fma(c.mu_b, an * an, c.mu_a), ms = fma(c.mu_b, as * as, c.mu_a);
+        // d mu_{e} / d u = mu'(a_e)/2 = mu_b a_e
+        const double de = c.mu_b * ae, dw = c.mu_b * aw, dn = c.mu_b * an, ds = c.mu_b * as;
+        aE = -c.vx * (me + de * (uE - uC));
+        aW = -c.vx * (mw - dw * (uC - uW));
+        aN = -c.vy * (mn + dn * (uN - uC));
+        aS = -c.vy * (ms - ds * (uC - uS));
+        aC = 1.0 + c.vx * (me + mw - de * (uE - uC) + dw * (uC - uW)) + c.vy * (mn + ms - dn * (uN - uC) + ds * (uC - uS));
+    } else {
+        aE = -c.vx * c.mu_a;
+        aW = aE;
+        aN = -c.vy * c.mu_a;
+        aS = aN;
+        aC = 1.0 + 2.0 * c.mu_a * (c.vx + c.vy);
+    }
+    if (CONV) {
+        aE += c.jx * uE;
+        aW -= c.jx * uW;
+        aN += c.jy * uN;
+        aS -= c.jy * uS;
+    }
+}
+
+// --------------------------------------------------------------- (a1) residual
+
+// One thread per node, all levels at once: grid (ceil(Ns/NT), M). Writes R and
+// folds |r| into *rinf_key (order-preserving max key, see abs_key).
+template <bool CONV, bool NLV, int NT>
+__global__ void __launch_bounds__(NT) residual_kernel(OpConst c, const double* __restrict__ u0,
+                                                      const double* __restrict__ U, const double* __restrict__ bc,
+                                                      const double* __restrict__ q, double* __restrict__ R,
+                                                      unsigned long long* __restrict__ rinf_key) {
+    __shared__ unsigned long long red[NT / 32];
+    const int n = blockIdx.y;  // level index 0..M-1 <-> u^{n+1}
+    const long long k = (long long)blockIdx.x * NT + threadIdx.x;
+    unsigned long long key = 0;
+    if (k < c.Ns) {
+        const int j = (int)(k / c.nx), i = (int)(k - (long long)j * c.nx);
+        const double* u = U + (long long)n * c.Ns;
+        const double* up = (n == 0) ? u0 : U + (long long)(n - 1) * c.Ns;
+        const double* bnd = bc ? bc + (long long)n * (2 * c.nx + 2 * c.ny) : nullptr;
+        const double uC = u[k];
+        const double uW = node_value(u, bnd, c.nx, c.ny, j, i - 1);
+        const double uE = node_value(u, bnd, c.nx, c.ny, j, i + 1);
+        const double uS = node_value(u, bnd, c.nx, c.ny, j - 1, i);
+        const double uN = node_value(u, bnd, c.nx, c.ny, j + 1, i);
+        double r = (up[k] - uC) - tau_F<CONV, NLV>(c, uC, uW, uE, uS, uN);
+        if (q) r = fma(c.dt, q[(long long)n * c.Ns + k], r);
+        R[(long long)n * c.Ns + k] = r;
+        key = abs_key(r);
+    }
+    key = block_max_u64<NT>(key, red);
+    if (threadIdx.x == 0 && key) atomicMax(rinf_key, key);
+}
+
+// ------------------------------------------------------------ (a2) assembly
+
+// One thread per node, all levels at once. SCALED = false writes the raw entries
+// coef[5][M][Ns] = C, W, E, S, N of A_n. SCALED = true writes the Jacobi-scaled
+// planes used by the level solver: 1/C, W/C, E/C, S/C, N/C, and folds the row sum
+// |W|+|E|+|S|+|N| over |C| into rho_key[n] (Gershgorin bound of I - D^{-1}A_n).
+template <bool CONV, bool NLV, bool SCALED, int NT>
+__global__ void __launch_bounds__(NT) assemble_kernel(OpConst c, const double* __restrict__ U,
+                                                      const double* __restrict__ bc, double* __restrict__ coef,
+                                                      unsigned long long* __restrict__ rho_key) {
+    __shared__ unsigned long long red[NT / 32];
+    const int n = blockIdx.y;
+    const long long k = (long long)blockIdx.x * NT + threadIdx.x;
+    const long long plane = (long long)c.M * c.Ns;
+    unsigned long long key = 0;
+    if (k < c.Ns) {
+        const int j = (int)(k / c.nx), i = (int)(k - (long long)j * c.nx);
+        const double* u = U + (long long)n * c.Ns;
+        const double* bnd = bc ? bc + (long long)n * (2 * c.nx + 2 * c.ny) : nullptr;
+        const double uC = u[k];
+        const double uW = node_value(u, bnd, c.nx, c.ny, j, i - 1);
+        const double uE = node_value(u, bnd, c.nx, c.ny, j, i + 1);
+        const double uS = node_value(u, bnd, c.nx, c.ny, j - 1, i);
+        const double uN = node_value(u, bnd, c.nx, c.ny, j + 1, i);
+        double aC, aW, aE, aS, aN;
+        jac_row<CONV, NLV>(c, uC, uW, uE, uS, uN, aC, aW, aE, aS, aN);
+        if (i == 0) aW = 0.0;
+        if (i == c.nx - 1) aE = 0.0;
+        if (j == 0) aS = 0.0;
+        if (j == c.ny - 1) aN = 0.0;
+        double* o = coef + (long long)n * c.Ns + k;
+        if (SCALED) {
+            const double d = 1.0 / aC;
+            aW *= d;
+            aE *= d;
+            aS *= d;
+            aN *= d;
+            o[0] = d;
+            key = abs_key(fabs(aW) + fabs(aE) + fabs(aS) + fabs(aN));
+        } else {
+            o[0] = aC;
+        }
+        o[plane] = aW;
+        o[2 * plane] = aE;
+        o[3 * plane] = aS;
+        o[4 * plane] = aN;
+    }
+    if (SCALED) {
+        key = block_max_u64<NT>(key, red);
+        if (threadIdx.x == 0 && key) atomicMax(rho_key + n, key);
+    }
+}
+
+// -------------------------------------------- copy u^0 into every level (guess)
+
+__global__ void plain_guess_kernel(const double* __restrict__ u0, double* __restrict__ U, long long Ns, int M) {
+    const long long total = Ns * (long long)M;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x)
+        U[t] = u0[t % Ns];
+}
+
+// ------------------------------------------------------ (a3) the level chain
+
+struct ChainArgs {
+    int nx, ny, M;
+    int G;                                  // CTAs per level (team size), = gridDim.x
+    int rows_base, rows_rem;                // CTA b owns rows_base + (b < rows_rem) rows
+    const double* R;                        // [M][Ns] right-hand sides r^n
+    const double* coef;                     // [5][M][Ns] scaled planes 1/C, W/C, E/C, S/C, N/C
+    const unsigned long long* rho_key;      // [M] Gershgorin bound per level
+    double* U;                              // [M][Ns] iterate, += dU when update_U
+    double* dU;                             // [M][Ns] receives dU, or nullptr
+    int update_U;
+    int method;                             // 0 auto, 1 SOR, 2 BiCGStab
+    double sor_rho_max;
+    double eta;                             // relative tolerance of every level solve
+    double atol;                            // absolute floor of the tolerance
+    int max_iter;                           // cap per level
+    long long wait_budget;
+    // team communication (zeroed before each launch by the host)
+    double* pub;                            // [2][G][2][nx] published boundary rows
+    unsigned long long* flags;              // [G] publication counters
+    double* red_part;                       // [4][G][4] reduction partials
+    unsigned long long* red_cnt;            // [4] arrival counters
+    int* abort_flag;
+    int* status;
+    // statistics
+    int* level_iters;                       // [M] sweeps / iterations of each level
+    int* level_method;                      // [M] 1 = SOR, 2 = BiCGStab
+    double* cta_sumsq;                      // [G] sum of dU^2 over the CTA's rows, all levels
+};
+
+// Per-CTA state of the team protocol.
+struct Team {
+    int b, G, nx;
+    int r0, nrows, nloc;
+    unsigned long long pub_seq;   // publications so far by this CTA
+    unsigned long long red_seq;   // reductions started so far
+};
+
+// Give up on a wait: record the status once and raise the abort flag.
+__device__ __forceinline__ void team_fail(const ChainArgs& a, int code) {
+    atomicCAS(a.status, 0, code);
+    atomicExch(a.abort_flag, 1);
+}
+
+// Spin (one thread) until *p >= target, the abort flag is raised, or the budget is spent.
+__device__ __forceinline__ bool wait_geq(const ChainArgs& a, const unsigned long long* p, unsigned long long target) {
+    long long spins = 0;
+    while (ld_acquire_u64(p) < target) {
+        if (ld_acquire_s32(a.abort_flag)) return false;
+        if (++spins > a.wait_budget) {
+            team_fail(a, ST_ETIMEOUT);
+            return false;
+        }
+        if (spins > 64) __nanosleep(32);
+    }
+    return true;
+}
+
+// Publish the first and last local rows of v for the neighbours; then fetch the
+// neighbours' rows published at the same step into haloS (row r0-1) and haloN
+// (row r0+nrows). Rows outside the domain are zero (the correction vanishes on
+// the Dirichlet boundary). Returns false when the team aborted.
+template <int NT>
+__device__ bool exchange_halo(const ChainArgs& a, Team& t, const double* v, double* haloS, double* haloN,
+                              int* s_ok) {
+    const int nx = t.nx;
+    const unsigned long long seq = ++t.pub_seq;
+    double* mine = a.pub + ((size_t)(seq & 1) * t.G + t.b) * 2 * nx;
+    for (int i = threadIdx.x; i < nx; i += NT) {
+        __stcg(mine + i, v[i]);
+        __stcg(mine + nx + i, v[(t.nrows - 1) * nx + i]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        st_release_u64(a.flags + t.b, seq);
+        bool ok = true;
+        if (t.b > 0) ok = wait_geq(a, a.flags + t.b - 1, seq);
+        if (ok && t.b + 1 < t.G) ok = wait_geq(a, a.flags + t.b + 1, seq);
+        __threadfence();
+        *s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!*s_ok) return false;
+    const double* par = a.pub + (size_t)(seq & 1) * t.G * 2 * nx;
+    if (t.b > 0) {  // neighbour below: its last row
+        const double* lo = par + (size_t)(t.b - 1) * 2 * nx + nx;
+        for (int i = threadIdx.x; i < nx; i += NT) haloS[i] = __ldcg(lo + i);
+    } else {
+        for (int i = threadIdx.x; i < nx; i += NT) haloS[i] = 0.0;
+    }
+    if (t.b + 1 < t.G) {  // neighbour above: its first row
+        const double* hi = par + (size_t)(t.b + 1) * 2 * nx;
+        for (int i = threadIdx.x; i < nx; i += NT) haloN[i] = __ldcg(hi + i);
+    } else {
+        for (int i = threadIdx.x; i < nx; i += NT) haloN[i] = 0.0;
+    }
+    __syncthreads();
+    return true;
+}
+
+// Start a team reduction of K <= 4 values (this CTA's partials already block-reduced
+// into vals). Deterministic: every CTA later sums the G partials in CTA order.
+template <int K>
+__device__ __forceinline__ unsigned long long reduce_arrive(const ChainArgs& a, Team& t, const double (&vals)[K]) {
+    const unsigned long long use = t.red_seq++;
+    const int slot = (int)(use & 3);
+    if (threadIdx.x == 0) {
+        double* part = a.red_part + ((size_t)slot * t.G + t.b) * 4;
+#pragma unroll
+        for (int k = 0; k < K; ++k) __stcg(part + k, vals[k]);
+        __threadfence();
+        atomicAdd(a.red_cnt + slot, 1ull);
+    }
+    return use;
+}
+
+// Finish reduction `use`: wait for all G arrivals, then sum the partials in order
+// (max instead of sum when MAXOP). Result is broadcast to every thread.
+template <int K, bool MAXOP>
+__device__ __forceinline__ bool reduce_finish(const ChainArgs& a, Team& t, unsigned long long use, double (&out)[K],
+                                              double* s_bcast, int* s_ok) {
+    const int slot = (int)(use & 3);
+    if (threadIdx.x == 0) {
+        const unsigned long long target = (unsigned long long)t.G * ((use >> 2) + 1);
+        *s_ok = wait_geq(a, a.red_cnt + slot, target) ? 1 : 0;
+        __threadfence();
+        if (*s_ok) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                double s = 0.0;
+                bool nan = false;
+                for (int b = 0; b < t.G; ++b) {
+                    const double v = __ldcg(a.red_part + ((size_t)slot * t.G + b) * 4 + k);
+                    s = MAXOP ? fmax(s, v) : s + v;
+                    nan |= (v != v);
+                }
+                s_bcast[k] = nan ? __longlong_as_double(0x7ff8000000000000ll) : s;
+            }
+        }
+    }
+    __syncthreads();
+    const bool ok = *s_ok != 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = s_bcast[k];
+    __syncthreads();
+    return ok;
+}
+
+// Shared-memory layout of one CTA (nloc = rows x nx doubles per array).
+struct Smem {
+    double *cw, *ce, *cs, *cn, *bs, *x;      // scaled couplings, scaled rhs, iterate
+    double *r, *rh, *p, *v, *s, *t;          // BiCGStab vectors
+    double *haloS, *haloN;                   // neighbour rows of the exchanged vector
+    double *red;                             // block-reduction scratch
+};
+
+// y = (D^{-1} A) v on the local rows (unit diagonal), halos of v in haloS/haloN.
+template <int NT>
+__device__ __forceinline__ void local_spmv(const Team& t, const Smem& m, const double* v, double* y) {
+    const int nx = t.nx;
+    for (int k = threadIdx.x; k < t.nloc; k += NT) {
+        const int jl = k / nx, i = k - jl * nx;
+        const double vW = i > 0 ? v[k - 1] : 0.0;
+        const double vE = i < nx - 1 ? v[k + 1] : 0.0;
+        const double vS = jl > 0 ? v[k - nx] : m.haloS[i];
+        const double vN = jl < t.nrows - 1 ? v[k + nx] : m.haloN[i];
+        y[k] = v[k] + m.cw[k] * vW + m.ce[k] * vE + m.cs[k] * vS + m.cn[k] * vN;
+    }
+}
+
+// Red-black SOR on the scaled level system x + W x_W + E x_E + S x_S + N x_N = bs,
+// starting from x. Stops when the error estimate d_s rho / (1 - rho) <= tol, where
+// d_s is the largest change of a sweep and rho = max(d_s / d_{s-1}, omega - 1); the
+// global d_s is known one sweep late (lagged team reduction), so every CTA takes
+// the same decision at the same sweep. Returns the sweep count (< 0 on abort).
+template <int NT>
+__device__ int level_sor(const ChainArgs& a, Team& t, const Smem& m, double omega, double tol, int* s_ok) {
+    const int nx = t.nx;
+    double prev = -1.0, prev2 = -1.0;  // global max change of sweeps s-1 and s-2
+    unsigned long long pending = 0;
+    bool have_pending = false;
+    for (int sweep = 1;; ++sweep) {
+        double dmax = 0.0;
+        for (int color = 0; color < 2; ++color) {
+            if (!exchange_halo<NT>(a, t, m.x, m.haloS, m.haloN, s_ok)) return -1;
+            for (int k = threadIdx.x; k < t.nloc; k += NT) {
+                const int jl = k / nx, i = k - jl * nx;
+                if (((t.r0 + jl + i) & 1) != color) continue;
+                const double xW = i > 0 ? m.x[k - 1] : 0.0;
+                const double xE = i < nx - 1 ? m.x[k + 1] : 0.0;
+                const double xS = jl > 0 ? m.x[k - nx] : m.haloS[i];
+                const double xN = jl < t.nrows - 1 ? m.x[k + nx] : m.haloN[i];
+                const double xk = m.x[k];
+                const double resid = m.bs[k] - xk - (m.cw[k] * xW + m.ce[k] * xE + m.cs[k] * xS + m.cn[k] * xN);
+                const double dx = omega * resid;
+                m.x[k] = xk + dx;
+                dmax = fmax(dmax, fabs(dx));
+                if (dx != dx) dmax = dx;
+            }
+            __syncthreads();
+        }
+        // this CTA's max change, then arrive at the team reduction of this sweep
+        double v[1] = {0.0};
+        {
+            unsigned long long key = block_max_u64<NT>(abs_key(dmax), reinterpret_cast<unsigned long long*>(m.red));
+            v[0] = key_val(key);
+        }
+        const unsigned long long use = reduce_arrive<1>(a, t, v);
+        if (have_pending) {
+            double g[1];
+            if (!reduce_finish<1, true>(a, t, pending, g, m.red + 32, s_ok)) return -1;
+            const double d = g[0];
+            if (d != d) {
+                if (threadIdx.x == 0) atomicCAS(a.status, 0, ST_EDIVERGED);
+                // consume the outstanding reduction so the sequence stays aligned
+                double h[1];
+                if (!reduce_finish<1, true>(a, t, use, h, m.red + 32, s_ok)) return -1;
+                return sweep;
+            }
+            prev2 = prev;
+            prev = d;
+            double rho = omega - 1.0;
+            if (prev2 > 0.0) rho = fmax(rho, prev / prev2);
+            const bool done = (prev == 0.0) || (prev2 > 0.0 && rho < 1.0 && prev * rho <= tol * (1.0 - rho)) ||
+                              sweep >= a.max_iter;
+            if (done) {
+                double h[1];
+                if (!reduce_finish<1, true>(a, t, use, h, m.red + 32, s_ok)) return -1;
+                return sweep;
+            }
+        }
+        pending = use;
+        have_pending = true;
+    }
+}
+
+// Jacobi-preconditioned BiCGStab (van der Vorst 1992) on the scaled level system,
+// from x = 0. Stops when ||r||_2 <= tol_rel ||bs||_2 or ||r||_2 <= atol sqrt(Ns).
+template <int NT>
+__device__ int level_bicgstab(const ChainArgs& a, Team& t, const Smem& m, double eta, double atol, int* s_ok) {
+    double* sb = m.red + 32;
+    const int nloc = t.nloc;
+    double loc[2];
+    // r = bs, rh = bs, x = 0, p = v = 0
+    loc[0] = 0.0;
+    for (int k = threadIdx.x; k < nloc; k += NT) {
+        const double b = m.bs[k];
+        m.x[k] = 0.0;
+        m.r[k] = b;
+        m.rh[k] = b;
+        m.p[k] = 0.0;
+        m.v[k] = 0.0;
+        loc[0] += b * b;
+    }
+    double one[1] = {loc[0]};
+    block_sum<NT, 1>(one, m.red);
+    double g1[1];
+    if (!reduce_finish<1, false>(a, t, reduce_arrive<1>(a, t, one), g1, sb, s_ok)) return -1;
+    const double bnorm = sqrt(g1[0]);
+    const double Ns = (double)t.nx * (double)a.ny;
+    const double tol = fmax(eta * bnorm, atol * sqrt(Ns));
+    if (bnorm <= tol) return 0;
+    double rho_old = 1.0, alpha = 1.0, omega = 1.0, rho = g1[0];  // (rh, r) = ||b||^2 at start
+    for (int it = 1; it <= a.max_iter; ++it) {
+        const double beta = (rho / rho_old) * (alpha / omega);
+        for (int k = threadIdx.x; k < nloc; k += NT) m.p[k] = m.r[k] + beta * (m.p[k] - omega * m.v[k]);
+        __syncthreads();
+        if (!exchange_halo<NT>(a, t, m.p, m.haloS, m.haloN, s_ok)) return -1;
+        local_spmv<NT>(t, m, m.p, m.v);
+        double d1[1] = {0.0};
+        for (int k = threadIdx.x; k < nloc; k += NT) d1[0] += m.rh[k] * m.v[k];
+        block_sum<NT, 1>(d1, m.red);
+        if (!reduce_finish<1, false>(a, t, reduce_arrive<1>(a, t, d1), d1, sb, s_ok)) return -1;
+        if (d1[0] == 0.0 || d1[0] != d1[0]) {
+            if (threadIdx.x == 0) atomicCAS(a.status, 0, d1[0] != d1[0] ? ST_EDIVERGED : ST_ENOCONV);
+            return it;
+        }
+        alpha = rho / d1[0];
+        for (int k = threadIdx.x; k < nloc; k += NT) m.s[k] = m.r[k] - alpha * m.v[k];
+        __syncthreads();
+        if (!exchange_halo<NT>(a, t, m.s, m.haloS, m.haloN, s_ok)) return -1;
+        local_spmv<NT>(t, m, m.s, m.t);
+        double d2[2] = {0.0, 0.0};
+        for (int k = threadIdx.x; k < nloc; k += NT) {
+            d2[0] += m.t[k] * m.s[k];
+            d2[1] += m.t[k] * m.t[k];
+        }
+        block_sum<NT, 2>(d2, m.red);
+        if (!reduce_finish<2, false>(a, t, reduce_arrive<2>(a, t, d2), d2, sb, s_ok)) return -1;
+        omega = d2[1] > 0.0 ? d2[0] / d2[1] : 0.0;
+        double d3[2] = {0.0, 0.0};
+        for (int k = threadIdx.x; k < nloc; k += NT) {
+            m.x[k] += alpha * m.p[k] + omega * m.s[k];
+            const double rk = m.s[k] - omega * m.t[k];
+            m.r[k] = rk;
+            d3[0] += m.rh[k] * rk;
+            d3[1] += rk * rk;
+        }
+        block_sum<NT, 2>(d3, m.red);
+        if (!reduce_finish<2, false>(a, t, reduce_arrive<2>(a, t, d3), d3, sb, s_ok)) return -1;
+        const double rnorm = sqrt(d3[1]);
+        if (rnorm != rnorm) {
+            if (threadIdx.x == 0) atomicCAS(a.status, 0, ST_EDIVERGED);
+            return it;
+        }
+        if (rnorm <= tol) return it;
+        if (omega == 0.0 || d3[0] == 0.0) {
+            if (threadIdx.x == 0) atomicCAS(a.status, 0, ST_ENOCONV);
+            return it;
+        }
+        rho_old = rho;
+        rho = d3[0];
+    }
+    if (threadIdx.x == 0) atomicCAS(a.status, 0, ST_ENOCONV);
+    return a.max_iter;
+}
+
+// Number of doubles of dynamic shared memory per CTA for nloc local unknowns.
+__host__ __device__ inline size_t chain_smem_doubles(int nloc, int nx) {
+    return (size_t)12 * nloc + 2 * (size_t)nx + 64;
+}
+
+// The chain: for n = 1..M, rhs = r^n + du^{n-1}; solve the level; U^n += du^n.
+// Must be launched cooperatively with gridDim.x = G (all CTAs co-resident).
+template <int NT>
+__global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
+    extern __shared__ double smem[];
+    __shared__ int s_ok;
+    Team t;
+    t.b = blockIdx.x;
+    t.G = a.G;
+    t.nx = a.nx;
+    t.nrows = a.rows_base + (t.b < a.rows_rem ? 1 : 0);
+    t.r0 = t.b * a.rows_base + (t.b < a.rows_rem ? t.b : a.rows_rem);
+    t.nloc = t.nrows * a.nx;
+    t.pub_seq = 0;
+    t.red_seq = 0;
+    const int nloc = t.nloc;
+    const int cap = (a.rows_base + (a.rows_rem ? 1 : 0)) * a.nx;  // largest nloc of the team
+    Smem m;
+    double* base = smem;
+    m.cw = base;
+    m.ce = base + cap;
+    m.cs = base + 2 * cap;
+    m.cn = base + 3 * cap;
+    m.bs = base + 4 * cap;
+    m.x = base + 5 * cap;
+    m.r = base + 6 * cap;
+    m.rh = base + 7 * cap;
+    m.p = base + 8 * cap;
+    m.v = base + 9 * cap;
+    m.s = base + 10 * cap;
+    m.t = base + 11 * cap;
+    m.haloS = base + 12 * cap;
+    m.haloN = m.haloS + a.nx;
+    m.red = m.haloN + a.nx;  // 64 doubles
+
+    const long long Ns = (long long)a.nx * a.ny;
+    const long long plane = (long long)a.M * Ns;
+    const long long off0 = (long long)t.r0 * a.nx;
+    double sumsq = 0.0;
+
+    // du^0 = 0 lives in x
+    for (int k = threadIdx.x; k < nloc; k += NT) m.x[k] = 0.0;
+    __syncthreads();
+
+    for (int n = 0; n < a.M; ++n) {
+        const long long lo = (long long)n * Ns + off0;
+        const double* cd = a.coef + lo;
+        // rhs b = r^n + du^{n-1}, scaled by 1/C; load the couplings
+        for (int k = threadIdx.x; k < nloc; k += NT) {
+            const double d = cd[k];
+            m.cw[k] = cd[plane + k];
+            m.ce[k] = cd[2 * plane + k];
+            m.cs[k] = cd[3 * plane + k];
+            m.cn[k] = cd[4 * plane + k];
+            const double b = a.R[lo + k] + m.x[k];
+            m.bs[k] = d * b;
+            m.x[k] = b;  // SOR start: unscaled rhs (exact for the smooth modes where A ~ I)
+        }
+        __syncthreads();
+        const double rho_g = key_val(a.rho_key[n]);
+        const bool use_sor = a.method == 1 || (a.method == 0 && rho_g < a.sor_rho_max);
+        int iters;
+        double tol_abs = 0.0;
+        if (use_sor) {
+            // tolerance relative to the level's unscaled ||b||_inf (team max reduction)
+            double bl = 0.0;
+            for (int k = threadIdx.x; k < nloc; k += NT) bl = fmax(bl, fabs(m.x[k]));
+            unsigned long long key = block_max_u64<NT>(abs_key(bl), reinterpret_cast<unsigned long long*>(m.red));
+            double v[1] = {key_val(key)};
+            double g[1];
+            if (!reduce_finish<1, true>(a, t, reduce_arrive<1>(a, t, v), g, m.red + 32, &s_ok)) return;
+            tol_abs = fmax(a.eta * g[0], a.atol);
+            const double rc = fmin(rho_g, 0.999999);
+            const double omega = rho_g < 1.0 ? 2.0 / (1.0 + sqrt(1.0 - rc * rc)) : 1.0;
+            iters = level_sor<NT>(a, t, m, omega, tol_abs, &s_ok);
+        } else {
+            iters = level_bicgstab<NT>(a, t, m, a.eta, a.atol, &s_ok);
+        }
+        if (iters < 0) return;  // aborted
+        // du^n = x: update the iterate and keep x as du^{n-1} of the next level
+        for (int k = threadIdx.x; k < nloc; k += NT) {
+            const double dx = m.x[k];
+            if (a.update_U) a.U[lo + k] += dx;
+            if (a.dU) a.dU[lo + k] = dx;
+            sumsq += dx * dx;
+        }
+        if (t.b == 0 && threadIdx.x == 0) {
+            a.level_iters[n] = iters;
+            a.level_method[n] = use_sor ? 1 : 2;
+            if (iters >= a.max_iter) atomicCAS(a.status, 0, ST_ENOCONV);
+        }
+        __syncthreads();
+    }
+    double ss[1] = {sumsq};
+    block_sum<NT, 1>(ss, m.red);
+    if (threadIdx.x == 0) a.cta_sumsq[t.b] = ss[0];
+}
+
+}  // namespace pit

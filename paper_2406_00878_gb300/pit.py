@@ -1,0 +1,275 @@
+"""ctypes binding of libpit.so (C ABI in include/pit.h), same names as the ABI.
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Device arrays are torch tensors (float64, contiguous, on the context's device);
+host arrays for ``pit_solve_host`` are numpy float64 arrays (or CPU tensors).
+A failing call raises ``PitError`` carrying the status and ``pit_last_error``.
+The library is loaded on first use and the call fails loudly if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+PIT_OK, PIT_EINVAL, PIT_ECUDA, PIT_ENOMEM, PIT_ENOCONV, PIT_EDIVERGED, PIT_ETIMEOUT, PIT_EUNSUPPORTED = range(8)
+PIT_HEAT, PIT_BURGERS = 0, 1
+PIT_LIN_AUTO, PIT_LIN_SOR, PIT_LIN_BICGSTAB = 0, 1, 2
+PIT_MAX_NEWTON = 64
+
+#: every symbol include/pit.h declares
+EXPORTS = ("pit_default_options", "pit_create", "pit_set_data", "pit_fill_plain_guess", "pit_residual",
+           "pit_assemble", "pit_block_solve", "pit_newton_step", "pit_solve", "pit_solve_host", "pit_last_error",
+           "pit_status_string", "pit_destroy")
+
+
+class pit_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("xl", ctypes.c_double), ("xr", ctypes.c_double),
+                ("yl", ctypes.c_double), ("yr", ctypes.c_double)]
+
+
+class pit_params(ctypes.Structure):
+    _fields_ = [("equation", ctypes.c_int), ("mu_a", ctypes.c_double), ("mu_b", ctypes.c_double)]
+
+
+class pit_options(ctypes.Structure):
+    _fields_ = [("newton_max", ctypes.c_int), ("tol_res", ctypes.c_double), ("lin_solver", ctypes.c_int),
+                ("eta_max", ctypes.c_double), ("eta_gamma", ctypes.c_double), ("lin_atol", ctypes.c_double),
+                ("lin_max_iter", ctypes.c_int), ("sor_rho_max", ctypes.c_double), ("team_ctas", ctypes.c_int),
+                ("wait_budget", ctypes.c_longlong)]
+
+
+class pit_step_info(ctypes.Structure):
+    _fields_ = [("res_inf", ctypes.c_double), ("upd_rms", ctypes.c_double), ("lin_iters_mean", ctypes.c_double),
+                ("lin_iters_max", ctypes.c_int), ("levels_sor", ctypes.c_int), ("levels_capped", ctypes.c_int),
+                ("ms_residual", ctypes.c_float), ("ms_assemble", ctypes.c_float), ("ms_solve", ctypes.c_float)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class pit_solve_info(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int), ("converged", ctypes.c_int),
+                ("res_inf", ctypes.c_double * (PIT_MAX_NEWTON + 1)), ("steps", pit_step_info * PIT_MAX_NEWTON),
+                ("ms_total", ctypes.c_double)]
+
+    def as_dict(self):
+        k = self.newton_iters
+        return {"newton_iters": k, "converged": bool(self.converged), "res_inf": list(self.res_inf[:k + 1]),
+                "steps": [self.steps[i].as_dict() for i in range(k)], "ms_total": self.ms_total}
+
+
+class PitError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libpit.so (building it first if needed); raises if it cannot be built or loaded."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                path = _build.build()
+            L = ctypes.CDLL(path)
+            P, D, V = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p
+            st = ctypes.c_int
+            L.pit_default_options.argtypes = [ctypes.POINTER(pit_options)]
+            L.pit_default_options.restype = None
+            L.pit_create.argtypes = [ctypes.POINTER(pit_grid), ctypes.c_int, ctypes.c_double,
+                                     ctypes.POINTER(pit_params), ctypes.POINTER(pit_options), V,
+                                     ctypes.POINTER(P)]
+            L.pit_create.restype = st
+            L.pit_set_data.argtypes = [P, V, V, V]
+            L.pit_set_data.restype = st
+            L.pit_fill_plain_guess.argtypes = [P, V]
+            L.pit_fill_plain_guess.restype = st
+            L.pit_residual.argtypes = [P, V, V, D]
+            L.pit_residual.restype = st
+            L.pit_assemble.argtypes = [P, V, V]
+            L.pit_assemble.restype = st
+            L.pit_block_solve.argtypes = [P, V, V, V, ctypes.c_double, ctypes.POINTER(pit_step_info)]
+            L.pit_block_solve.restype = st
+            L.pit_newton_step.argtypes = [P, V, ctypes.POINTER(pit_step_info)]
+            L.pit_newton_step.restype = st
+            L.pit_solve.argtypes = [P, V, ctypes.POINTER(pit_solve_info)]
+            L.pit_solve.restype = st
+            L.pit_solve_host.argtypes = [P, V, V, ctypes.POINTER(pit_solve_info)]
+            L.pit_solve_host.restype = st
+            L.pit_last_error.argtypes = [P]
+            L.pit_last_error.restype = ctypes.c_char_p
+            L.pit_status_string.argtypes = [ctypes.c_int]
+            L.pit_status_string.restype = ctypes.c_char_p
+            L.pit_destroy.argtypes = [P]
+            L.pit_destroy.restype = None
+            _lib = L
+        return _lib
+
+
+def _status_name(s: int) -> str:
+    try:
+        return lib().pit_status_string(int(s)).decode()
+    except Exception:
+        return f"status {s}"
+
+
+def _dptr(t, name: str, numel: Optional[int] = None):
+    """Device pointer of a contiguous float64 CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a, name: str, numel: int):
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.size != numel:
+            raise TypeError(f"{name} must be a contiguous float64 array of {numel} values")
+        return ctypes.c_void_p(a.ctypes.data)
+    import torch
+    if isinstance(a, torch.Tensor) and not a.is_cuda and a.dtype == torch.float64 and a.is_contiguous() \
+            and a.numel() == numel:
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError(f"{name} must be a contiguous float64 host array of {numel} values")
+
+
+class Context:
+    """A pit_ctx handle plus its sizes; release with ``pit_destroy`` (or ``close``)."""
+
+    def __init__(self, handle, grid: pit_grid, M: int):
+        self.handle = handle
+        self.nx, self.ny, self.M = grid.nx, grid.ny, M
+        self.ns = grid.nx * grid.ny
+        self.dof = self.ns * M
+
+    def _check(self, status: int):
+        if status != PIT_OK:
+            raise PitError(status, lib().pit_last_error(self.handle).decode())
+
+    def close(self):
+        if self.handle:
+            lib().pit_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pit_default_options() -> pit_options:
+    o = pit_options()
+    lib().pit_default_options(ctypes.byref(o))
+    return o
+
+
+def pit_create(grid, M: int, dt: float, params, opt: Optional[pit_options] = None, stream=None) -> Context:
+    """grid/params: pit_grid/pit_params or any object with the same fields (e.g. workloads.Grid/Params).
+    stream: a torch.cuda.Stream, an int handle, or None (torch's current stream)."""
+    g = grid if isinstance(grid, pit_grid) else pit_grid(int(grid.nx), int(grid.ny), float(grid.xl),
+                                                          float(grid.xr), float(grid.yl), float(grid.yr))
+    p = params if isinstance(params, pit_params) else pit_params(int(params.equation), float(params.mu_a),
+                                                                 float(params.mu_b))
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif not isinstance(stream, int):
+        stream = stream.cuda_stream
+    h = ctypes.c_void_p()
+    s = lib().pit_create(ctypes.byref(g), int(M), float(dt), ctypes.byref(p),
+                         ctypes.byref(opt) if opt is not None else None, ctypes.c_void_p(stream), ctypes.byref(h))
+    if s != PIT_OK:
+        raise PitError(s, "pit_create failed (see stderr)")
+    return Context(h, g, int(M))
+
+
+def pit_set_data(ctx: Context, u0, bc=None, q=None):
+    ctx._check(lib().pit_set_data(ctx.handle, _dptr(u0, "u0", ctx.ns),
+                                  _dptr(bc, "bc", ctx.M * (2 * ctx.nx + 2 * ctx.ny)), _dptr(q, "q", ctx.dof)))
+
+
+def pit_fill_plain_guess(ctx: Context, U):
+    ctx._check(lib().pit_fill_plain_guess(ctx.handle, _dptr(U, "U", ctx.dof)))
+
+
+def pit_residual(ctx: Context, U, R, want_norm: bool = True) -> Optional[float]:
+    out = ctypes.c_double(0.0)
+    ctx._check(lib().pit_residual(ctx.handle, _dptr(U, "U", ctx.dof), _dptr(R, "R", ctx.dof),
+                                  ctypes.byref(out) if want_norm else None))
+    return out.value if want_norm else None
+
+
+def pit_assemble(ctx: Context, U, coef):
+    ctx._check(lib().pit_assemble(ctx.handle, _dptr(U, "U", ctx.dof), _dptr(coef, "coef", 5 * ctx.dof)))
+
+
+def pit_block_solve(ctx: Context, U, R, dU, eta: float = 1e-14) -> dict:
+    info = pit_step_info()
+    ctx._check(lib().pit_block_solve(ctx.handle, _dptr(U, "U", ctx.dof), _dptr(R, "R", ctx.dof),
+                                     _dptr(dU, "dU", ctx.dof), float(eta), ctypes.byref(info)))
+    return info.as_dict()
+
+
+def pit_newton_step(ctx: Context, U) -> dict:
+    info = pit_step_info()
+    ctx._check(lib().pit_newton_step(ctx.handle, _dptr(U, "U", ctx.dof), ctypes.byref(info)))
+    return info.as_dict()
+
+
+def pit_solve(ctx: Context, U, check: bool = True):
+    """Returns (status, info dict). Raises on failure when check is True."""
+    info = pit_solve_info()
+    s = lib().pit_solve(ctx.handle, _dptr(U, "U", ctx.dof), ctypes.byref(info))
+    if check:
+        ctx._check(s)
+    return s, info.as_dict()
+
+
+def pit_solve_host(ctx: Context, u0_host, U_host, check: bool = True):
+    info = pit_solve_info()
+    s = lib().pit_solve_host(ctx.handle, _hptr(u0_host, "u0_host", ctx.ns), _hptr(U_host, "U_host", ctx.dof),
+                             ctypes.byref(info))
+    if check:
+        ctx._check(s)
+    return s, info.as_dict()
+
+
+def pit_destroy(ctx: Context):
+    ctx.close()
+
+
+# ------------------------------------------------------------- convenience
+
+def context_for(problem, opt: Optional[pit_options] = None, stream=None) -> Context:
+    """Create a context for a workloads.Problem and upload its data (device tensors)."""
+    import torch
+    ctx = pit_create(problem.grid, problem.M, problem.dt, problem.params, opt, stream)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    u0 = torch.as_tensor(np.ascontiguousarray(problem.u0), dtype=torch.float64, device=dev)
+    bc = None if problem.bc is None else torch.as_tensor(np.ascontiguousarray(problem.bc), device=dev)
+    q = None if problem.q is None else torch.as_tensor(np.ascontiguousarray(problem.q), device=dev)
+    pit_set_data(ctx, u0, bc, q)
+    torch.cuda.current_stream().synchronize()
+    return ctx

@@ -1,0 +1,74 @@
+"""The C ABI library builds, loads without a GPU and exports every declared symbol;
+argument checks reject bad input before touching CUDA."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2406_00878_gb300 import build as B
+from paper_2406_00878_gb300 import pit
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(pit_\w+)\s*\(", text, flags=re.M))
+    return names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = B.build()
+    lib = ctypes.CDLL(path)
+    declared = _declared()
+    assert {"pit_create", "pit_residual", "pit_newton_step", "pit_solve", "pit_destroy"} <= declared
+    assert declared == set(pit.EXPORTS), declared ^ set(pit.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_default_options_and_status_strings():
+    o = pit.pit_default_options()
+    assert o.newton_max == 30 and o.tol_res == 1e-12 and o.lin_solver == pit.PIT_LIN_AUTO
+    assert o.wait_budget > 0 and o.lin_max_iter > 0
+    assert pit._status_name(pit.PIT_ETIMEOUT) == "PIT_ETIMEOUT"
+
+
+@pytest.mark.parametrize("grid,M,dt,params", [
+    (pit.pit_grid(0, 4, 0, 1, 0, 1), 3, 0.1, pit.pit_params(0, 1.0, 0.0)),
+    (pit.pit_grid(4, 4, 1, 0, 0, 1), 3, 0.1, pit.pit_params(0, 1.0, 0.0)),
+    (pit.pit_grid(4, 4, 0, 1, 0, 1), 0, 0.1, pit.pit_params(0, 1.0, 0.0)),
+    (pit.pit_grid(4, 4, 0, 1, 0, 1), 3, -0.1, pit.pit_params(0, 1.0, 0.0)),
+    (pit.pit_grid(4, 4, 0, 1, 0, 1), 3, float("nan"), pit.pit_params(0, 1.0, 0.0)),
+    (pit.pit_grid(4, 4, 0, 1, 0, 1), 3, 0.1, pit.pit_params(2, 1.0, 0.0)),
+    (pit.pit_grid(4, 4, 0, 1, 0, 1), 3, 0.1, pit.pit_params(1, -1.0, 0.0)),
+    (pit.pit_grid(4, 4, 0, 1, 0, 1), 3, 0.1, pit.pit_params(0, 1.0, -0.5)),
+])
+def test_create_rejects_invalid_arguments_without_cuda(grid, M, dt, params):
+    h = ctypes.c_void_p()
+    s = pit.lib().pit_create(ctypes.byref(grid), M, dt, ctypes.byref(params), None, None, ctypes.byref(h))
+    assert s == pit.PIT_EINVAL and not h.value
+
+
+def test_create_rejects_invalid_options_without_cuda():
+    for field, value in [("newton_max", -1), ("lin_solver", 7), ("eta_max", 0.0), ("lin_max_iter", 0),
+                         ("wait_budget", 0), ("team_ctas", -2)]:
+        o = pit.pit_default_options()
+        setattr(o, field, value)
+        h = ctypes.c_void_p()
+        g, p = pit.pit_grid(4, 4, 0, 1, 0, 1), pit.pit_params(0, 1.0, 0.0)
+        s = pit.lib().pit_create(ctypes.byref(g), 3, 0.1, ctypes.byref(p), ctypes.byref(o), None, ctypes.byref(h))
+        assert s == pit.PIT_EINVAL, field
+
+
+def test_null_context_calls_return_einval():
+    L = pit.lib()
+    assert L.pit_residual(None, None, None, None) == pit.PIT_EINVAL
+    assert L.pit_solve(None, None, None) == pit.PIT_EINVAL
+    assert L.pit_last_error(None) == b"null context"
+    L.pit_destroy(None)
