@@ -205,6 +205,9 @@ def run_ours(args, ws, rank, local):
                        "lin_iters_mean_per_level": [round(s["lin_iters_mean"], 2) for s in steps],
                        "levels_sor": [s["levels_sor"] for s in steps],
                        "stage_ms": {"residual": ms_res, "assemble": ms_asm, "level_chain": ms_sol},
+                       "chain_cta0_us": [{"halo_wait": round(s["us_halo_wait"], 1),
+                                          "reduce_wait": round(s["us_reduce_wait"], 1),
+                                          "total": round(s["us_chain"], 1)} for s in steps],
                        "max_rel_err_first_levels_vs_oracle": err},
             "gpu_launches": launches * args.steps,
             "e2e": {"value": ws * p.dof / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(p.grid.ns * 8),

@@ -105,6 +105,9 @@ typedef struct {
     int levels_sor;         /* levels solved by SOR in this step */
     int levels_capped;      /* levels that hit lin_max_iter */
     float ms_residual, ms_assemble, ms_solve;  /* device time of the three stages */
+    float us_halo_wait;     /* time the first CTA of the level chain waited for neighbours */
+    float us_reduce_wait;   /* time the first CTA of the level chain waited on team reductions */
+    float us_chain;         /* the first CTA's total time in the level chain */
 } pit_step_info;
 
 typedef struct {

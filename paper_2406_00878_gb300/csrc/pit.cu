@@ -56,10 +56,12 @@ struct pit_ctx {
     unsigned long long* sync_words = nullptr;  // flags[G], red_cnt[4]
     int* ints = nullptr;                       // abort, status, level_iters[M], level_method[M]
     double* cta_sumsq = nullptr;               // [G]
+    unsigned long long* timers = nullptr;      // [4] chain kernel, CTA 0
 
     // host mirrors
     std::vector<int> h_ints;
     std::vector<double> h_sumsq;
+    unsigned long long h_timers[4] = {0, 0, 0, 0};
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 
     char err[512] = "";
@@ -185,7 +187,8 @@ static pit_status enqueue_assemble(pit_ctx* ctx, const double* U, double* coef) 
 
 // Run the level chain on the scaled planes in ctx->coef with right-hand sides R.
 // update_U: U += dU; dU (may be null) receives the solution. Fills the statistics.
-static pit_status run_chain(pit_ctx* ctx, const double* R, double* U, double* dU, double eta, pit_step_info* info) {
+static pit_status run_chain(pit_ctx* ctx, const double* R, double* U, double* dU, double eta, double sor_tol_abs,
+                            pit_step_info* info) {
     const int G = ctx->G, M = ctx->M;
     CK(cudaMemsetAsync(ctx->sync_words, 0, sizeof(unsigned long long) * (G + 4), ctx->stream));
     CK(cudaMemsetAsync(ctx->ints, 0, sizeof(int) * (2 + 2 * (size_t)M), ctx->stream));
@@ -205,6 +208,7 @@ static pit_status run_chain(pit_ctx* ctx, const double* R, double* U, double* dU
     a.method = ctx->opt.lin_solver;
     a.sor_rho_max = ctx->opt.sor_rho_max;
     a.eta = eta;
+    a.sor_tol_abs = sor_tol_abs;
     a.atol = ctx->opt.lin_atol;
     a.max_iter = ctx->opt.lin_max_iter;
     a.wait_budget = ctx->opt.wait_budget;
@@ -217,6 +221,7 @@ static pit_status run_chain(pit_ctx* ctx, const double* R, double* U, double* dU
     a.level_iters = ctx->ints + 2;
     a.level_method = ctx->ints + 2 + M;
     a.cta_sumsq = ctx->cta_sumsq;
+    a.timers = ctx->timers;
     void* args[] = {&a};
     CK(cudaEventRecord(ctx->ev[2], ctx->stream));
     CK(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(chain_kernel<kNT>), dim3(G), dim3(kNT), args,
@@ -225,6 +230,7 @@ static pit_status run_chain(pit_ctx* ctx, const double* R, double* U, double* dU
     CK(cudaMemcpyAsync(ctx->h_ints.data(), ctx->ints, sizeof(int) * (2 + 2 * (size_t)M), cudaMemcpyDeviceToHost,
                        ctx->stream));
     CK(cudaMemcpyAsync(ctx->h_sumsq.data(), ctx->cta_sumsq, sizeof(double) * G, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_timers, ctx->timers, sizeof(ctx->h_timers), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     const int status = ctx->h_ints[1];
     if (info) {
@@ -244,6 +250,9 @@ static pit_status run_chain(pit_ctx* ctx, const double* R, double* U, double* dU
         info->lin_iters_max = mx;
         info->levels_sor = nsor;
         info->levels_capped = ncap;
+        info->us_halo_wait = (float)(ctx->h_timers[0] * 1e-3);
+        info->us_reduce_wait = (float)(ctx->h_timers[1] * 1e-3);
+        info->us_chain = (float)(ctx->h_timers[2] * 1e-3);
     }
     if (status == ST_ETIMEOUT) return fail(ctx, PIT_ETIMEOUT, "chain kernel: a device wait ran out of budget");
     if (status == ST_EDIVERGED) return fail(ctx, PIT_EDIVERGED, "chain kernel: NaN/Inf in a level solve");
@@ -357,6 +366,8 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
         CK(dalloc(&ctx->sync_words, (size_t)ctx->G + 4));
         CK(dalloc(&ctx->ints, 2 + 2 * (size_t)M));
         CK(dalloc(&ctx->cta_sumsq, (size_t)ctx->G));
+        CK(dalloc(&ctx->timers, 4));
+        CK(cudaMemsetAsync(ctx->timers, 0, sizeof(unsigned long long) * 4, ctx->stream));
         ctx->h_ints.assign(2 + 2 * (size_t)M, 0);
         ctx->h_sumsq.assign(ctx->G, 0.0);
         for (auto& e : ctx->ev) CK(cudaEventCreate(&e));
@@ -387,6 +398,7 @@ extern "C" void pit_destroy(pit_ctx* ctx) {
     cudaFree(ctx->sync_words);
     cudaFree(ctx->ints);
     cudaFree(ctx->cta_sumsq);
+    cudaFree(ctx->timers);
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
     delete ctx;
@@ -439,15 +451,17 @@ extern "C" pit_status pit_block_solve(pit_ctx* ctx, const double* U_dev, const d
     if (!(eta > 0.0)) return fail(ctx, PIT_EINVAL, "pit_block_solve: eta must be > 0");
     if (info) std::memset(info, 0, sizeof(*info));
     CHECK_RET(enqueue_assemble<true>(ctx, U_dev, ctx->coef));
-    return run_chain(ctx, R_dev, nullptr, dU_dev, eta, info);
+    return run_chain(ctx, R_dev, nullptr, dU_dev, eta, 0.0, info);
 }
 
 // One Newton update given that ctx->R holds the residual of U and res its max norm.
 static pit_status newton_update(pit_ctx* ctx, double* U, double res, pit_step_info* info) {
+    // inexact-Newton forcing: relative eta for BiCGStab, absolute eta*||R||_inf for SOR
     const double eta = std::max(std::min(ctx->opt.eta_max, ctx->opt.eta_gamma * res), 1e-300);
+    const double sor_tol = std::max(ctx->opt.lin_atol, eta * res);
     CK(cudaEventRecord(ctx->ev[1], ctx->stream));
     CHECK_RET(enqueue_assemble<true>(ctx, U, ctx->coef));
-    pit_status st = run_chain(ctx, ctx->R, U, nullptr, eta, info);  // records ev[2], ev[3] around the launch
+    pit_status st = run_chain(ctx, ctx->R, U, nullptr, eta, sor_tol, info);  // records ev[2], ev[3] around the launch
     if (info) {
         CK(cudaEventSynchronize(ctx->ev[3]));
         CK(cudaEventElapsedTime(&info->ms_residual, ctx->ev[0], ctx->ev[1]));

@@ -277,6 +277,7 @@ struct ChainArgs {
     int method;                             // 0 auto, 1 SOR, 2 BiCGStab
     double sor_rho_max;
     double eta;                             // relative tolerance of every level solve
+    double sor_tol_abs;                     // > 0: absolute SOR tolerance instead of eta*||b||_inf
     double atol;                            // absolute floor of the tolerance
     int max_iter;                           // cap per level
     long long wait_budget;
@@ -291,7 +292,14 @@ struct ChainArgs {
     int* level_iters;                       // [M] sweeps / iterations of each level
     int* level_method;                      // [M] 1 = SOR, 2 = BiCGStab
     double* cta_sumsq;                      // [G] sum of dU^2 over the CTA's rows, all levels
+    unsigned long long* timers;             // [4] CTA 0: ns waiting on halos, on reductions, total
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Per-CTA state of the team protocol.
 struct Team {
@@ -299,6 +307,8 @@ struct Team {
     int r0, nrows, nloc;
     unsigned long long pub_seq;   // publications so far by this CTA
     unsigned long long red_seq;   // reductions started so far
+    unsigned long long t_halo;    // ns spent waiting for neighbours (thread 0 of CTA 0)
+    unsigned long long t_red;     // ns spent waiting for team reductions (thread 0 of CTA 0)
 };
 
 // Give up on a wait: record the status once and raise the abort flag.
@@ -316,7 +326,7 @@ __device__ __forceinline__ bool wait_geq(const ChainArgs& a, const unsigned long
             team_fail(a, ST_ETIMEOUT);
             return false;
         }
-        if (spins > 64) __nanosleep(32);
+        if (spins > 4096) __nanosleep(64);
     }
     return true;
 }
@@ -339,11 +349,13 @@ __device__ bool exchange_halo(const ChainArgs& a, Team& t, const double* v, doub
     if (threadIdx.x == 0) {
         __threadfence();
         st_release_u64(a.flags + t.b, seq);
+        const unsigned long long t0 = global_ns();
         bool ok = true;
         if (t.b > 0) ok = wait_geq(a, a.flags + t.b - 1, seq);
         if (ok && t.b + 1 < t.G) ok = wait_geq(a, a.flags + t.b + 1, seq);
         __threadfence();
         *s_ok = ok ? 1 : 0;
+        t.t_halo += global_ns() - t0;
     }
     __syncthreads();
     if (!*s_ok) return false;
@@ -380,32 +392,44 @@ __device__ __forceinline__ unsigned long long reduce_arrive(const ChainArgs& a, 
     return use;
 }
 
-// Finish reduction `use`: wait for all G arrivals, then sum the partials in order
-// (max instead of sum when MAXOP). Result is broadcast to every thread.
+// Finish reduction `use`: wait for all G arrivals, then one warp sums the partials
+// (lane l takes CTAs l, l+32, ... in order, then a fixed xor-shuffle tree), or takes
+// their max when MAXOP. Every CTA performs the identical sequence of operations, so
+// all CTAs obtain the same value. Result is broadcast to every thread.
 template <int K, bool MAXOP>
 __device__ __forceinline__ bool reduce_finish(const ChainArgs& a, Team& t, unsigned long long use, double (&out)[K],
                                               double* s_bcast, int* s_ok) {
     const int slot = (int)(use & 3);
     if (threadIdx.x == 0) {
         const unsigned long long target = (unsigned long long)t.G * ((use >> 2) + 1);
+        const unsigned long long t0 = global_ns();
         *s_ok = wait_geq(a, a.red_cnt + slot, target) ? 1 : 0;
         __threadfence();
-        if (*s_ok) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                double s = 0.0;
-                bool nan = false;
-                for (int b = 0; b < t.G; ++b) {
-                    const double v = __ldcg(a.red_part + ((size_t)slot * t.G + b) * 4 + k);
-                    s = MAXOP ? fmax(s, v) : s + v;
-                    nan |= (v != v);
-                }
-                s_bcast[k] = nan ? __longlong_as_double(0x7ff8000000000000ll) : s;
-            }
-        }
+        t.t_red += global_ns() - t0;
     }
     __syncthreads();
     const bool ok = *s_ok != 0;
+    if (ok && threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const double* part = a.red_part + (size_t)slot * t.G * 4;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double s = 0.0;
+            bool nan = false;
+            for (int b = lane; b < t.G; b += 32) {
+                const double v = __ldcg(part + (size_t)b * 4 + k);
+                s = MAXOP ? fmax(s, v) : s + v;
+                nan |= (v != v);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double w = __shfl_xor_sync(0xffffffffu, s, o);
+                s = MAXOP ? fmax(s, w) : s + w;
+            }
+            nan = __any_sync(0xffffffffu, nan);
+            if (lane == 0) s_bcast[k] = nan ? __longlong_as_double(0x7ff8000000000000ll) : s;
+        }
+    }
+    __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; ++k) out[k] = s_bcast[k];
     __syncthreads();
@@ -438,20 +462,27 @@ __device__ __forceinline__ void local_spmv(const Team& t, const Smem& m, const d
 // starting from x. Stops when the error estimate d_s rho / (1 - rho) <= tol, where
 // d_s is the largest change of a sweep and rho = max(d_s / d_{s-1}, omega - 1); the
 // global d_s is known one sweep late (lagged team reduction), so every CTA takes
-// the same decision at the same sweep. Returns the sweep count (< 0 on abort).
+// the same decision at the same sweep. Threads walk the points of one colour only
+// (every lane of a warp does useful FP64 work). Scalar decisions are taken by
+// thread 0 and broadcast. Returns the sweep count (< 0 on abort).
 template <int NT>
 __device__ int level_sor(const ChainArgs& a, Team& t, const Smem& m, double omega, double tol, int* s_ok) {
     const int nx = t.nx;
-    double prev = -1.0, prev2 = -1.0;  // global max change of sweeps s-1 and s-2
+    const int half = (nx + 1) >> 1;            // points of one colour per row, at most
+    const int npts = t.nrows * half;
+    double prev = -1.0, prev2 = -1.0;          // global max change of sweeps s-1 and s-2 (thread 0)
     unsigned long long pending = 0;
     bool have_pending = false;
+    int* s_flag = reinterpret_cast<int*>(m.red + 48);
     for (int sweep = 1;; ++sweep) {
         double dmax = 0.0;
         for (int color = 0; color < 2; ++color) {
             if (!exchange_halo<NT>(a, t, m.x, m.haloS, m.haloN, s_ok)) return -1;
-            for (int k = threadIdx.x; k < t.nloc; k += NT) {
-                const int jl = k / nx, i = k - jl * nx;
-                if (((t.r0 + jl + i) & 1) != color) continue;
+            for (int q = threadIdx.x; q < npts; q += NT) {
+                const int jl = q / half;
+                const int i = ((t.r0 + jl + color) & 1) + 2 * (q - jl * half);
+                if (i >= nx) continue;
+                const int k = jl * nx + i;
                 const double xW = i > 0 ? m.x[k - 1] : 0.0;
                 const double xE = i < nx - 1 ? m.x[k + 1] : 0.0;
                 const double xS = jl > 0 ? m.x[k - nx] : m.haloS[i];
@@ -466,7 +497,7 @@ __device__ int level_sor(const ChainArgs& a, Team& t, const Smem& m, double omeg
             __syncthreads();
         }
         // this CTA's max change, then arrive at the team reduction of this sweep
-        double v[1] = {0.0};
+        double v[1];
         {
             unsigned long long key = block_max_u64<NT>(abs_key(dmax), reinterpret_cast<unsigned long long*>(m.red));
             v[0] = key_val(key);
@@ -475,21 +506,28 @@ __device__ int level_sor(const ChainArgs& a, Team& t, const Smem& m, double omeg
         if (have_pending) {
             double g[1];
             if (!reduce_finish<1, true>(a, t, pending, g, m.red + 32, s_ok)) return -1;
-            const double d = g[0];
-            if (d != d) {
-                if (threadIdx.x == 0) atomicCAS(a.status, 0, ST_EDIVERGED);
-                // consume the outstanding reduction so the sequence stays aligned
-                double h[1];
-                if (!reduce_finish<1, true>(a, t, use, h, m.red + 32, s_ok)) return -1;
-                return sweep;
+            if (threadIdx.x == 0) {
+                const double d = g[0];
+                int decision = 0;  // 0 continue, 1 converged / capped, 2 NaN
+                if (d != d) {
+                    decision = 2;
+                } else {
+                    prev2 = prev;
+                    prev = d;
+                    double rho = omega - 1.0;
+                    if (prev2 > 0.0) rho = fmax(rho, prev / prev2);
+                    if (prev == 0.0 || (prev2 > 0.0 && rho < 1.0 && prev * rho <= tol * (1.0 - rho)) ||
+                        sweep >= a.max_iter)
+                        decision = 1;
+                }
+                *s_flag = decision;
             }
-            prev2 = prev;
-            prev = d;
-            double rho = omega - 1.0;
-            if (prev2 > 0.0) rho = fmax(rho, prev / prev2);
-            const bool done = (prev == 0.0) || (prev2 > 0.0 && rho < 1.0 && prev * rho <= tol * (1.0 - rho)) ||
-                              sweep >= a.max_iter;
-            if (done) {
+            __syncthreads();
+            const int decision = *s_flag;
+            __syncthreads();
+            if (decision) {
+                if (decision == 2 && threadIdx.x == 0) atomicCAS(a.status, 0, ST_EDIVERGED);
+                // consume the outstanding reduction so the sequence stays aligned
                 double h[1];
                 if (!reduce_finish<1, true>(a, t, use, h, m.red + 32, s_ok)) return -1;
                 return sweep;
@@ -500,15 +538,25 @@ __device__ int level_sor(const ChainArgs& a, Team& t, const Smem& m, double omeg
     }
 }
 
+// Broadcast a double computed by thread 0 to every thread of the CTA.
+__device__ __forceinline__ double bcast0(double v, double* slot) {
+    if (threadIdx.x == 0) *slot = v;
+    __syncthreads();
+    v = *slot;
+    __syncthreads();
+    return v;
+}
+
 // Jacobi-preconditioned BiCGStab (van der Vorst 1992) on the scaled level system,
-// from x = 0. Stops when ||r||_2 <= tol_rel ||bs||_2 or ||r||_2 <= atol sqrt(Ns).
+// from x = 0. Stops when ||r||_2 <= max(eta ||bs||_2, atol sqrt(Ns)). Scalars are
+// formed by thread 0 and broadcast (FP64 division is costly on this part).
 template <int NT>
 __device__ int level_bicgstab(const ChainArgs& a, Team& t, const Smem& m, double eta, double atol, int* s_ok) {
     double* sb = m.red + 32;
+    double* slot = m.red + 48;
     const int nloc = t.nloc;
-    double loc[2];
     // r = bs, rh = bs, x = 0, p = v = 0
-    loc[0] = 0.0;
+    double one[1] = {0.0};
     for (int k = threadIdx.x; k < nloc; k += NT) {
         const double b = m.bs[k];
         m.x[k] = 0.0;
@@ -516,20 +564,21 @@ __device__ int level_bicgstab(const ChainArgs& a, Team& t, const Smem& m, double
         m.rh[k] = b;
         m.p[k] = 0.0;
         m.v[k] = 0.0;
-        loc[0] += b * b;
+        one[0] += b * b;
     }
-    double one[1] = {loc[0]};
     block_sum<NT, 1>(one, m.red);
     double g1[1];
     if (!reduce_finish<1, false>(a, t, reduce_arrive<1>(a, t, one), g1, sb, s_ok)) return -1;
-    const double bnorm = sqrt(g1[0]);
-    const double Ns = (double)t.nx * (double)a.ny;
-    const double tol = fmax(eta * bnorm, atol * sqrt(Ns));
-    if (bnorm <= tol) return 0;
-    double rho_old = 1.0, alpha = 1.0, omega = 1.0, rho = g1[0];  // (rh, r) = ||b||^2 at start
+    // thread 0 keeps the recurrence scalars; others receive what they need
+    double tol = 0.0, rho_old = 1.0, alpha = 1.0, omega = 1.0, rho = g1[0];
+    if (threadIdx.x == 0) tol = fmax(eta * sqrt(g1[0]), atol * sqrt((double)t.nx * (double)a.ny));
+    if (bcast0(threadIdx.x == 0 ? (sqrt(g1[0]) <= tol ? 1.0 : 0.0) : 0.0, slot) != 0.0) return 0;
     for (int it = 1; it <= a.max_iter; ++it) {
-        const double beta = (rho / rho_old) * (alpha / omega);
-        for (int k = threadIdx.x; k < nloc; k += NT) m.p[k] = m.r[k] + beta * (m.p[k] - omega * m.v[k]);
+        double beta = 0.0;
+        if (threadIdx.x == 0) beta = (rho / rho_old) * (alpha / omega);
+        beta = bcast0(beta, slot);
+        const double om_b = bcast0(omega, slot);
+        for (int k = threadIdx.x; k < nloc; k += NT) m.p[k] = m.r[k] + beta * (m.p[k] - om_b * m.v[k]);
         __syncthreads();
         if (!exchange_halo<NT>(a, t, m.p, m.haloS, m.haloN, s_ok)) return -1;
         local_spmv<NT>(t, m, m.p, m.v);
@@ -537,12 +586,20 @@ __device__ int level_bicgstab(const ChainArgs& a, Team& t, const Smem& m, double
         for (int k = threadIdx.x; k < nloc; k += NT) d1[0] += m.rh[k] * m.v[k];
         block_sum<NT, 1>(d1, m.red);
         if (!reduce_finish<1, false>(a, t, reduce_arrive<1>(a, t, d1), d1, sb, s_ok)) return -1;
-        if (d1[0] == 0.0 || d1[0] != d1[0]) {
-            if (threadIdx.x == 0) atomicCAS(a.status, 0, d1[0] != d1[0] ? ST_EDIVERGED : ST_ENOCONV);
+        // code: 0 go on, 1 NaN, 2 breakdown
+        double code = 0.0;
+        if (threadIdx.x == 0) {
+            if (d1[0] != d1[0]) code = 1.0;
+            else if (d1[0] == 0.0) code = 2.0;
+            else alpha = rho / d1[0];
+        }
+        code = bcast0(code, slot);
+        if (code != 0.0) {
+            if (threadIdx.x == 0) atomicCAS(a.status, 0, code == 1.0 ? ST_EDIVERGED : ST_ENOCONV);
             return it;
         }
-        alpha = rho / d1[0];
-        for (int k = threadIdx.x; k < nloc; k += NT) m.s[k] = m.r[k] - alpha * m.v[k];
+        const double al_b = bcast0(alpha, slot);
+        for (int k = threadIdx.x; k < nloc; k += NT) m.s[k] = m.r[k] - al_b * m.v[k];
         __syncthreads();
         if (!exchange_halo<NT>(a, t, m.s, m.haloS, m.haloN, s_ok)) return -1;
         local_spmv<NT>(t, m, m.s, m.t);
@@ -553,29 +610,34 @@ __device__ int level_bicgstab(const ChainArgs& a, Team& t, const Smem& m, double
         }
         block_sum<NT, 2>(d2, m.red);
         if (!reduce_finish<2, false>(a, t, reduce_arrive<2>(a, t, d2), d2, sb, s_ok)) return -1;
-        omega = d2[1] > 0.0 ? d2[0] / d2[1] : 0.0;
+        if (threadIdx.x == 0) omega = d2[1] > 0.0 ? d2[0] / d2[1] : 0.0;
+        const double om2 = bcast0(omega, slot);
         double d3[2] = {0.0, 0.0};
         for (int k = threadIdx.x; k < nloc; k += NT) {
-            m.x[k] += alpha * m.p[k] + omega * m.s[k];
-            const double rk = m.s[k] - omega * m.t[k];
+            m.x[k] += al_b * m.p[k] + om2 * m.s[k];
+            const double rk = m.s[k] - om2 * m.t[k];
             m.r[k] = rk;
             d3[0] += m.rh[k] * rk;
             d3[1] += rk * rk;
         }
         block_sum<NT, 2>(d3, m.red);
         if (!reduce_finish<2, false>(a, t, reduce_arrive<2>(a, t, d3), d3, sb, s_ok)) return -1;
-        const double rnorm = sqrt(d3[1]);
-        if (rnorm != rnorm) {
-            if (threadIdx.x == 0) atomicCAS(a.status, 0, ST_EDIVERGED);
+        // code: 0 go on, 1 NaN, 2 breakdown, 3 converged
+        code = 0.0;
+        if (threadIdx.x == 0) {
+            const double rnorm = sqrt(d3[1]);
+            if (rnorm != rnorm) code = 1.0;
+            else if (rnorm <= tol) code = 3.0;
+            else if (omega == 0.0 || d3[0] == 0.0) code = 2.0;
+            rho_old = rho;
+            rho = d3[0];
+        }
+        code = bcast0(code, slot);
+        if (code == 3.0) return it;
+        if (code != 0.0) {
+            if (threadIdx.x == 0) atomicCAS(a.status, 0, code == 1.0 ? ST_EDIVERGED : ST_ENOCONV);
             return it;
         }
-        if (rnorm <= tol) return it;
-        if (omega == 0.0 || d3[0] == 0.0) {
-            if (threadIdx.x == 0) atomicCAS(a.status, 0, ST_ENOCONV);
-            return it;
-        }
-        rho_old = rho;
-        rho = d3[0];
     }
     if (threadIdx.x == 0) atomicCAS(a.status, 0, ST_ENOCONV);
     return a.max_iter;
@@ -601,6 +663,9 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
     t.nloc = t.nrows * a.nx;
     t.pub_seq = 0;
     t.red_seq = 0;
+    t.t_halo = 0;
+    t.t_red = 0;
+    const unsigned long long t_start = global_ns();
     const int nloc = t.nloc;
     const int cap = (a.rows_base + (a.rows_rem ? 1 : 0)) * a.nx;  // largest nloc of the team
     Smem m;
@@ -648,18 +713,24 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
         const double rho_g = key_val(a.rho_key[n]);
         const bool use_sor = a.method == 1 || (a.method == 0 && rho_g < a.sor_rho_max);
         int iters;
-        double tol_abs = 0.0;
         if (use_sor) {
-            // tolerance relative to the level's unscaled ||b||_inf (team max reduction)
-            double bl = 0.0;
-            for (int k = threadIdx.x; k < nloc; k += NT) bl = fmax(bl, fabs(m.x[k]));
-            unsigned long long key = block_max_u64<NT>(abs_key(bl), reinterpret_cast<unsigned long long*>(m.red));
-            double v[1] = {key_val(key)};
-            double g[1];
-            if (!reduce_finish<1, true>(a, t, reduce_arrive<1>(a, t, v), g, m.red + 32, &s_ok)) return;
-            tol_abs = fmax(a.eta * g[0], a.atol);
-            const double rc = fmin(rho_g, 0.999999);
-            const double omega = rho_g < 1.0 ? 2.0 / (1.0 + sqrt(1.0 - rc * rc)) : 1.0;
+            double tol_abs = a.sor_tol_abs;
+            if (!(tol_abs > 0.0)) {
+                // tolerance relative to the level's unscaled ||b||_inf (team max reduction)
+                double bl = 0.0;
+                for (int k = threadIdx.x; k < nloc; k += NT) bl = fmax(bl, fabs(m.x[k]));
+                unsigned long long key = block_max_u64<NT>(abs_key(bl), reinterpret_cast<unsigned long long*>(m.red));
+                double v[1] = {key_val(key)};
+                double g[1];
+                if (!reduce_finish<1, true>(a, t, reduce_arrive<1>(a, t, v), g, m.red + 32, &s_ok)) return;
+                tol_abs = fmax(a.eta * g[0], a.atol);
+            }
+            double omega = 1.0;
+            if (threadIdx.x == 0 && rho_g < 1.0) {
+                const double rc = fmin(rho_g, 0.999999);
+                omega = 2.0 / (1.0 + sqrt(1.0 - rc * rc));
+            }
+            omega = bcast0(omega, m.red + 48);
             iters = level_sor<NT>(a, t, m, omega, tol_abs, &s_ok);
         } else {
             iters = level_bicgstab<NT>(a, t, m, a.eta, a.atol, &s_ok);
@@ -682,6 +753,11 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
     double ss[1] = {sumsq};
     block_sum<NT, 1>(ss, m.red);
     if (threadIdx.x == 0) a.cta_sumsq[t.b] = ss[0];
+    if (t.b == 0 && threadIdx.x == 0) {
+        a.timers[0] = t.t_halo;
+        a.timers[1] = t.t_red;
+        a.timers[2] = global_ns() - t_start;
+    }
 }
 
 }  // namespace pit

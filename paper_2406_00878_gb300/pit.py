@@ -47,7 +47,8 @@ class pit_options(ctypes.Structure):
 class pit_step_info(ctypes.Structure):
     _fields_ = [("res_inf", ctypes.c_double), ("upd_rms", ctypes.c_double), ("lin_iters_mean", ctypes.c_double),
                 ("lin_iters_max", ctypes.c_int), ("levels_sor", ctypes.c_int), ("levels_capped", ctypes.c_int),
-                ("ms_residual", ctypes.c_float), ("ms_assemble", ctypes.c_float), ("ms_solve", ctypes.c_float)]
+                ("ms_residual", ctypes.c_float), ("ms_assemble", ctypes.c_float), ("ms_solve", ctypes.c_float),
+                ("us_halo_wait", ctypes.c_float), ("us_reduce_wait", ctypes.c_float), ("us_chain", ctypes.c_float)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
