@@ -178,6 +178,33 @@ pit_status pit_solve(pit_ctx* ctx, double* U_dev, pit_solve_info* info);
  * the boundary data and sources set by pit_set_data are kept. */
 pit_status pit_solve_host(pit_ctx* ctx, const double* u0_host, double* U_host, pit_solve_info* info);
 
+/* Limits of pit_block_solve_noalloc's built-in workspace. */
+#define PIT_NOALLOC_MAX_NX 512       /* interior nodes per grid row */
+#define PIT_NOALLOC_MAX_TEAM 160     /* CTAs sharing one level */
+#define PIT_NOALLOC_MAX_LEVELS 4096  /* time levels M */
+
+/* The paper has no counterpart to this entry point: it is pit_block_solve for
+ * callers that cannot allocate device memory -- code that runs from a fixed
+ * memory budget, a real-time loop that may not take an allocation's implicit
+ * synchronisation, or an embedding that owns all GPU memory itself. It needs no
+ * context and allocates nothing: the caller passes the raw Jacobian entries
+ * coef_dev [5][M][Ns] (C, W, E, S, N of every A_n, e.g. from pit_assemble) and
+ * R_dev [M][Ns]; dU_dev [M][Ns] receives the nested block inverse of eq. 7 as in
+ * pit_block_solve (level tolerance eta, solver choice from opt, NULL = defaults).
+ * The level chain's team workspace is a static device array of about 2.7 MB in
+ * this library, held by every GPU that loads it until the process exits. The
+ * first call on a device looks up that array's device address (with the device
+ * current); make that first call before any stream capture. Sizes beyond the
+ * workspace (nx > PIT_NOALLOC_MAX_NX, M > PIT_NOALLOC_MAX_LEVELS, a team larger
+ * than PIT_NOALLOC_MAX_TEAM) return PIT_EUNSUPPORTED. All calls on a device share
+ * the workspace: it is re-initialised at the start of each call, and calls that
+ * overlap on the GPU race on it, so serialise them. Ordered on `stream`;
+ * synchronises it before returning. err (may be NULL) receives a message of up to
+ * err_len bytes. */
+pit_status pit_block_solve_noalloc(int nx, int ny, int M, const double* coef_dev, const double* R_dev,
+                                   double* dU_dev, double eta, const pit_options* opt, void* stream, char* err,
+                                   int err_len);
+
 /* Message for the last failing call on ctx (never NULL). */
 const char* pit_last_error(const pit_ctx* ctx);
 

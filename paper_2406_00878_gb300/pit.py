@@ -21,11 +21,12 @@ PIT_OK, PIT_EINVAL, PIT_ECUDA, PIT_ENOMEM, PIT_ENOCONV, PIT_EDIVERGED, PIT_ETIME
 PIT_HEAT, PIT_BURGERS = 0, 1
 PIT_LIN_AUTO, PIT_LIN_SOR, PIT_LIN_BICGSTAB = 0, 1, 2
 PIT_MAX_NEWTON = 64
+PIT_NOALLOC_MAX_NX, PIT_NOALLOC_MAX_TEAM, PIT_NOALLOC_MAX_LEVELS = 512, 160, 4096
 
 #: every symbol include/pit.h declares
 EXPORTS = ("pit_default_options", "pit_create", "pit_set_data", "pit_fill_plain_guess", "pit_residual",
            "pit_assemble", "pit_block_solve", "pit_newton_step", "pit_solve", "pit_solve_host", "pit_last_error",
-           "pit_status_string", "pit_destroy")
+           "pit_status_string", "pit_destroy", "pit_block_solve_noalloc")
 
 
 class pit_grid(ctypes.Structure):
@@ -114,6 +115,9 @@ def lib():
             L.pit_status_string.restype = ctypes.c_char_p
             L.pit_destroy.argtypes = [P]
             L.pit_destroy.restype = None
+            L.pit_block_solve_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, V, V, V, ctypes.c_double,
+                                                  ctypes.POINTER(pit_options), V, ctypes.c_char_p, ctypes.c_int]
+            L.pit_block_solve_noalloc.restype = st
             _lib = L
         return _lib
 
@@ -259,6 +263,27 @@ def pit_solve_host(ctx: Context, u0_host, U_host, check: bool = True):
 
 def pit_destroy(ctx: Context):
     ctx.close()
+
+
+def pit_block_solve_noalloc(nx: int, ny: int, M: int, coef, R, dU, eta: float = 1e-14,
+                            opt: Optional[pit_options] = None, stream=None, check: bool = True):
+    """Context-free block solve from raw Jacobian entries that allocates nothing on the
+    device (for callers that cannot allocate). Returns (status, message)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif not isinstance(stream, int):
+        stream = stream.cuda_stream
+    dof = nx * ny * M
+    buf = ctypes.create_string_buffer(512)
+    s = lib().pit_block_solve_noalloc(int(nx), int(ny), int(M), _dptr(coef, "coef", 5 * dof), _dptr(R, "R", dof),
+                                      _dptr(dU, "dU", dof), float(eta),
+                                      ctypes.byref(opt) if opt is not None else None, ctypes.c_void_p(stream), buf,
+                                      len(buf))
+    msg = buf.value.decode()
+    if check and s != PIT_OK:
+        raise PitError(s, msg)
+    return s, msg
 
 
 # ------------------------------------------------------------- convenience
