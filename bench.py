@@ -41,6 +41,10 @@ FP64_PEAK_TFLOPS = 1.25
 # (4 couplings, rhs, relaxation) and one BiCGStab iteration (2 SpMV + 6 axpy + 5 dots).
 FLOPS_PER_SOR_UPDATE = 11
 FLOPS_PER_BICGSTAB_ITER = 2 * 9 + 6 * 2 + 5 * 2
+# per node and Newton iteration, Burgers with constant viscosity: residual (convective
+# and viscous differences, time term) and the four scaled couplings
+FLOPS_PER_RESIDUAL = 18
+FLOPS_PER_JACOBIAN = 8
 
 
 def _dist():
@@ -167,23 +171,29 @@ def run_ours(args, ws, rank, local):
     last = infos[-1]
     k = last["newton_iters"]
     steps = last["steps"]
+    wave = last["wave_teams"] > 0
     ms_res = sum(s["ms_residual"] for s in steps)
     ms_asm = sum(s["ms_assemble"] for s in steps)
     ms_sol = sum(s["ms_solve"] for s in steps)
-    launches = 1 + 3 * k + 1  # plain guess + (residual, assembly, chain) per update + final residual
-    # dominant kernel: the level chain; its algorithmic FP64 flops per launch from the
-    # measured sweeps / iterations of each level
+    # algorithmic FP64 flops of the level solves, from the measured sweeps / iterations
     flops = 0.0
     for s in steps:
-        n_sor = s["levels_sor"]
-        n_bcg = p.M - n_sor
         it = s["lin_iters_mean"] * p.M
-        # split iterations between methods in proportion (all levels share a method here)
-        frac_sor = n_sor / p.M
+        frac_sor = s["levels_sor"] / p.M
         flops += p.grid.ns * (it * frac_sor * FLOPS_PER_SOR_UPDATE + it * (1 - frac_sor) * FLOPS_PER_BICGSTAB_ITER)
-    flops_per_launch = flops / max(k, 1)
-    chain_ms_per_launch = ms_sol / max(k, 1)
-    achieved_tflops = flops_per_launch / (chain_ms_per_launch * 1e-3) / 1e12
+    if wave:
+        # one wavefront launch does residual, Jacobian and level solves of every iteration
+        launches = 1 + last["wave_launches"] + 1  # plain guess + wavefront + final residual
+        flops += k * p.dof * (FLOPS_PER_RESIDUAL + FLOPS_PER_JACOBIAN)
+        kernel_ms = last["ms_wave"] / max(last["wave_launches"], 1)
+        flops_per_launch = flops / max(last["wave_launches"], 1)
+        kernel_name = "wave_kernel (Newton wavefront: residual, Jacobian, nested inverse of eq. 7)"
+    else:
+        launches = 1 + 3 * k + 1  # plain guess + (residual, assembly, chain) per update + final residual
+        kernel_ms = ms_sol / max(k, 1)
+        flops_per_launch = flops / max(k, 1)
+        kernel_name = "chain_kernel (level chain, eq. 7 nested inverse)"
+    achieved_tflops = flops_per_launch / (kernel_ms * 1e-3) / 1e12
     out = None
     if rank == 0:
         value = ws * p.dof / (ms * 1e-3)
@@ -207,12 +217,17 @@ def run_ours(args, ws, rank, local):
                        "stage_ms": {"residual": ms_res, "assemble": ms_asm, "level_chain": ms_sol},
                        "chain_cta0_us": [{"halo_wait": round(s["us_halo_wait"], 1),
                                           "reduce_wait": round(s["us_reduce_wait"], 1),
-                                          "total": round(s["us_chain"], 1)} for s in steps],
+                                          "total": round(s["us_chain"], 1)} for s in steps] if not wave else None,
+                       "wavefront": {"teams": last["wave_teams"], "ctas_per_team": last["wave_team_ctas"],
+                                     "launches": last["wave_launches"], "ms": last["ms_wave"],
+                                     "cta0_us": {"predecessor_wait": round(last["us_pred_wait"], 1),
+                                                 "halo_wait": round(last["us_halo_wait"], 1),
+                                                 "reduce_wait": round(last["us_reduce_wait"], 1)}} if wave else None,
                        "max_rel_err_first_levels_vs_oracle": err},
             "gpu_launches": launches * args.steps,
             "e2e": {"value": ws * p.dof / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(p.grid.ns * 8),
                     "d2h_bytes_per_step": int(p.dof * 8)},
-            "roofline": {"kernel": "chain_kernel (level chain, eq. 7 nested inverse)", "bound": "alu",
+            "roofline": {"kernel": kernel_name, "bound": "alu",
                          "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
                          "peak_source": "FP64 nominal 1.25 TFLOP/s (profiling recipe); FP64 not in MEASURED_PEAKS"},

@@ -93,6 +93,9 @@ typedef struct {
     double sor_rho_max;     /* AUTO uses SOR below this Gershgorin bound (default 0.95) */
     int team_ctas;          /* CTAs that share one level in the chain kernel (0 = auto) */
     long long wait_budget;  /* spin iterations before a device wait gives up (default 1<<26) */
+    int wave_teams;         /* pit_solve: Newton iterations in flight in the wavefront kernel
+                               (0 = auto (4), >= 1 that many, -1 = one launch per stage and
+                               Newton iteration, as pit_newton_step) */
 } pit_options;
 
 #define PIT_MAX_NEWTON 64
@@ -116,6 +119,12 @@ typedef struct {
     double res_inf[PIT_MAX_NEWTON + 1];    /* ||R_k||_inf, k = 0..newton_iters */
     pit_step_info steps[PIT_MAX_NEWTON];
     double ms_total;                       /* device time of the whole solve */
+    int wave_teams;                        /* Newton iterations in flight (0: per-stage launches) */
+    int wave_team_ctas;                    /* CTAs per team */
+    int wave_launches;                     /* wavefront launches (more than 1 after a restart) */
+    float ms_wave;                         /* device time of the wavefront launches */
+    float us_pred_wait;                    /* first CTA of team 0: waiting for the previous iteration */
+    float us_halo_wait, us_reduce_wait;    /* first CTA of team 0: team synchronisation */
 } pit_solve_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -169,7 +178,12 @@ pit_status pit_block_solve(pit_ctx* ctx, const double* U_dev, const double* R_de
 pit_status pit_newton_step(pit_ctx* ctx, double* U_dev, pit_step_info* info);
 
 /* Row (a4): Newton from the iterate in U_dev until ||R||_inf <= tol_res or
- * newton_max updates (PIT_ENOCONV; U_dev holds the last iterate). */
+ * newton_max updates (PIT_ENOCONV; U_dev holds the last iterate). By default all
+ * Newton iterations run in one cooperative wavefront launch: iteration k works on
+ * level n as soon as iteration k-1 has finished it, so up to wave_teams iterations
+ * are in flight (same iterates as plain Newton; the level solves' forcing uses the
+ * running max of ||r^j||_inf over the levels j <= n already visited). The final
+ * ||R||_inf is always recomputed from U_dev by the residual kernel. */
 pit_status pit_solve(pit_ctx* ctx, double* U_dev, pit_solve_info* info);
 
 /* pit_solve with host buffers: copies u0_host [Ns] to the device (replacing u^0),

@@ -58,6 +58,21 @@ struct pit_ctx {
     double* cta_sumsq = nullptr;               // [G]
     unsigned long long* timers = nullptr;      // [4] chain kernel, CTA 0
 
+    // Newton wavefront (pit_solve): K teams of Gw CTAs
+    int K = 0, Gw = 0, w_rows_base = 0, w_rows_rem = 0, kcap = 0;
+    size_t wave_smem = 0;
+    double* w_pub = nullptr;
+    double* w_red = nullptr;
+    unsigned long long* w_sync = nullptr;  // flags[K*Gw], red_cnt[K*4], prog[K*Gw]
+    int* w_ints = nullptr;                  // abort, status, stop[2]
+    double* w_res = nullptr;                // [kcap]
+    int* w_cell = nullptr;                  // [kcap][M]
+    double* w_sumsq = nullptr;              // [kcap][Gw]
+    unsigned long long* w_timers = nullptr; // [K][4]
+    std::vector<double> h_wres, h_wsumsq;
+    std::vector<int> h_wcell;
+    std::vector<unsigned long long> h_wtimers;
+
     // host mirrors
     std::vector<int> h_ints;
     std::vector<double> h_sumsq;
@@ -116,6 +131,7 @@ extern "C" void pit_default_options(pit_options* o) {
     o->sor_rho_max = 0.95;
     o->team_ctas = 0;
     o->wait_budget = 1ll << 26;
+    o->wave_teams = 0;
 }
 
 extern "C" const char* pit_status_string(pit_status s) {
@@ -287,7 +303,8 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
     const pit_options& o = ctx->opt;
     if (o.newton_max < 0 || o.newton_max > PIT_MAX_NEWTON || !(o.tol_res >= 0.0) || o.lin_solver < 0 ||
         o.lin_solver > 2 || !(o.eta_max > 0.0) || !(o.eta_gamma >= 0.0) || !(o.lin_atol >= 0.0) ||
-        o.lin_max_iter < 1 || !(o.sor_rho_max > 0.0) || o.team_ctas < 0 || o.wait_budget < 1) {
+        o.lin_max_iter < 1 || !(o.sor_rho_max > 0.0) || o.team_ctas < 0 || o.wait_budget < 1 || o.wave_teams < -1 ||
+        o.wave_teams > 64) {
         delete ctx;
         return PIT_EINVAL;
     }
@@ -355,6 +372,59 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
         if ((long long)per_sm * ctx->num_sms < ctx->G)
             return fail(ctx, PIT_EUNSUPPORTED, "team of %d CTAs cannot be co-resident (%d per SM x %d SMs)", ctx->G,
                         per_sm, ctx->num_sms);
+        // wavefront teams: K teams of Gw CTAs, one CTA per SM, level strips in shared memory
+        if (o.wave_teams >= 0) {
+            cudaFuncAttributes fa;
+            CK(cudaFuncGetAttributes(&fa, wave_kernel<kNT, true, false>));
+            const size_t dyn_max = ctx->smem_optin - fa.sharedSizeBytes;
+            int K = o.wave_teams == 0 ? 4 : o.wave_teams;
+            K = std::max(1, std::min(K, std::max(1, o.newton_max)));
+            const int rows_min = (kMinLocal + nx - 1) / nx;
+            for (; K >= 1; --K) {
+                int Gw = std::min(ctx->num_sms / K, (ny + rows_min - 1) / rows_min);
+                if (o.team_ctas > 0) Gw = std::min(Gw, o.team_ctas);
+                Gw = std::max(1, std::min(Gw, ny));
+                const int rows = (ny + Gw - 1) / Gw;
+                Gw = (ny + rows - 1) / rows;
+                const size_t bytes = sizeof(double) * wave_smem_doubles(rows * nx, nx);
+                if (bytes <= dyn_max && K * Gw <= ctx->num_sms) {
+                    ctx->K = K;
+                    ctx->Gw = Gw;
+                    ctx->w_rows_base = ny / Gw;
+                    ctx->w_rows_rem = ny % Gw;
+                    ctx->wave_smem = bytes;
+                    break;
+                }
+            }
+            if (ctx->K > 0) {
+                const void* kernels[4] = {reinterpret_cast<const void*>(wave_kernel<kNT, false, false>),
+                                          reinterpret_cast<const void*>(wave_kernel<kNT, false, true>),
+                                          reinterpret_cast<const void*>(wave_kernel<kNT, true, false>),
+                                          reinterpret_cast<const void*>(wave_kernel<kNT, true, true>)};
+                for (const void* kf : kernels)
+                    CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->wave_smem));
+                int per = 0;
+                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, wave_kernel<kNT, true, true>, kNT,
+                                                                 ctx->wave_smem));
+                if ((long long)per * ctx->num_sms < (long long)ctx->K * ctx->Gw) ctx->K = 0;  // fall back
+            }
+            if (ctx->K > 0) {
+                const int K = ctx->K, Gw = ctx->Gw;
+                ctx->kcap = std::max(1, o.newton_max);
+                CK(dalloc(&ctx->w_pub, (size_t)K * 2 * Gw * 2 * nx));
+                CK(dalloc(&ctx->w_red, (size_t)K * 4 * Gw * 4));
+                CK(dalloc(&ctx->w_sync, (size_t)K * Gw * 2 + (size_t)K * 4));
+                CK(dalloc(&ctx->w_ints, 4));
+                CK(dalloc(&ctx->w_res, (size_t)ctx->kcap));
+                CK(dalloc(&ctx->w_cell, (size_t)ctx->kcap * M));
+                CK(dalloc(&ctx->w_sumsq, (size_t)ctx->kcap * Gw));
+                CK(dalloc(&ctx->w_timers, (size_t)K * 4));
+                ctx->h_wres.assign(ctx->kcap, 0.0);
+                ctx->h_wcell.assign((size_t)ctx->kcap * M, 0);
+                ctx->h_wsumsq.assign((size_t)ctx->kcap * Gw, 0.0);
+                ctx->h_wtimers.assign((size_t)K * 4, 0);
+            }
+        }
         CK(dalloc(&ctx->u0, ctx->Ns));
         CK(cudaMemsetAsync(ctx->u0, 0, sizeof(double) * ctx->Ns, ctx->stream));
         CK(dalloc(&ctx->R, ctx->DOF));
@@ -399,6 +469,14 @@ extern "C" void pit_destroy(pit_ctx* ctx) {
     cudaFree(ctx->ints);
     cudaFree(ctx->cta_sumsq);
     cudaFree(ctx->timers);
+    cudaFree(ctx->w_pub);
+    cudaFree(ctx->w_red);
+    cudaFree(ctx->w_sync);
+    cudaFree(ctx->w_ints);
+    cudaFree(ctx->w_res);
+    cudaFree(ctx->w_cell);
+    cudaFree(ctx->w_sumsq);
+    cudaFree(ctx->w_timers);
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
     delete ctx;
@@ -484,9 +562,164 @@ extern "C" pit_status pit_newton_step(pit_ctx* ctx, double* U_dev, pit_step_info
     return newton_update(ctx, U_dev, res, info);
 }
 
+// One wavefront launch running Newton iterations k_begin <= k < k_end on U. Fills
+// info->steps[k] and res_inf[k] for the iterations that completed; *k_done receives
+// one past the last completed iteration, *stopped whether a converged iteration
+// raised the stop flag.
+static pit_status run_wave(pit_ctx* ctx, double* U, int k_begin, int k_end, pit_solve_info* inf, int* k_done,
+                           bool* stopped) {
+    const int K = ctx->K, Gw = ctx->Gw, M = ctx->M;
+    const size_t nsync = (size_t)K * Gw * 2 + (size_t)K * 4;
+    CK(cudaMemsetAsync(ctx->w_sync, 0, sizeof(unsigned long long) * nsync, ctx->stream));
+    CK(cudaMemsetAsync(ctx->w_ints, 0, sizeof(int) * 3, ctx->stream));
+    CK(cudaMemsetAsync(ctx->w_ints + 3, 0x7f, sizeof(int), ctx->stream));  // stop[1] = first converged k: large
+    CK(cudaMemsetAsync(ctx->w_cell, 0, sizeof(int) * (size_t)ctx->kcap * M, ctx->stream));
+    CK(cudaMemsetAsync(ctx->w_timers, 0, sizeof(unsigned long long) * K * 4, ctx->stream));
+    WaveArgs a{};
+    a.c = ctx->oc;
+    a.u0 = ctx->u0;
+    a.bc = ctx->has_bc ? ctx->bc : nullptr;
+    a.q = ctx->has_q ? ctx->q : nullptr;
+    a.U = U;
+    a.K = K;
+    a.G = Gw;
+    a.rows_base = ctx->w_rows_base;
+    a.rows_rem = ctx->w_rows_rem;
+    a.k_begin = k_begin;
+    a.k_end = k_end;
+    a.tol_res = ctx->opt.tol_res;
+    a.eta_max = ctx->opt.eta_max;
+    a.eta_gamma = ctx->opt.eta_gamma;
+    a.atol = ctx->opt.lin_atol;
+    a.sor_rho_max = ctx->opt.sor_rho_max;
+    a.method = ctx->opt.lin_solver;
+    a.max_iter = ctx->opt.lin_max_iter;
+    a.wait_budget = ctx->opt.wait_budget;
+    a.pub = ctx->w_pub;
+    a.red_part = ctx->w_red;
+    a.flags = ctx->w_sync;
+    a.prog = ctx->w_sync + (size_t)K * Gw;
+    a.red_cnt = ctx->w_sync + (size_t)K * Gw * 2;
+    a.abort_flag = ctx->w_ints;
+    a.status = ctx->w_ints + 1;
+    a.stop = ctx->w_ints + 2;
+    a.res_inf = ctx->w_res;
+    a.cell_iters = ctx->w_cell;
+    a.cta_sumsq = ctx->w_sumsq;
+    a.timers = ctx->w_timers;
+    void* args[] = {&a};
+    const void* kf = ctx->conv ? (ctx->nlv ? reinterpret_cast<const void*>(wave_kernel<kNT, true, true>)
+                                           : reinterpret_cast<const void*>(wave_kernel<kNT, true, false>))
+                               : (ctx->nlv ? reinterpret_cast<const void*>(wave_kernel<kNT, false, true>)
+                                           : reinterpret_cast<const void*>(wave_kernel<kNT, false, false>));
+    CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+    CK(cudaLaunchCooperativeKernel(kf, dim3(K * Gw), dim3(kNT), args, ctx->wave_smem, ctx->stream));
+    CK(cudaEventRecord(ctx->ev[3], ctx->stream));
+    int hi[4];
+    CK(cudaMemcpyAsync(hi, ctx->w_ints, sizeof(hi), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_wres.data(), ctx->w_res, sizeof(double) * ctx->kcap, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_wcell.data(), ctx->w_cell, sizeof(int) * (size_t)ctx->kcap * M, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_wsumsq.data(), ctx->w_sumsq, sizeof(double) * (size_t)ctx->kcap * Gw,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_wtimers.data(), ctx->w_timers, sizeof(unsigned long long) * K * 4,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]));
+    inf->ms_wave += ms;
+    inf->wave_launches += 1;
+    inf->us_pred_wait += (float)(ctx->h_wtimers[2] * 1e-3);
+    inf->us_halo_wait += (float)(ctx->h_wtimers[0] * 1e-3);
+    inf->us_reduce_wait += (float)(ctx->h_wtimers[1] * 1e-3);
+    *stopped = hi[2] != 0 && hi[3] < k_end;
+    // completed iterations: every level of iteration k ran (cell statistics all set)
+    int done = k_begin;
+    for (int k = k_begin; k < k_end; ++k) {
+        bool full = true;
+        for (int n = 0; n < M && full; ++n) full = ctx->h_wcell[(size_t)k * M + n] != 0;
+        if (!full) break;
+        done = k + 1;
+        pit_step_info& st = inf->steps[k];
+        std::memset(&st, 0, sizeof(st));
+        st.res_inf = ctx->h_wres[k];
+        inf->res_inf[k] = ctx->h_wres[k];
+        long long tot = 0;
+        int mx = 0, nsor = 0;
+        for (int n = 0; n < M; ++n) {
+            const int c = ctx->h_wcell[(size_t)k * M + n];
+            const int it = (c < 0 ? -c : c) - 1;
+            tot += it;
+            mx = std::max(mx, it);
+            nsor += c > 0;
+        }
+        double ss = 0.0;
+        for (int b = 0; b < Gw; ++b) ss += ctx->h_wsumsq[(size_t)k * Gw + b];
+        st.upd_rms = std::sqrt(ss / (double)ctx->DOF);
+        st.lin_iters_mean = (double)tot / M;
+        st.lin_iters_max = mx;
+        st.levels_sor = nsor;
+        if (*stopped && k >= hi[3]) break;
+    }
+    *k_done = done;
+    const int status = hi[1];
+    if (status == ST_ETIMEOUT) return fail(ctx, PIT_ETIMEOUT, "wavefront kernel: a device wait ran out of budget");
+    if (status == ST_EDIVERGED) return fail(ctx, PIT_EDIVERGED, "wavefront kernel: NaN/Inf in a residual or solve");
+    return PIT_OK;  // a capped level solve (ST_ENOCONV) is not fatal: Newton continues
+}
+
+static pit_status solve_wave(pit_ctx* ctx, double* U_dev, pit_solve_info* inf) {
+    inf->wave_teams = ctx->K;
+    inf->wave_team_ctas = ctx->Gw;
+    int k = 0;
+    pit_status st = PIT_OK;
+    for (;;) {
+        int k_done = k;
+        bool stopped = false;
+        if (k < ctx->opt.newton_max) {
+            st = run_wave(ctx, U_dev, k, ctx->opt.newton_max, inf, &k_done, &stopped);
+            if (st != PIT_OK) return st;
+        }
+        // the residual of the final iterate decides convergence
+        CHECK_RET(enqueue_residual(ctx, U_dev, ctx->R));
+        double res = 0.0;
+        CHECK_RET(read_res_inf(ctx, &res));
+        inf->newton_iters = k_done;
+        inf->res_inf[k_done] = res;
+        if (!std::isfinite(res)) return fail(ctx, PIT_EDIVERGED, "pit_solve: final residual is not finite");
+        if (res <= ctx->opt.tol_res) {
+            inf->converged = 1;
+            return PIT_OK;
+        }
+        if (k_done >= ctx->opt.newton_max || k_done == k)
+            return fail(ctx, PIT_ENOCONV, "pit_solve: ||R||_inf = %.3e > %.3e after %d Newton updates", res,
+                        ctx->opt.tol_res, k_done);
+        k = k_done;  // continue Newton from the current iterate
+    }
+}
+
 extern "C" pit_status pit_solve(pit_ctx* ctx, double* U_dev, pit_solve_info* info) {
     if (!ctx) return PIT_EINVAL;
     if (!U_dev) return fail(ctx, PIT_EINVAL, "pit_solve: U is NULL");
+    if (ctx->K > 0) {
+        pit_solve_info local;
+        pit_solve_info* inf = info ? info : &local;
+        std::memset(inf, 0, sizeof(*inf));
+        cudaEvent_t t0 = nullptr, t1 = nullptr;
+        CK(cudaEventCreate(&t0));
+        CK(cudaEventCreate(&t1));
+        CK(cudaEventRecord(t0, ctx->stream));
+        pit_status st = solve_wave(ctx, U_dev, inf);
+        CK(cudaEventRecord(t1, ctx->stream));
+        CK(cudaEventSynchronize(t1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, t0, t1));
+        inf->ms_total = ms;
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        return st;
+    }
     pit_solve_info local;
     pit_solve_info* inf = info ? info : &local;
     std::memset(inf, 0, sizeof(*inf));

@@ -264,66 +264,73 @@ static __global__ void plain_guess_kernel(const double* __restrict__ u0, double*
 
 // ------------------------------------------------------ (a3) the level chain
 
-struct ChainArgs {
-    int nx, ny, M;
-    int G;                                  // CTAs per level (team size), = gridDim.x
-    int rows_base, rows_rem;                // CTA b owns rows_base + (b < rows_rem) rows
-    const double* R;                        // [M][Ns] right-hand sides r^n
-    const double* coef;                     // [5][M][Ns] scaled planes 1/C, W/C, E/C, S/C, N/C
-    const unsigned long long* rho_key;      // [M] Gershgorin bound per level
-    double* U;                              // [M][Ns] iterate, += dU when update_U
-    double* dU;                             // [M][Ns] receives dU, or nullptr
-    int update_U;
-    int method;                             // 0 auto, 1 SOR, 2 BiCGStab
-    double sor_rho_max;
-    double eta;                             // relative tolerance of every level solve
-    double sor_tol_abs;                     // > 0: absolute SOR tolerance instead of eta*||b||_inf
-    double atol;                            // absolute floor of the tolerance
-    int max_iter;                           // cap per level
-    long long wait_budget;
-    // team communication (zeroed before each launch by the host)
-    double* pub;                            // [2][G][2][nx] published boundary rows
-    unsigned long long* flags;              // [G] publication counters
-    double* red_part;                       // [4][G][4] reduction partials
-    unsigned long long* red_cnt;            // [4] arrival counters
-    int* abort_flag;
-    int* status;
-    // statistics
-    int* level_iters;                       // [M] sweeps / iterations of each level
-    int* level_method;                      // [M] 1 = SOR, 2 = BiCGStab
-    double* cta_sumsq;                      // [G] sum of dU^2 over the CTA's rows, all levels
-    unsigned long long* timers;             // [4] CTA 0: ns waiting on halos, on reductions, total
-};
-
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
     return t;
 }
 
-// Per-CTA state of the team protocol.
+// Control words shared by every CTA of a launch that uses the team protocol.
+struct TeamCtl {
+    int* abort_flag;        // raised by the first CTA that gives up; every wait watches it
+    int* status;            // first error code (ST_*)
+    long long wait_budget;  // spin iterations before a wait gives up
+    int max_iter;           // cap on sweeps / iterations per level solve
+};
+
+// Per-CTA state of the team protocol: a team of G CTAs shares one level as row
+// strips; CTA b owns rows [r0, r0 + nrows). The team's workspace:
+//   pub      [2][G][2][nx] published first/last rows (double-buffered by sequence)
+//   flags    [G]           publication counters
+//   red_part [4][G][4]     reduction partials (4 slots in rotation)
+//   red_cnt  [4]           arrival counters of the slots
 struct Team {
     int b, G, nx;
     int r0, nrows, nloc;
+    long long Ns;
+    double* pub;
+    unsigned long long* flags;
+    double* red_part;
+    unsigned long long* red_cnt;
     unsigned long long pub_seq;   // publications so far by this CTA
     unsigned long long red_seq;   // reductions started so far
-    unsigned long long t_halo;    // ns spent waiting for neighbours (thread 0 of CTA 0)
-    unsigned long long t_red;     // ns spent waiting for team reductions (thread 0 of CTA 0)
+    unsigned long long t_halo;    // ns spent waiting for neighbours (thread 0)
+    unsigned long long t_red;     // ns spent waiting for team reductions (thread 0)
 };
 
+__device__ __forceinline__ void team_init(Team& t, int b, int G, int nx, int ny, int rows_base, int rows_rem,
+                                          double* pub, unsigned long long* flags, double* red_part,
+                                          unsigned long long* red_cnt) {
+    t.b = b;
+    t.G = G;
+    t.nx = nx;
+    t.nrows = rows_base + (b < rows_rem ? 1 : 0);
+    t.r0 = b * rows_base + (b < rows_rem ? b : rows_rem);
+    t.nloc = t.nrows * nx;
+    t.Ns = (long long)nx * ny;
+    t.pub = pub;
+    t.flags = flags;
+    t.red_part = red_part;
+    t.red_cnt = red_cnt;
+    t.pub_seq = 0;
+    t.red_seq = 0;
+    t.t_halo = 0;
+    t.t_red = 0;
+}
+
 // Give up on a wait: record the status once and raise the abort flag.
-__device__ __forceinline__ void team_fail(const ChainArgs& a, int code) {
-    atomicCAS(a.status, 0, code);
-    atomicExch(a.abort_flag, 1);
+__device__ __forceinline__ void team_fail(const TeamCtl& c, int code) {
+    atomicCAS(c.status, 0, code);
+    atomicExch(c.abort_flag, 1);
 }
 
 // Spin (one thread) until *p >= target, the abort flag is raised, or the budget is spent.
-__device__ __forceinline__ bool wait_geq(const ChainArgs& a, const unsigned long long* p, unsigned long long target) {
+__device__ __forceinline__ bool wait_geq(const TeamCtl& c, const unsigned long long* p, unsigned long long target) {
     long long spins = 0;
     while (ld_acquire_u64(p) < target) {
-        if (ld_acquire_s32(a.abort_flag)) return false;
-        if (++spins > a.wait_budget) {
-            team_fail(a, ST_ETIMEOUT);
+        if (ld_acquire_s32(c.abort_flag)) return false;
+        if (++spins > c.wait_budget) {
+            team_fail(c, ST_ETIMEOUT);
             return false;
         }
         if (spins > 4096) __nanosleep(64);
@@ -334,13 +341,13 @@ __device__ __forceinline__ bool wait_geq(const ChainArgs& a, const unsigned long
 // Publish the first and last local rows of v for the neighbours; then fetch the
 // neighbours' rows published at the same step into haloS (row r0-1) and haloN
 // (row r0+nrows). Rows outside the domain are zero (the correction vanishes on
-// the Dirichlet boundary). Returns false when the team aborted.
+// the Dirichlet boundary). Returns false when the launch aborted.
 template <int NT>
-__device__ bool exchange_halo(const ChainArgs& a, Team& t, const double* v, double* haloS, double* haloN,
+__device__ bool exchange_halo(const TeamCtl& c, Team& t, const double* v, double* haloS, double* haloN,
                               int* s_ok) {
     const int nx = t.nx;
     const unsigned long long seq = ++t.pub_seq;
-    double* mine = a.pub + ((size_t)(seq & 1) * t.G + t.b) * 2 * nx;
+    double* mine = t.pub + ((size_t)(seq & 1) * t.G + t.b) * 2 * nx;
     for (int i = threadIdx.x; i < nx; i += NT) {
         __stcg(mine + i, v[i]);
         __stcg(mine + nx + i, v[(t.nrows - 1) * nx + i]);
@@ -348,18 +355,18 @@ __device__ bool exchange_halo(const ChainArgs& a, Team& t, const double* v, doub
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        st_release_u64(a.flags + t.b, seq);
+        st_release_u64(t.flags + t.b, seq);
         const unsigned long long t0 = global_ns();
         bool ok = true;
-        if (t.b > 0) ok = wait_geq(a, a.flags + t.b - 1, seq);
-        if (ok && t.b + 1 < t.G) ok = wait_geq(a, a.flags + t.b + 1, seq);
+        if (t.b > 0) ok = wait_geq(c, t.flags + t.b - 1, seq);
+        if (ok && t.b + 1 < t.G) ok = wait_geq(c, t.flags + t.b + 1, seq);
         __threadfence();
         *s_ok = ok ? 1 : 0;
         t.t_halo += global_ns() - t0;
     }
     __syncthreads();
     if (!*s_ok) return false;
-    const double* par = a.pub + (size_t)(seq & 1) * t.G * 2 * nx;
+    const double* par = t.pub + (size_t)(seq & 1) * t.G * 2 * nx;
     if (t.b > 0) {  // neighbour below: its last row
         const double* lo = par + (size_t)(t.b - 1) * 2 * nx + nx;
         for (int i = threadIdx.x; i < nx; i += NT) haloS[i] = __ldcg(lo + i);
@@ -377,17 +384,17 @@ __device__ bool exchange_halo(const ChainArgs& a, Team& t, const double* v, doub
 }
 
 // Start a team reduction of K <= 4 values (this CTA's partials already block-reduced
-// into vals). Deterministic: every CTA later sums the G partials in CTA order.
+// into vals). Deterministic: every CTA later combines the G partials in CTA order.
 template <int K>
-__device__ __forceinline__ unsigned long long reduce_arrive(const ChainArgs& a, Team& t, const double (&vals)[K]) {
+__device__ __forceinline__ unsigned long long reduce_arrive(Team& t, const double (&vals)[K]) {
     const unsigned long long use = t.red_seq++;
     const int slot = (int)(use & 3);
     if (threadIdx.x == 0) {
-        double* part = a.red_part + ((size_t)slot * t.G + t.b) * 4;
+        double* part = t.red_part + ((size_t)slot * t.G + t.b) * 4;
 #pragma unroll
         for (int k = 0; k < K; ++k) __stcg(part + k, vals[k]);
         __threadfence();
-        atomicAdd(a.red_cnt + slot, 1ull);
+        atomicAdd(t.red_cnt + slot, 1ull);
     }
     return use;
 }
@@ -397,13 +404,13 @@ __device__ __forceinline__ unsigned long long reduce_arrive(const ChainArgs& a, 
 // their max when MAXOP. Every CTA performs the identical sequence of operations, so
 // all CTAs obtain the same value. Result is broadcast to every thread.
 template <int K, bool MAXOP>
-__device__ __forceinline__ bool reduce_finish(const ChainArgs& a, Team& t, unsigned long long use, double (&out)[K],
+__device__ __forceinline__ bool reduce_finish(const TeamCtl& c, Team& t, unsigned long long use, double (&out)[K],
                                               double* s_bcast, int* s_ok) {
     const int slot = (int)(use & 3);
     if (threadIdx.x == 0) {
         const unsigned long long target = (unsigned long long)t.G * ((use >> 2) + 1);
         const unsigned long long t0 = global_ns();
-        *s_ok = wait_geq(a, a.red_cnt + slot, target) ? 1 : 0;
+        *s_ok = wait_geq(c, t.red_cnt + slot, target) ? 1 : 0;
         __threadfence();
         t.t_red += global_ns() - t0;
     }
@@ -411,7 +418,7 @@ __device__ __forceinline__ bool reduce_finish(const ChainArgs& a, Team& t, unsig
     const bool ok = *s_ok != 0;
     if (ok && threadIdx.x < 32) {
         const int lane = threadIdx.x;
-        const double* part = a.red_part + (size_t)slot * t.G * 4;
+        const double* part = t.red_part + (size_t)slot * t.G * 4;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             double s = 0.0;
@@ -436,13 +443,33 @@ __device__ __forceinline__ bool reduce_finish(const ChainArgs& a, Team& t, unsig
     return ok;
 }
 
-// Shared-memory layout of one CTA (nloc = rows x nx doubles per array).
+// Shared-memory arrays of one CTA (cap doubles each, cap = largest rows x nx).
 struct Smem {
     double *cw, *ce, *cs, *cn, *bs, *x;      // scaled couplings, scaled rhs, iterate
-    double *r, *rh, *p, *v, *s, *t;          // BiCGStab vectors
+    double *r, *rh, *p, *v, *t;              // BiCGStab vectors (s shares r)
     double *haloS, *haloN;                   // neighbour rows of the exchanged vector
-    double *red;                             // block-reduction scratch
+    double *red;                             // 64 doubles: block reductions [0,32), broadcast [32,48), flags [48,64)
 };
+
+// Carve the layout: cw ce cs cn bs x r rh p v t | haloS haloN | red.
+__device__ __forceinline__ Smem smem_layout(double* base, int cap, int nx) {
+    Smem m;
+    m.cw = base;
+    m.ce = base + cap;
+    m.cs = base + 2 * cap;
+    m.cn = base + 3 * cap;
+    m.bs = base + 4 * cap;
+    m.x = base + 5 * cap;
+    m.r = base + 6 * cap;
+    m.rh = base + 7 * cap;
+    m.p = base + 8 * cap;
+    m.v = base + 9 * cap;
+    m.t = base + 10 * cap;
+    m.haloS = base + 11 * cap;
+    m.haloN = m.haloS + nx;
+    m.red = m.haloN + nx;
+    return m;
+}
 
 // y = (D^{-1} A) v on the local rows (unit diagonal), halos of v in haloS/haloN.
 template <int NT>
@@ -466,7 +493,7 @@ __device__ __forceinline__ void local_spmv(const Team& t, const Smem& m, const d
 // (every lane of a warp does useful FP64 work). Scalar decisions are taken by
 // thread 0 and broadcast. Returns the sweep count (< 0 on abort).
 template <int NT>
-__device__ int level_sor(const ChainArgs& a, Team& t, const Smem& m, double omega, double tol, int* s_ok) {
+__device__ int level_sor(const TeamCtl& c, Team& t, const Smem& m, double omega, double tol, int* s_ok) {
     const int nx = t.nx;
     const int half = (nx + 1) >> 1;            // points of one colour per row, at most
     const int npts = t.nrows * half;
@@ -477,7 +504,7 @@ __device__ int level_sor(const ChainArgs& a, Team& t, const Smem& m, double omeg
     for (int sweep = 1;; ++sweep) {
         double dmax = 0.0;
         for (int color = 0; color < 2; ++color) {
-            if (!exchange_halo<NT>(a, t, m.x, m.haloS, m.haloN, s_ok)) return -1;
+            if (!exchange_halo<NT>(c, t, m.x, m.haloS, m.haloN, s_ok)) return -1;
             for (int q = threadIdx.x; q < npts; q += NT) {
                 const int jl = q / half;
                 const int i = ((t.r0 + jl + color) & 1) + 2 * (q - jl * half);
@@ -502,10 +529,10 @@ __device__ int level_sor(const ChainArgs& a, Team& t, const Smem& m, double omeg
             unsigned long long key = block_max_u64<NT>(abs_key(dmax), reinterpret_cast<unsigned long long*>(m.red));
             v[0] = key_val(key);
         }
-        const unsigned long long use = reduce_arrive<1>(a, t, v);
+        const unsigned long long use = reduce_arrive<1>(t, v);
         if (have_pending) {
             double g[1];
-            if (!reduce_finish<1, true>(a, t, pending, g, m.red + 32, s_ok)) return -1;
+            if (!reduce_finish<1, true>(c, t, pending, g, m.red + 32, s_ok)) return -1;
             if (threadIdx.x == 0) {
                 const double d = g[0];
                 int decision = 0;  // 0 continue, 1 converged / capped, 2 NaN
@@ -517,7 +544,7 @@ __device__ int level_sor(const ChainArgs& a, Team& t, const Smem& m, double omeg
                     double rho = omega - 1.0;
                     if (prev2 > 0.0) rho = fmax(rho, prev / prev2);
                     if (prev == 0.0 || (prev2 > 0.0 && rho < 1.0 && prev * rho <= tol * (1.0 - rho)) ||
-                        sweep >= a.max_iter)
+                        sweep >= c.max_iter)
                         decision = 1;
                 }
                 *s_flag = decision;
@@ -526,10 +553,10 @@ __device__ int level_sor(const ChainArgs& a, Team& t, const Smem& m, double omeg
             const int decision = *s_flag;
             __syncthreads();
             if (decision) {
-                if (decision == 2 && threadIdx.x == 0) atomicCAS(a.status, 0, ST_EDIVERGED);
+                if (decision == 2 && threadIdx.x == 0) atomicCAS(c.status, 0, ST_EDIVERGED);
                 // consume the outstanding reduction so the sequence stays aligned
                 double h[1];
-                if (!reduce_finish<1, true>(a, t, use, h, m.red + 32, s_ok)) return -1;
+                if (!reduce_finish<1, true>(c, t, use, h, m.red + 32, s_ok)) return -1;
                 return sweep;
             }
         }
@@ -548,10 +575,11 @@ __device__ __forceinline__ double bcast0(double v, double* slot) {
 }
 
 // Jacobi-preconditioned BiCGStab (van der Vorst 1992) on the scaled level system,
-// from x = 0. Stops when ||r||_2 <= max(eta ||bs||_2, atol sqrt(Ns)). Scalars are
-// formed by thread 0 and broadcast (FP64 division is costly on this part).
+// from x = 0; s shares storage with r. Stops when ||r||_2 <= max(eta ||bs||_2,
+// atol sqrt(Ns)). Scalars are formed by thread 0 and broadcast (FP64 division is
+// costly on this part). Returns the iteration count (< 0 on abort).
 template <int NT>
-__device__ int level_bicgstab(const ChainArgs& a, Team& t, const Smem& m, double eta, double atol, int* s_ok) {
+__device__ int level_bicgstab(const TeamCtl& c, Team& t, const Smem& m, double eta, double atol, int* s_ok) {
     double* sb = m.red + 32;
     double* slot = m.red + 48;
     const int nloc = t.nloc;
@@ -568,24 +596,24 @@ __device__ int level_bicgstab(const ChainArgs& a, Team& t, const Smem& m, double
     }
     block_sum<NT, 1>(one, m.red);
     double g1[1];
-    if (!reduce_finish<1, false>(a, t, reduce_arrive<1>(a, t, one), g1, sb, s_ok)) return -1;
+    if (!reduce_finish<1, false>(c, t, reduce_arrive<1>(t, one), g1, sb, s_ok)) return -1;
     // thread 0 keeps the recurrence scalars; others receive what they need
     double tol = 0.0, rho_old = 1.0, alpha = 1.0, omega = 1.0, rho = g1[0];
-    if (threadIdx.x == 0) tol = fmax(eta * sqrt(g1[0]), atol * sqrt((double)t.nx * (double)a.ny));
+    if (threadIdx.x == 0) tol = fmax(eta * sqrt(g1[0]), atol * sqrt((double)t.Ns));
     if (bcast0(threadIdx.x == 0 ? (sqrt(g1[0]) <= tol ? 1.0 : 0.0) : 0.0, slot) != 0.0) return 0;
-    for (int it = 1; it <= a.max_iter; ++it) {
+    for (int it = 1; it <= c.max_iter; ++it) {
         double beta = 0.0;
         if (threadIdx.x == 0) beta = (rho / rho_old) * (alpha / omega);
         beta = bcast0(beta, slot);
         const double om_b = bcast0(omega, slot);
         for (int k = threadIdx.x; k < nloc; k += NT) m.p[k] = m.r[k] + beta * (m.p[k] - om_b * m.v[k]);
         __syncthreads();
-        if (!exchange_halo<NT>(a, t, m.p, m.haloS, m.haloN, s_ok)) return -1;
+        if (!exchange_halo<NT>(c, t, m.p, m.haloS, m.haloN, s_ok)) return -1;
         local_spmv<NT>(t, m, m.p, m.v);
         double d1[1] = {0.0};
         for (int k = threadIdx.x; k < nloc; k += NT) d1[0] += m.rh[k] * m.v[k];
         block_sum<NT, 1>(d1, m.red);
-        if (!reduce_finish<1, false>(a, t, reduce_arrive<1>(a, t, d1), d1, sb, s_ok)) return -1;
+        if (!reduce_finish<1, false>(c, t, reduce_arrive<1>(t, d1), d1, sb, s_ok)) return -1;
         // code: 0 go on, 1 NaN, 2 breakdown
         double code = 0.0;
         if (threadIdx.x == 0) {
@@ -595,33 +623,34 @@ __device__ int level_bicgstab(const ChainArgs& a, Team& t, const Smem& m, double
         }
         code = bcast0(code, slot);
         if (code != 0.0) {
-            if (threadIdx.x == 0) atomicCAS(a.status, 0, code == 1.0 ? ST_EDIVERGED : ST_ENOCONV);
+            if (threadIdx.x == 0) atomicCAS(c.status, 0, code == 1.0 ? ST_EDIVERGED : ST_ENOCONV);
             return it;
         }
         const double al_b = bcast0(alpha, slot);
-        for (int k = threadIdx.x; k < nloc; k += NT) m.s[k] = m.r[k] - al_b * m.v[k];
+        for (int k = threadIdx.x; k < nloc; k += NT) m.r[k] -= al_b * m.v[k];  // r holds s
         __syncthreads();
-        if (!exchange_halo<NT>(a, t, m.s, m.haloS, m.haloN, s_ok)) return -1;
-        local_spmv<NT>(t, m, m.s, m.t);
+        if (!exchange_halo<NT>(c, t, m.r, m.haloS, m.haloN, s_ok)) return -1;
+        local_spmv<NT>(t, m, m.r, m.t);
         double d2[2] = {0.0, 0.0};
         for (int k = threadIdx.x; k < nloc; k += NT) {
-            d2[0] += m.t[k] * m.s[k];
+            d2[0] += m.t[k] * m.r[k];
             d2[1] += m.t[k] * m.t[k];
         }
         block_sum<NT, 2>(d2, m.red);
-        if (!reduce_finish<2, false>(a, t, reduce_arrive<2>(a, t, d2), d2, sb, s_ok)) return -1;
+        if (!reduce_finish<2, false>(c, t, reduce_arrive<2>(t, d2), d2, sb, s_ok)) return -1;
         if (threadIdx.x == 0) omega = d2[1] > 0.0 ? d2[0] / d2[1] : 0.0;
         const double om2 = bcast0(omega, slot);
         double d3[2] = {0.0, 0.0};
         for (int k = threadIdx.x; k < nloc; k += NT) {
-            m.x[k] += al_b * m.p[k] + om2 * m.s[k];
-            const double rk = m.s[k] - om2 * m.t[k];
+            const double sk = m.r[k];
+            m.x[k] += al_b * m.p[k] + om2 * sk;
+            const double rk = sk - om2 * m.t[k];
             m.r[k] = rk;
             d3[0] += m.rh[k] * rk;
             d3[1] += rk * rk;
         }
         block_sum<NT, 2>(d3, m.red);
-        if (!reduce_finish<2, false>(a, t, reduce_arrive<2>(a, t, d3), d3, sb, s_ok)) return -1;
+        if (!reduce_finish<2, false>(c, t, reduce_arrive<2>(t, d3), d3, sb, s_ok)) return -1;
         // code: 0 go on, 1 NaN, 2 breakdown, 3 converged
         code = 0.0;
         if (threadIdx.x == 0) {
@@ -635,18 +664,70 @@ __device__ int level_bicgstab(const ChainArgs& a, Team& t, const Smem& m, double
         code = bcast0(code, slot);
         if (code == 3.0) return it;
         if (code != 0.0) {
-            if (threadIdx.x == 0) atomicCAS(a.status, 0, code == 1.0 ? ST_EDIVERGED : ST_ENOCONV);
+            if (threadIdx.x == 0) atomicCAS(c.status, 0, code == 1.0 ? ST_EDIVERGED : ST_ENOCONV);
             return it;
         }
     }
-    if (threadIdx.x == 0) atomicCAS(a.status, 0, ST_ENOCONV);
-    return a.max_iter;
+    if (threadIdx.x == 0) atomicCAS(c.status, 0, ST_ENOCONV);
+    return c.max_iter;
 }
 
-// Number of doubles of dynamic shared memory per CTA for nloc local unknowns.
-__host__ __device__ inline size_t chain_smem_doubles(int nloc, int nx) {
-    return (size_t)12 * nloc + 2 * (size_t)nx + 64;
+// Solve the scaled level system in m with the method chosen from the level's
+// Gershgorin bound rho_g; SOR's omega = 2/(1 + sqrt(1 - rho^2)) is formed by
+// thread 0. Returns iterations (< 0 on abort) and the method used (1 SOR, 2 BiCGStab).
+template <int NT>
+__device__ __forceinline__ int level_solve(const TeamCtl& c, Team& t, const Smem& m, int method, double sor_rho_max,
+                                           double rho_g, double sor_tol, double eta, double atol, int* s_ok,
+                                           int* used) {
+    const bool use_sor = method == 1 || (method == 0 && rho_g < sor_rho_max);
+    *used = use_sor ? 1 : 2;
+    if (use_sor) {
+        double omega = 1.0;
+        if (threadIdx.x == 0 && rho_g < 1.0) {
+            const double rc = fmin(rho_g, 0.999999);
+            omega = 2.0 / (1.0 + sqrt(1.0 - rc * rc));
+        }
+        omega = bcast0(omega, m.red + 48);
+        return level_sor<NT>(c, t, m, omega, sor_tol, s_ok);
+    }
+    return level_bicgstab<NT>(c, t, m, eta, atol, s_ok);
 }
+
+// Number of doubles of dynamic shared memory per CTA of chain_kernel.
+__host__ __device__ inline size_t chain_smem_doubles(int nloc, int nx) {
+    return (size_t)11 * nloc + 2 * (size_t)nx + 64;
+}
+
+struct ChainArgs {
+    int nx, ny, M;
+    int G;                                  // CTAs per level (team size), = gridDim.x
+    int rows_base, rows_rem;                // CTA b owns rows_base + (b < rows_rem) rows
+    const double* R;                        // [M][Ns] right-hand sides r^n
+    const double* coef;                     // [5][M][Ns] scaled planes (raw entries when RAW)
+    const unsigned long long* rho_key;      // [M] Gershgorin bound per level (unused when RAW)
+    double* U;                              // [M][Ns] iterate, += dU when update_U
+    double* dU;                             // [M][Ns] receives dU, or nullptr
+    int update_U;
+    int method;                             // 0 auto, 1 SOR, 2 BiCGStab
+    double sor_rho_max;
+    double eta;                             // relative tolerance of every level solve
+    double sor_tol_abs;                     // > 0: absolute SOR tolerance instead of eta*||b||_inf
+    double atol;                            // absolute floor of the tolerance
+    int max_iter;                           // cap per level
+    long long wait_budget;
+    // team communication (zeroed before each launch by the host)
+    double* pub;                            // [2][G][2][nx] published boundary rows
+    unsigned long long* flags;              // [G] publication counters
+    double* red_part;                       // [4][G][4] reduction partials
+    unsigned long long* red_cnt;            // [4] arrival counters
+    int* abort_flag;
+    int* status;
+    // statistics
+    int* level_iters;                       // [M] sweeps / iterations of each level
+    int* level_method;                      // [M] 1 = SOR, 2 = BiCGStab
+    double* cta_sumsq;                      // [G] sum of dU^2 over the CTA's rows, all levels
+    unsigned long long* timers;             // [4] CTA 0: ns waiting on halos, on reductions, total
+};
 
 // The chain: for n = 1..M, rhs = r^n + du^{n-1}; solve the level; U^n += du^n.
 // Must be launched cooperatively with gridDim.x = G (all CTAs co-resident).
@@ -658,39 +739,15 @@ template <int NT, bool RAW = false>
 __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
     extern __shared__ double smem[];
     __shared__ int s_ok;
+    TeamCtl c{a.abort_flag, a.status, a.wait_budget, a.max_iter};
     Team t;
-    t.b = blockIdx.x;
-    t.G = a.G;
-    t.nx = a.nx;
-    t.nrows = a.rows_base + (t.b < a.rows_rem ? 1 : 0);
-    t.r0 = t.b * a.rows_base + (t.b < a.rows_rem ? t.b : a.rows_rem);
-    t.nloc = t.nrows * a.nx;
-    t.pub_seq = 0;
-    t.red_seq = 0;
-    t.t_halo = 0;
-    t.t_red = 0;
+    team_init(t, blockIdx.x, a.G, a.nx, a.ny, a.rows_base, a.rows_rem, a.pub, a.flags, a.red_part, a.red_cnt);
     const unsigned long long t_start = global_ns();
     const int nloc = t.nloc;
     const int cap = (a.rows_base + (a.rows_rem ? 1 : 0)) * a.nx;  // largest nloc of the team
-    Smem m;
-    double* base = smem;
-    m.cw = base;
-    m.ce = base + cap;
-    m.cs = base + 2 * cap;
-    m.cn = base + 3 * cap;
-    m.bs = base + 4 * cap;
-    m.x = base + 5 * cap;
-    m.r = base + 6 * cap;
-    m.rh = base + 7 * cap;
-    m.p = base + 8 * cap;
-    m.v = base + 9 * cap;
-    m.s = base + 10 * cap;
-    m.t = base + 11 * cap;
-    m.haloS = base + 12 * cap;
-    m.haloN = m.haloS + a.nx;
-    m.red = m.haloN + a.nx;  // 64 doubles
+    const Smem m = smem_layout(smem, cap, a.nx);
 
-    const long long Ns = (long long)a.nx * a.ny;
+    const long long Ns = t.Ns;
     const long long plane = (long long)a.M * Ns;
     const long long off0 = (long long)t.r0 * a.nx;
     double sumsq = 0.0;
@@ -735,33 +792,23 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
             unsigned long long key = block_max_u64<NT>(abs_key(rs), reinterpret_cast<unsigned long long*>(m.red));
             double v[1] = {key_val(key)};
             double g[1];
-            if (!reduce_finish<1, true>(a, t, reduce_arrive<1>(a, t, v), g, m.red + 32, &s_ok)) return;
+            if (!reduce_finish<1, true>(c, t, reduce_arrive<1>(t, v), g, m.red + 32, &s_ok)) return;
             rho_g = g[0];
         }
-        const bool use_sor = a.method == 1 || (a.method == 0 && rho_g < a.sor_rho_max);
-        int iters;
-        if (use_sor) {
-            double tol_abs = a.sor_tol_abs;
-            if (!(tol_abs > 0.0)) {
-                // tolerance relative to the level's unscaled ||b||_inf (team max reduction)
-                double bl = 0.0;
-                for (int k = threadIdx.x; k < nloc; k += NT) bl = fmax(bl, fabs(m.x[k]));
-                unsigned long long key = block_max_u64<NT>(abs_key(bl), reinterpret_cast<unsigned long long*>(m.red));
-                double v[1] = {key_val(key)};
-                double g[1];
-                if (!reduce_finish<1, true>(a, t, reduce_arrive<1>(a, t, v), g, m.red + 32, &s_ok)) return;
-                tol_abs = fmax(a.eta * g[0], a.atol);
-            }
-            double omega = 1.0;
-            if (threadIdx.x == 0 && rho_g < 1.0) {
-                const double rc = fmin(rho_g, 0.999999);
-                omega = 2.0 / (1.0 + sqrt(1.0 - rc * rc));
-            }
-            omega = bcast0(omega, m.red + 48);
-            iters = level_sor<NT>(a, t, m, omega, tol_abs, &s_ok);
-        } else {
-            iters = level_bicgstab<NT>(a, t, m, a.eta, a.atol, &s_ok);
+        double sor_tol = a.sor_tol_abs;
+        const bool sor_here = a.method == 1 || (a.method == 0 && rho_g < a.sor_rho_max);
+        if (sor_here && !(sor_tol > 0.0)) {
+            // tolerance relative to the level's unscaled ||b||_inf (team max reduction)
+            double bl = 0.0;
+            for (int k = threadIdx.x; k < nloc; k += NT) bl = fmax(bl, fabs(m.x[k]));
+            unsigned long long key = block_max_u64<NT>(abs_key(bl), reinterpret_cast<unsigned long long*>(m.red));
+            double v[1] = {key_val(key)};
+            double g[1];
+            if (!reduce_finish<1, true>(c, t, reduce_arrive<1>(t, v), g, m.red + 32, &s_ok)) return;
+            sor_tol = fmax(a.eta * g[0], a.atol);
         }
+        int used = 0;
+        const int iters = level_solve<NT>(c, t, m, a.method, a.sor_rho_max, rho_g, sor_tol, a.eta, a.atol, &s_ok, &used);
         if (iters < 0) return;  // aborted
         // du^n = x: update the iterate and keep x as du^{n-1} of the next level
         for (int k = threadIdx.x; k < nloc; k += NT) {
@@ -772,7 +819,7 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
         }
         if (t.b == 0 && threadIdx.x == 0) {
             a.level_iters[n] = iters;
-            a.level_method[n] = use_sor ? 1 : 2;
+            a.level_method[n] = used;
             if (iters >= a.max_iter) atomicCAS(a.status, 0, ST_ENOCONV);
         }
         __syncthreads();
@@ -784,6 +831,246 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
         a.timers[0] = t.t_halo;
         a.timers[1] = t.t_red;
         a.timers[2] = global_ns() - t_start;
+    }
+}
+
+// --------------------------------------- the Newton wavefront (a1 + a2 + a3 + a4)
+
+// All Newton iterations of the all-at-once system in one cooperative launch.
+// K teams of G CTAs; team t runs iterations k = k_begin + t, k_begin + t + K, ...
+// Cell (k, n) -- Newton iteration k at level n -- needs u^n_k, final once cell
+// (k-1, n) has updated it, and du^{n-1}_k, which the same team produced one level
+// earlier and still holds in shared memory. So iteration k walks the levels right
+// behind iteration k - 1: up to K iterations are in flight, and the latency of
+// one level solve is overlapped with the others. Per cell, the team computes the
+// residual r^n_k (eq. 3-5) and the scaled Jacobian entries (eq. 5-6) of its rows
+// from u^n_k (global, own and halo rows) and u^{n-1}_k (shared memory), then
+// solves A_n du^n = r^n + du^{n-1} (eq. 7 nested) and updates U^n. The iterates are
+// those of plain Newton; the forcing term uses the running max of ||r^j_k||_inf
+// over the levels j <= n seen so far. When a team finishes an iteration whose
+// residual max is <= tol_res it raises the stop flag; every team reads the flag in
+// its level-start team reduction, so all CTAs of a team stop at the same cell.
+struct WaveArgs {
+    OpConst c;
+    const double* u0;
+    const double* bc;
+    const double* q;
+    double* U;
+    int K, G, rows_base, rows_rem;
+    int k_begin, k_end;                 // iterations k_begin <= k < k_end may run
+    double tol_res, eta_max, eta_gamma, atol, sor_rho_max;
+    int method;
+    int max_iter;
+    long long wait_budget;
+    // workspace, zeroed by the host before the launch (stop[1] set to INT_MAX)
+    double* pub;                        // [K][2][G][2][nx]
+    unsigned long long* flags;          // [K][G]
+    double* red_part;                   // [K][4][G][4]
+    unsigned long long* red_cnt;        // [K][4]
+    unsigned long long* prog;           // [K][G] cells completed: k * M + n + 1
+    int* abort_flag;
+    int* status;
+    int* stop;                          // [0] stop flag, [1] first converged iteration
+    // per iteration records, indexed by k
+    double* res_inf;                    // [k_end] ||R_k||_inf
+    int* cell_iters;                    // [k_end][M] 1 + sweeps (SOR) or -(1 + iterations) (BiCGStab); 0 = not run
+    double* cta_sumsq;                  // [k_end][G] sum of du_k^2 over the CTA's rows
+    unsigned long long* timers;         // [K][4] CTA 0 of each team: halo, reduction, predecessor waits, total
+};
+
+__host__ __device__ inline size_t wave_smem_doubles(int cap, int nx) {
+    return (size_t)12 * cap + 2 * (size_t)nx + 64;
+}
+
+template <int NT, bool CONV, bool NLV>
+__global__ void __launch_bounds__(NT) wave_kernel(WaveArgs a) {
+    extern __shared__ double smem[];
+    __shared__ int s_ok;
+    const OpConst& oc = a.c;
+    const int nx = oc.nx, ny = oc.ny, M = oc.M;
+    const int team = blockIdx.x / a.G;
+    const int b = blockIdx.x - team * a.G;
+    TeamCtl c{a.abort_flag, a.status, a.wait_budget, a.max_iter};
+    Team t;
+    team_init(t, b, a.G, nx, ny, a.rows_base, a.rows_rem, a.pub + (size_t)team * 2 * a.G * 2 * nx,
+              a.flags + (size_t)team * a.G, a.red_part + (size_t)team * 4 * a.G * 4, a.red_cnt + (size_t)team * 4);
+    const unsigned long long t_start = global_ns();
+    unsigned long long t_pred = 0;
+    const int nloc = t.nloc;
+    const int cap = (a.rows_base + (a.rows_rem ? 1 : 0)) * nx;
+    const Smem m = smem_layout(smem, cap, nx);
+    double* uprev = m.haloN + nx + 64;        // u^{n-1}_k, own rows (cap)
+    double* u = m.r;                          // u^n_k with one halo row each side: (nrows + 2) x nx, aliases r..t
+    const long long Ns = t.Ns;
+    const long long off0 = (long long)t.r0 * nx;
+    const int nb = 2 * nx + 2 * ny;
+    const int pred_team = (team + a.K - 1) % a.K;
+    unsigned long long* pred_prog = a.prog + (size_t)pred_team * a.G;
+    unsigned long long* my_prog = a.prog + (size_t)team * a.G;
+    double* slot = m.red + 48;
+    // Burgers-type closures with constant viscosity have a constant diagonal 1 + 2 mu_a (vx + vy)
+    const double dconst = 1.0 / (1.0 + 2.0 * oc.mu_a * (oc.vx + oc.vy));
+
+    for (int k = a.k_begin + team; k < a.k_end; k += a.K) {
+        for (int i = threadIdx.x; i < nloc; i += NT) {
+            m.x[i] = 0.0;               // du^{-1} = 0
+            uprev[i] = a.u0[off0 + i];  // u^0
+        }
+        double prefix = 0.0;            // running max of ||r^j_k||_inf, j <= n (thread 0)
+        double sumsq = 0.0;
+        __syncthreads();
+        for (int n = 0; n < M; ++n) {
+            // 1. wait until iteration k - 1 has finished level n on rows r0-1 .. r0+nrows
+            if (threadIdx.x == 0) {
+                bool stop_seen = false;
+                if (k > a.k_begin) {
+                    const unsigned long long target = (unsigned long long)(k - 1) * M + n + 1;
+                    const unsigned long long t0 = global_ns();
+                    for (int nbr = b - 1; nbr <= b + 1 && !stop_seen; ++nbr) {
+                        if (nbr < 0 || nbr >= a.G) continue;
+                        long long spins = 0;
+                        while (ld_acquire_u64(pred_prog + nbr) < target) {
+                            if (ld_acquire_s32(a.stop) || ld_acquire_s32(a.abort_flag)) {
+                                stop_seen = true;
+                                break;
+                            }
+                            if (++spins > a.wait_budget) {
+                                team_fail(c, ST_ETIMEOUT);
+                                stop_seen = true;
+                                break;
+                            }
+                            if (spins > 4096) __nanosleep(64);
+                        }
+                    }
+                    __threadfence();
+                    t_pred += global_ns() - t0;
+                }
+                s_ok = (stop_seen || ld_acquire_s32(a.stop) || ld_acquire_s32(a.abort_flag)) ? 1 : 0;
+            }
+            __syncthreads();
+            const int stop_local = s_ok;
+            __syncthreads();
+            // 2. u^n_k: own rows and one halo row each side (Dirichlet data off the domain)
+            const double* Un = a.U + (long long)n * Ns;
+            const double* bnd = a.bc ? a.bc + (long long)n * nb : nullptr;
+            double rmax = 0.0, rs = 0.0;
+            if (!stop_local) {
+                for (int i = threadIdx.x; i < (t.nrows + 2) * nx; i += NT) {
+                    const int jr = i / nx, ii = i - jr * nx, j = t.r0 - 1 + jr;
+                    double val;
+                    if (j < 0) val = bnd ? bnd[ii] : 0.0;
+                    else if (j >= ny) val = bnd ? bnd[nx + ii] : 0.0;
+                    else val = __ldcg(Un + (long long)j * nx + ii);
+                    u[i] = val;
+                }
+                __syncthreads();
+                // 3. residual r^n_k, scaled couplings, rhs; uprev <- u^n_k
+                const double* qn = a.q ? a.q + (long long)n * Ns + off0 : nullptr;
+                for (int i = threadIdx.x; i < nloc; i += NT) {
+                    const int jl = i / nx, ii = i - jl * nx, j = t.r0 + jl;
+                    const int ku = (jl + 1) * nx + ii;
+                    const double uC = u[ku];
+                    const double uW = ii > 0 ? u[ku - 1] : (bnd ? bnd[2 * nx + j] : 0.0);
+                    const double uE = ii < nx - 1 ? u[ku + 1] : (bnd ? bnd[2 * nx + ny + j] : 0.0);
+                    const double uS = u[ku - nx];
+                    const double uN = u[ku + nx];
+                    double r = (uprev[i] - uC) - tau_F<CONV, NLV>(oc, uC, uW, uE, uS, uN);
+                    if (qn) r = fma(oc.dt, qn[i], r);
+                    double aC, aW, aE, aS, aN;
+                    jac_row<CONV, NLV>(oc, uC, uW, uE, uS, uN, aC, aW, aE, aS, aN);
+                    if (ii == 0) aW = 0.0;
+                    if (ii == nx - 1) aE = 0.0;
+                    if (j == 0) aS = 0.0;
+                    if (j == ny - 1) aN = 0.0;
+                    const double d = NLV ? 1.0 / aC : dconst;
+                    aW *= d;
+                    aE *= d;
+                    aS *= d;
+                    aN *= d;
+                    m.cw[i] = aW;
+                    m.ce[i] = aE;
+                    m.cs[i] = aS;
+                    m.cn[i] = aN;
+                    const double bval = r + m.x[i];  // r^n + du^{n-1}
+                    m.bs[i] = d * bval;
+                    m.x[i] = bval;                   // SOR start
+                    uprev[i] = uC;                   // u^n_k for the next level's time difference
+                    rmax = fmax(rmax, fabs(r));
+                    if (r != r) rmax = r;
+                    rs = fmax(rs, fabs(aW) + fabs(aE) + fabs(aS) + fabs(aN));
+                }
+            }
+            // 4. team reduction: max |r|, Gershgorin bound, stop flag (consistent decisions)
+            double v3[3];
+            v3[0] = key_val(block_max_u64<NT>(abs_key(rmax), reinterpret_cast<unsigned long long*>(m.red)));
+            v3[1] = key_val(block_max_u64<NT>(abs_key(rs), reinterpret_cast<unsigned long long*>(m.red)));
+            v3[2] = stop_local ? 1.0 : 0.0;
+            double g3[3];
+            if (!reduce_finish<3, true>(c, t, reduce_arrive<3>(t, v3), g3, m.red + 32, &s_ok)) return;
+            if (g3[2] != 0.0) goto done;  // another iteration has converged (or the launch aborts)
+            if (g3[0] != g3[0]) {
+                if (threadIdx.x == 0) {
+                    atomicCAS(a.status, 0, ST_EDIVERGED);
+                    __threadfence();
+                    atomicExch(a.stop, 1);
+                }
+                goto done;
+            }
+            {
+                // 5. forcing from the running max; SOR tolerance absolute, BiCGStab relative
+                double eta = 0.0, sor_tol = 0.0;
+                if (threadIdx.x == 0) {
+                    prefix = fmax(prefix, g3[0]);
+                    eta = fmax(fmin(a.eta_max, a.eta_gamma * prefix), 1e-300);
+                    sor_tol = fmax(a.atol, eta * prefix);
+                }
+                eta = bcast0(eta, slot);
+                sor_tol = bcast0(sor_tol, slot);
+                int used = 0;
+                const int iters = level_solve<NT>(c, t, m, a.method, a.sor_rho_max, g3[1], sor_tol, eta, a.atol,
+                                                  &s_ok, &used);
+                if (iters < 0) return;  // aborted
+                // 6. U^n += du^n; du^n stays in x for the next level
+                double* Uw = a.U + (long long)n * Ns + off0;
+                for (int i = threadIdx.x; i < nloc; i += NT) {
+                    const double dx = m.x[i];
+                    __stcg(Uw + i, uprev[i] + dx);
+                    sumsq += dx * dx;
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    st_release_u64(my_prog + b, (unsigned long long)k * M + n + 1);
+                    if (b == 0) a.cell_iters[(size_t)k * M + n] = used == 1 ? iters + 1 : -(iters + 1);
+                    if (iters >= c.max_iter) atomicCAS(a.status, 0, ST_ENOCONV);
+                }
+            }
+        }
+        {
+            // iteration k done on every level
+            double ss[1] = {sumsq};
+            block_sum<NT, 1>(ss, m.red);
+            if (threadIdx.x == 0) {
+                a.cta_sumsq[(size_t)k * a.G + b] = ss[0];
+                if (b == 0) {
+                    a.res_inf[k] = prefix;
+                    if (prefix <= a.tol_res) {
+                        atomicMin(a.stop + 1, k);
+                        __threadfence();
+                        atomicExch(a.stop, 1);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+done:
+    if (b == 0 && threadIdx.x == 0) {
+        unsigned long long* tm = a.timers + (size_t)team * 4;
+        tm[0] = t.t_halo;
+        tm[1] = t.t_red;
+        tm[2] = t_pred;
+        tm[3] = global_ns() - t_start;
     }
 }
 

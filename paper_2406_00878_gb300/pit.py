@@ -42,7 +42,7 @@ class pit_options(ctypes.Structure):
     _fields_ = [("newton_max", ctypes.c_int), ("tol_res", ctypes.c_double), ("lin_solver", ctypes.c_int),
                 ("eta_max", ctypes.c_double), ("eta_gamma", ctypes.c_double), ("lin_atol", ctypes.c_double),
                 ("lin_max_iter", ctypes.c_int), ("sor_rho_max", ctypes.c_double), ("team_ctas", ctypes.c_int),
-                ("wait_budget", ctypes.c_longlong)]
+                ("wait_budget", ctypes.c_longlong), ("wave_teams", ctypes.c_int)]
 
 
 class pit_step_info(ctypes.Structure):
@@ -58,12 +58,17 @@ class pit_step_info(ctypes.Structure):
 class pit_solve_info(ctypes.Structure):
     _fields_ = [("newton_iters", ctypes.c_int), ("converged", ctypes.c_int),
                 ("res_inf", ctypes.c_double * (PIT_MAX_NEWTON + 1)), ("steps", pit_step_info * PIT_MAX_NEWTON),
-                ("ms_total", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("wave_teams", ctypes.c_int), ("wave_team_ctas", ctypes.c_int),
+                ("wave_launches", ctypes.c_int), ("ms_wave", ctypes.c_float), ("us_pred_wait", ctypes.c_float),
+                ("us_halo_wait", ctypes.c_float), ("us_reduce_wait", ctypes.c_float)]
 
     def as_dict(self):
         k = self.newton_iters
         return {"newton_iters": k, "converged": bool(self.converged), "res_inf": list(self.res_inf[:k + 1]),
-                "steps": [self.steps[i].as_dict() for i in range(k)], "ms_total": self.ms_total}
+                "steps": [self.steps[i].as_dict() for i in range(k)], "ms_total": self.ms_total,
+                "wave_teams": self.wave_teams, "wave_team_ctas": self.wave_team_ctas,
+                "wave_launches": self.wave_launches, "ms_wave": self.ms_wave, "us_pred_wait": self.us_pred_wait,
+                "us_halo_wait": self.us_halo_wait, "us_reduce_wait": self.us_reduce_wait}
 
 
 class PitError(RuntimeError):

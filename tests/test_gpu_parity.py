@@ -201,3 +201,47 @@ def test_errors_are_reported():
         assert status == pit.PIT_EDIVERGED
         with pytest.raises(pit.PitError):
             pit.pit_residual(ctx, U, U)
+
+
+WAVE_CASES = [
+    (lambda: W.heat32(1), "heat32s1"),
+    (lambda: W.random_problem(31, 37, 45, 7, W.BURGERS, with_bc=True, with_q=True), "burg37x45"),
+    (lambda: W.random_problem(32, 20, 26, 9, W.HEAT, with_bc=True, with_q=True, mu_b=0.0), "linheat20x26"),
+]
+
+
+@pytest.mark.parametrize("teams", [-1, 1, 2, 3, 4, 6])
+@pytest.mark.parametrize("make,name", WAVE_CASES, ids=[c[1] for c in WAVE_CASES])
+def test_wavefront_solve_matches_oracle(make, name, teams):
+    p = make()
+    Uo, _, _, _ = oracle.solve(p, tol=1e-13)
+    opt = pit.pit_default_options()
+    opt.wave_teams = teams
+    with pit.context_for(p, opt) as ctx:
+        U = torch.empty(p.dof, dtype=torch.float64, device="cuda")
+        pit.pit_fill_plain_guess(ctx, U)
+        status, info = pit.pit_solve(ctx, U)
+        Ug = U.cpu().numpy().reshape(p.M, -1)
+    assert info["converged"] and info["res_inf"][-1] <= 1e-12
+    if teams >= 1:
+        assert info["wave_teams"] >= 1 and info["wave_launches"] >= 1
+    assert np.abs(Ug - Uo).max() <= 1e-10 * np.abs(Uo).max()
+
+
+def test_wavefront_iterates_equal_classic_newton_iterates():
+    # with exact level solves the wavefront runs the same Newton iterates as the
+    # per-stage launches: compare after a fixed number of iterations
+    p = W.random_problem(33, 30, 22, 6, W.BURGERS, with_bc=True)
+    outs = []
+    for teams in (-1, 3):
+        opt = pit.pit_default_options()
+        opt.wave_teams = teams
+        opt.newton_max = 2
+        opt.eta_max = 1e-14
+        opt.eta_gamma = 0.0
+        with pit.context_for(p, opt) as ctx:
+            U = torch.empty(p.dof, dtype=torch.float64, device="cuda")
+            pit.pit_fill_plain_guess(ctx, U)
+            pit.pit_solve(ctx, U, check=False)
+            outs.append(U.cpu().numpy())
+    np.testing.assert_allclose(outs[1], outs[0], rtol=0, atol=1e-11 * np.abs(outs[0]).max())
