@@ -94,9 +94,22 @@ typedef struct {
     int team_ctas;          /* CTAs that share one level in the chain kernel (0 = auto) */
     long long wait_budget;  /* spin iterations before a device wait gives up (default 1<<26) */
     int wave_teams;         /* pit_solve: Newton iterations in flight in the wavefront kernel
-                               (0 = auto (4), >= 1 that many, -1 = one launch per stage and
+                               (0 = auto: the most teams, up to 6, whose level strips fit in
+                               shared memory; >= 1 that many; -1 = one launch per stage and
                                Newton iteration, as pit_newton_step) */
+    int precision;          /* pit_solve level solves: PIT_FP64 (default) or PIT_FP32_INNER: the
+                               Jacobian entries, right-hand sides and level-solve iterates are
+                               held and updated in FP32, inside FP64 Newton (residual, update
+                               and norms stay FP64; Newton then acts as iterative refinement) */
+    int window;             /* pit_solve with the wavefront: 0 (default) = all M levels at once;
+                               W > 0 = levels in consecutive windows of W. The all-at-once system
+                               is block lower-triangular in time, so the solution is the same;
+                               each window starts from the plain guess u^n = u^{s-1} at its first
+                               level s (the caller's iterate is not used), which keeps Newton in
+                               its convergence region over long horizons */
 } pit_options;
+
+enum { PIT_FP64 = 0, PIT_FP32_INNER = 1 };
 
 #define PIT_MAX_NEWTON 64
 
@@ -125,6 +138,8 @@ typedef struct {
     float ms_wave;                         /* device time of the wavefront launches */
     float us_pred_wait;                    /* first CTA of team 0: waiting for the previous iteration */
     float us_halo_wait, us_reduce_wait;    /* first CTA of team 0: team synchronisation */
+    int windows;                           /* windows of levels solved (1 without windowing) */
+    int newton_iters_total;                /* Newton updates summed over the windows */
 } pit_solve_info;
 
 /* Fill *opt with the defaults listed above. */

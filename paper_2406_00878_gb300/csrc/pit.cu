@@ -46,7 +46,7 @@ struct pit_ctx {
     double* R = nullptr;     // [M][Ns]
     double* coef = nullptr;  // [5][M][Ns] scaled planes
     double* Uh = nullptr;    // [M][Ns] iterate of pit_solve_host
-    unsigned long long* keys = nullptr;  // [0] ||R||_inf key, [1..M] Gershgorin keys
+    unsigned long long* keys = nullptr;  // [0] ||R||_inf key, [1..M] Gershgorin keys, [M+1..2M] nonsymmetric flags
 
     // chain team workspace
     int G = 0, rows_base = 0, rows_rem = 0;
@@ -66,6 +66,7 @@ struct pit_ctx {
     unsigned long long* w_sync = nullptr;  // flags[K*Gw], red_cnt[K*4], prog[K*Gw]
     int* w_ints = nullptr;                  // abort, status, stop[2]
     double* w_res = nullptr;                // [kcap]
+    double* w_prefix = nullptr;             // [kcap][M]
     int* w_cell = nullptr;                  // [kcap][M]
     double* w_sumsq = nullptr;              // [kcap][Gw]
     unsigned long long* w_timers = nullptr; // [K][4]
@@ -132,6 +133,8 @@ extern "C" void pit_default_options(pit_options* o) {
     o->team_ctas = 0;
     o->wait_budget = 1ll << 26;
     o->wave_teams = 0;
+    o->precision = PIT_FP64;
+    o->window = 0;
 }
 
 extern "C" const char* pit_status_string(pit_status s) {
@@ -152,11 +155,33 @@ extern "C" const char* pit_last_error(const pit_ctx* ctx) { return ctx ? ctx->er
 
 // ------------------------------------------------------------ kernel dispatch
 
+// Residual of a window of levels [s, s + oc.M): u_prev is u^{s-1} (u^0 when s = 0);
+// U, bc, q, R point at level s.
 template <bool CONV, bool NLV>
-static void launch_residual(pit_ctx* c, const double* U, double* R) {
-    dim3 grid((unsigned)((c->Ns + kNT - 1) / kNT), (unsigned)c->M);
-    residual_kernel<CONV, NLV, kNT><<<grid, kNT, 0, c->stream>>>(c->oc, c->u0, U, c->has_bc ? c->bc : nullptr,
-                                                                 c->has_q ? c->q : nullptr, R, c->keys);
+static void launch_residual(pit_ctx* c, const OpConst& oc, const double* u_prev, const double* U, const double* bc,
+                            const double* q, double* R) {
+    dim3 grid((unsigned)((c->Ns + kNT - 1) / kNT), (unsigned)oc.M);
+    residual_kernel<CONV, NLV, kNT><<<grid, kNT, 0, c->stream>>>(oc, u_prev, U, bc, q, R, c->keys);
+}
+
+static pit_status enqueue_residual_range(pit_ctx* ctx, int s, int Mw, const double* U, double* R) {
+    OpConst oc = ctx->oc;
+    oc.M = Mw;
+    const double* u_prev = s == 0 ? ctx->u0 : U + (size_t)(s - 1) * ctx->Ns;
+    const double* bc = ctx->has_bc ? ctx->bc + (size_t)s * ctx->nb : nullptr;
+    const double* q = ctx->has_q ? ctx->q + (size_t)s * ctx->Ns : nullptr;
+    const double* Uw = U + (size_t)s * ctx->Ns;
+    double* Rw = R + (size_t)s * ctx->Ns;
+    CK(cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long), ctx->stream));
+    if (ctx->conv) {
+        if (ctx->nlv) launch_residual<true, true>(ctx, oc, u_prev, Uw, bc, q, Rw);
+        else launch_residual<true, false>(ctx, oc, u_prev, Uw, bc, q, Rw);
+    } else {
+        if (ctx->nlv) launch_residual<false, true>(ctx, oc, u_prev, Uw, bc, q, Rw);
+        else launch_residual<false, false>(ctx, oc, u_prev, Uw, bc, q, Rw);
+    }
+    CK(cudaGetLastError());
+    return PIT_OK;
 }
 
 template <bool CONV, bool NLV, bool SCALED>
@@ -167,16 +192,7 @@ static void launch_assemble(pit_ctx* c, const double* U, double* coef) {
 }
 
 static pit_status enqueue_residual(pit_ctx* ctx, const double* U, double* R) {
-    CK(cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long), ctx->stream));
-    if (ctx->conv) {
-        if (ctx->nlv) launch_residual<true, true>(ctx, U, R);
-        else launch_residual<true, false>(ctx, U, R);
-    } else {
-        if (ctx->nlv) launch_residual<false, true>(ctx, U, R);
-        else launch_residual<false, false>(ctx, U, R);
-    }
-    CK(cudaGetLastError());
-    return PIT_OK;
+    return enqueue_residual_range(ctx, 0, ctx->M, U, R);
 }
 
 static pit_status read_res_inf(pit_ctx* ctx, double* out) {
@@ -189,7 +205,7 @@ static pit_status read_res_inf(pit_ctx* ctx, double* out) {
 
 template <bool SCALED>
 static pit_status enqueue_assemble(pit_ctx* ctx, const double* U, double* coef) {
-    if (SCALED) CK(cudaMemsetAsync(ctx->keys + 1, 0, sizeof(unsigned long long) * ctx->M, ctx->stream));
+    if (SCALED) CK(cudaMemsetAsync(ctx->keys + 1, 0, sizeof(unsigned long long) * 2 * ctx->M, ctx->stream));
     if (ctx->conv) {
         if (ctx->nlv) launch_assemble<true, true, SCALED>(ctx, U, coef);
         else launch_assemble<true, false, SCALED>(ctx, U, coef);
@@ -278,6 +294,20 @@ static pit_status run_chain(pit_ctx* ctx, const double* R, double* U, double* dU
 
 static bool finite_positive(double v) { return std::isfinite(v) && v > 0.0; }
 
+// The wavefront kernel for a closure and a level-solve precision.
+static const void* wave_fn(bool conv, bool nlv, bool fp32) {
+    if (fp32) {
+        if (conv) return nlv ? reinterpret_cast<const void*>(wave_kernel<kNT, true, true, float>)
+                             : reinterpret_cast<const void*>(wave_kernel<kNT, true, false, float>);
+        return nlv ? reinterpret_cast<const void*>(wave_kernel<kNT, false, true, float>)
+                   : reinterpret_cast<const void*>(wave_kernel<kNT, false, false, float>);
+    }
+    if (conv) return nlv ? reinterpret_cast<const void*>(wave_kernel<kNT, true, true, double>)
+                         : reinterpret_cast<const void*>(wave_kernel<kNT, true, false, double>);
+    return nlv ? reinterpret_cast<const void*>(wave_kernel<kNT, false, true, double>)
+               : reinterpret_cast<const void*>(wave_kernel<kNT, false, false, double>);
+}
+
 // ------------------------------------------------------------------ the ABI
 
 extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const pit_params* params,
@@ -304,7 +334,7 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
     if (o.newton_max < 0 || o.newton_max > PIT_MAX_NEWTON || !(o.tol_res >= 0.0) || o.lin_solver < 0 ||
         o.lin_solver > 2 || !(o.eta_max > 0.0) || !(o.eta_gamma >= 0.0) || !(o.lin_atol >= 0.0) ||
         o.lin_max_iter < 1 || !(o.sor_rho_max > 0.0) || o.team_ctas < 0 || o.wait_budget < 1 || o.wave_teams < -1 ||
-        o.wave_teams > 64) {
+        o.wave_teams > 64 || (o.precision != PIT_FP64 && o.precision != PIT_FP32_INNER) || o.window < 0) {
         delete ctx;
         return PIT_EINVAL;
     }
@@ -374,10 +404,12 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
                         per_sm, ctx->num_sms);
         // wavefront teams: K teams of Gw CTAs, one CTA per SM, level strips in shared memory
         if (o.wave_teams >= 0) {
+            const bool fp32 = o.precision == PIT_FP32_INNER;
+            const void* wf = wave_fn(ctx->conv, ctx->nlv, fp32);
             cudaFuncAttributes fa;
-            CK(cudaFuncGetAttributes(&fa, wave_kernel<kNT, true, false>));
+            CK(cudaFuncGetAttributes(&fa, wf));
             const size_t dyn_max = ctx->smem_optin - fa.sharedSizeBytes;
-            int K = o.wave_teams == 0 ? 4 : o.wave_teams;
+            int K = o.wave_teams == 0 ? 6 : o.wave_teams;  // auto: the most teams (<= 6) that fit
             K = std::max(1, std::min(K, std::max(1, o.newton_max)));
             const int rows_min = (kMinLocal + nx - 1) / nx;
             for (; K >= 1; --K) {
@@ -386,7 +418,7 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
                 Gw = std::max(1, std::min(Gw, ny));
                 const int rows = (ny + Gw - 1) / Gw;
                 Gw = (ny + rows - 1) / rows;
-                const size_t bytes = sizeof(double) * wave_smem_doubles(rows * nx, nx);
+                const size_t bytes = fp32 ? wave_smem_bytes<float>(rows * nx, nx) : wave_smem_bytes<double>(rows * nx, nx);
                 if (bytes <= dyn_max && K * Gw <= ctx->num_sms) {
                     ctx->K = K;
                     ctx->Gw = Gw;
@@ -397,15 +429,9 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
                 }
             }
             if (ctx->K > 0) {
-                const void* kernels[4] = {reinterpret_cast<const void*>(wave_kernel<kNT, false, false>),
-                                          reinterpret_cast<const void*>(wave_kernel<kNT, false, true>),
-                                          reinterpret_cast<const void*>(wave_kernel<kNT, true, false>),
-                                          reinterpret_cast<const void*>(wave_kernel<kNT, true, true>)};
-                for (const void* kf : kernels)
-                    CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->wave_smem));
+                CK(cudaFuncSetAttribute(wf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->wave_smem));
                 int per = 0;
-                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, wave_kernel<kNT, true, true>, kNT,
-                                                                 ctx->wave_smem));
+                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, wf, kNT, ctx->wave_smem));
                 if ((long long)per * ctx->num_sms < (long long)ctx->K * ctx->Gw) ctx->K = 0;  // fall back
             }
             if (ctx->K > 0) {
@@ -416,6 +442,7 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
                 CK(dalloc(&ctx->w_sync, (size_t)K * Gw * 2 + (size_t)K * 4));
                 CK(dalloc(&ctx->w_ints, 4));
                 CK(dalloc(&ctx->w_res, (size_t)ctx->kcap));
+                CK(dalloc(&ctx->w_prefix, (size_t)ctx->kcap * M));
                 CK(dalloc(&ctx->w_cell, (size_t)ctx->kcap * M));
                 CK(dalloc(&ctx->w_sumsq, (size_t)ctx->kcap * Gw));
                 CK(dalloc(&ctx->w_timers, (size_t)K * 4));
@@ -430,7 +457,7 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
         CK(dalloc(&ctx->R, ctx->DOF));
         CK(dalloc(&ctx->coef, 5 * (size_t)ctx->DOF));
         CK(dalloc(&ctx->Uh, ctx->DOF));
-        CK(dalloc(&ctx->keys, (size_t)M + 1));
+        CK(dalloc(&ctx->keys, 2 * (size_t)M + 1));
         CK(dalloc(&ctx->pub, (size_t)2 * ctx->G * 2 * nx));
         CK(dalloc(&ctx->red_part, (size_t)4 * ctx->G * 4));
         CK(dalloc(&ctx->sync_words, (size_t)ctx->G + 4));
@@ -474,6 +501,7 @@ extern "C" void pit_destroy(pit_ctx* ctx) {
     cudaFree(ctx->w_sync);
     cudaFree(ctx->w_ints);
     cudaFree(ctx->w_res);
+    cudaFree(ctx->w_prefix);
     cudaFree(ctx->w_cell);
     cudaFree(ctx->w_sumsq);
     cudaFree(ctx->w_timers);
@@ -566,9 +594,10 @@ extern "C" pit_status pit_newton_step(pit_ctx* ctx, double* U_dev, pit_step_info
 // info->steps[k] and res_inf[k] for the iterations that completed; *k_done receives
 // one past the last completed iteration, *stopped whether a converged iteration
 // raised the stop flag.
-static pit_status run_wave(pit_ctx* ctx, double* U, int k_begin, int k_end, pit_solve_info* inf, int* k_done,
-                           bool* stopped) {
-    const int K = ctx->K, Gw = ctx->Gw, M = ctx->M;
+static pit_status run_wave(pit_ctx* ctx, int s, int Mw, double* Uall, int k_begin, int k_end, pit_solve_info* inf,
+                           int* k_done, bool* stopped) {
+    const int K = ctx->K, Gw = ctx->Gw, M = Mw;
+    double* U = Uall + (size_t)s * ctx->Ns;
     const size_t nsync = (size_t)K * Gw * 2 + (size_t)K * 4;
     CK(cudaMemsetAsync(ctx->w_sync, 0, sizeof(unsigned long long) * nsync, ctx->stream));
     CK(cudaMemsetAsync(ctx->w_ints, 0, sizeof(int) * 3, ctx->stream));
@@ -577,9 +606,10 @@ static pit_status run_wave(pit_ctx* ctx, double* U, int k_begin, int k_end, pit_
     CK(cudaMemsetAsync(ctx->w_timers, 0, sizeof(unsigned long long) * K * 4, ctx->stream));
     WaveArgs a{};
     a.c = ctx->oc;
-    a.u0 = ctx->u0;
-    a.bc = ctx->has_bc ? ctx->bc : nullptr;
-    a.q = ctx->has_q ? ctx->q : nullptr;
+    a.c.M = Mw;
+    a.u0 = s == 0 ? ctx->u0 : Uall + (size_t)(s - 1) * ctx->Ns;
+    a.bc = ctx->has_bc ? ctx->bc + (size_t)s * ctx->nb : nullptr;
+    a.q = ctx->has_q ? ctx->q + (size_t)s * ctx->Ns : nullptr;
     a.U = U;
     a.K = K;
     a.G = Gw;
@@ -604,14 +634,12 @@ static pit_status run_wave(pit_ctx* ctx, double* U, int k_begin, int k_end, pit_
     a.status = ctx->w_ints + 1;
     a.stop = ctx->w_ints + 2;
     a.res_inf = ctx->w_res;
+    a.cell_prefix = ctx->w_prefix;
     a.cell_iters = ctx->w_cell;
     a.cta_sumsq = ctx->w_sumsq;
     a.timers = ctx->w_timers;
     void* args[] = {&a};
-    const void* kf = ctx->conv ? (ctx->nlv ? reinterpret_cast<const void*>(wave_kernel<kNT, true, true>)
-                                           : reinterpret_cast<const void*>(wave_kernel<kNT, true, false>))
-                               : (ctx->nlv ? reinterpret_cast<const void*>(wave_kernel<kNT, false, true>)
-                                           : reinterpret_cast<const void*>(wave_kernel<kNT, false, false>));
+    const void* kf = wave_fn(ctx->conv, ctx->nlv, ctx->opt.precision == PIT_FP32_INNER);
     CK(cudaEventRecord(ctx->ev[2], ctx->stream));
     CK(cudaLaunchCooperativeKernel(kf, dim3(K * Gw), dim3(kNT), args, ctx->wave_smem, ctx->stream));
     CK(cudaEventRecord(ctx->ev[3], ctx->stream));
@@ -656,7 +684,7 @@ static pit_status run_wave(pit_ctx* ctx, double* U, int k_begin, int k_end, pit_
         }
         double ss = 0.0;
         for (int b = 0; b < Gw; ++b) ss += ctx->h_wsumsq[(size_t)k * Gw + b];
-        st.upd_rms = std::sqrt(ss / (double)ctx->DOF);
+        st.upd_rms = std::sqrt(ss / (double)((size_t)Mw * ctx->Ns));
         st.lin_iters_mean = (double)tot / M;
         st.lin_iters_max = mx;
         st.levels_sor = nsor;
@@ -669,34 +697,62 @@ static pit_status run_wave(pit_ctx* ctx, double* U, int k_begin, int k_end, pit_
     return PIT_OK;  // a capped level solve (ST_ENOCONV) is not fatal: Newton continues
 }
 
-static pit_status solve_wave(pit_ctx* ctx, double* U_dev, pit_solve_info* inf) {
-    inf->wave_teams = ctx->K;
-    inf->wave_team_ctas = ctx->Gw;
+// Newton for one window of levels [s, s + Mw) with the wavefront kernel, until the
+// window's residual is <= tol_res (the window's first level uses the converged
+// level s - 1, or u^0).
+static pit_status solve_window(pit_ctx* ctx, double* U_dev, int s, int Mw, pit_solve_info* inf, int* iters) {
     int k = 0;
-    pit_status st = PIT_OK;
     for (;;) {
         int k_done = k;
         bool stopped = false;
-        if (k < ctx->opt.newton_max) {
-            st = run_wave(ctx, U_dev, k, ctx->opt.newton_max, inf, &k_done, &stopped);
-            if (st != PIT_OK) return st;
-        }
-        // the residual of the final iterate decides convergence
-        CHECK_RET(enqueue_residual(ctx, U_dev, ctx->R));
+        if (k < ctx->opt.newton_max) CHECK_RET(run_wave(ctx, s, Mw, U_dev, k, ctx->opt.newton_max, inf, &k_done, &stopped));
+        CHECK_RET(enqueue_residual_range(ctx, s, Mw, U_dev, ctx->R));
         double res = 0.0;
         CHECK_RET(read_res_inf(ctx, &res));
-        inf->newton_iters = k_done;
         inf->res_inf[k_done] = res;
-        if (!std::isfinite(res)) return fail(ctx, PIT_EDIVERGED, "pit_solve: final residual is not finite");
-        if (res <= ctx->opt.tol_res) {
-            inf->converged = 1;
-            return PIT_OK;
-        }
+        *iters = k_done;
+        if (!std::isfinite(res))
+            return fail(ctx, PIT_EDIVERGED, "pit_solve: residual of levels %d..%d is not finite", s, s + Mw - 1);
+        if (res <= ctx->opt.tol_res) return PIT_OK;
         if (k_done >= ctx->opt.newton_max || k_done == k)
-            return fail(ctx, PIT_ENOCONV, "pit_solve: ||R||_inf = %.3e > %.3e after %d Newton updates", res,
-                        ctx->opt.tol_res, k_done);
+            return fail(ctx, PIT_ENOCONV, "pit_solve: ||R||_inf = %.3e > %.3e on levels %d..%d after %d Newton updates",
+                        res, ctx->opt.tol_res, s, s + Mw - 1, k_done);
         k = k_done;  // continue Newton from the current iterate
     }
+}
+
+static pit_status solve_wave(pit_ctx* ctx, double* U_dev, pit_solve_info* inf) {
+    inf->wave_teams = ctx->K;
+    inf->wave_team_ctas = ctx->Gw;
+    const int M = ctx->M;
+    const int Wn = ctx->opt.window > 0 ? std::min(ctx->opt.window, M) : M;
+    for (int s = 0; s < M; s += Wn) {
+        const int Mw = std::min(Wn, M - s);
+        if (Wn < M) {
+            // plain guess for the window from the converged level before it
+            const double* from = s == 0 ? ctx->u0 : U_dev + (size_t)(s - 1) * ctx->Ns;
+            const int blocks = std::max(1, std::min(ctx->num_sms * 8, (int)(((size_t)Mw * ctx->Ns + kNT - 1) / kNT)));
+            plain_guess_kernel<<<blocks, kNT, 0, ctx->stream>>>(from, U_dev + (size_t)s * ctx->Ns, ctx->Ns, Mw);
+            CK(cudaGetLastError());
+        }
+        int iters = 0;
+        const pit_status st = solve_window(ctx, U_dev, s, Mw, inf, &iters);
+        inf->windows += 1;
+        inf->newton_iters_total += iters;
+        inf->newton_iters = std::max(inf->newton_iters, iters);
+        if (st != PIT_OK) return st;
+    }
+    // the residual of the whole final iterate decides convergence
+    CHECK_RET(enqueue_residual(ctx, U_dev, ctx->R));
+    double res = 0.0;
+    CHECK_RET(read_res_inf(ctx, &res));
+    inf->res_inf[inf->newton_iters] = res;
+    if (!std::isfinite(res)) return fail(ctx, PIT_EDIVERGED, "pit_solve: final residual is not finite");
+    if (res <= ctx->opt.tol_res) {
+        inf->converged = 1;
+        return PIT_OK;
+    }
+    return fail(ctx, PIT_ENOCONV, "pit_solve: final ||R||_inf = %.3e > %.3e", res, ctx->opt.tol_res);
 }
 
 extern "C" pit_status pit_solve(pit_ctx* ctx, double* U_dev, pit_solve_info* info) {

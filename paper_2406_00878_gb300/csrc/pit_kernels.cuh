@@ -206,7 +206,8 @@ __global__ void __launch_bounds__(NT) residual_kernel(OpConst c, const double* _
 // One thread per node, all levels at once. SCALED = false writes the raw entries
 // coef[5][M][Ns] = C, W, E, S, N of A_n. SCALED = true writes the Jacobi-scaled
 // planes used by the level solver: 1/C, W/C, E/C, S/C, N/C, and folds the row sum
-// |W|+|E|+|S|+|N| over |C| into rho_key[n] (Gershgorin bound of I - D^{-1}A_n).
+// |W|+|E|+|S|+|N| over |C| into rho_key[n] (Gershgorin bound of I - D^{-1}A_n) and
+// sets rho_key[M + n] when a row has opposite-signed couplings in x or y.
 template <bool CONV, bool NLV, bool SCALED, int NT>
 __global__ void __launch_bounds__(NT) assemble_kernel(OpConst c, const double* __restrict__ U,
                                                       const double* __restrict__ bc, double* __restrict__ coef,
@@ -240,6 +241,7 @@ __global__ void __launch_bounds__(NT) assemble_kernel(OpConst c, const double* _
             aN *= d;
             o[0] = d;
             key = abs_key(fabs(aW) + fabs(aE) + fabs(aS) + fabs(aN));
+            if (aW * aE < 0.0 || aS * aN < 0.0) atomicMax(rho_key + c.M + n, 1ull);
         } else {
             o[0] = aC;
         }
@@ -342,12 +344,12 @@ __device__ __forceinline__ bool wait_geq(const TeamCtl& c, const unsigned long l
 // neighbours' rows published at the same step into haloS (row r0-1) and haloN
 // (row r0+nrows). Rows outside the domain are zero (the correction vanishes on
 // the Dirichlet boundary). Returns false when the launch aborted.
-template <int NT>
-__device__ bool exchange_halo(const TeamCtl& c, Team& t, const double* v, double* haloS, double* haloN,
-                              int* s_ok) {
+template <int NT, typename T>
+__device__ bool exchange_halo(const TeamCtl& c, Team& t, const T* v, T* haloS, T* haloN, int* s_ok) {
     const int nx = t.nx;
     const unsigned long long seq = ++t.pub_seq;
-    double* mine = t.pub + ((size_t)(seq & 1) * t.G + t.b) * 2 * nx;
+    T* const pubT = reinterpret_cast<T*>(t.pub);
+    T* mine = pubT + ((size_t)(seq & 1) * t.G + t.b) * 2 * nx;
     for (int i = threadIdx.x; i < nx; i += NT) {
         __stcg(mine + i, v[i]);
         __stcg(mine + nx + i, v[(t.nrows - 1) * nx + i]);
@@ -366,18 +368,18 @@ __device__ bool exchange_halo(const TeamCtl& c, Team& t, const double* v, double
     }
     __syncthreads();
     if (!*s_ok) return false;
-    const double* par = t.pub + (size_t)(seq & 1) * t.G * 2 * nx;
+    const T* par = pubT + (size_t)(seq & 1) * t.G * 2 * nx;
     if (t.b > 0) {  // neighbour below: its last row
-        const double* lo = par + (size_t)(t.b - 1) * 2 * nx + nx;
+        const T* lo = par + (size_t)(t.b - 1) * 2 * nx + nx;
         for (int i = threadIdx.x; i < nx; i += NT) haloS[i] = __ldcg(lo + i);
     } else {
-        for (int i = threadIdx.x; i < nx; i += NT) haloS[i] = 0.0;
+        for (int i = threadIdx.x; i < nx; i += NT) haloS[i] = T(0);
     }
     if (t.b + 1 < t.G) {  // neighbour above: its first row
-        const double* hi = par + (size_t)(t.b + 1) * 2 * nx;
+        const T* hi = par + (size_t)(t.b + 1) * 2 * nx;
         for (int i = threadIdx.x; i < nx; i += NT) haloN[i] = __ldcg(hi + i);
     } else {
-        for (int i = threadIdx.x; i < nx; i += NT) haloN[i] = 0.0;
+        for (int i = threadIdx.x; i < nx; i += NT) haloN[i] = T(0);
     }
     __syncthreads();
     return true;
@@ -443,44 +445,61 @@ __device__ __forceinline__ bool reduce_finish(const TeamCtl& c, Team& t, unsigne
     return ok;
 }
 
-// Shared-memory arrays of one CTA (cap doubles each, cap = largest rows x nx).
+// Machine epsilon of the level-solve precision.
+template <typename T> struct Eps;
+template <> struct Eps<double> { static constexpr double value = 1.1102230246251565e-16; };
+template <> struct Eps<float> { static constexpr double value = 5.9604644775390625e-08; };
+
+// Shared-memory arrays of one CTA (cap elements each, cap = largest rows x nx). T is
+// the precision of the level solve: double, or float for FP32 inner solves.
+template <typename T>
 struct Smem {
-    double *cw, *ce, *cs, *cn, *bs, *x;      // scaled couplings, scaled rhs, iterate
-    double *r, *rh, *p, *v, *t;              // BiCGStab vectors (s shares r)
-    double *haloS, *haloN;                   // neighbour rows of the exchanged vector
-    double *red;                             // 64 doubles: block reductions [0,32), broadcast [32,48), flags [48,64)
+    T *cw, *ce, *cs, *cn, *bs, *x;           // scaled couplings, scaled rhs, iterate
+    T *r, *rh, *p, *v, *t;                   // BiCGStab vectors (s shares r)
+    T *haloS, *haloN;                        // neighbour rows of the exchanged vector
+    double* red;                             // 64 doubles: block reductions [0,32), broadcast [32,48), flags [48,64)
 };
 
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Byte offset of the 64-double reduction area after the solver arrays and halos.
+template <typename T>
+__host__ __device__ inline size_t smem_red_offset(int cap, int nx) {
+    return align_up(sizeof(T) * (11 * (size_t)cap + 2 * (size_t)nx), 16);
+}
+
 // Carve the layout: cw ce cs cn bs x r rh p v t | haloS haloN | red.
-__device__ __forceinline__ Smem smem_layout(double* base, int cap, int nx) {
-    Smem m;
-    m.cw = base;
-    m.ce = base + cap;
-    m.cs = base + 2 * cap;
-    m.cn = base + 3 * cap;
-    m.bs = base + 4 * cap;
-    m.x = base + 5 * cap;
-    m.r = base + 6 * cap;
-    m.rh = base + 7 * cap;
-    m.p = base + 8 * cap;
-    m.v = base + 9 * cap;
-    m.t = base + 10 * cap;
-    m.haloS = base + 11 * cap;
+template <typename T>
+__device__ __forceinline__ Smem<T> smem_layout(unsigned char* base, int cap, int nx) {
+    Smem<T> m;
+    T* b = reinterpret_cast<T*>(base);
+    m.cw = b;
+    m.ce = b + cap;
+    m.cs = b + 2 * cap;
+    m.cn = b + 3 * cap;
+    m.bs = b + 4 * cap;
+    m.x = b + 5 * cap;
+    m.r = b + 6 * cap;
+    m.rh = b + 7 * cap;
+    m.p = b + 8 * cap;
+    m.v = b + 9 * cap;
+    m.t = b + 10 * cap;
+    m.haloS = b + 11 * cap;
     m.haloN = m.haloS + nx;
-    m.red = m.haloN + nx;
+    m.red = reinterpret_cast<double*>(base + smem_red_offset<T>(cap, nx));
     return m;
 }
 
 // y = (D^{-1} A) v on the local rows (unit diagonal), halos of v in haloS/haloN.
-template <int NT>
-__device__ __forceinline__ void local_spmv(const Team& t, const Smem& m, const double* v, double* y) {
+template <int NT, typename T>
+__device__ __forceinline__ void local_spmv(const Team& t, const Smem<T>& m, const T* v, T* y) {
     const int nx = t.nx;
     for (int k = threadIdx.x; k < t.nloc; k += NT) {
         const int jl = k / nx, i = k - jl * nx;
-        const double vW = i > 0 ? v[k - 1] : 0.0;
-        const double vE = i < nx - 1 ? v[k + 1] : 0.0;
-        const double vS = jl > 0 ? v[k - nx] : m.haloS[i];
-        const double vN = jl < t.nrows - 1 ? v[k + nx] : m.haloN[i];
+        const T vW = i > 0 ? v[k - 1] : T(0);
+        const T vE = i < nx - 1 ? v[k + 1] : T(0);
+        const T vS = jl > 0 ? v[k - nx] : m.haloS[i];
+        const T vN = jl < t.nrows - 1 ? v[k + nx] : m.haloN[i];
         y[k] = v[k] + m.cw[k] * vW + m.ce[k] * vE + m.cs[k] * vS + m.cn[k] * vN;
     }
 }
@@ -490,33 +509,34 @@ __device__ __forceinline__ void local_spmv(const Team& t, const Smem& m, const d
 // d_s is the largest change of a sweep and rho = max(d_s / d_{s-1}, omega - 1); the
 // global d_s is known one sweep late (lagged team reduction), so every CTA takes
 // the same decision at the same sweep. Threads walk the points of one colour only
-// (every lane of a warp does useful FP64 work). Scalar decisions are taken by
-// thread 0 and broadcast. Returns the sweep count (< 0 on abort).
-template <int NT>
-__device__ int level_sor(const TeamCtl& c, Team& t, const Smem& m, double omega, double tol, int* s_ok) {
+// (every lane of a warp does useful work). Scalar decisions are taken by thread 0
+// and broadcast. Returns the sweep count (< 0 on abort).
+template <int NT, typename T>
+__device__ int level_sor(const TeamCtl& c, Team& t, const Smem<T>& m, double omega, double tol, int* s_ok) {
     const int nx = t.nx;
     const int half = (nx + 1) >> 1;            // points of one colour per row, at most
     const int npts = t.nrows * half;
+    const T om = (T)omega;
     double prev = -1.0, prev2 = -1.0;          // global max change of sweeps s-1 and s-2 (thread 0)
     unsigned long long pending = 0;
     bool have_pending = false;
     int* s_flag = reinterpret_cast<int*>(m.red + 48);
     for (int sweep = 1;; ++sweep) {
-        double dmax = 0.0;
+        T dmax = T(0);
         for (int color = 0; color < 2; ++color) {
-            if (!exchange_halo<NT>(c, t, m.x, m.haloS, m.haloN, s_ok)) return -1;
+            if (!exchange_halo<NT, T>(c, t, m.x, m.haloS, m.haloN, s_ok)) return -1;
             for (int q = threadIdx.x; q < npts; q += NT) {
                 const int jl = q / half;
                 const int i = ((t.r0 + jl + color) & 1) + 2 * (q - jl * half);
                 if (i >= nx) continue;
                 const int k = jl * nx + i;
-                const double xW = i > 0 ? m.x[k - 1] : 0.0;
-                const double xE = i < nx - 1 ? m.x[k + 1] : 0.0;
-                const double xS = jl > 0 ? m.x[k - nx] : m.haloS[i];
-                const double xN = jl < t.nrows - 1 ? m.x[k + nx] : m.haloN[i];
-                const double xk = m.x[k];
-                const double resid = m.bs[k] - xk - (m.cw[k] * xW + m.ce[k] * xE + m.cs[k] * xS + m.cn[k] * xN);
-                const double dx = omega * resid;
+                const T xW = i > 0 ? m.x[k - 1] : T(0);
+                const T xE = i < nx - 1 ? m.x[k + 1] : T(0);
+                const T xS = jl > 0 ? m.x[k - nx] : m.haloS[i];
+                const T xN = jl < t.nrows - 1 ? m.x[k + nx] : m.haloN[i];
+                const T xk = m.x[k];
+                const T resid = m.bs[k] - xk - (m.cw[k] * xW + m.ce[k] * xE + m.cs[k] * xS + m.cn[k] * xN);
+                const T dx = om * resid;
                 m.x[k] = xk + dx;
                 dmax = fmax(dmax, fabs(dx));
                 if (dx != dx) dmax = dx;
@@ -526,7 +546,7 @@ __device__ int level_sor(const TeamCtl& c, Team& t, const Smem& m, double omega,
         // this CTA's max change, then arrive at the team reduction of this sweep
         double v[1];
         {
-            unsigned long long key = block_max_u64<NT>(abs_key(dmax), reinterpret_cast<unsigned long long*>(m.red));
+            unsigned long long key = block_max_u64<NT>(abs_key((double)dmax), reinterpret_cast<unsigned long long*>(m.red));
             v[0] = key_val(key);
         }
         const unsigned long long use = reduce_arrive<1>(t, v);
@@ -575,43 +595,47 @@ __device__ __forceinline__ double bcast0(double v, double* slot) {
 }
 
 // Jacobi-preconditioned BiCGStab (van der Vorst 1992) on the scaled level system,
-// from x = 0; s shares storage with r. Stops when ||r||_2 <= max(eta ||bs||_2,
-// atol sqrt(Ns)). Scalars are formed by thread 0 and broadcast (FP64 division is
-// costly on this part). Returns the iteration count (< 0 on abort).
-template <int NT>
-__device__ int level_bicgstab(const TeamCtl& c, Team& t, const Smem& m, double eta, double atol, int* s_ok) {
+// from x = 0; s shares storage with r. Vectors in precision T, dot products and
+// recurrence scalars in FP64. Stops when ||r||_2 <= max(eta ||bs||_2, atol sqrt(Ns),
+// 16 eps_T ||bs||_2). Scalars are formed by thread 0 and broadcast (FP64 division
+// is costly on this part). Returns the iteration count (< 0 on abort).
+template <int NT, typename T>
+__device__ int level_bicgstab(const TeamCtl& c, Team& t, const Smem<T>& m, double eta, double atol, int* s_ok) {
     double* sb = m.red + 32;
     double* slot = m.red + 48;
     const int nloc = t.nloc;
     // r = bs, rh = bs, x = 0, p = v = 0
     double one[1] = {0.0};
     for (int k = threadIdx.x; k < nloc; k += NT) {
-        const double b = m.bs[k];
-        m.x[k] = 0.0;
+        const T b = m.bs[k];
+        m.x[k] = T(0);
         m.r[k] = b;
         m.rh[k] = b;
-        m.p[k] = 0.0;
-        m.v[k] = 0.0;
-        one[0] += b * b;
+        m.p[k] = T(0);
+        m.v[k] = T(0);
+        one[0] += (double)b * (double)b;
     }
     block_sum<NT, 1>(one, m.red);
     double g1[1];
     if (!reduce_finish<1, false>(c, t, reduce_arrive<1>(t, one), g1, sb, s_ok)) return -1;
     // thread 0 keeps the recurrence scalars; others receive what they need
     double tol = 0.0, rho_old = 1.0, alpha = 1.0, omega = 1.0, rho = g1[0];
-    if (threadIdx.x == 0) tol = fmax(eta * sqrt(g1[0]), atol * sqrt((double)t.Ns));
+    if (threadIdx.x == 0) {
+        const double bn = sqrt(g1[0]);
+        tol = fmax(fmax(eta * bn, atol * sqrt((double)t.Ns)), 16.0 * Eps<T>::value * bn);
+    }
     if (bcast0(threadIdx.x == 0 ? (sqrt(g1[0]) <= tol ? 1.0 : 0.0) : 0.0, slot) != 0.0) return 0;
     for (int it = 1; it <= c.max_iter; ++it) {
         double beta = 0.0;
         if (threadIdx.x == 0) beta = (rho / rho_old) * (alpha / omega);
-        beta = bcast0(beta, slot);
-        const double om_b = bcast0(omega, slot);
-        for (int k = threadIdx.x; k < nloc; k += NT) m.p[k] = m.r[k] + beta * (m.p[k] - om_b * m.v[k]);
+        const T beta_t = (T)bcast0(beta, slot);
+        const T om_b = (T)bcast0(omega, slot);
+        for (int k = threadIdx.x; k < nloc; k += NT) m.p[k] = m.r[k] + beta_t * (m.p[k] - om_b * m.v[k]);
         __syncthreads();
-        if (!exchange_halo<NT>(c, t, m.p, m.haloS, m.haloN, s_ok)) return -1;
-        local_spmv<NT>(t, m, m.p, m.v);
+        if (!exchange_halo<NT, T>(c, t, m.p, m.haloS, m.haloN, s_ok)) return -1;
+        local_spmv<NT, T>(t, m, m.p, m.v);
         double d1[1] = {0.0};
-        for (int k = threadIdx.x; k < nloc; k += NT) d1[0] += m.rh[k] * m.v[k];
+        for (int k = threadIdx.x; k < nloc; k += NT) d1[0] += (double)m.rh[k] * (double)m.v[k];
         block_sum<NT, 1>(d1, m.red);
         if (!reduce_finish<1, false>(c, t, reduce_arrive<1>(t, d1), d1, sb, s_ok)) return -1;
         // code: 0 go on, 1 NaN, 2 breakdown
@@ -626,28 +650,28 @@ __device__ int level_bicgstab(const TeamCtl& c, Team& t, const Smem& m, double e
             if (threadIdx.x == 0) atomicCAS(c.status, 0, code == 1.0 ? ST_EDIVERGED : ST_ENOCONV);
             return it;
         }
-        const double al_b = bcast0(alpha, slot);
+        const T al_b = (T)bcast0(alpha, slot);
         for (int k = threadIdx.x; k < nloc; k += NT) m.r[k] -= al_b * m.v[k];  // r holds s
         __syncthreads();
-        if (!exchange_halo<NT>(c, t, m.r, m.haloS, m.haloN, s_ok)) return -1;
-        local_spmv<NT>(t, m, m.r, m.t);
+        if (!exchange_halo<NT, T>(c, t, m.r, m.haloS, m.haloN, s_ok)) return -1;
+        local_spmv<NT, T>(t, m, m.r, m.t);
         double d2[2] = {0.0, 0.0};
         for (int k = threadIdx.x; k < nloc; k += NT) {
-            d2[0] += m.t[k] * m.r[k];
-            d2[1] += m.t[k] * m.t[k];
+            d2[0] += (double)m.t[k] * (double)m.r[k];
+            d2[1] += (double)m.t[k] * (double)m.t[k];
         }
         block_sum<NT, 2>(d2, m.red);
         if (!reduce_finish<2, false>(c, t, reduce_arrive<2>(t, d2), d2, sb, s_ok)) return -1;
         if (threadIdx.x == 0) omega = d2[1] > 0.0 ? d2[0] / d2[1] : 0.0;
-        const double om2 = bcast0(omega, slot);
+        const T om2 = (T)bcast0(omega, slot);
         double d3[2] = {0.0, 0.0};
         for (int k = threadIdx.x; k < nloc; k += NT) {
-            const double sk = m.r[k];
+            const T sk = m.r[k];
             m.x[k] += al_b * m.p[k] + om2 * sk;
-            const double rk = sk - om2 * m.t[k];
+            const T rk = sk - om2 * m.t[k];
             m.r[k] = rk;
-            d3[0] += m.rh[k] * rk;
-            d3[1] += rk * rk;
+            d3[0] += (double)m.rh[k] * (double)rk;
+            d3[1] += (double)rk * (double)rk;
         }
         block_sum<NT, 2>(d3, m.red);
         if (!reduce_finish<2, false>(c, t, reduce_arrive<2>(t, d3), d3, sb, s_ok)) return -1;
@@ -675,10 +699,14 @@ __device__ int level_bicgstab(const TeamCtl& c, Team& t, const Smem& m, double e
 // Solve the scaled level system in m with the method chosen from the level's
 // Gershgorin bound rho_g; SOR's omega = 2/(1 + sqrt(1 - rho^2)) is formed by
 // thread 0. Returns iterations (< 0 on abort) and the method used (1 SOR, 2 BiCGStab).
-template <int NT>
-__device__ __forceinline__ int level_solve(const TeamCtl& c, Team& t, const Smem& m, int method, double sor_rho_max,
-                                           double rho_g, double sor_tol, double eta, double atol, int* s_ok,
-                                           int* used) {
+// When some row has opposite-signed couplings in x or y (a cell Peclet number
+// above 2) the Jacobi spectrum may be complex and Young's omega may diverge; omega is
+// then capped below 2/(1 + rho), the bound under which SOR converges for any
+// strictly diagonally dominant matrix with Jacobi row sums <= rho.
+template <int NT, typename T>
+__device__ __forceinline__ int level_solve(const TeamCtl& c, Team& t, const Smem<T>& m, int method, double sor_rho_max,
+                                           double rho_g, bool nonsym, double sor_tol, double eta, double atol,
+                                           int* s_ok, int* used) {
     const bool use_sor = method == 1 || (method == 0 && rho_g < sor_rho_max);
     *used = use_sor ? 1 : 2;
     if (use_sor) {
@@ -686,16 +714,17 @@ __device__ __forceinline__ int level_solve(const TeamCtl& c, Team& t, const Smem
         if (threadIdx.x == 0 && rho_g < 1.0) {
             const double rc = fmin(rho_g, 0.999999);
             omega = 2.0 / (1.0 + sqrt(1.0 - rc * rc));
+            if (nonsym) omega = fmax(1.0, fmin(omega, 0.99 * 2.0 / (1.0 + rho_g)));
         }
         omega = bcast0(omega, m.red + 48);
-        return level_sor<NT>(c, t, m, omega, sor_tol, s_ok);
+        return level_sor<NT, T>(c, t, m, omega, sor_tol, s_ok);
     }
-    return level_bicgstab<NT>(c, t, m, eta, atol, s_ok);
+    return level_bicgstab<NT, T>(c, t, m, eta, atol, s_ok);
 }
 
 // Number of doubles of dynamic shared memory per CTA of chain_kernel.
 __host__ __device__ inline size_t chain_smem_doubles(int nloc, int nx) {
-    return (size_t)11 * nloc + 2 * (size_t)nx + 64;
+    return smem_red_offset<double>(nloc, nx) / sizeof(double) + 64;
 }
 
 struct ChainArgs {
@@ -704,7 +733,7 @@ struct ChainArgs {
     int rows_base, rows_rem;                // CTA b owns rows_base + (b < rows_rem) rows
     const double* R;                        // [M][Ns] right-hand sides r^n
     const double* coef;                     // [5][M][Ns] scaled planes (raw entries when RAW)
-    const unsigned long long* rho_key;      // [M] Gershgorin bound per level (unused when RAW)
+    const unsigned long long* rho_key;      // [2M] Gershgorin bound, then nonsymmetric-row flag, per level (unused when RAW)
     double* U;                              // [M][Ns] iterate, += dU when update_U
     double* dU;                             // [M][Ns] receives dU, or nullptr
     int update_U;
@@ -737,7 +766,7 @@ struct ChainArgs {
 // bound is formed by a team max-reduction.
 template <int NT, bool RAW = false>
 __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_ok;
     TeamCtl c{a.abort_flag, a.status, a.wait_budget, a.max_iter};
     Team t;
@@ -745,7 +774,7 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
     const unsigned long long t_start = global_ns();
     const int nloc = t.nloc;
     const int cap = (a.rows_base + (a.rows_rem ? 1 : 0)) * a.nx;  // largest nloc of the team
-    const Smem m = smem_layout(smem, cap, a.nx);
+    const Smem<double> m = smem_layout<double>(smem, cap, a.nx);
 
     const long long Ns = t.Ns;
     const long long plane = (long long)a.M * Ns;
@@ -761,6 +790,7 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
         const double* cd = a.coef + lo;
         // rhs b = r^n + du^{n-1}, scaled by 1/C; load the couplings
         double rho_g;
+        bool nonsym;
         if (!RAW) {
             for (int k = threadIdx.x; k < nloc; k += NT) {
                 const double d = cd[k];
@@ -774,8 +804,10 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
             }
             __syncthreads();
             rho_g = key_val(a.rho_key[n]);
+            nonsym = a.rho_key[a.M + n] != 0ull;
         } else {
             double rs = 0.0;
+            bool ns = false;
             for (int k = threadIdx.x; k < nloc; k += NT) {
                 const double d = 1.0 / cd[k];
                 const double w = cd[plane + k] * d, e = cd[2 * plane + k] * d;
@@ -788,12 +820,15 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
                 m.bs[k] = d * b;
                 m.x[k] = b;
                 rs = fmax(rs, fabs(w) + fabs(e) + fabs(sv) + fabs(nv));
+                ns |= (w * e < 0.0 || sv * nv < 0.0);
             }
-            unsigned long long key = block_max_u64<NT>(abs_key(rs), reinterpret_cast<unsigned long long*>(m.red));
-            double v[1] = {key_val(key)};
-            double g[1];
-            if (!reduce_finish<1, true>(c, t, reduce_arrive<1>(t, v), g, m.red + 32, &s_ok)) return;
+            double v[2];
+            v[0] = key_val(block_max_u64<NT>(abs_key(rs), reinterpret_cast<unsigned long long*>(m.red)));
+            v[1] = key_val(block_max_u64<NT>(ns ? abs_key(1.0) : 0ull, reinterpret_cast<unsigned long long*>(m.red)));
+            double g[2];
+            if (!reduce_finish<2, true>(c, t, reduce_arrive<2>(t, v), g, m.red + 32, &s_ok)) return;
             rho_g = g[0];
+            nonsym = g[1] != 0.0;
         }
         double sor_tol = a.sor_tol_abs;
         const bool sor_here = a.method == 1 || (a.method == 0 && rho_g < a.sor_rho_max);
@@ -808,7 +843,8 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
             sor_tol = fmax(a.eta * g[0], a.atol);
         }
         int used = 0;
-        const int iters = level_solve<NT>(c, t, m, a.method, a.sor_rho_max, rho_g, sor_tol, a.eta, a.atol, &s_ok, &used);
+        const int iters = level_solve<NT, double>(c, t, m, a.method, a.sor_rho_max, rho_g, nonsym, sor_tol, a.eta,
+                                                  a.atol, &s_ok, &used);
         if (iters < 0) return;  // aborted
         // du^n = x: update the iterate and keep x as du^{n-1} of the next level
         for (int k = threadIdx.x; k < nloc; k += NT) {
@@ -847,9 +883,12 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
 // from u^n_k (global, own and halo rows) and u^{n-1}_k (shared memory), then
 // solves A_n du^n = r^n + du^{n-1} (eq. 7 nested) and updates U^n. The iterates are
 // those of plain Newton; the forcing term uses the running max of ||r^j_k||_inf
-// over the levels j <= n seen so far. When a team finishes an iteration whose
-// residual max is <= tol_res it raises the stop flag; every team reads the flag in
-// its level-start team reduction, so all CTAs of a team stop at the same cell.
+// over the levels j <= n seen so far. Cell (k, n) is skipped (du^n_k = 0) when the
+// previous iteration's running max at level n is already <= tol_res: the levels
+// 0..n have converged and, the system being block lower-triangular in time, need
+// no further update. The rule depends only on finished cells, so the result is
+// the same on every run. When an iteration ends with a running max <= tol_res,
+// every later cell is a skip; the team raises a stop flag so the others leave early.
 struct WaveArgs {
     OpConst c;
     const double* u0;
@@ -873,18 +912,31 @@ struct WaveArgs {
     int* stop;                          // [0] stop flag, [1] first converged iteration
     // per iteration records, indexed by k
     double* res_inf;                    // [k_end] ||R_k||_inf
+    double* cell_prefix;                // [k_end][M] max_{j <= n} ||r^j_k||_inf (written by CTA 0 of the team)
     int* cell_iters;                    // [k_end][M] 1 + sweeps (SOR) or -(1 + iterations) (BiCGStab); 0 = not run
     double* cta_sumsq;                  // [k_end][G] sum of du_k^2 over the CTA's rows
     unsigned long long* timers;         // [K][4] CTA 0 of each team: halo, reduction, predecessor waits, total
 };
 
-__host__ __device__ inline size_t wave_smem_doubles(int cap, int nx) {
-    return (size_t)12 * cap + 2 * (size_t)nx + 64;
+// u^n_k with its halo rows ((cap + 2 nx) doubles) shares the BiCGStab scratch r..t
+// when it fits there; otherwise it follows uprev.
+template <typename T>
+__host__ __device__ inline bool wave_u_aliases(int cap, int nx) {
+    return (size_t)(cap + 2 * (size_t)nx) * sizeof(double) <= 5 * (size_t)cap * sizeof(T);
 }
 
-template <int NT, bool CONV, bool NLV>
+// Dynamic shared memory of wave_kernel<T>: solver arrays, halos, reduction area,
+// uprev (cap doubles) and, unless aliased, u.
+template <typename T>
+__host__ __device__ inline size_t wave_smem_bytes(int cap, int nx) {
+    size_t bytes = smem_red_offset<T>(cap, nx) + 64 * sizeof(double) + sizeof(double) * (size_t)cap;
+    if (!wave_u_aliases<T>(cap, nx)) bytes += sizeof(double) * (cap + 2 * (size_t)nx);
+    return bytes;
+}
+
+template <int NT, bool CONV, bool NLV, typename T = double>
 __global__ void __launch_bounds__(NT) wave_kernel(WaveArgs a) {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_ok;
     const OpConst& oc = a.c;
     const int nx = oc.nx, ny = oc.ny, M = oc.M;
@@ -898,9 +950,11 @@ __global__ void __launch_bounds__(NT) wave_kernel(WaveArgs a) {
     unsigned long long t_pred = 0;
     const int nloc = t.nloc;
     const int cap = (a.rows_base + (a.rows_rem ? 1 : 0)) * nx;
-    const Smem m = smem_layout(smem, cap, nx);
-    double* uprev = m.haloN + nx + 64;        // u^{n-1}_k, own rows (cap)
-    double* u = m.r;                          // u^n_k with one halo row each side: (nrows + 2) x nx, aliases r..t
+    const Smem<T> m = smem_layout<T>(smem, cap, nx);
+    // u^{n-1}_k, own rows (cap doubles), after the reduction area
+    double* uprev = reinterpret_cast<double*>(smem + smem_red_offset<T>(cap, nx) + 64 * sizeof(double));
+    // u^n_k with one halo row each side: (nrows + 2) x nx doubles
+    double* u = wave_u_aliases<T>(cap, nx) ? reinterpret_cast<double*>(m.r) : uprev + cap;
     const long long Ns = t.Ns;
     const long long off0 = (long long)t.r0 * nx;
     const int nb = 2 * nx + 2 * ny;
@@ -913,21 +967,25 @@ __global__ void __launch_bounds__(NT) wave_kernel(WaveArgs a) {
 
     for (int k = a.k_begin + team; k < a.k_end; k += a.K) {
         for (int i = threadIdx.x; i < nloc; i += NT) {
-            m.x[i] = 0.0;               // du^{-1} = 0
+            m.x[i] = T(0);              // du^{-1} = 0
             uprev[i] = a.u0[off0 + i];  // u^0
         }
         double prefix = 0.0;            // running max of ||r^j_k||_inf, j <= n (thread 0)
         double sumsq = 0.0;
+        bool uprev_valid = true;        // uprev holds u^{n-1}_k (false after a skipped level)
         __syncthreads();
         for (int n = 0; n < M; ++n) {
-            // 1. wait until iteration k - 1 has finished level n on rows r0-1 .. r0+nrows
+            // 1. wait until iteration k - 1 has finished level n on rows r0-1 .. r0+nrows and
+            //    on CTA 0 (which publishes its running residual max), then read that max
             if (threadIdx.x == 0) {
                 bool stop_seen = false;
+                double pred_prefix = 1.0 / 0.0;
                 if (k > a.k_begin) {
                     const unsigned long long target = (unsigned long long)(k - 1) * M + n + 1;
                     const unsigned long long t0 = global_ns();
-                    for (int nbr = b - 1; nbr <= b + 1 && !stop_seen; ++nbr) {
-                        if (nbr < 0 || nbr >= a.G) continue;
+                    for (int q = 0; q < 4 && !stop_seen; ++q) {
+                        const int nbr = q < 3 ? b - 1 + q : 0;
+                        if (nbr < 0 || nbr >= a.G || (q == 3 && b <= 1)) continue;
                         long long spins = 0;
                         while (ld_acquire_u64(pred_prog + nbr) < target) {
                             if (ld_acquire_s32(a.stop) || ld_acquire_s32(a.abort_flag)) {
@@ -944,16 +1002,46 @@ __global__ void __launch_bounds__(NT) wave_kernel(WaveArgs a) {
                     }
                     __threadfence();
                     t_pred += global_ns() - t0;
+                    if (!stop_seen) pred_prefix = __ldcg(a.cell_prefix + (size_t)(k - 1) * M + n);
                 }
                 s_ok = (stop_seen || ld_acquire_s32(a.stop) || ld_acquire_s32(a.abort_flag)) ? 1 : 0;
+                slot[0] = pred_prefix;
             }
             __syncthreads();
             const int stop_local = s_ok;
+            const double pred_prefix = slot[0];
             __syncthreads();
+            // every later cell is a skip once the stop flag is up (or the launch aborts)
+            if (stop_local) goto done;
+            if (pred_prefix <= a.tol_res) {
+                // levels 0..n converged in iteration k - 1: du^n_k = 0, nothing to solve
+                for (int i = threadIdx.x; i < nloc; i += NT) m.x[i] = T(0);
+                uprev_valid = false;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    prefix = pred_prefix;
+                    __threadfence();
+                    if (b == 0) {
+                        __stcg(a.cell_prefix + (size_t)k * M + n, prefix);
+                        a.cell_iters[(size_t)k * M + n] = 1;
+                        __threadfence();
+                    }
+                    st_release_u64(my_prog + b, (unsigned long long)k * M + n + 1);
+                }
+                continue;
+            }
+            if (!uprev_valid) {
+                // the previous level was skipped: u^{n-1}_k is the global (final) iterate
+                const double* up = n == 0 ? a.u0 + off0 : a.U + (long long)(n - 1) * Ns + off0;
+                for (int i = threadIdx.x; i < nloc; i += NT) uprev[i] = __ldcg(up + i);
+                uprev_valid = true;
+                __syncthreads();
+            }
             // 2. u^n_k: own rows and one halo row each side (Dirichlet data off the domain)
             const double* Un = a.U + (long long)n * Ns;
             const double* bnd = a.bc ? a.bc + (long long)n * nb : nullptr;
-            double rmax = 0.0, rs = 0.0;
+            double rmax = 0.0, rs = 0.0, bmax = 0.0;
+            bool ns = false;
             if (!stop_local) {
                 for (int i = threadIdx.x; i < (t.nrows + 2) * nx; i += NT) {
                     const int jr = i / nx, ii = i - jr * nx, j = t.r0 - 1 + jr;
@@ -987,33 +1075,34 @@ __global__ void __launch_bounds__(NT) wave_kernel(WaveArgs a) {
                     aE *= d;
                     aS *= d;
                     aN *= d;
-                    m.cw[i] = aW;
-                    m.ce[i] = aE;
-                    m.cs[i] = aS;
-                    m.cn[i] = aN;
-                    const double bval = r + m.x[i];  // r^n + du^{n-1}
-                    m.bs[i] = d * bval;
-                    m.x[i] = bval;                   // SOR start
-                    uprev[i] = uC;                   // u^n_k for the next level's time difference
+                    m.cw[i] = (T)aW;
+                    m.ce[i] = (T)aE;
+                    m.cs[i] = (T)aS;
+                    m.cn[i] = (T)aN;
+                    const double bval = r + (double)m.x[i];  // r^n + du^{n-1}
+                    m.bs[i] = (T)(d * bval);
+                    m.x[i] = (T)bval;                        // SOR start
+                    uprev[i] = uC;                           // u^n_k for the next level's time difference
                     rmax = fmax(rmax, fabs(r));
                     if (r != r) rmax = r;
                     rs = fmax(rs, fabs(aW) + fabs(aE) + fabs(aS) + fabs(aN));
+                    ns |= (aW * aE < 0.0 || aS * aN < 0.0);
+                    bmax = fmax(bmax, fabs(bval));
                 }
             }
-            // 4. team reduction: max |r|, Gershgorin bound, stop flag (consistent decisions)
-            double v3[3];
+            // 4. team reduction: max |r|, Gershgorin bound, 2 stop + nonsymmetric-row flag, max |rhs|
+            //    (every CTA of the team takes the same decisions from these)
+            const int flags_local = (stop_local ? 2 : 0) + (ns ? 1 : 0);
+            double v3[4];
             v3[0] = key_val(block_max_u64<NT>(abs_key(rmax), reinterpret_cast<unsigned long long*>(m.red)));
             v3[1] = key_val(block_max_u64<NT>(abs_key(rs), reinterpret_cast<unsigned long long*>(m.red)));
-            v3[2] = stop_local ? 1.0 : 0.0;
-            double g3[3];
-            if (!reduce_finish<3, true>(c, t, reduce_arrive<3>(t, v3), g3, m.red + 32, &s_ok)) return;
-            if (g3[2] != 0.0) goto done;  // another iteration has converged (or the launch aborts)
+            v3[2] = key_val(block_max_u64<NT>(abs_key((double)flags_local), reinterpret_cast<unsigned long long*>(m.red)));
+            v3[3] = key_val(block_max_u64<NT>(abs_key(bmax), reinterpret_cast<unsigned long long*>(m.red)));
+            double g3[4];
+            if (!reduce_finish<4, true>(c, t, reduce_arrive<4>(t, v3), g3, m.red + 32, &s_ok)) return;
+            if (g3[2] >= 2.0) goto done;  // another iteration has converged (or the launch aborts)
             if (g3[0] != g3[0]) {
-                if (threadIdx.x == 0) {
-                    atomicCAS(a.status, 0, ST_EDIVERGED);
-                    __threadfence();
-                    atomicExch(a.stop, 1);
-                }
+                if (threadIdx.x == 0) team_fail(c, ST_EDIVERGED);
                 goto done;
             }
             {
@@ -1022,26 +1111,30 @@ __global__ void __launch_bounds__(NT) wave_kernel(WaveArgs a) {
                 if (threadIdx.x == 0) {
                     prefix = fmax(prefix, g3[0]);
                     eta = fmax(fmin(a.eta_max, a.eta_gamma * prefix), 1e-300);
-                    sor_tol = fmax(a.atol, eta * prefix);
+                    // absolute, not below the level-solve precision's round-off of the rhs
+                    sor_tol = fmax(fmax(a.atol, eta * prefix), 16.0 * Eps<T>::value * g3[3]);
                 }
                 eta = bcast0(eta, slot);
                 sor_tol = bcast0(sor_tol, slot);
                 int used = 0;
-                const int iters = level_solve<NT>(c, t, m, a.method, a.sor_rho_max, g3[1], sor_tol, eta, a.atol,
-                                                  &s_ok, &used);
+                const int iters = level_solve<NT, T>(c, t, m, a.method, a.sor_rho_max, g3[1], g3[2] != 0.0, sor_tol,
+                                                     eta, a.atol, &s_ok, &used);
                 if (iters < 0) return;  // aborted
                 // 6. U^n += du^n; du^n stays in x for the next level
                 double* Uw = a.U + (long long)n * Ns + off0;
                 for (int i = threadIdx.x; i < nloc; i += NT) {
-                    const double dx = m.x[i];
+                    const double dx = (double)m.x[i];
                     __stcg(Uw + i, uprev[i] + dx);
                     sumsq += dx * dx;
                 }
                 __syncthreads();
                 if (threadIdx.x == 0) {
+                    if (b == 0) {
+                        __stcg(a.cell_prefix + (size_t)k * M + n, prefix);
+                        a.cell_iters[(size_t)k * M + n] = used == 1 ? iters + 1 : -(iters + 1);
+                    }
                     __threadfence();
                     st_release_u64(my_prog + b, (unsigned long long)k * M + n + 1);
-                    if (b == 0) a.cell_iters[(size_t)k * M + n] = used == 1 ? iters + 1 : -(iters + 1);
                     if (iters >= c.max_iter) atomicCAS(a.status, 0, ST_ENOCONV);
                 }
             }

@@ -20,6 +20,7 @@ from . import build as _build
 PIT_OK, PIT_EINVAL, PIT_ECUDA, PIT_ENOMEM, PIT_ENOCONV, PIT_EDIVERGED, PIT_ETIMEOUT, PIT_EUNSUPPORTED = range(8)
 PIT_HEAT, PIT_BURGERS = 0, 1
 PIT_LIN_AUTO, PIT_LIN_SOR, PIT_LIN_BICGSTAB = 0, 1, 2
+PIT_FP64, PIT_FP32_INNER = 0, 1
 PIT_MAX_NEWTON = 64
 PIT_NOALLOC_MAX_NX, PIT_NOALLOC_MAX_TEAM, PIT_NOALLOC_MAX_LEVELS = 512, 160, 4096
 
@@ -42,7 +43,8 @@ class pit_options(ctypes.Structure):
     _fields_ = [("newton_max", ctypes.c_int), ("tol_res", ctypes.c_double), ("lin_solver", ctypes.c_int),
                 ("eta_max", ctypes.c_double), ("eta_gamma", ctypes.c_double), ("lin_atol", ctypes.c_double),
                 ("lin_max_iter", ctypes.c_int), ("sor_rho_max", ctypes.c_double), ("team_ctas", ctypes.c_int),
-                ("wait_budget", ctypes.c_longlong), ("wave_teams", ctypes.c_int)]
+                ("wait_budget", ctypes.c_longlong), ("wave_teams", ctypes.c_int), ("precision", ctypes.c_int),
+                ("window", ctypes.c_int)]
 
 
 class pit_step_info(ctypes.Structure):
@@ -60,7 +62,8 @@ class pit_solve_info(ctypes.Structure):
                 ("res_inf", ctypes.c_double * (PIT_MAX_NEWTON + 1)), ("steps", pit_step_info * PIT_MAX_NEWTON),
                 ("ms_total", ctypes.c_double), ("wave_teams", ctypes.c_int), ("wave_team_ctas", ctypes.c_int),
                 ("wave_launches", ctypes.c_int), ("ms_wave", ctypes.c_float), ("us_pred_wait", ctypes.c_float),
-                ("us_halo_wait", ctypes.c_float), ("us_reduce_wait", ctypes.c_float)]
+                ("us_halo_wait", ctypes.c_float), ("us_reduce_wait", ctypes.c_float), ("windows", ctypes.c_int),
+                ("newton_iters_total", ctypes.c_int)]
 
     def as_dict(self):
         k = self.newton_iters
@@ -68,7 +71,8 @@ class pit_solve_info(ctypes.Structure):
                 "steps": [self.steps[i].as_dict() for i in range(k)], "ms_total": self.ms_total,
                 "wave_teams": self.wave_teams, "wave_team_ctas": self.wave_team_ctas,
                 "wave_launches": self.wave_launches, "ms_wave": self.ms_wave, "us_pred_wait": self.us_pred_wait,
-                "us_halo_wait": self.us_halo_wait, "us_reduce_wait": self.us_reduce_wait}
+                "us_halo_wait": self.us_halo_wait, "us_reduce_wait": self.us_reduce_wait, "windows": self.windows,
+                "newton_iters_total": self.newton_iters_total}
 
 
 class PitError(RuntimeError):

@@ -245,3 +245,74 @@ def test_wavefront_iterates_equal_classic_newton_iterates():
             pit.pit_solve(ctx, U, check=False)
             outs.append(U.cpu().numpy())
     np.testing.assert_allclose(outs[1], outs[0], rtol=0, atol=1e-11 * np.abs(outs[0]).max())
+
+
+def _window_residual(p, U, start, count):
+    """Oracle residual of levels start..start+count-1 of U (level n depends only on U[n-1], U[n])."""
+    u_prev = p.u0 if start == 0 else U[start - 1]
+    sub = W.Problem("window", p.grid, p.params, count, p.dt, np.ascontiguousarray(u_prev),
+                    None if p.bc is None else np.ascontiguousarray(p.bc[start:start + count]),
+                    None if p.q is None else np.ascontiguousarray(p.q[start:start + count]))
+    return oracle.residual(sub.grid, sub.params, count, sub.dt, sub.u0, U[start:start + count], sub.bc, sub.q)
+
+
+MIXED_CASES = [
+    (lambda: W.heat32(2), "heat32s2"),
+    (lambda: W.random_problem(41, 33, 29, 6, W.BURGERS, with_bc=True, with_q=True), "burg33x29"),
+    (lambda: W.truncated(W.burgers256(0), 4), "b256[:4]"),
+    (lambda: W.truncated(W.burgers512(0), 2), "b512[:2]"),
+]
+
+
+@pytest.mark.parametrize("make,name", MIXED_CASES, ids=[c[1] for c in MIXED_CASES])
+def test_fp32_inner_solves_reach_the_fp64_solution(make, name):
+    # f1: level solves in FP32 inside FP64 Newton; the converged iterate must still
+    # satisfy the FP64 system to 1e-12 and match the FP64 oracle to 1e-10
+    p = make()
+    Uo, _, _, _ = oracle.solve(p, tol=1e-13)
+    opt = pit.pit_default_options()
+    opt.precision = pit.PIT_FP32_INNER
+    with pit.context_for(p, opt) as ctx:
+        U = torch.empty(p.dof, dtype=torch.float64, device="cuda")
+        pit.pit_fill_plain_guess(ctx, U)
+        status, info = pit.pit_solve(ctx, U)
+        Ug = U.cpu().numpy().reshape(p.M, -1)
+    assert info["converged"] and info["res_inf"][-1] <= 1e-12
+    assert np.abs(Ug - Uo).max() <= 1e-10 * np.abs(Uo).max()
+
+
+def test_fp32_inner_full_size_burgers512():
+    # the mixed-precision workload at full size (512 x 512, M = 1024, windows of 32
+    # levels): first levels against the oracle, and the oracle's residual on level
+    # windows across the range
+    p = W.burgers512(0)
+    opt = pit.pit_default_options()
+    opt.precision = pit.PIT_FP32_INNER
+    opt.window = 32
+    with pit.context_for(p, opt) as ctx:
+        U = torch.empty(p.dof, dtype=torch.float64, device="cuda")
+        pit.pit_fill_plain_guess(ctx, U)
+        status, info = pit.pit_solve(ctx, U)
+        Ug = U.cpu().numpy().reshape(p.M, -1)
+    assert info["converged"]
+    Uo, _, _, _ = oracle.solve(W.truncated(p, 2), tol=1e-13)
+    assert np.abs(Ug[:2] - Uo).max() <= 1e-10 * np.abs(Uo).max()
+    for start in (0, 511, 1020):
+        assert np.abs(_window_residual(p, Ug, start, 4)).max() <= 2e-12
+
+
+@pytest.mark.parametrize("window,teams,prec", [(1, 0, 0), (3, 2, 0), (4, 0, 1), (7, 3, 1)])
+def test_windowed_solve_matches_oracle(window, teams, prec):
+    # the all-at-once system is block lower-triangular in time: solving it window by
+    # window gives the same solution
+    p = W.random_problem(51, 27, 31, 9, W.BURGERS, with_bc=True, with_q=True)
+    Uo, _, _, _ = oracle.solve(p, tol=1e-13)
+    opt = pit.pit_default_options()
+    opt.window, opt.wave_teams, opt.precision = window, teams, prec
+    with pit.context_for(p, opt) as ctx:
+        U = torch.empty(p.dof, dtype=torch.float64, device="cuda")
+        pit.pit_fill_plain_guess(ctx, U)
+        status, info = pit.pit_solve(ctx, U)
+        Ug = U.cpu().numpy().reshape(p.M, -1)
+    assert info["converged"] and info["windows"] == -(-p.M // window)
+    assert np.abs(Ug - Uo).max() <= 1e-10 * np.abs(Uo).max()
