@@ -233,10 +233,48 @@ def run_ours(args, ws, rank, local):
                          "peak_source": "FP64 nominal 1.25 TFLOP/s (profiling recipe); FP64 not in MEASURED_PEAKS"},
             "clocks": clk.summary(),
         }
+        if args.variants:
+            out["variants"] = variants(args)
         if args.cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args)
     if ws > 1:
         torch.distributed.destroy_process_group()
+    return out
+
+
+def variants(args):
+    """The other forms of the metric on this GPU: FP32 level solves in FP64 Newton on the same
+    workload, and the discontinuous 512 x 512, M = 1024 workload (FP32 inner, windows of 32)."""
+    import torch
+    from paper_2406_00878_gb300 import pit
+    from paper_2406_00878_gb300 import workloads as W
+    out = {}
+    cases = [("mixed_fp32_inner", W.burgers256(seed=0, M=args.levels), 0, 3),
+             ("burgers512_mixed_window32", W.burgers512(seed=0), 32, 1)]
+    for name, p, window, steps in cases:
+        opt = pit.pit_default_options()
+        opt.precision = pit.PIT_FP32_INNER
+        opt.window = window
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            ctx = pit.context_for(p, opt, stream=stream)
+            U = torch.empty(p.dof, dtype=torch.float64, device="cuda")
+            for _ in range(2):
+                pit.pit_fill_plain_guess(ctx, U)
+                pit.pit_solve(ctx, U)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                pit.pit_fill_plain_guess(ctx, U)
+                _, info = pit.pit_solve(ctx, U)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            ctx.close()
+        out[name] = {"value": p.dof / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "dof": p.dof,
+                     "workload": p.name, "M": p.M, "window": window, "precision": "fp32 level solves / fp64 newton",
+                     "newton_iters_total": info["newton_iters_total"], "res_inf_final": info["res_inf"][-1],
+                     "wave_teams": info["wave_teams"], "ctas_per_team": info["wave_team_ctas"]}
     return out
 
 
@@ -289,10 +327,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--levels", type=int, default=256)
-    ap.add_argument("--cpu-levels", type=int, default=48)
+    ap.add_argument("--cpu-levels", type=int, default=160)
     ap.add_argument("--ref-levels", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-check", dest="check", action="store_false")
+    ap.add_argument("--no-variants", dest="variants", action="store_false")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":

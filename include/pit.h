@@ -207,6 +207,55 @@ pit_status pit_solve(pit_ctx* ctx, double* U_dev, pit_solve_info* info);
  * the boundary data and sources set by pit_set_data are kept. */
 pit_status pit_solve_host(pit_ctx* ctx, const double* u0_host, double* U_host, pit_solve_info* info);
 
+/* ----------------------------------------------------------- batched solves
+ * Many independent problems (grids, level counts, closures and viscosities may
+ * all differ) solved in ONE persistent cooperative launch. Each problem is solved
+ * by a team of CTAs (the level chain of eq. 7 with Newton iterations until its
+ * residual is <= tol_res, in windows of opt->window levels, default 32); teams of
+ * different sizes run side by side on the GPU. pit_batch_create picks every
+ * problem's team size with an autotuner (short timed runs of each distinct grid
+ * size at candidate team sizes; opt->team_ctas > 0 fixes it instead) and
+ * list-schedules the teams over the SMs, longest first. pit_batch_solve replays
+ * the launch as a captured CUDA graph after its first call; the batch works on a
+ * stream of its own, ordered after the caller's `stream` at every solve, and
+ * returns when the solve is complete. Level solves follow opt->precision
+ * (PIT_FP32_INNER is the intended use). */
+typedef struct pit_batch pit_batch;
+
+typedef struct {
+    pit_grid grid;
+    int M;
+    double dt;
+    pit_params params;
+    const double* u0_dev;   /* [Ns] initial data (required) */
+    const double* bc_dev;   /* [M][2nx+2ny] Dirichlet data or NULL */
+    const double* q_dev;    /* [M][Ns] source or NULL */
+    double* U_dev;          /* [M][Ns] out: the solution (its input content is ignored; every
+                               window starts from the plain guess at its first level) */
+} pit_instance;             /* all pointers caller-owned, valid until pit_batch_destroy */
+
+typedef struct {
+    int count;              /* problems */
+    int ctas;               /* CTAs of the persistent launch */
+    int teams;              /* teams (one per problem) */
+    int min_team, max_team; /* team sizes chosen */
+    int converged;          /* problems whose final ||R||_inf <= tol_res */
+    int graph;              /* 1 when the launch was replayed from a CUDA graph */
+    double ms;              /* device time of the launch */
+    double est_makespan_ms; /* the schedule's estimate from the autotuner's timings */
+    double ms_tuning;       /* host time spent in pit_batch_create's autotuner */
+} pit_batch_info;
+
+pit_status pit_batch_create(const pit_instance* inst, int count, const pit_options* opt, void* stream,
+                            pit_batch** out);
+pit_status pit_batch_solve(pit_batch* batch, pit_batch_info* info);
+/* Results of problem i after pit_batch_solve: final ||R||_inf of U (FP64), Newton
+ * updates summed over windows, and the number of windows that converged. */
+pit_status pit_batch_result(const pit_batch* batch, int i, double* res_inf, int* newton_iters, int* windows_converged,
+                            int* team_ctas);
+const char* pit_batch_last_error(const pit_batch* batch);
+void pit_batch_destroy(pit_batch* batch);
+
 /* Limits of pit_block_solve_noalloc's built-in workspace. */
 #define PIT_NOALLOC_MAX_NX 512       /* interior nodes per grid row */
 #define PIT_NOALLOC_MAX_TEAM 160     /* CTAs sharing one level */

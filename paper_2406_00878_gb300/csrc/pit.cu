@@ -633,6 +633,7 @@ static pit_status run_wave(pit_ctx* ctx, int s, int Mw, double* Uall, int k_begi
     a.abort_flag = ctx->w_ints;
     a.status = ctx->w_ints + 1;
     a.stop = ctx->w_ints + 2;
+    a.kconv = nullptr;
     a.res_inf = ctx->w_res;
     a.cell_prefix = ctx->w_prefix;
     a.cell_iters = ctx->w_cell;

@@ -1,0 +1,534 @@
+// pit_batch.cu -- many independent problems in one persistent cooperative launch.
+//
+// Each problem gets a team of CTAs that runs the level chain (nested block inverse
+// of eq. 7) with Newton iterations per window of levels until the window's residual
+// is below tol_res, then a final FP64 residual pass (batch_kernel in pit_kernels.cuh).
+// Here: the autotuner that picks a team size per problem from short timed runs, the
+// list schedule that places the teams on the SMs, the workspace pools, and the
+// launch, which is captured once into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <vector>
+
+#include "pit.h"
+#include "pit_kernels.cuh"
+
+using namespace pit;
+
+namespace {
+constexpr int kNT = 256;
+constexpr int kMaxTeam = 160;
+}
+
+struct pit_batch {
+    int count = 0;
+    pit_options opt{};
+    cudaStream_t stream = nullptr;       // the batch's own stream (capturable)
+    cudaStream_t user_stream = nullptr;  // the caller's stream: the batch's work is ordered after it
+    cudaEvent_t ev_user = nullptr;
+    int num_sms = 0;
+    size_t dyn_max = 0;
+    bool fp32 = false;
+    std::vector<pit_instance> in;
+    std::vector<int> team_of;          // team size per problem
+    // device data
+    BatchInstance* d_inst = nullptr;
+    BatchJob* d_jobs = nullptr;
+    int* d_job_off = nullptr;
+    BatchTeamWs* d_ws = nullptr;
+    unsigned char* pool = nullptr;     // team workspaces
+    size_t pool_bytes = 0, sync_bytes = 0;  // sync region (zeroed per launch) at the start of the pool
+    double* d_res = nullptr;
+    int* d_iters = nullptr;            // [count] iters, [count] converged windows
+    int* d_ctl = nullptr;              // abort, status
+    int ctas = 0;
+    size_t smem = 0;
+    // results (pinned)
+    double* h_res = nullptr;
+    int* h_iters = nullptr;
+    int* h_ctl = nullptr;
+    // graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool graph_ok = true;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double est_ms = 0.0, ms_tuning = 0.0;
+    int min_team = 0, max_team = 0;
+    char err[512] = "";
+};
+
+static pit_status bfail(pit_batch* b, pit_status s, const char* fmt, ...) {
+    if (b) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(b->err, sizeof(b->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+#define BCK(call)                                                                                          \
+    do {                                                                                                   \
+        cudaError_t e_ = (call);                                                                           \
+        if (e_ != cudaSuccess)                                                                             \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? PIT_ENOMEM : PIT_ECUDA, "%s: %s (%s:%d)", #call, \
+                         cudaGetErrorString(e_), __FILE__, __LINE__);                                      \
+    } while (0)
+
+#define BRET(expr)                  \
+    do {                            \
+        pit_status s_ = (expr);     \
+        if (s_ != PIT_OK) return s_; \
+    } while (0)
+
+static const void* batch_fn(bool fp32) {
+    return fp32 ? reinterpret_cast<const void*>(batch_kernel<kNT, float>)
+                : reinterpret_cast<const void*>(batch_kernel<kNT, double>);
+}
+
+static size_t team_smem(bool fp32, int nx, int ny, int G) {
+    const int rows = (ny + G - 1) / G;
+    return fp32 ? wave_smem_bytes<float>(rows * nx, nx) : wave_smem_bytes<double>(rows * nx, nx);
+}
+
+// Bytes of one team's workspace: sync part (flags, red_cnt, prog, kconv) and data part.
+struct WsSize {
+    size_t sync, data;
+};
+static WsSize ws_size(int G, int nx, int newton_max, int window) {
+    WsSize w;
+    w.sync = align_up(sizeof(unsigned long long) * ((size_t)G * 2 + 4) + sizeof(int) * 4, 256);
+    w.data = align_up(sizeof(double) * ((size_t)2 * G * 2 * nx + (size_t)4 * G * 4 + (size_t)newton_max * window), 256);
+    return w;
+}
+
+struct Job {
+    int inst, G;
+    double start, dur;
+    std::vector<int> ctas;
+};
+
+// Build jobs, workspace and device descriptors for team sizes `team` (per problem)
+// and problems `which` (calibration runs use a subset with truncated levels).
+static pit_status build_launch(pit_batch* b, const std::vector<pit_instance>& in, const std::vector<int>& team,
+                               const std::vector<double>& cost) {
+    const int n = (int)in.size();
+    const int P = b->num_sms;
+    // list schedule, longest first: each team takes the G CTAs that free up earliest
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] * 1 > cost[c] * 1; });
+    std::vector<double> free_at(P, 0.0);
+    std::vector<Job> jobs;
+    for (int i : order) {
+        std::vector<int> idx(P);
+        std::iota(idx.begin(), idx.end(), 0);
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return free_at[a] < free_at[c]; });
+        Job j;
+        j.inst = i;
+        j.G = team[i];
+        j.ctas.assign(idx.begin(), idx.begin() + team[i]);
+        std::sort(j.ctas.begin(), j.ctas.end());
+        double start = 0.0;
+        for (int c : j.ctas) start = std::max(start, free_at[c]);
+        j.start = start;
+        j.dur = cost[i];
+        for (int c : j.ctas) free_at[c] = start + cost[i];
+        jobs.push_back(j);
+    }
+    b->est_ms = *std::max_element(free_at.begin(), free_at.end());
+    // CTAs used and their job lists, in the global (assignment) order
+    int used = 0;
+    for (const Job& j : jobs)
+        for (int c : j.ctas) used = std::max(used, c + 1);
+    std::vector<std::vector<BatchJob>> per(used);
+    std::vector<WsSize> wss(jobs.size());
+    size_t sync_total = 0, data_total = 0;
+    const int W = b->opt.window > 0 ? b->opt.window : 32;
+    for (size_t q = 0; q < jobs.size(); ++q) {
+        const pit_instance& I = in[jobs[q].inst];
+        wss[q] = ws_size(jobs[q].G, I.grid.nx, b->opt.newton_max, std::min(W, I.M));
+        sync_total += wss[q].sync;
+        data_total += wss[q].data;
+        for (int r = 0; r < jobs[q].G; ++r) per[jobs[q].ctas[r]].push_back(BatchJob{jobs[q].inst, r, jobs[q].G, (int)q});
+    }
+    // device buffers (freed and rebuilt for every build)
+    cudaFree(b->pool);
+    cudaFree(b->d_jobs);
+    cudaFree(b->d_job_off);
+    cudaFree(b->d_ws);
+    cudaFree(b->d_inst);
+    b->pool = nullptr;
+    b->pool_bytes = sync_total + data_total;
+    b->sync_bytes = sync_total;
+    BCK(cudaMalloc(&b->pool, b->pool_bytes));
+    std::vector<BatchTeamWs> ws(jobs.size());
+    size_t so = 0, dof = sync_total;
+    for (size_t q = 0; q < jobs.size(); ++q) {
+        const int G = jobs[q].G, nx = in[jobs[q].inst].grid.nx;
+        unsigned long long* sw = reinterpret_cast<unsigned long long*>(b->pool + so);
+        ws[q].flags = sw;
+        ws[q].prog = sw + G;
+        ws[q].red_cnt = sw + 2 * G;
+        ws[q].kconv = reinterpret_cast<int*>(sw + 2 * G + 4);
+        so += wss[q].sync;
+        double* dw = reinterpret_cast<double*>(b->pool + dof);
+        ws[q].pub = dw;
+        ws[q].red_part = dw + (size_t)2 * G * 2 * nx;
+        ws[q].cell_prefix = ws[q].red_part + (size_t)4 * G * 4;
+        dof += wss[q].data;
+    }
+    std::vector<BatchJob> flat;
+    std::vector<int> off(used + 1, 0);
+    for (int c = 0; c < used; ++c) {
+        off[c] = (int)flat.size();
+        flat.insert(flat.end(), per[c].begin(), per[c].end());
+    }
+    off[used] = (int)flat.size();
+    std::vector<BatchInstance> bi(n);
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i) {
+        const pit_instance& I = in[i];
+        const double hx = (I.grid.xr - I.grid.xl) / (I.grid.nx + 1), hy = (I.grid.yr - I.grid.yl) / (I.grid.ny + 1);
+        OpConst& c = bi[i].c;
+        c.nx = I.grid.nx;
+        c.ny = I.grid.ny;
+        c.M = I.M;
+        c.Ns = (long long)I.grid.nx * I.grid.ny;
+        c.dt = I.dt;
+        c.cx = I.dt / (4.0 * hx);
+        c.cy = I.dt / (4.0 * hy);
+        c.jx = I.dt / (2.0 * hx);
+        c.jy = I.dt / (2.0 * hy);
+        c.vx = I.dt / (hx * hx);
+        c.vy = I.dt / (hy * hy);
+        c.mu_a = I.params.mu_a;
+        c.mu_b = I.params.mu_b;
+        bi[i].conv = I.params.equation == PIT_BURGERS;
+        bi[i].nlv = I.params.mu_b != 0.0;
+        bi[i].window = std::min(W, I.M);
+        bi[i].u0 = I.u0_dev;
+        bi[i].bc = I.bc_dev;
+        bi[i].q = I.q_dev;
+        bi[i].U = I.U_dev;
+        bi[i].res_inf = b->d_res + i;
+        bi[i].newton_iters = b->d_iters + i;
+        bi[i].converged_windows = b->d_iters + b->count + i;
+        smem = std::max(smem, team_smem(b->fp32, I.grid.nx, I.grid.ny, team[i]));
+    }
+    b->smem = smem;
+    b->ctas = used;
+    BCK(cudaMalloc(&b->d_inst, sizeof(BatchInstance) * n));
+    BCK(cudaMalloc(&b->d_jobs, sizeof(BatchJob) * std::max<size_t>(flat.size(), 1)));
+    BCK(cudaMalloc(&b->d_job_off, sizeof(int) * (used + 1)));
+    BCK(cudaMalloc(&b->d_ws, sizeof(BatchTeamWs) * std::max<size_t>(ws.size(), 1)));
+    BCK(cudaMemcpy(b->d_inst, bi.data(), sizeof(BatchInstance) * n, cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(b->d_jobs, flat.data(), sizeof(BatchJob) * flat.size(), cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(b->d_job_off, off.data(), sizeof(int) * (used + 1), cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(b->d_ws, ws.data(), sizeof(BatchTeamWs) * ws.size(), cudaMemcpyHostToDevice));
+    b->min_team = *std::min_element(team.begin(), team.end());
+    b->max_team = *std::max_element(team.begin(), team.end());
+    return PIT_OK;
+}
+
+static pit_status enqueue_launch(pit_batch* b, bool timed) {
+    BCK(cudaMemsetAsync(b->pool, 0, b->sync_bytes, b->stream));
+    BCK(cudaMemsetAsync(b->d_ctl, 0, sizeof(int) * 2, b->stream));
+    BatchArgs a{};
+    a.inst = b->d_inst;
+    a.jobs = b->d_jobs;
+    a.job_off = b->d_job_off;
+    a.ws = b->d_ws;
+    a.abort_flag = b->d_ctl;
+    a.status = b->d_ctl + 1;
+    a.newton_max = b->opt.newton_max;
+    a.tol_res = b->opt.tol_res;
+    a.eta_max = b->opt.eta_max;
+    a.eta_gamma = b->opt.eta_gamma;
+    a.atol = b->opt.lin_atol;
+    a.sor_rho_max = b->opt.sor_rho_max;
+    a.method = b->opt.lin_solver;
+    a.max_iter = b->opt.lin_max_iter;
+    a.wait_budget = b->opt.wait_budget;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(b->ctas);
+    cfg.blockDim = dim3(kNT);
+    cfg.dynamicSmemBytes = b->smem;
+    cfg.stream = b->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (timed) BCK(cudaEventRecord(b->e0, b->stream));
+    if (b->fp32) BCK(cudaLaunchKernelEx(&cfg, batch_kernel<kNT, float>, a));
+    else BCK(cudaLaunchKernelEx(&cfg, batch_kernel<kNT, double>, a));
+    if (timed) BCK(cudaEventRecord(b->e1, b->stream));
+    BCK(cudaMemcpyAsync(b->h_res, b->d_res, sizeof(double) * b->count, cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaMemcpyAsync(b->h_iters, b->d_iters, sizeof(int) * 2 * b->count, cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(int) * 2, cudaMemcpyDeviceToHost, b->stream));
+    return PIT_OK;
+}
+
+static pit_status run_direct(pit_batch* b, double* ms) {
+    BRET(enqueue_launch(b, true));
+    BCK(cudaStreamSynchronize(b->stream));
+    float f = 0.f;
+    BCK(cudaEventElapsedTime(&f, b->e0, b->e1));
+    *ms = f;
+    if (b->h_ctl[1] == ST_ETIMEOUT) return bfail(b, PIT_ETIMEOUT, "batch kernel: a device wait ran out of budget");
+    if (b->h_ctl[1] == ST_EDIVERGED) return bfail(b, PIT_EDIVERGED, "batch kernel: NaN/Inf in a problem");
+    return PIT_OK;
+}
+
+extern "C" pit_status pit_batch_create(const pit_instance* inst, int count, const pit_options* opt, void* stream,
+                                       pit_batch** out) {
+    if (!out) return PIT_EINVAL;
+    *out = nullptr;
+    if (!inst || count < 1) return PIT_EINVAL;
+    pit_batch* b = new (std::nothrow) pit_batch();
+    if (!b) return PIT_ENOMEM;
+    pit_default_options(&b->opt);
+    if (opt) b->opt = *opt;
+    if (b->opt.window <= 0) b->opt.window = 32;
+    b->count = count;
+    b->user_stream = static_cast<cudaStream_t>(stream);
+    b->fp32 = b->opt.precision == PIT_FP32_INNER;
+    b->in.assign(inst, inst + count);
+    const auto t_start = std::chrono::steady_clock::now();
+    auto setup = [&]() -> pit_status {
+        if (b->opt.newton_max < 1 || b->opt.newton_max > PIT_MAX_NEWTON || b->opt.lin_max_iter < 1 ||
+            b->opt.wait_budget < 1 || b->opt.team_ctas < 0)
+            return bfail(b, PIT_EINVAL, "invalid options");
+        for (int i = 0; i < count; ++i) {
+            const pit_instance& I = inst[i];
+            if (I.grid.nx < 1 || I.grid.ny < 1 || I.M < 1 || !(I.dt > 0.0) || !(I.grid.xr > I.grid.xl) ||
+                !(I.grid.yr > I.grid.yl) || !I.u0_dev || !I.U_dev || !(I.params.mu_a >= 0.0) ||
+                !(I.params.mu_b >= 0.0) || (I.params.equation != PIT_HEAT && I.params.equation != PIT_BURGERS))
+                return bfail(b, PIT_EINVAL, "problem %d: invalid grid, levels, step, parameters or pointers", i);
+        }
+        int dev = 0, optin = 0, coop = 0;
+        BCK(cudaGetDevice(&dev));
+        BCK(cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev));
+        BCK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        BCK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        if (!coop) return bfail(b, PIT_EUNSUPPORTED, "device lacks cooperative launch");
+        cudaFuncAttributes fa;
+        BCK(cudaFuncGetAttributes(&fa, batch_fn(b->fp32)));
+        b->dyn_max = (size_t)optin - fa.sharedSizeBytes;
+        BCK(cudaFuncSetAttribute(batch_fn(b->fp32), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->dyn_max));
+        int per = 0;
+        BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_fn(b->fp32), kNT, b->dyn_max));
+        if (per < 1) return bfail(b, PIT_EUNSUPPORTED, "batch kernel does not fit on an SM");
+        BCK(cudaMalloc(&b->d_res, sizeof(double) * count));
+        BCK(cudaMalloc(&b->d_iters, sizeof(int) * 2 * count));
+        BCK(cudaMalloc(&b->d_ctl, sizeof(int) * 2));
+        BCK(cudaMallocHost(&b->h_res, sizeof(double) * count));
+        BCK(cudaMallocHost(&b->h_iters, sizeof(int) * 2 * count));
+        BCK(cudaMallocHost(&b->h_ctl, sizeof(int) * 2));
+        BCK(cudaEventCreate(&b->e0));
+        BCK(cudaEventCreate(&b->e1));
+        BCK(cudaEventCreateWithFlags(&b->ev_user, cudaEventDisableTiming));
+        BCK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        BCK(cudaEventRecord(b->ev_user, b->user_stream));
+        BCK(cudaStreamWaitEvent(b->stream, b->ev_user, 0));
+        // smallest team whose strips fit in shared memory, per problem
+        std::vector<int> gmin(count);
+        for (int i = 0; i < count; ++i) {
+            const pit_instance& I = inst[i];
+            int g = 1;
+            while (g <= std::min(I.grid.ny, kMaxTeam) && team_smem(b->fp32, I.grid.nx, I.grid.ny, g) > b->dyn_max) ++g;
+            if (g > std::min(I.grid.ny, std::min(kMaxTeam, b->num_sms)))
+                return bfail(b, PIT_EUNSUPPORTED, "problem %d: a level strip does not fit in shared memory", i);
+            gmin[i] = g;
+        }
+        std::vector<int> team(count);
+        std::vector<double> cost(count, 1.0);
+        if (b->opt.team_ctas > 0) {
+            for (int i = 0; i < count; ++i)
+                team[i] = std::max(gmin[i], std::min({b->opt.team_ctas, inst[i].grid.ny, b->num_sms}));
+            for (int i = 0; i < count; ++i) cost[i] = (double)inst[i].M * inst[i].grid.nx * inst[i].grid.ny / team[i];
+        } else {
+            // autotuner: per distinct grid, time candidate team sizes on the first problem of
+            // that grid truncated to a few levels; per-level time t(G) -> cost = t(G) * M
+            std::map<std::pair<int, int>, int> rep;
+            for (int i = 0; i < count; ++i) rep.emplace(std::make_pair(inst[i].grid.nx, inst[i].grid.ny), i);
+            std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> table;
+            for (auto& kv : rep) {
+                const int i = kv.second;
+                const pit_instance& I = inst[i];
+                std::vector<int> cands;
+                const int gmax = std::min({I.grid.ny, kMaxTeam, b->num_sms});
+                for (double f : {1.0, 1.5, 2.0, 3.0, 4.0, 6.0}) {
+                    const int g = std::min(gmax, std::max(gmin[i], (int)std::lround(gmin[i] * f)));
+                    if (std::find(cands.begin(), cands.end(), g) == cands.end()) cands.push_back(g);
+                }
+                pit_instance cal = I;
+                cal.M = std::min(I.M, 8);
+                for (int g : cands) {
+                    std::vector<pit_instance> one{cal};
+                    double best = 1e300;
+                    BRET(build_launch(b, one, std::vector<int>{g}, std::vector<double>{1.0}));
+                    // results land in slot 0 of the real arrays; harmless before the real solve
+                    for (int rep2 = 0; rep2 < 2; ++rep2) {
+                        double ms = 0.0;
+                        BRET(run_direct(b, &ms));
+                        best = std::min(best, ms);
+                    }
+                    table[kv.first].push_back({g, best / cal.M});
+                }
+            }
+            // per problem: the team size with the least SM time (t * G), then give the
+            // longest problems more CTAs while they bound the makespan
+            for (int i = 0; i < count; ++i) {
+                const auto& tb = table[std::make_pair(inst[i].grid.nx, inst[i].grid.ny)];
+                double bestv = 1e300;
+                for (auto& e : tb) {
+                    if (e.second * e.first < bestv) {
+                        bestv = e.second * e.first;
+                        team[i] = e.first;
+                        cost[i] = e.second * inst[i].M;
+                    }
+                }
+            }
+            for (int round = 0; round < 64; ++round) {
+                double total = 0.0, worst = 0.0;
+                int wi = 0;
+                for (int i = 0; i < count; ++i) {
+                    total += cost[i] * team[i];
+                    if (cost[i] > worst) {
+                        worst = cost[i];
+                        wi = i;
+                    }
+                }
+                if (worst <= total / b->num_sms) break;
+                const auto& tb = table[std::make_pair(inst[wi].grid.nx, inst[wi].grid.ny)];
+                bool grew = false;
+                for (auto& e : tb) {
+                    if (e.first > team[wi] && e.second * inst[wi].M < cost[wi]) {
+                        team[wi] = e.first;
+                        cost[wi] = e.second * inst[wi].M;
+                        grew = true;
+                        break;
+                    }
+                }
+                if (!grew) break;
+            }
+        }
+        b->team_of = team;
+        BRET(build_launch(b, b->in, team, cost));
+        return PIT_OK;
+    };
+    pit_status st = setup();
+    b->ms_tuning = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    if (st != PIT_OK) {
+        fprintf(stderr, "pit_batch_create: %s\n", b->err);
+        pit_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return PIT_OK;
+}
+
+extern "C" pit_status pit_batch_solve(pit_batch* b, pit_batch_info* info) {
+    if (!b) return PIT_EINVAL;
+    double ms = 0.0;
+    bool used_graph = false;
+    // the caller's stream may hold the producers of the problems' data
+    BCK(cudaEventRecord(b->ev_user, b->user_stream));
+    BCK(cudaStreamWaitEvent(b->stream, b->ev_user, 0));
+    if (b->graph_ok && !b->exec) {
+        // capture the launch sequence once
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(b->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
+            cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const pit_status s = enqueue_launch(b, false);  // events in a graph cannot be timed
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+            if (s == PIT_OK && e == cudaSuccess && g &&
+                cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess) {
+                b->graph = g;
+            } else {
+                if (g) cudaGraphDestroy(g);
+                b->exec = nullptr;
+                b->graph_ok = false;
+                cudaGetLastError();
+            }
+        } else {
+            b->graph_ok = false;
+            cudaGetLastError();
+        }
+    }
+    if (b->exec) {
+        BCK(cudaEventRecord(b->e0, b->stream));
+        BCK(cudaGraphLaunch(b->exec, b->stream));
+        BCK(cudaEventRecord(b->e1, b->stream));
+        BCK(cudaStreamSynchronize(b->stream));
+        float f = 0.f;
+        BCK(cudaEventElapsedTime(&f, b->e0, b->e1));
+        ms = f;
+        used_graph = true;
+        if (b->h_ctl[1] == ST_ETIMEOUT) return bfail(b, PIT_ETIMEOUT, "batch kernel: a device wait ran out of budget");
+        if (b->h_ctl[1] == ST_EDIVERGED) return bfail(b, PIT_EDIVERGED, "batch kernel: NaN/Inf in a problem");
+    } else {
+        BRET(run_direct(b, &ms));
+    }
+    int conv = 0;
+    for (int i = 0; i < b->count; ++i) conv += (b->h_res[i] <= b->opt.tol_res);
+    if (info) {
+        info->count = b->count;
+        info->ctas = b->ctas;
+        info->teams = b->count;
+        info->min_team = b->min_team;
+        info->max_team = b->max_team;
+        info->converged = conv;
+        info->graph = used_graph ? 1 : 0;
+        info->ms = ms;
+        info->est_makespan_ms = b->est_ms;
+        info->ms_tuning = b->ms_tuning;
+    }
+    if (conv < b->count) return bfail(b, PIT_ENOCONV, "%d of %d problems did not reach tol_res", b->count - conv, b->count);
+    return PIT_OK;
+}
+
+extern "C" pit_status pit_batch_result(const pit_batch* b, int i, double* res_inf, int* newton_iters,
+                                       int* windows_converged, int* team_ctas) {
+    if (!b || i < 0 || i >= b->count) return PIT_EINVAL;
+    if (res_inf) *res_inf = b->h_res[i];
+    if (newton_iters) *newton_iters = b->h_iters[i];
+    if (windows_converged) *windows_converged = b->h_iters[b->count + i];
+    if (team_ctas) *team_ctas = b->team_of.empty() ? 0 : b->team_of[i];
+    return PIT_OK;
+}
+
+extern "C" const char* pit_batch_last_error(const pit_batch* b) { return b ? b->err : "null batch"; }
+
+extern "C" void pit_batch_destroy(pit_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->d_inst);
+    cudaFree(b->d_jobs);
+    cudaFree(b->d_job_off);
+    cudaFree(b->d_ws);
+    cudaFree(b->pool);
+    cudaFree(b->d_res);
+    cudaFree(b->d_iters);
+    cudaFree(b->d_ctl);
+    cudaFreeHost(b->h_res);
+    cudaFreeHost(b->h_iters);
+    cudaFreeHost(b->h_ctl);
+    if (b->e0) cudaEventDestroy(b->e0);
+    if (b->e1) cudaEventDestroy(b->e1);
+    if (b->ev_user) cudaEventDestroy(b->ev_user);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}

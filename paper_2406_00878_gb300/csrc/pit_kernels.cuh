@@ -897,6 +897,7 @@ struct WaveArgs {
     double* U;
     int K, G, rows_base, rows_rem;
     int k_begin, k_end;                 // iterations k_begin <= k < k_end may run
+    unsigned long long cell_base;       // added to every progress value (monotonic across calls)
     double tol_res, eta_max, eta_gamma, atol, sor_rho_max;
     int method;
     int max_iter;
@@ -909,7 +910,8 @@ struct WaveArgs {
     unsigned long long* prog;           // [K][G] cells completed: k * M + n + 1
     int* abort_flag;
     int* status;
-    int* stop;                          // [0] stop flag, [1] first converged iteration
+    int* stop;                          // [0] stop flag, [1] first converged iteration (K > 1; may be null)
+    int* kconv;                         // one team (K = 1): CTA 0 writes the converged iteration (may be null)
     // per iteration records, indexed by k
     double* res_inf;                    // [k_end] ||R_k||_inf
     double* cell_prefix;                // [k_end][M] max_{j <= n} ||r^j_k||_inf (written by CTA 0 of the team)
@@ -934,18 +936,14 @@ __host__ __device__ inline size_t wave_smem_bytes(int cap, int nx) {
     return bytes;
 }
 
-template <int NT, bool CONV, bool NLV, typename T = double>
-__global__ void __launch_bounds__(NT) wave_kernel(WaveArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_ok;
+// The work of CTA b of team `team` in a wavefront launch (or one window of one
+// instance of a batched launch). t is the CTA's team state, already initialised
+// with the team's workspace; its sequence counters carry over between calls.
+template <int NT, bool CONV, bool NLV, typename T>
+__device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned char* smem, int& s_ok) {
     const OpConst& oc = a.c;
     const int nx = oc.nx, ny = oc.ny, M = oc.M;
-    const int team = blockIdx.x / a.G;
-    const int b = blockIdx.x - team * a.G;
     TeamCtl c{a.abort_flag, a.status, a.wait_budget, a.max_iter};
-    Team t;
-    team_init(t, b, a.G, nx, ny, a.rows_base, a.rows_rem, a.pub + (size_t)team * 2 * a.G * 2 * nx,
-              a.flags + (size_t)team * a.G, a.red_part + (size_t)team * 4 * a.G * 4, a.red_cnt + (size_t)team * 4);
     const unsigned long long t_start = global_ns();
     unsigned long long t_pred = 0;
     const int nloc = t.nloc;
@@ -981,14 +979,14 @@ __global__ void __launch_bounds__(NT) wave_kernel(WaveArgs a) {
                 bool stop_seen = false;
                 double pred_prefix = 1.0 / 0.0;
                 if (k > a.k_begin) {
-                    const unsigned long long target = (unsigned long long)(k - 1) * M + n + 1;
+                    const unsigned long long target = a.cell_base + (unsigned long long)(k - 1) * M + n + 1;
                     const unsigned long long t0 = global_ns();
                     for (int q = 0; q < 4 && !stop_seen; ++q) {
                         const int nbr = q < 3 ? b - 1 + q : 0;
                         if (nbr < 0 || nbr >= a.G || (q == 3 && b <= 1)) continue;
                         long long spins = 0;
                         while (ld_acquire_u64(pred_prog + nbr) < target) {
-                            if (ld_acquire_s32(a.stop) || ld_acquire_s32(a.abort_flag)) {
+                            if ((a.stop && ld_acquire_s32(a.stop)) || ld_acquire_s32(a.abort_flag)) {
                                 stop_seen = true;
                                 break;
                             }
@@ -1004,7 +1002,7 @@ __global__ void __launch_bounds__(NT) wave_kernel(WaveArgs a) {
                     t_pred += global_ns() - t0;
                     if (!stop_seen) pred_prefix = __ldcg(a.cell_prefix + (size_t)(k - 1) * M + n);
                 }
-                s_ok = (stop_seen || ld_acquire_s32(a.stop) || ld_acquire_s32(a.abort_flag)) ? 1 : 0;
+                s_ok = (stop_seen || (a.stop && ld_acquire_s32(a.stop)) || ld_acquire_s32(a.abort_flag)) ? 1 : 0;
                 slot[0] = pred_prefix;
             }
             __syncthreads();
@@ -1023,10 +1021,10 @@ __global__ void __launch_bounds__(NT) wave_kernel(WaveArgs a) {
                     __threadfence();
                     if (b == 0) {
                         __stcg(a.cell_prefix + (size_t)k * M + n, prefix);
-                        a.cell_iters[(size_t)k * M + n] = 1;
+                        if (a.cell_iters) a.cell_iters[(size_t)k * M + n] = 1;
                         __threadfence();
                     }
-                    st_release_u64(my_prog + b, (unsigned long long)k * M + n + 1);
+                    st_release_u64(my_prog + b, a.cell_base + (unsigned long long)k * M + n + 1);
                 }
                 continue;
             }
@@ -1134,7 +1132,7 @@ __global__ void __launch_bounds__(NT) wave_kernel(WaveArgs a) {
                         a.cell_iters[(size_t)k * M + n] = used == 1 ? iters + 1 : -(iters + 1);
                     }
                     __threadfence();
-                    st_release_u64(my_prog + b, (unsigned long long)k * M + n + 1);
+                    st_release_u64(my_prog + b, a.cell_base + (unsigned long long)k * M + n + 1);
                     if (iters >= c.max_iter) atomicCAS(a.status, 0, ST_ENOCONV);
                 }
             }
@@ -1144,26 +1142,243 @@ __global__ void __launch_bounds__(NT) wave_kernel(WaveArgs a) {
             double ss[1] = {sumsq};
             block_sum<NT, 1>(ss, m.red);
             if (threadIdx.x == 0) {
-                a.cta_sumsq[(size_t)k * a.G + b] = ss[0];
+                if (a.cta_sumsq) a.cta_sumsq[(size_t)k * a.G + b] = ss[0];
                 if (b == 0) {
-                    a.res_inf[k] = prefix;
-                    if (prefix <= a.tol_res) {
+                    if (a.res_inf) a.res_inf[k] = prefix;
+                    if (prefix <= a.tol_res && a.K > 1 && a.stop) {
                         atomicMin(a.stop + 1, k);
                         __threadfence();
                         atomicExch(a.stop, 1);
                     }
                 }
             }
-            __syncthreads();
+            // one team: every CTA holds the same running max and leaves by itself
+            const double fin = bcast0(prefix, slot);
+            if (a.K == 1 && fin <= a.tol_res) {
+                if (threadIdx.x == 0 && b == 0 && a.kconv) *a.kconv = k;
+                goto done;
+            }
         }
     }
 done:
-    if (b == 0 && threadIdx.x == 0) {
+    if (b == 0 && threadIdx.x == 0 && a.timers) {
         unsigned long long* tm = a.timers + (size_t)team * 4;
         tm[0] = t.t_halo;
         tm[1] = t.t_red;
         tm[2] = t_pred;
         tm[3] = global_ns() - t_start;
+    }
+    __syncthreads();
+}
+
+template <int NT, bool CONV, bool NLV, typename T = double>
+__global__ void __launch_bounds__(NT) wave_kernel(WaveArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_ok;
+    const int team = blockIdx.x / a.G;
+    const int b = blockIdx.x - team * a.G;
+    Team t;
+    team_init(t, b, a.G, a.c.nx, a.c.ny, a.rows_base, a.rows_rem, a.pub + (size_t)team * 2 * a.G * 2 * a.c.nx,
+              a.flags + (size_t)team * a.G, a.red_part + (size_t)team * 4 * a.G * 4, a.red_cnt + (size_t)team * 4);
+    wave_body<NT, CONV, NLV, T>(a, team, b, t, smem, s_ok);
+}
+
+// ------------------------------------------------ batched instances (one launch)
+
+// One problem of a batch and its results.
+struct BatchInstance {
+    OpConst c;                          // grid, all M levels, dt, closure
+    int conv, nlv;                      // closure: Burgers convection, u-dependent viscosity
+    int window;                         // levels per window
+    const double* u0;
+    const double* bc;
+    const double* q;
+    double* U;                          // [M][Ns] solution (the plain guess is filled in here)
+    double* res_inf;                    // out: ||R||_inf of the final U
+    int* newton_iters;                  // out: Newton updates summed over windows
+    int* converged_windows;             // out
+};
+
+// Job of one CTA: CTA `rank` of a team of G CTAs on instance `inst`. Jobs are listed
+// per CTA in one global order, so the lowest unfinished job always has all of its
+// CTAs (no cyclic waits). The team's workspace is given by offsets into the pools.
+struct BatchJob {
+    int inst, rank, G;
+    int team;                           // index of the team's workspace
+};
+
+struct BatchTeamWs {
+    double* pub;                        // [2][G][2][nx]
+    unsigned long long* flags;          // [G]
+    double* red_part;                   // [4][G][4]
+    unsigned long long* red_cnt;        // [4]
+    unsigned long long* prog;           // [G]
+    double* cell_prefix;                // [newton_max][window]
+    int* kconv;                         // converged iteration of the current window (CTA 0 only)
+};
+
+struct BatchArgs {
+    const BatchInstance* inst;
+    const BatchJob* jobs;               // jobs of CTA c: jobs[job_off[c] .. job_off[c+1])
+    const int* job_off;
+    const BatchTeamWs* ws;
+    int* abort_flag;
+    int* status;
+    int newton_max;
+    double tol_res, eta_max, eta_gamma, atol, sor_rho_max;
+    int method, max_iter;
+    long long wait_budget;
+};
+
+// A team-wide barrier built on the team reduction (every CTA of the team passes it
+// only after all have arrived).
+template <int NT>
+__device__ __forceinline__ bool team_barrier(const TeamCtl& c, Team& t, double* red, int* s_ok) {
+    double v[1] = {0.0};
+    return reduce_finish<1, true>(c, t, reduce_arrive<1>(t, v), v, red + 32, s_ok);
+}
+
+template <int NT, typename T>
+__device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigned char* smem, int& s_ok) {
+    const BatchInstance& in = ba.inst[job.inst];
+    const BatchTeamWs& ws = ba.ws[job.team];
+    const OpConst& oc = in.c;
+    const int nx = oc.nx, ny = oc.ny, M = oc.M;
+    const int G = job.G, b = job.rank;
+    const int rows_base = ny / G, rows_rem = ny % G;
+    TeamCtl c{ba.abort_flag, ba.status, ba.wait_budget, ba.max_iter};
+    Team t;
+    team_init(t, b, G, nx, ny, rows_base, rows_rem, ws.pub, ws.flags, ws.red_part, ws.red_cnt);
+    const long long Ns = t.Ns;
+    const long long off0 = (long long)t.r0 * nx;
+    const int nloc = t.nloc;
+    const int cap = (rows_base + (rows_rem ? 1 : 0)) * nx;
+    double* red = smem_layout<T>(smem, cap, nx).red;
+    const int W = in.window > 0 ? in.window : M;
+    unsigned long long base = 0;
+    int iters_total = 0, conv_windows = 0;
+    for (int s = 0; s < M; s += W) {
+        const int Mw = min(W, M - s);
+        // plain guess for the window from its previous level: own rows only
+        const double* from = s == 0 ? in.u0 : in.U + (long long)(s - 1) * Ns;
+        for (int n = 0; n < Mw; ++n) {
+            double* dst = in.U + (long long)(s + n) * Ns + off0;
+            for (int i = threadIdx.x; i < nloc; i += NT) dst[i] = __ldcg(from + off0 + i);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) __threadfence();
+        if (!team_barrier<NT>(c, t, red, &s_ok)) return;  // neighbours' rows are filled
+        WaveArgs a{};
+        a.c = oc;
+        a.c.M = Mw;
+        a.u0 = from;
+        a.bc = in.bc ? in.bc + (long long)s * (2 * nx + 2 * ny) : nullptr;
+        a.q = in.q ? in.q + (long long)s * Ns : nullptr;
+        a.U = in.U + (long long)s * Ns;
+        a.K = 1;
+        a.G = G;
+        a.rows_base = rows_base;
+        a.rows_rem = rows_rem;
+        a.k_begin = 0;
+        a.k_end = ba.newton_max;
+        a.cell_base = base;
+        a.tol_res = ba.tol_res;
+        a.eta_max = ba.eta_max;
+        a.eta_gamma = ba.eta_gamma;
+        a.atol = ba.atol;
+        a.sor_rho_max = ba.sor_rho_max;
+        a.method = ba.method;
+        a.max_iter = ba.max_iter;
+        a.wait_budget = ba.wait_budget;
+        a.pub = ws.pub;
+        a.flags = ws.flags;
+        a.red_part = ws.red_part;
+        a.red_cnt = ws.red_cnt;
+        a.prog = ws.prog;
+        a.abort_flag = ba.abort_flag;
+        a.status = ba.status;
+        a.stop = nullptr;
+        a.res_inf = nullptr;
+        a.cell_prefix = ws.cell_prefix;
+        a.cell_iters = nullptr;
+        a.cta_sumsq = nullptr;
+        a.timers = nullptr;
+        // converged iteration index: written by CTA 0 of the team, read back by it
+        __shared__ int s_kdone;
+        a.kconv = b == 0 ? ws.kconv : nullptr;
+        if (threadIdx.x == 0 && b == 0) *ws.kconv = -1;
+        if (in.conv) {
+            if (in.nlv) wave_body<NT, true, true, T>(a, 0, b, t, smem, s_ok);
+            else wave_body<NT, true, false, T>(a, 0, b, t, smem, s_ok);
+        } else {
+            if (in.nlv) wave_body<NT, false, true, T>(a, 0, b, t, smem, s_ok);
+            else wave_body<NT, false, false, T>(a, 0, b, t, smem, s_ok);
+        }
+        if (threadIdx.x == 0) {
+            s_ok = ld_acquire_s32(ba.abort_flag);
+            s_kdone = b == 0 ? *ws.kconv : 0;
+        }
+        __syncthreads();
+        if (s_ok) return;  // the launch aborts (read once per CTA)
+        if (s_kdone >= 0) {
+            iters_total += s_kdone + 1;
+            ++conv_windows;
+        } else {
+            iters_total += ba.newton_max;
+        }
+        base += (unsigned long long)ba.newton_max * Mw + 1;
+        __syncthreads();
+    }
+    // final residual of the whole solution, all levels (needs the neighbours' last updates)
+    if (threadIdx.x == 0) __threadfence();
+    if (!team_barrier<NT>(c, t, red, &s_ok)) return;
+    double rmax = 0.0;
+    const int nb = 2 * nx + 2 * ny;
+    for (int n = 0; n < M; ++n) {
+        const double* Un = in.U + (long long)n * Ns;
+        const double* Up = n == 0 ? in.u0 : in.U + (long long)(n - 1) * Ns;
+        const double* bnd = in.bc ? in.bc + (long long)n * nb : nullptr;
+        for (int i = threadIdx.x; i < nloc; i += NT) {
+            const int jl = i / nx, ii = i - jl * nx, j = t.r0 + jl;
+            const long long k = (long long)j * nx + ii;
+            const double uC = __ldcg(Un + k);
+            const double uW = ii > 0 ? __ldcg(Un + k - 1) : (bnd ? bnd[2 * nx + j] : 0.0);
+            const double uE = ii < nx - 1 ? __ldcg(Un + k + 1) : (bnd ? bnd[2 * nx + ny + j] : 0.0);
+            const double uS = j > 0 ? __ldcg(Un + k - nx) : (bnd ? bnd[ii] : 0.0);
+            const double uN = j < ny - 1 ? __ldcg(Un + k + nx) : (bnd ? bnd[nx + ii] : 0.0);
+            double tf;
+            if (in.conv) tf = in.nlv ? tau_F<true, true>(oc, uC, uW, uE, uS, uN) : tau_F<true, false>(oc, uC, uW, uE, uS, uN);
+            else tf = in.nlv ? tau_F<false, true>(oc, uC, uW, uE, uS, uN) : tau_F<false, false>(oc, uC, uW, uE, uS, uN);
+            double r = (__ldcg(Up + k) - uC) - tf;
+            if (in.q) r = fma(oc.dt, in.q[(long long)n * Ns + k], r);
+            rmax = fmax(rmax, fabs(r));
+            if (r != r) rmax = r;
+        }
+    }
+    double v[1] = {key_val(block_max_u64<NT>(abs_key(rmax), reinterpret_cast<unsigned long long*>(red)))};
+    double g[1];
+    if (!reduce_finish<1, true>(c, t, reduce_arrive<1>(t, v), g, red + 32, &s_ok)) return;
+    if (b == 0 && threadIdx.x == 0) {
+        *in.res_inf = g[0];
+        *in.newton_iters = iters_total;
+        *in.converged_windows = conv_windows;
+    }
+    __syncthreads();
+}
+
+// Persistent launch over a batch: CTA c works through its job list in order.
+template <int NT, typename T>
+__global__ void __launch_bounds__(NT) batch_kernel(BatchArgs ba) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_ok;
+    const int c = blockIdx.x;
+    for (int j = ba.job_off[c]; j < ba.job_off[c + 1]; ++j) {
+        const BatchJob job = ba.jobs[j];
+        batch_instance<NT, T>(ba, job, smem, s_ok);
+        __syncthreads();
+        if (threadIdx.x == 0) s_ok = ld_acquire_s32(ba.abort_flag);
+        __syncthreads();
+        if (s_ok) return;
     }
 }
 

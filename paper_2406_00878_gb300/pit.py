@@ -27,7 +27,8 @@ PIT_NOALLOC_MAX_NX, PIT_NOALLOC_MAX_TEAM, PIT_NOALLOC_MAX_LEVELS = 512, 160, 409
 #: every symbol include/pit.h declares
 EXPORTS = ("pit_default_options", "pit_create", "pit_set_data", "pit_fill_plain_guess", "pit_residual",
            "pit_assemble", "pit_block_solve", "pit_newton_step", "pit_solve", "pit_solve_host", "pit_last_error",
-           "pit_status_string", "pit_destroy", "pit_block_solve_noalloc")
+           "pit_status_string", "pit_destroy", "pit_block_solve_noalloc", "pit_batch_create", "pit_batch_solve",
+           "pit_batch_result", "pit_batch_last_error", "pit_batch_destroy")
 
 
 class pit_grid(ctypes.Structure):
@@ -73,6 +74,21 @@ class pit_solve_info(ctypes.Structure):
                 "wave_launches": self.wave_launches, "ms_wave": self.ms_wave, "us_pred_wait": self.us_pred_wait,
                 "us_halo_wait": self.us_halo_wait, "us_reduce_wait": self.us_reduce_wait, "windows": self.windows,
                 "newton_iters_total": self.newton_iters_total}
+
+
+class pit_instance(ctypes.Structure):
+    _fields_ = [("grid", pit_grid), ("M", ctypes.c_int), ("dt", ctypes.c_double), ("params", pit_params),
+                ("u0_dev", ctypes.c_void_p), ("bc_dev", ctypes.c_void_p), ("q_dev", ctypes.c_void_p),
+                ("U_dev", ctypes.c_void_p)]
+
+
+class pit_batch_info(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("ctas", ctypes.c_int), ("teams", ctypes.c_int), ("min_team", ctypes.c_int),
+                ("max_team", ctypes.c_int), ("converged", ctypes.c_int), ("graph", ctypes.c_int),
+                ("ms", ctypes.c_double), ("est_makespan_ms", ctypes.c_double), ("ms_tuning", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class PitError(RuntimeError):
@@ -127,6 +143,18 @@ def lib():
             L.pit_block_solve_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, V, V, V, ctypes.c_double,
                                                   ctypes.POINTER(pit_options), V, ctypes.c_char_p, ctypes.c_int]
             L.pit_block_solve_noalloc.restype = st
+            L.pit_batch_create.argtypes = [ctypes.POINTER(pit_instance), ctypes.c_int, ctypes.POINTER(pit_options), V,
+                                           ctypes.POINTER(P)]
+            L.pit_batch_create.restype = st
+            L.pit_batch_solve.argtypes = [P, ctypes.POINTER(pit_batch_info)]
+            L.pit_batch_solve.restype = st
+            L.pit_batch_result.argtypes = [P, ctypes.c_int, D, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+            L.pit_batch_result.restype = st
+            L.pit_batch_last_error.argtypes = [P]
+            L.pit_batch_last_error.restype = ctypes.c_char_p
+            L.pit_batch_destroy.argtypes = [P]
+            L.pit_batch_destroy.restype = None
             _lib = L
         return _lib
 
@@ -308,3 +336,86 @@ def context_for(problem, opt: Optional[pit_options] = None, stream=None) -> Cont
     pit_set_data(ctx, u0, bc, q)
     torch.cuda.current_stream().synchronize()
     return ctx
+
+
+class Batch:
+    """A pit_batch handle plus the device tensors its problems point at (kept alive here)."""
+
+    def __init__(self, handle, problems, tensors):
+        self.handle = handle
+        self.problems = problems
+        self.tensors = tensors       # per problem: dict(u0=, bc=, q=, U=)
+
+    def _check(self, status: int):
+        if status != PIT_OK:
+            raise PitError(status, lib().pit_batch_last_error(self.handle).decode())
+
+    def close(self):
+        if self.handle:
+            lib().pit_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pit_batch_create(problems, opt: Optional[pit_options] = None, stream=None) -> Batch:
+    """Upload a list of workloads.Problem and create a batch (runs the autotuner)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    elif not isinstance(stream, int):
+        stream = stream.cuda_stream
+    arr = (pit_instance * len(problems))()
+    tensors = []
+    for i, p in enumerate(problems):
+        t = {"u0": torch.as_tensor(np.ascontiguousarray(p.u0), dtype=torch.float64, device="cuda"),
+             "bc": None if p.bc is None else torch.as_tensor(np.ascontiguousarray(p.bc), device="cuda"),
+             "q": None if p.q is None else torch.as_tensor(np.ascontiguousarray(p.q), device="cuda"),
+             "U": torch.empty(p.dof, dtype=torch.float64, device="cuda")}
+        tensors.append(t)
+        g = p.grid
+        arr[i].grid = pit_grid(int(g.nx), int(g.ny), float(g.xl), float(g.xr), float(g.yl), float(g.yr))
+        arr[i].M = int(p.M)
+        arr[i].dt = float(p.dt)
+        arr[i].params = pit_params(int(p.params.equation), float(p.params.mu_a), float(p.params.mu_b))
+        arr[i].u0_dev = t["u0"].data_ptr()
+        arr[i].bc_dev = t["bc"].data_ptr() if t["bc"] is not None else None
+        arr[i].q_dev = t["q"].data_ptr() if t["q"] is not None else None
+        arr[i].U_dev = t["U"].data_ptr()
+    torch.cuda.synchronize()
+    h = ctypes.c_void_p()
+    s = lib().pit_batch_create(arr, len(problems), ctypes.byref(opt) if opt is not None else None,
+                               ctypes.c_void_p(stream), ctypes.byref(h))
+    if s != PIT_OK:
+        raise PitError(s, "pit_batch_create failed (see stderr)")
+    return Batch(h, problems, tensors)
+
+
+def pit_batch_solve(batch: Batch, check: bool = True):
+    info = pit_batch_info()
+    s = lib().pit_batch_solve(batch.handle, ctypes.byref(info))
+    if check:
+        batch._check(s)
+    return s, info.as_dict()
+
+
+def pit_batch_result(batch: Batch, i: int) -> dict:
+    r = ctypes.c_double()
+    it, wc, tc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    batch._check(lib().pit_batch_result(batch.handle, int(i), ctypes.byref(r), ctypes.byref(it), ctypes.byref(wc),
+                                        ctypes.byref(tc)))
+    return {"res_inf": r.value, "newton_iters": it.value, "windows_converged": wc.value, "team_ctas": tc.value}
+
+
+def pit_batch_destroy(batch: Batch):
+    batch.close()

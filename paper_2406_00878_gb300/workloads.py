@@ -153,3 +153,39 @@ def random_problem(seed: int, nx: int, ny: int, M: int, equation: int, with_bc: 
         q = np.ascontiguousarray(0.5 * amp * rng.standard_normal((M, g.ns)))
     return Problem(f"rand{seed}_{nx}x{ny}x{M}_{'heat' if equation == HEAT else 'burgers'}", g, params, M, dt,
                    np.ascontiguousarray(u0.ravel()), bc, q, meta={"seed": seed})
+
+
+def fourier_u0(grid: Grid, rng, kmax: int = 8) -> np.ndarray:
+    """u0 = sum over kx, ky >= 1 with kx^2 + ky^2 <= kmax^2 of a_k sin(kx pi x') sin(ky pi y'),
+    a_k ~ N(0, 1/(kx^2 + ky^2)), x' = (x - xl)/(xr - xl): a random smooth field that
+    vanishes on the boundary (zero Dirichlet data)."""
+    X, Y = grid.nodes()
+    xs = (X - grid.xl) / (grid.xr - grid.xl)
+    ys = (Y - grid.yl) / (grid.yr - grid.yl)
+    u = np.zeros_like(X)
+    for kx in range(1, kmax + 1):
+        for ky in range(1, kmax + 1):
+            k2 = kx * kx + ky * ky
+            if k2 > kmax * kmax:
+                continue
+            u += rng.normal(0.0, 1.0 / np.sqrt(k2)) * np.sin(kx * np.pi * xs) * np.sin(ky * np.pi * ys)
+    return np.ascontiguousarray(u.ravel())
+
+
+def batched(seed: int = 0, count: int = 64, sizes=tuple(range(64, 385, 32)), levels=tuple(range(32, 513, 32)),
+            dt: float = 1e-3):
+    """Independent problems of uneven size: square grids drawn from `sizes` (interior
+    nodes), M from `levels`, nu log-uniform in [1e-3, 1e-1], Burgers or heat by a coin
+    flip (heat: mu = nu (1 + u^2)), u0 a random sine series with modes k <= 8."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice(sizes))
+        M = int(rng.choice(levels))
+        nu = float(10.0 ** rng.uniform(-3.0, -1.0))
+        heat = bool(rng.integers(0, 2))
+        g = Grid(n, n)
+        params = Params(HEAT, nu, nu) if heat else Params(BURGERS, nu, 0.0)
+        out.append(Problem(f"batch{seed}_{i}_{'heat' if heat else 'burgers'}{n}x{M}", g, params, M, dt,
+                           fourier_u0(g, rng), meta={"seed": seed, "index": i, "nu": nu}))
+    return out
