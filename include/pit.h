@@ -88,9 +88,10 @@ typedef struct {
                                estimate to eta * ||rhs||, eta = min(eta_max, eta_gamma*||R||_inf)
                                (default 1e-2) */
     double eta_gamma;       /* (default 1.0) */
-    double lin_atol;        /* absolute floor of the level-solve tolerance (default 1e-15) */
+    double lin_atol;        /* absolute floor of SOR's error tolerance (default 1e-15); BiCGStab stops
+                               relative to its Jacobi-scaled rhs */
     int lin_max_iter;       /* cap on sweeps / iterations per level solve (default 4000) */
-    double sor_rho_max;     /* AUTO uses SOR below this Gershgorin bound (default 0.95) */
+    double sor_rho_max;     /* AUTO uses SOR below this Gershgorin bound (default 0.99) */
     int team_ctas;          /* CTAs that share one level in the chain kernel (0 = auto) */
     long long wait_budget;  /* spin iterations before a device wait gives up (default 1<<26) */
     int wave_teams;         /* pit_solve: Newton iterations in flight in the wavefront kernel

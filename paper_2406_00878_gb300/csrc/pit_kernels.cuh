@@ -596,8 +596,7 @@ __device__ __forceinline__ double bcast0(double v, double* slot) {
 
 // Jacobi-preconditioned BiCGStab (van der Vorst 1992) on the scaled level system,
 // from x = 0; s shares storage with r. Vectors in precision T, dot products and
-// recurrence scalars in FP64. Stops when ||r||_2 <= max(eta ||bs||_2, atol sqrt(Ns),
-// 16 eps_T ||bs||_2). Scalars are formed by thread 0 and broadcast (FP64 division
+// recurrence scalars in FP64. Stops when ||r||_2 <= max(eta, 16 eps_T) ||bs||_2. Scalars are formed by thread 0 and broadcast (FP64 division
 // is costly on this part). Returns the iteration count (< 0 on abort).
 template <int NT, typename T>
 __device__ int level_bicgstab(const TeamCtl& c, Team& t, const Smem<T>& m, double eta, double atol, int* s_ok) {
@@ -621,8 +620,10 @@ __device__ int level_bicgstab(const TeamCtl& c, Team& t, const Smem<T>& m, doubl
     // thread 0 keeps the recurrence scalars; others receive what they need
     double tol = 0.0, rho_old = 1.0, alpha = 1.0, omega = 1.0, rho = g1[0];
     if (threadIdx.x == 0) {
+        // relative to the scaled rhs only: an absolute floor would act on a residual that
+        // the Jacobi scaling has divided by the diagonal
         const double bn = sqrt(g1[0]);
-        tol = fmax(fmax(eta * bn, atol * sqrt((double)t.Ns)), 16.0 * Eps<T>::value * bn);
+        tol = fmax(eta * bn, 16.0 * Eps<T>::value * bn);
     }
     if (bcast0(threadIdx.x == 0 ? (sqrt(g1[0]) <= tol ? 1.0 : 0.0) : 0.0, slot) != 0.0) return 0;
     for (int it = 1; it <= c.max_iter; ++it) {
