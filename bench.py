@@ -275,6 +275,22 @@ def variants(args):
                      "workload": p.name, "M": p.M, "window": window, "precision": "fp32 level solves / fp64 newton",
                      "newton_iters_total": info["newton_iters_total"], "res_inf_final": info["res_inf"][-1],
                      "wave_teams": info["wave_teams"], "ctas_per_team": info["wave_team_ctas"]}
+    # 64 independent problems of uneven size in one persistent launch (graph replay)
+    probs = W.batched(seed=0)
+    dof = sum(p.dof for p in probs)
+    opt = pit.pit_default_options()
+    opt.precision = pit.PIT_FP32_INNER
+    opt.window = 32
+    with pit.pit_batch_create(probs, opt) as batch:
+        pit.pit_batch_solve(batch)
+        st, info = pit.pit_batch_solve(batch)
+        res = max(pit.pit_batch_result(batch, i)["res_inf"] for i in range(len(probs)))
+    out["batched64_mixed_window32"] = {
+        "value": dof / (info["ms"] * 1e-3), "unit": UNIT, "ms_per_step": info["ms"], "dof": dof,
+        "problems": len(probs), "grids": "64..384 squared", "levels": "32..512",
+        "precision": "fp32 level solves / fp64 newton", "converged": info["converged"], "max_res_inf_final": res,
+        "graph_replay": bool(info["graph"]), "team_ctas": [info["min_team"], info["max_team"]],
+        "autotune_ms": info["ms_tuning"], "schedule_estimate_ms": info["est_makespan_ms"]}
     return out
 
 
