@@ -257,6 +257,44 @@ pit_status pit_batch_result(const pit_batch* batch, int i, double* res_inf, int*
 const char* pit_batch_last_error(const pit_batch* batch);
 void pit_batch_destroy(pit_batch* batch);
 
+/* ------------------------------------------------- learned initial guess
+ * A small residual conv net maps (u^0, log10 nu) on the grid to the corrections
+ * u^n - u^0 of all M levels; u^0 + correction replaces the plain guess u^n = u^0
+ * as Newton's starting iterate (the converged solution is the same; the net only
+ * moves the start). Layers: 3x3 conv 2 -> C, ReLU; per block h = ReLU(conv(x)),
+ * x = x + conv(h); head 3x3 conv C -> M. BF16 weights and activations, FP32
+ * accumulation on the tensor cores, FP32 master weights, Adam, MSE loss. The head
+ * starts at zero, so an untrained net returns the plain guess. Parameters travel
+ * as one FP32 vector: per layer W [Cout][3][3][Cin] then bias [Cout], in the order
+ * input, (block conv 1, block conv 2) x blocks, head. Targets are BF16 [B][H][W][M]
+ * (pit_net_make_target). All calls are ordered on the stream of pit_net_create. */
+typedef struct pit_net pit_net;
+
+typedef struct {
+    int height, width;      /* grid (interior nodes ny, nx) */
+    int levels;             /* M, a multiple of 16 */
+    int channels;           /* C, a multiple of 16 */
+    int blocks;             /* residual blocks */
+    int max_batch;          /* largest batch passed to the calls below */
+} pit_net_shape;
+
+long long pit_net_param_count(const pit_net_shape* shape);
+pit_status pit_net_create(const pit_net_shape* shape, unsigned long long seed, void* stream, pit_net** out);
+pit_status pit_net_get_params(pit_net* net, float* params_host);
+pit_status pit_net_set_params(pit_net* net, const float* params_host);
+/* U_dev [B][M][Ns] = u0 + net(u0, log10 nu): the starting iterate of B problems. */
+pit_status pit_net_guess(pit_net* net, const double* u0_dev, const float* lognu_host, int B, double* U_dev);
+/* target_dev (BF16 [H][W][M]) = U - u^0 for one solution U_dev [M][Ns]. */
+pit_status pit_net_make_target(pit_net* net, const double* u0_dev, const double* U_dev, void* target_dev);
+/* Mean squared error of a batch and its gradient (public layout, may be NULL). */
+pit_status pit_net_gradients(pit_net* net, const double* u0_dev, const float* lognu_host, const void* target_dev,
+                             int B, float* loss_out, float* grads_host);
+/* One Adam step (beta 0.9 / 0.999) on a batch; loss_out (may be NULL) synchronises. */
+pit_status pit_net_train_step(pit_net* net, const double* u0_dev, const float* lognu_host, const void* target_dev,
+                              int B, float lr, float* loss_out);
+const char* pit_net_last_error(const pit_net* net);
+void pit_net_destroy(pit_net* net);
+
 /* Limits of pit_block_solve_noalloc's built-in workspace. */
 #define PIT_NOALLOC_MAX_NX 512       /* interior nodes per grid row */
 #define PIT_NOALLOC_MAX_TEAM 160     /* CTAs sharing one level */

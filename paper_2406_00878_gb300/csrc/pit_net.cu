@@ -1,0 +1,718 @@
+// pit_net.cu -- the learned initial guess: a small residual conv net that maps
+// (u^0, log10 nu) on the grid to the corrections u^n - u^0 of all M levels, used as
+// the starting iterate of Newton in place of the plain guess u^n = u^0.
+//
+//   z0 = conv(in); x = relu(z0); per block: h = relu(conv(x)); x = x + conv(h);
+//   out = conv(x)                                   (3x3 convs, zero padding, bias)
+//
+// Activations are BF16 NHWC, weights BF16 [Cout][9][Cin] with FP32 master copies,
+// products accumulate in FP32 on the tensor cores (mma.sync m16n8k16). The input has
+// 2 channels, padded to 16 for the tensor-core K step. Training: MSE loss, manual
+// backward (data gradients through the forward kernel on flipped, transposed
+// weights; weight gradients by a split-K tensor-core kernel with a deterministic
+// two-pass reduction), Adam on the FP32 masters.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "pit.h"
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+constexpr int kCinPad0 = 16;   // input channels padded for the K step
+constexpr int kPixTile = 64;   // pixels of one image row per CTA
+constexpr int kCoTile = 64;    // output channels per CTA
+
+__device__ __forceinline__ unsigned pack2(bf16 lo, bf16 hi) {
+    return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// ---------------------------------------------------------------- forward conv
+//
+// CTA: 64 pixels of one image row (n, h, w0..w0+63) x 64 output channels. Per
+// 16-channel input chunk it stages the three input rows h-1..h+1 (66 columns, zero
+// outside the image) and the chunk's weights of all 9 taps in shared memory; each
+// of the 4 warps computes 16 pixels x 64 channels with one k16 mma per tap and
+// 8-wide output tile. Epilogue: bias, optional residual add, optional ReLU, BF16.
+constexpr int kAStride = 16 + 8;        // bf16 per staged pixel (padding against bank conflicts)
+constexpr int kBStride = 9 * 16 + 8;    // bf16 per staged output channel
+
+__global__ void __launch_bounds__(128) conv3x3_fwd_kernel(const bf16* __restrict__ X, const bf16* __restrict__ Wt,
+                                                          const float* __restrict__ bias,
+                                                          const bf16* __restrict__ residual, bf16* __restrict__ Y,
+                                                          int N, int H, int W, int Cin, int Cout, int relu) {
+    __shared__ __align__(16) bf16 sA[3][kPixTile + 2][kAStride];
+    __shared__ __align__(16) bf16 sB[kCoTile][kBStride];
+    const int tiles_w = (W + kPixTile - 1) / kPixTile;
+    const int row = blockIdx.x / tiles_w;          // n * H + h
+    const int w0 = (blockIdx.x - row * tiles_w) * kPixTile;
+    const int n = row / H, h = row - n * H;
+    const int co0 = blockIdx.y * kCoTile;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, q = lane & 3;
+    float acc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+
+    for (int c0 = 0; c0 < Cin; c0 += 16) {
+        // stage input rows: 3 x 66 pixels x 16 channels, as 2 x 16-byte pieces
+        for (int t = threadIdx.x; t < 3 * (kPixTile + 2) * 2; t += blockDim.x) {
+            const int half = t & 1, pc = t >> 1;
+            const int r = pc / (kPixTile + 2), col = pc - r * (kPixTile + 2);
+            const int hh = h + r - 1, ww = w0 + col - 1;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (hh >= 0 && hh < H && ww >= 0 && ww < W)
+                v = *reinterpret_cast<const uint4*>(X + (((size_t)n * H + hh) * W + ww) * Cin + c0 + half * 8);
+            *reinterpret_cast<uint4*>(&sA[r][col][half * 8]) = v;
+        }
+        // stage weights: 64 output channels x 9 taps x 16 channels
+        for (int t = threadIdx.x; t < kCoTile * 9 * 2; t += blockDim.x) {
+            const int half = t & 1, ot = t >> 1;
+            const int o = ot / 9, tap = ot - o * 9;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (co0 + o < Cout)
+                v = *reinterpret_cast<const uint4*>(Wt + ((size_t)(co0 + o) * 9 + tap) * Cin + c0 + half * 8);
+            *reinterpret_cast<uint4*>(&sB[o][tap * 16 + half * 8]) = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int r = tap / 3, s = tap - r * 3;
+            const int p = warp * 16 + g;  // pixel rows g and g + 8 of the warp's 16
+            unsigned a[4];
+            a[0] = *reinterpret_cast<const unsigned*>(&sA[r][p + s][q * 2]);
+            a[1] = *reinterpret_cast<const unsigned*>(&sA[r][p + 8 + s][q * 2]);
+            a[2] = *reinterpret_cast<const unsigned*>(&sA[r][p + s][q * 2 + 8]);
+            a[3] = *reinterpret_cast<const unsigned*>(&sA[r][p + 8 + s][q * 2 + 8]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                unsigned bb[2];
+                bb[0] = *reinterpret_cast<const unsigned*>(&sB[j * 8 + g][tap * 16 + q * 2]);
+                bb[1] = *reinterpret_cast<const unsigned*>(&sB[j * 8 + g][tap * 16 + q * 2 + 8]);
+                mma_bf16(acc[j], a, bb);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int co = co0 + j * 8 + q * 2;
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+            const int w = w0 + warp * 16 + g + hf * 8;
+            if (w >= W || co >= Cout) continue;
+            const size_t o = (((size_t)n * H + h) * W + w) * Cout + co;
+            float v0 = acc[j][hf * 2] + bias[co];
+            float v1 = co + 1 < Cout ? acc[j][hf * 2 + 1] + bias[co + 1] : 0.f;
+            if (residual) {
+                v0 += __bfloat162float(residual[o]);
+                if (co + 1 < Cout) v1 += __bfloat162float(residual[o + 1]);
+            }
+            if (relu) {
+                v0 = fmaxf(v0, 0.f);
+                v1 = fmaxf(v1, 0.f);
+            }
+            Y[o] = __float2bfloat16(v0);
+            if (co + 1 < Cout) Y[o + 1] = __float2bfloat16(v1);
+        }
+    }
+}
+
+// ----------------------------------------------------- weight gradient (split K)
+//
+// dW[o][tap][c] = sum over pixels of dY[pix][o] * X[pix shifted by tap][c]. Grid:
+// x = pixel splits (rows_per_split image rows each), y = tap * (Cin / ct) + c-tile,
+// z = Cout / 64. Each of the 4 warps computes 16 output channels x ct input
+// channels with k16 mma steps over the pixels; partial sums go to
+// part[split][Cout][9][Cin] and a second kernel adds the splits in order.
+template <int CT>
+__global__ void __launch_bounds__(128) conv3x3_bwdw_kernel(const bf16* __restrict__ X, const bf16* __restrict__ dY,
+                                                           float* __restrict__ part, int N, int H, int W, int Cin,
+                                                           int Cout, int rows_per_split) {
+    __shared__ __align__(16) bf16 sY[kPixTile][kCoTile + 8];
+    __shared__ __align__(16) bf16 sX[kPixTile][CT + 8];
+    const int ctiles = Cin / CT;
+    const int tap = blockIdx.y / ctiles, ct = blockIdx.y - tap * ctiles;
+    const int r = tap / 3, s = tap - r * 3;
+    const int c0 = ct * CT, co0 = blockIdx.z * kCoTile;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, q = lane & 3;
+    constexpr int NT = CT / 8;
+    float acc[NT][4];
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+    const int row_begin = blockIdx.x * rows_per_split, row_end = min(row_begin + rows_per_split, N * H);
+    for (int rowi = row_begin; rowi < row_end; ++rowi) {
+        const int n = rowi / H, h = rowi - n * H;
+        const int hh = h + r - 1;
+        for (int w0 = 0; w0 < W; w0 += kPixTile) {
+            for (int t = threadIdx.x; t < kPixTile * (kCoTile / 8); t += blockDim.x) {
+                const int p = t / (kCoTile / 8), piece = t - p * (kCoTile / 8);
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (w0 + p < W && co0 + piece * 8 < Cout)
+                    v = *reinterpret_cast<const uint4*>(dY + (((size_t)n * H + h) * W + w0 + p) * Cout + co0 + piece * 8);
+                *reinterpret_cast<uint4*>(&sY[p][piece * 8]) = v;
+            }
+            for (int t = threadIdx.x; t < kPixTile * (CT / 8); t += blockDim.x) {
+                const int p = t / (CT / 8), piece = t - p * (CT / 8);
+                const int ww = w0 + p + s - 1;
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (w0 + p < W && hh >= 0 && hh < H && ww >= 0 && ww < W)
+                    v = *reinterpret_cast<const uint4*>(X + (((size_t)n * H + hh) * W + ww) * Cin + c0 + piece * 8);
+                *reinterpret_cast<uint4*>(&sX[p][piece * 8]) = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k0 = 0; k0 < kPixTile; k0 += 16) {
+                // A = dY^T: rows o (warp*16 + g, +8), columns pixels k0 + 2q (+1, +8, +9)
+                const int o = warp * 16 + g;
+                unsigned a[4];
+                a[0] = pack2(sY[k0 + q * 2][o], sY[k0 + q * 2 + 1][o]);
+                a[1] = pack2(sY[k0 + q * 2][o + 8], sY[k0 + q * 2 + 1][o + 8]);
+                a[2] = pack2(sY[k0 + q * 2 + 8][o], sY[k0 + q * 2 + 9][o]);
+                a[3] = pack2(sY[k0 + q * 2 + 8][o + 8], sY[k0 + q * 2 + 9][o + 8]);
+#pragma unroll
+                for (int j = 0; j < NT; ++j) {
+                    const int c = j * 8 + g;
+                    unsigned bb[2];
+                    bb[0] = pack2(sX[k0 + q * 2][c], sX[k0 + q * 2 + 1][c]);
+                    bb[1] = pack2(sX[k0 + q * 2 + 8][c], sX[k0 + q * 2 + 9][c]);
+                    mma_bf16(acc[j], a, bb);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    float* P = part + (size_t)blockIdx.x * Cout * 9 * Cin;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        const int c = c0 + j * 8 + q * 2;
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+            const int o = co0 + warp * 16 + g + hf * 8;
+            if (o >= Cout) continue;
+            P[((size_t)o * 9 + tap) * Cin + c] = acc[j][hf * 2];
+            P[((size_t)o * 9 + tap) * Cin + c + 1] = acc[j][hf * 2 + 1];
+        }
+    }
+}
+
+// Sum the split partials in split order (deterministic).
+__global__ void sum_partials_kernel(const float* __restrict__ part, float* __restrict__ out, int splits, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int k = 0; k < splits; ++k) s += part[(size_t)k * n + i];
+        out[i] = s;
+    }
+}
+
+// db[o] = sum over pixels of dY[pix][o]: one CTA per channel block, fixed order.
+__global__ void bias_grad_kernel(const bf16* __restrict__ dY, float* __restrict__ db, size_t pixels, int Cout) {
+    __shared__ float red[256];
+    const int o = blockIdx.x;
+    float s = 0.f;
+    for (size_t p = threadIdx.x; p < pixels; p += blockDim.x) s += __bfloat162float(dY[p * Cout + o]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) db[o] = red[0];
+}
+
+// W'[c][8 - tap][o] = W[o][tap][c]: the weights of the data-gradient convolution.
+__global__ void flip_transpose_kernel(const bf16* __restrict__ Wt, bf16* __restrict__ Wf, int Cout, int Cin) {
+    const size_t n = (size_t)Cout * 9 * Cin;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % Cin);
+        const int tap = (int)((i / Cin) % 9);
+        const int o = (int)(i / ((size_t)9 * Cin));
+        Wf[((size_t)c * 9 + (8 - tap)) * Cout + o] = Wt[i];
+    }
+}
+
+// d *= (act > 0): back through a ReLU whose output was act.
+__global__ void relu_back_kernel(bf16* __restrict__ d, const bf16* __restrict__ act, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        if (!(__bfloat162float(act[i]) > 0.f)) d[i] = __float2bfloat16(0.f);
+}
+
+// a += b (BF16 tensors, FP32 add).
+__global__ void add_kernel(bf16* __restrict__ a, const bf16* __restrict__ b, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        a[i] = __float2bfloat16(__bfloat162float(a[i]) + __bfloat162float(b[i]));
+}
+
+// Network input: channel 0 = u0, channel 1 = log10 nu, channels 2..15 = 0.
+__global__ void input_kernel(const double* __restrict__ u0, const float* __restrict__ lognu, bf16* __restrict__ X,
+                             int N, size_t Ns) {
+    const size_t n_total = (size_t)N * Ns;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_total; i += (size_t)gridDim.x * blockDim.x) {
+        const int n = (int)(i / Ns);
+        bf16* x = X + i * kCinPad0;
+        x[0] = __float2bfloat16((float)u0[i]);
+        x[1] = __float2bfloat16(lognu[n]);
+#pragma unroll
+        for (int c = 2; c < kCinPad0; ++c) x[c] = __float2bfloat16(0.f);
+    }
+}
+
+// U_init[n][m][pix] = u0[n][pix] + out[n][pix][m] (solver layout, FP64).
+__global__ void output_kernel(const bf16* __restrict__ out, const double* __restrict__ u0, double* __restrict__ U,
+                              int N, int M, size_t Ns) {
+    const size_t total = (size_t)N * M * Ns;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t pix = i % Ns;
+        const int m = (int)((i / Ns) % M);
+        const int n = (int)(i / (Ns * M));
+        U[i] = u0[(size_t)n * Ns + pix] + (double)__bfloat162float(out[((size_t)n * Ns + pix) * M + m]);
+    }
+}
+
+// Training target of one solution: T[pix][m] = U[m][pix] - u0[pix] in BF16.
+__global__ void target_kernel(const double* __restrict__ U, const double* __restrict__ u0, bf16* __restrict__ T,
+                              int M, size_t Ns) {
+    const size_t total = (size_t)M * Ns;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int m = (int)(i % M);
+        const size_t pix = i / M;
+        T[i] = __float2bfloat16((float)(U[(size_t)m * Ns + pix] - u0[pix]));
+    }
+}
+
+// dout = 2 (out - target) / count and per-CTA partial sums of (out - target)^2.
+__global__ void mse_kernel(const bf16* __restrict__ out, const bf16* __restrict__ target, bf16* __restrict__ dout,
+                           float* __restrict__ partial, size_t n, float scale) {
+    __shared__ float red[256];
+    float s = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float d = __bfloat162float(out[i]) - __bfloat162float(target[i]);
+        s += d * d;
+        dout[i] = __float2bfloat16(2.f * d * scale);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// Adam on the FP32 masters (bias-corrected), then refresh the BF16 weights.
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ a, bf16* __restrict__ b, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        b[i] = __float2bfloat16(a[i]);
+}
+
+int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 16); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ the network
+
+struct Layer {
+    int cin, cout;          // cin as stored (input layer padded to 16)
+    int cin_public;         // cin in the public parameter layout
+    size_t w_off, b_off;    // offsets of weights [cout][9][cin] and bias in the FP32 master buffer
+};
+
+struct pit_net {
+    pit_net_shape shape{};
+    cudaStream_t stream = nullptr;
+    std::vector<Layer> layers;
+    size_t nparam = 0;       // stored parameters (padded input layer)
+    size_t nparam_public = 0;
+    float* p = nullptr;      // FP32 masters
+    float* g = nullptr;      // gradients
+    float* m = nullptr;
+    float* v = nullptr;
+    bf16* wb = nullptr;      // BF16 weights (same offsets)
+    bf16* wf = nullptr;      // flipped/transposed weights of one layer (scratch)
+    float* part = nullptr;   // split partials of the weight gradient
+    size_t part_n = 0;
+    float* loss_part = nullptr;
+    int step = 0;
+    // activations for max_batch images
+    bf16* in = nullptr;                 // [B][H][W][16]
+    std::vector<bf16*> xs;              // x after the lift and after each block: blocks + 1
+    std::vector<bf16*> hs;              // h inside each block
+    bf16* out = nullptr;                // [B][H][W][M]
+    bf16* d0 = nullptr;                 // gradient buffers
+    bf16* d1 = nullptr;
+    bf16* d2 = nullptr;
+    bf16* dout = nullptr;
+    float* lognu = nullptr;
+    char err[512] = "";
+};
+
+static pit_status nfail(pit_net* net, pit_status s, const char* fmt, ...) {
+    if (net) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(net->err, sizeof(net->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+#define NCK(call)                                                                                            \
+    do {                                                                                                     \
+        cudaError_t e_ = (call);                                                                             \
+        if (e_ != cudaSuccess)                                                                               \
+            return nfail(net, e_ == cudaErrorMemoryAllocation ? PIT_ENOMEM : PIT_ECUDA, "%s: %s (%s:%d)", #call, \
+                         cudaGetErrorString(e_), __FILE__, __LINE__);                                        \
+    } while (0)
+
+extern "C" long long pit_net_param_count(const pit_net_shape* s) {
+    if (!s) return -1;
+    const long long C = s->channels, M = s->levels;
+    return (C * 9 * 2 + C) + 2LL * s->blocks * (C * 9 * C + C) + (M * 9 * C + M);
+}
+
+static pit_status conv_fwd(pit_net* net, const bf16* X, const Layer& L, const bf16* res, bf16* Y, int B, int relu) {
+    const pit_net_shape& s = net->shape;
+    if (L.cin % 16 != 0 || L.cout % 16 != 0) return nfail(net, PIT_EINVAL, "conv channels must be multiples of 16");
+    dim3 grid((unsigned)(B * s.height * ((s.width + kPixTile - 1) / kPixTile)), (unsigned)((L.cout + kCoTile - 1) / kCoTile));
+    conv3x3_fwd_kernel<<<grid, 128, 0, net->stream>>>(X, net->wb + L.w_off, net->p + L.b_off, res, Y, B, s.height,
+                                                      s.width, L.cin, L.cout, relu);
+    NCK(cudaGetLastError());
+    return PIT_OK;
+}
+
+// dX = conv(dY, flipped W) without bias; dW, db into net->g.
+static pit_status conv_bwd(pit_net* net, const bf16* X, const bf16* dY, const Layer& L, bf16* dX, int B) {
+    const pit_net_shape& s = net->shape;
+    // the data-gradient convolution reads L.cout input channels in chunks of 16
+    if (L.cin % 16 != 0 || L.cout % 16 != 0) return nfail(net, PIT_EINVAL, "conv channels must be multiples of 16");
+    const int rows = B * s.height;
+    const int rows_per_split = std::max(1, (rows + 127) / 128);
+    const int splits = (rows + rows_per_split - 1) / rows_per_split;
+    const int ct = L.cin >= 64 ? 64 : 16;
+    dim3 grid((unsigned)splits, (unsigned)(9 * (L.cin / ct)), (unsigned)((L.cout + kCoTile - 1) / kCoTile));
+    if (ct == 64)
+        conv3x3_bwdw_kernel<64><<<grid, 128, 0, net->stream>>>(X, dY, net->part, B, s.height, s.width, L.cin, L.cout,
+                                                              rows_per_split);
+    else
+        conv3x3_bwdw_kernel<16><<<grid, 128, 0, net->stream>>>(X, dY, net->part, B, s.height, s.width, L.cin, L.cout,
+                                                              rows_per_split);
+    NCK(cudaGetLastError());
+    const size_t nw = (size_t)L.cout * 9 * L.cin;
+    sum_partials_kernel<<<grid_for(nw), 256, 0, net->stream>>>(net->part, net->g + L.w_off, splits, nw);
+    bias_grad_kernel<<<L.cout, 256, 0, net->stream>>>(dY, net->g + L.b_off, (size_t)B * s.height * s.width, L.cout);
+    if (dX) {
+        flip_transpose_kernel<<<grid_for(nw), 256, 0, net->stream>>>(net->wb + L.w_off, net->wf, L.cout, L.cin);
+        dim3 g2((unsigned)(B * s.height * ((s.width + kPixTile - 1) / kPixTile)), (unsigned)((L.cin + kCoTile - 1) / kCoTile));
+        // zero bias for the data gradient: use the tail of the gradient buffer's zero area
+        conv3x3_fwd_kernel<<<g2, 128, 0, net->stream>>>(dY, net->wf, net->loss_part + 1024, nullptr, dX, B, s.height,
+                                                        s.width, L.cout, L.cin, 0);
+    }
+    NCK(cudaGetLastError());
+    return PIT_OK;
+}
+
+static pit_status forward(pit_net* net, const double* u0, const float* lognu_dev, int B) {
+    const pit_net_shape& s = net->shape;
+    const size_t Ns = (size_t)s.height * s.width;
+    input_kernel<<<grid_for(B * Ns), 256, 0, net->stream>>>(u0, lognu_dev, net->in, B, Ns);
+    NCK(cudaGetLastError());
+    const int nb = s.blocks;
+    if (pit_status st = conv_fwd(net, net->in, net->layers[0], nullptr, net->xs[0], B, 1)) return st;
+    for (int k = 0; k < nb; ++k) {
+        if (pit_status st = conv_fwd(net, net->xs[k], net->layers[1 + 2 * k], nullptr, net->hs[k], B, 1)) return st;
+        if (pit_status st = conv_fwd(net, net->hs[k], net->layers[2 + 2 * k], net->xs[k], net->xs[k + 1], B, 0))
+            return st;
+    }
+    return conv_fwd(net, net->xs[nb], net->layers.back(), nullptr, net->out, B, 0);
+}
+
+extern "C" pit_status pit_net_create(const pit_net_shape* shape, unsigned long long seed, void* stream,
+                                     pit_net** out) {
+    if (!out) return PIT_EINVAL;
+    *out = nullptr;
+    if (!shape || shape->height < 1 || shape->width < 1 || shape->levels < 1 || shape->levels > 4096 ||
+        shape->channels < 16 || shape->channels % 16 != 0 || shape->channels > 4096 || shape->blocks < 0 ||
+        shape->max_batch < 1 || shape->levels % 16 != 0)
+        return PIT_EINVAL;
+    pit_net* net = new (std::nothrow) pit_net();
+    if (!net) return PIT_ENOMEM;
+    net->shape = *shape;
+    net->stream = static_cast<cudaStream_t>(stream);
+    const int C = shape->channels, M = shape->levels;
+    auto add = [&](int cin, int cout, int cin_pub) {
+        Layer L;
+        L.cin = cin;
+        L.cout = cout;
+        L.cin_public = cin_pub;
+        L.w_off = net->nparam;
+        net->nparam += (size_t)cout * 9 * cin;
+        L.b_off = net->nparam;
+        net->nparam += cout;
+        net->layers.push_back(L);
+    };
+    add(kCinPad0, C, 2);
+    for (int k = 0; k < shape->blocks; ++k) {
+        add(C, C, C);
+        add(C, C, C);
+    }
+    add(C, M, C);
+    net->nparam_public = (size_t)pit_net_param_count(shape);
+    auto setup = [&]() -> pit_status {
+        const size_t B = shape->max_batch, Ns = (size_t)shape->height * shape->width;
+        NCK(cudaMalloc(&net->p, sizeof(float) * net->nparam));
+        NCK(cudaMalloc(&net->g, sizeof(float) * net->nparam));
+        NCK(cudaMalloc(&net->m, sizeof(float) * net->nparam));
+        NCK(cudaMalloc(&net->v, sizeof(float) * net->nparam));
+        NCK(cudaMalloc(&net->wb, sizeof(bf16) * net->nparam));
+        size_t wmax = 0;
+        for (auto& L : net->layers) wmax = std::max(wmax, (size_t)L.cout * 9 * L.cin);
+        NCK(cudaMalloc(&net->wf, sizeof(bf16) * wmax));
+        net->part_n = 128 * wmax;
+        NCK(cudaMalloc(&net->part, sizeof(float) * net->part_n));
+        NCK(cudaMalloc(&net->loss_part, sizeof(float) * (1024 + 4096)));
+        NCK(cudaMemsetAsync(net->loss_part, 0, sizeof(float) * (1024 + 4096), net->stream));
+        NCK(cudaMalloc(&net->in, sizeof(bf16) * B * Ns * kCinPad0));
+        for (int k = 0; k <= shape->blocks; ++k) {
+            bf16* x;
+            NCK(cudaMalloc(&x, sizeof(bf16) * B * Ns * C));
+            net->xs.push_back(x);
+        }
+        for (int k = 0; k < shape->blocks; ++k) {
+            bf16* hbuf;
+            NCK(cudaMalloc(&hbuf, sizeof(bf16) * B * Ns * C));
+            net->hs.push_back(hbuf);
+        }
+        const size_t cm = std::max<size_t>(C, M);
+        NCK(cudaMalloc(&net->out, sizeof(bf16) * B * Ns * M));
+        NCK(cudaMalloc(&net->dout, sizeof(bf16) * B * Ns * M));
+        NCK(cudaMalloc(&net->d0, sizeof(bf16) * B * Ns * cm));
+        NCK(cudaMalloc(&net->d1, sizeof(bf16) * B * Ns * cm));
+        NCK(cudaMalloc(&net->d2, sizeof(bf16) * B * Ns * std::max<size_t>(cm, kCinPad0)));
+        NCK(cudaMalloc(&net->lognu, sizeof(float) * B));
+        // He-normal init (seeded) for hidden layers, zero head: the untrained net predicts
+        // zero corrections, i.e. the plain guess
+        std::vector<float> h(net->nparam, 0.f);
+        std::mt19937_64 rng(seed);
+        for (size_t li = 0; li < net->layers.size(); ++li) {
+            const Layer& L = net->layers[li];
+            if (li + 1 == net->layers.size()) break;
+            std::normal_distribution<float> nd(0.f, std::sqrt(2.f / (9.f * L.cin_public)));
+            for (int o = 0; o < L.cout; ++o)
+                for (int t = 0; t < 9; ++t)
+                    for (int c = 0; c < L.cin; ++c)
+                        h[L.w_off + ((size_t)o * 9 + t) * L.cin + c] = c < L.cin_public ? nd(rng) : 0.f;
+        }
+        // residual branches start small so each block begins near the identity
+        for (int k = 0; k < shape->blocks; ++k) {
+            const Layer& L = net->layers[2 + 2 * k];
+            for (size_t i = 0; i < (size_t)L.cout * 9 * L.cin; ++i) h[L.w_off + i] *= 0.1f;
+        }
+        NCK(cudaMemcpyAsync(net->p, h.data(), sizeof(float) * net->nparam, cudaMemcpyHostToDevice, net->stream));
+        NCK(cudaMemsetAsync(net->m, 0, sizeof(float) * net->nparam, net->stream));
+        NCK(cudaMemsetAsync(net->v, 0, sizeof(float) * net->nparam, net->stream));
+        to_bf16_kernel<<<grid_for(net->nparam), 256, 0, net->stream>>>(net->p, net->wb, net->nparam);
+        NCK(cudaGetLastError());
+        NCK(cudaStreamSynchronize(net->stream));
+        return PIT_OK;
+    };
+    const pit_status st = setup();
+    if (st != PIT_OK) {
+        fprintf(stderr, "pit_net_create: %s\n", net->err);
+        pit_net_destroy(net);
+        return st;
+    }
+    *out = net;
+    return PIT_OK;
+}
+
+extern "C" void pit_net_destroy(pit_net* net) {
+    if (!net) return;
+    cudaFree(net->p);
+    cudaFree(net->g);
+    cudaFree(net->m);
+    cudaFree(net->v);
+    cudaFree(net->wb);
+    cudaFree(net->wf);
+    cudaFree(net->part);
+    cudaFree(net->loss_part);
+    cudaFree(net->in);
+    for (auto x : net->xs) cudaFree(x);
+    for (auto x : net->hs) cudaFree(x);
+    cudaFree(net->out);
+    cudaFree(net->dout);
+    cudaFree(net->d0);
+    cudaFree(net->d1);
+    cudaFree(net->d2);
+    cudaFree(net->lognu);
+    delete net;
+}
+
+extern "C" const char* pit_net_last_error(const pit_net* net) { return net ? net->err : "null network"; }
+
+// Public flat layout <-> stored layout (the input layer stores 16 channels, 2 public).
+static void public_to_stored(const pit_net* net, const float* pub, std::vector<float>& st) {
+    st.assign(net->nparam, 0.f);
+    size_t o = 0;
+    for (const Layer& L : net->layers) {
+        for (int co = 0; co < L.cout; ++co)
+            for (int t = 0; t < 9; ++t)
+                for (int c = 0; c < L.cin_public; ++c) st[L.w_off + ((size_t)co * 9 + t) * L.cin + c] = pub[o++];
+        for (int co = 0; co < L.cout; ++co) st[L.b_off + co] = pub[o++];
+    }
+}
+
+static void stored_to_public(const pit_net* net, const std::vector<float>& st, float* pub) {
+    size_t o = 0;
+    for (const Layer& L : net->layers) {
+        for (int co = 0; co < L.cout; ++co)
+            for (int t = 0; t < 9; ++t)
+                for (int c = 0; c < L.cin_public; ++c) pub[o++] = st[L.w_off + ((size_t)co * 9 + t) * L.cin + c];
+        for (int co = 0; co < L.cout; ++co) pub[o++] = st[L.b_off + co];
+    }
+}
+
+extern "C" pit_status pit_net_get_params(pit_net* net, float* params_host) {
+    if (!net || !params_host) return PIT_EINVAL;
+    std::vector<float> st(net->nparam);
+    NCK(cudaMemcpyAsync(st.data(), net->p, sizeof(float) * net->nparam, cudaMemcpyDeviceToHost, net->stream));
+    NCK(cudaStreamSynchronize(net->stream));
+    stored_to_public(net, st, params_host);
+    return PIT_OK;
+}
+
+extern "C" pit_status pit_net_set_params(pit_net* net, const float* params_host) {
+    if (!net || !params_host) return PIT_EINVAL;
+    std::vector<float> st;
+    public_to_stored(net, params_host, st);
+    NCK(cudaMemcpyAsync(net->p, st.data(), sizeof(float) * net->nparam, cudaMemcpyHostToDevice, net->stream));
+    to_bf16_kernel<<<grid_for(net->nparam), 256, 0, net->stream>>>(net->p, net->wb, net->nparam);
+    NCK(cudaGetLastError());
+    NCK(cudaStreamSynchronize(net->stream));
+    return PIT_OK;
+}
+
+static pit_status set_lognu(pit_net* net, const float* lognu_host, int B) {
+    NCK(cudaMemcpyAsync(net->lognu, lognu_host, sizeof(float) * B, cudaMemcpyHostToDevice, net->stream));
+    return PIT_OK;
+}
+
+extern "C" pit_status pit_net_guess(pit_net* net, const double* u0_dev, const float* lognu_host, int B,
+                                    double* U_dev) {
+    if (!net || !u0_dev || !lognu_host || !U_dev || B < 1 || B > net->shape.max_batch) return PIT_EINVAL;
+    if (pit_status st = set_lognu(net, lognu_host, B)) return st;
+    if (pit_status st = forward(net, u0_dev, net->lognu, B)) return st;
+    const size_t Ns = (size_t)net->shape.height * net->shape.width;
+    output_kernel<<<grid_for((size_t)B * net->shape.levels * Ns), 256, 0, net->stream>>>(net->out, u0_dev, U_dev, B,
+                                                                                       net->shape.levels, Ns);
+    NCK(cudaGetLastError());
+    return PIT_OK;
+}
+
+extern "C" pit_status pit_net_make_target(pit_net* net, const double* u0_dev, const double* U_dev, void* target_dev) {
+    if (!net || !u0_dev || !U_dev || !target_dev) return PIT_EINVAL;
+    const size_t Ns = (size_t)net->shape.height * net->shape.width;
+    target_kernel<<<grid_for((size_t)net->shape.levels * Ns), 256, 0, net->stream>>>(
+        U_dev, u0_dev, static_cast<bf16*>(target_dev), net->shape.levels, Ns);
+    NCK(cudaGetLastError());
+    return PIT_OK;
+}
+
+// Loss and gradients of one batch (targets: BF16 [B][H][W][M]).
+static pit_status loss_grad(pit_net* net, const double* u0_dev, const float* lognu_host, const void* target_dev,
+                            int B, float* loss_out) {
+    const pit_net_shape& s = net->shape;
+    const size_t Ns = (size_t)s.height * s.width;
+    if (pit_status st = set_lognu(net, lognu_host, B)) return st;
+    if (pit_status st = forward(net, u0_dev, net->lognu, B)) return st;
+    const size_t nout = (size_t)B * Ns * s.levels;
+    const int blocks = std::min(1024, grid_for(nout));
+    mse_kernel<<<blocks, 256, 0, net->stream>>>(net->out, static_cast<const bf16*>(target_dev), net->dout,
+                                                net->loss_part, nout, 1.f / (float)nout);
+    NCK(cudaGetLastError());
+    // backward: head, blocks in reverse, lift
+    const int nb = s.blocks;
+    bf16* dx = net->d0;
+    if (pit_status st = conv_bwd(net, net->xs[nb], net->dout, net->layers.back(), dx, B)) return st;
+    for (int k = nb - 1; k >= 0; --k) {
+        // x_{k+1} = x_k + conv2(h_k): gradient dx flows to conv2 and straight to x_k
+        bf16* dh = net->d1;
+        if (pit_status st = conv_bwd(net, net->hs[k], dx, net->layers[2 + 2 * k], dh, B)) return st;
+        relu_back_kernel<<<grid_for(B * Ns * s.channels), 256, 0, net->stream>>>(dh, net->hs[k], B * Ns * s.channels);
+        bf16* dxi = net->d2;
+        if (pit_status st = conv_bwd(net, net->xs[k], dh, net->layers[1 + 2 * k], dxi, B)) return st;
+        add_kernel<<<grid_for(B * Ns * s.channels), 256, 0, net->stream>>>(dx, dxi, B * Ns * s.channels);
+        NCK(cudaGetLastError());
+    }
+    relu_back_kernel<<<grid_for(B * Ns * s.channels), 256, 0, net->stream>>>(dx, net->xs[0], B * Ns * s.channels);
+    if (pit_status st = conv_bwd(net, net->in, dx, net->layers[0], nullptr, B)) return st;
+    if (loss_out) {
+        std::vector<float> part(blocks);
+        NCK(cudaMemcpyAsync(part.data(), net->loss_part, sizeof(float) * blocks, cudaMemcpyDeviceToHost, net->stream));
+        NCK(cudaStreamSynchronize(net->stream));
+        double sum = 0.0;
+        for (float f : part) sum += f;
+        *loss_out = (float)(sum / (double)nout);
+    }
+    return PIT_OK;
+}
+
+extern "C" pit_status pit_net_gradients(pit_net* net, const double* u0_dev, const float* lognu_host,
+                                        const void* target_dev, int B, float* loss_out, float* grads_host) {
+    if (!net || !u0_dev || !lognu_host || !target_dev || B < 1 || B > net->shape.max_batch) return PIT_EINVAL;
+    if (pit_status st = loss_grad(net, u0_dev, lognu_host, target_dev, B, loss_out)) return st;
+    if (grads_host) {
+        std::vector<float> st(net->nparam);
+        NCK(cudaMemcpyAsync(st.data(), net->g, sizeof(float) * net->nparam, cudaMemcpyDeviceToHost, net->stream));
+        NCK(cudaStreamSynchronize(net->stream));
+        stored_to_public(net, st, grads_host);
+    }
+    return PIT_OK;
+}
+
+extern "C" pit_status pit_net_train_step(pit_net* net, const double* u0_dev, const float* lognu_host,
+                                         const void* target_dev, int B, float lr, float* loss_out) {
+    if (!net || !u0_dev || !lognu_host || !target_dev || B < 1 || B > net->shape.max_batch || !(lr > 0.f))
+        return PIT_EINVAL;
+    if (pit_status st = loss_grad(net, u0_dev, lognu_host, target_dev, B, loss_out)) return st;
+    net->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)net->step), c2 = 1.f - std::pow(b2, (float)net->step);
+    adam_kernel<<<grid_for(net->nparam), 256, 0, net->stream>>>(net->p, net->g, net->m, net->v, net->nparam, lr, b1,
+                                                                b2, 1e-8f, c1, c2);
+    to_bf16_kernel<<<grid_for(net->nparam), 256, 0, net->stream>>>(net->p, net->wb, net->nparam);
+    NCK(cudaGetLastError());
+    return PIT_OK;
+}

@@ -28,7 +28,9 @@ PIT_NOALLOC_MAX_NX, PIT_NOALLOC_MAX_TEAM, PIT_NOALLOC_MAX_LEVELS = 512, 160, 409
 EXPORTS = ("pit_default_options", "pit_create", "pit_set_data", "pit_fill_plain_guess", "pit_residual",
            "pit_assemble", "pit_block_solve", "pit_newton_step", "pit_solve", "pit_solve_host", "pit_last_error",
            "pit_status_string", "pit_destroy", "pit_block_solve_noalloc", "pit_batch_create", "pit_batch_solve",
-           "pit_batch_result", "pit_batch_last_error", "pit_batch_destroy")
+           "pit_batch_result", "pit_batch_last_error", "pit_batch_destroy", "pit_net_param_count", "pit_net_create",
+           "pit_net_get_params", "pit_net_set_params", "pit_net_guess", "pit_net_make_target", "pit_net_gradients",
+           "pit_net_train_step", "pit_net_last_error", "pit_net_destroy")
 
 
 class pit_grid(ctypes.Structure):
@@ -89,6 +91,11 @@ class pit_batch_info(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class pit_net_shape(ctypes.Structure):
+    _fields_ = [("height", ctypes.c_int), ("width", ctypes.c_int), ("levels", ctypes.c_int),
+                ("channels", ctypes.c_int), ("blocks", ctypes.c_int), ("max_batch", ctypes.c_int)]
 
 
 class PitError(RuntimeError):
@@ -155,6 +162,28 @@ def lib():
             L.pit_batch_last_error.restype = ctypes.c_char_p
             L.pit_batch_destroy.argtypes = [P]
             L.pit_batch_destroy.restype = None
+            F = ctypes.POINTER(ctypes.c_float)
+            NS = ctypes.POINTER(pit_net_shape)
+            L.pit_net_param_count.argtypes = [NS]
+            L.pit_net_param_count.restype = ctypes.c_longlong
+            L.pit_net_create.argtypes = [NS, ctypes.c_ulonglong, V, ctypes.POINTER(P)]
+            L.pit_net_create.restype = st
+            L.pit_net_get_params.argtypes = [P, F]
+            L.pit_net_get_params.restype = st
+            L.pit_net_set_params.argtypes = [P, F]
+            L.pit_net_set_params.restype = st
+            L.pit_net_guess.argtypes = [P, V, F, ctypes.c_int, V]
+            L.pit_net_guess.restype = st
+            L.pit_net_make_target.argtypes = [P, V, V, V]
+            L.pit_net_make_target.restype = st
+            L.pit_net_gradients.argtypes = [P, V, F, V, ctypes.c_int, F, F]
+            L.pit_net_gradients.restype = st
+            L.pit_net_train_step.argtypes = [P, V, F, V, ctypes.c_int, ctypes.c_float, F]
+            L.pit_net_train_step.restype = st
+            L.pit_net_last_error.argtypes = [P]
+            L.pit_net_last_error.restype = ctypes.c_char_p
+            L.pit_net_destroy.argtypes = [P]
+            L.pit_net_destroy.restype = None
             _lib = L
         return _lib
 
@@ -419,3 +448,103 @@ def pit_batch_result(batch: Batch, i: int) -> dict:
 
 def pit_batch_destroy(batch: Batch):
     batch.close()
+
+
+# ------------------------------------------------------- learned initial guess
+
+class Net:
+    """A pit_net handle (the learned initial-guess network)."""
+
+    def __init__(self, handle, shape: pit_net_shape):
+        self.handle = handle
+        self.shape = shape
+        self.nparam = int(lib().pit_net_param_count(ctypes.byref(shape)))
+
+    def _check(self, status: int):
+        if status != PIT_OK:
+            raise PitError(status, lib().pit_net_last_error(self.handle).decode())
+
+    def close(self):
+        if self.handle:
+            lib().pit_net_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _fptr(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def pit_net_create(height, width, levels, channels=64, blocks=4, max_batch=16, seed=0, stream=None) -> Net:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif not isinstance(stream, int):
+        stream = stream.cuda_stream
+    shape = pit_net_shape(int(height), int(width), int(levels), int(channels), int(blocks), int(max_batch))
+    h = ctypes.c_void_p()
+    s = lib().pit_net_create(ctypes.byref(shape), ctypes.c_ulonglong(seed), ctypes.c_void_p(stream), ctypes.byref(h))
+    if s != PIT_OK:
+        raise PitError(s, "pit_net_create failed (see stderr)")
+    return Net(h, shape)
+
+
+def pit_net_get_params(net: Net) -> np.ndarray:
+    out = np.empty(net.nparam, dtype=np.float32)
+    net._check(lib().pit_net_get_params(net.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return out
+
+
+def pit_net_set_params(net: Net, params):
+    arr, ptr = _fptr(params)
+    assert arr.size == net.nparam
+    net._check(lib().pit_net_set_params(net.handle, ptr))
+
+
+def pit_net_guess(net: Net, u0, lognu, U):
+    """u0: float64 CUDA tensor [B, Ns]; lognu: B floats; U: float64 CUDA tensor [B, M, Ns] (out)."""
+    B = len(lognu)
+    arr, ptr = _fptr(lognu)
+    net._check(lib().pit_net_guess(net.handle, _dptr(u0, "u0"), ptr, B, _dptr(U, "U")))
+
+
+def pit_net_make_target(net: Net, u0, U, target):
+    """target: a CUDA tensor of int16 / bfloat16 with H*W*M elements."""
+    net._check(lib().pit_net_make_target(net.handle, _dptr(u0, "u0"), _dptr(U, "U"),
+                                         ctypes.c_void_p(target.data_ptr())))
+
+
+def pit_net_gradients(net: Net, u0, lognu, target, want_grads=True):
+    B = len(lognu)
+    arr, ptr = _fptr(lognu)
+    loss = ctypes.c_float()
+    grads = np.empty(net.nparam, dtype=np.float32) if want_grads else None
+    net._check(lib().pit_net_gradients(net.handle, _dptr(u0, "u0"), ptr, ctypes.c_void_p(target.data_ptr()), B,
+                                       ctypes.byref(loss),
+                                       grads.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if want_grads else None))
+    return loss.value, grads
+
+
+def pit_net_train_step(net: Net, u0, lognu, target, lr, want_loss=False):
+    B = len(lognu)
+    arr, ptr = _fptr(lognu)
+    loss = ctypes.c_float()
+    net._check(lib().pit_net_train_step(net.handle, _dptr(u0, "u0"), ptr, ctypes.c_void_p(target.data_ptr()), B,
+                                        ctypes.c_float(lr), ctypes.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def pit_net_destroy(net: Net):
+    net.close()
