@@ -102,12 +102,14 @@ typedef struct {
                                Jacobian entries, right-hand sides and level-solve iterates are
                                held and updated in FP32, inside FP64 Newton (residual, update
                                and norms stay FP64; Newton then acts as iterative refinement) */
-    int window;             /* pit_solve with the wavefront: 0 (default) = all M levels at once;
-                               W > 0 = levels in consecutive windows of W. The all-at-once system
-                               is block lower-triangular in time, so the solution is the same;
-                               each window starts from the plain guess u^n = u^{s-1} at its first
-                               level s (the caller's iterate is not used), which keeps Newton in
-                               its convergence region over long horizons */
+    int window;             /* pit_solve with the wavefront: 0 (default) = all M levels at once
+                               from the caller's iterate; W > 0 = levels in consecutive windows of
+                               W, each starting from the plain guess u^n = u^{s-1} at its first
+                               level s. The all-at-once system is block lower-triangular in time,
+                               so the solution is the same. In both modes a window whose Newton
+                               diverges (residual not finite or above 1e10) or does not converge
+                               is halved and restarted from the plain guess, and grows back
+                               after a success */
 } pit_options;
 
 enum { PIT_FP64 = 0, PIT_FP32_INNER = 1 };

@@ -722,26 +722,42 @@ static pit_status solve_window(pit_ctx* ctx, double* U_dev, int s, int Mw, pit_s
     }
 }
 
+static pit_status fill_window_guess(pit_ctx* ctx, double* U_dev, int s, int Mw) {
+    const double* from = s == 0 ? ctx->u0 : U_dev + (size_t)(s - 1) * ctx->Ns;
+    const int blocks = std::max(1, std::min(ctx->num_sms * 8, (int)(((size_t)Mw * ctx->Ns + kNT - 1) / kNT)));
+    plain_guess_kernel<<<blocks, kNT, 0, ctx->stream>>>(from, U_dev + (size_t)s * ctx->Ns, ctx->Ns, Mw);
+    CK(cudaGetLastError());
+    return PIT_OK;
+}
+
+// Levels in windows (all M at once when window = 0). A window whose Newton diverges
+// or does not converge is halved and restarted from the plain guess at its first
+// level (the solution is the same: the system is block lower-triangular in time);
+// after a success the window grows back toward its nominal length.
 static pit_status solve_wave(pit_ctx* ctx, double* U_dev, pit_solve_info* inf) {
     inf->wave_teams = ctx->K;
     inf->wave_team_ctas = ctx->Gw;
     const int M = ctx->M;
     const int Wn = ctx->opt.window > 0 ? std::min(ctx->opt.window, M) : M;
-    for (int s = 0; s < M; s += Wn) {
-        const int Mw = std::min(Wn, M - s);
-        if (Wn < M) {
-            // plain guess for the window from the converged level before it
-            const double* from = s == 0 ? ctx->u0 : U_dev + (size_t)(s - 1) * ctx->Ns;
-            const int blocks = std::max(1, std::min(ctx->num_sms * 8, (int)(((size_t)Mw * ctx->Ns + kNT - 1) / kNT)));
-            plain_guess_kernel<<<blocks, kNT, 0, ctx->stream>>>(from, U_dev + (size_t)s * ctx->Ns, ctx->Ns, Mw);
-            CK(cudaGetLastError());
-        }
+    int w = Wn;
+    bool caller_iterate = Wn == M;  // the first attempt over all levels starts from the caller's U
+    for (int s = 0; s < M;) {
+        const int Mw = std::min(w, M - s);
+        if (!caller_iterate) CHECK_RET(fill_window_guess(ctx, U_dev, s, Mw));
+        caller_iterate = false;
         int iters = 0;
         const pit_status st = solve_window(ctx, U_dev, s, Mw, inf, &iters);
         inf->windows += 1;
         inf->newton_iters_total += iters;
         inf->newton_iters = std::max(inf->newton_iters, iters);
-        if (st != PIT_OK) return st;
+        if (st == PIT_OK) {
+            s += Mw;
+            w = std::min(Wn, 2 * w);
+        } else if ((st == PIT_ENOCONV || st == PIT_EDIVERGED) && Mw > 1) {
+            w = std::max(1, Mw / 2);
+        } else {
+            return st;
+        }
     }
     // the residual of the whole final iterate decides convergence
     CHECK_RET(enqueue_residual(ctx, U_dev, ctx->R));

@@ -34,6 +34,9 @@ struct OpConst {
 // Status codes shared with the host (values of pit_status).
 enum : int { ST_OK = 0, ST_ENOCONV = 4, ST_EDIVERGED = 5, ST_ETIMEOUT = 6 };
 
+// A Newton residual above this (or not finite) counts as divergence.
+constexpr double kDiverged = 1e10;
+
 // --------------------------------------------------------- memory primitives
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
@@ -1100,8 +1103,17 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
             double g3[4];
             if (!reduce_finish<4, true>(c, t, reduce_arrive<4>(t, v3), g3, m.red + 32, &s_ok)) return;
             if (g3[2] >= 2.0) goto done;  // another iteration has converged (or the launch aborts)
-            if (g3[0] != g3[0]) {
-                if (threadIdx.x == 0) team_fail(c, ST_EDIVERGED);
+            if (!(g3[0] < kDiverged)) {
+                // NaN/Inf or a runaway residual: Newton diverges on this range of levels. One
+                // team (a batch problem) ends its window and lets the caller retry a shorter
+                // one; several teams end the launch with PIT_EDIVERGED.
+                if (threadIdx.x == 0) {
+                    if (a.K == 1) {
+                        if (b == 0 && a.kconv) *a.kconv = -2;
+                    } else {
+                        team_fail(c, ST_EDIVERGED);
+                    }
+                }
                 goto done;
             }
             {
@@ -1258,8 +1270,12 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
     const int W = in.window > 0 ? in.window : M;
     unsigned long long base = 0;
     int iters_total = 0, conv_windows = 0;
-    for (int s = 0; s < M; s += W) {
-        const int Mw = min(W, M - s);
+    // Windows adapt: a window whose Newton diverges or does not converge is halved and
+    // restarted from the plain guess at its first level; after a success the window
+    // length grows back toward W.
+    int w = W;
+    for (int s = 0; s < M;) {
+        const int Mw = min(w, M - s);
         // plain guess for the window from its previous level: own rows only
         const double* from = s == 0 ? in.u0 : in.U + (long long)(s - 1) * Ns;
         for (int n = 0; n < Mw; ++n) {
@@ -1304,7 +1320,9 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
         a.cell_iters = nullptr;
         a.cta_sumsq = nullptr;
         a.timers = nullptr;
-        // converged iteration index: written by CTA 0 of the team, read back by it
+        // converged iteration index (or -1 / -2 for not converged / diverged): written
+        // by CTA 0 of the team; the decision below must be the same on every CTA, so it
+        // goes through a team reduction
         __shared__ int s_kdone;
         a.kconv = b == 0 ? ws.kconv : nullptr;
         if (threadIdx.x == 0 && b == 0) *ws.kconv = -1;
@@ -1321,13 +1339,25 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
         }
         __syncthreads();
         if (s_ok) return;  // the launch aborts (read once per CTA)
-        if (s_kdone >= 0) {
-            iters_total += s_kdone + 1;
+        double kv[1] = {b == 0 ? (double)(s_kdone + 3) : 0.0};  // CTA 0's result, shared by max
+        double kg[1];
+        if (!reduce_finish<1, true>(c, t, reduce_arrive<1>(t, kv), kg, red + 32, &s_ok)) return;
+        const int kdone = (int)kg[0] - 3;
+        base += (unsigned long long)ba.newton_max * Mw + 1;
+        if (kdone >= 0) {
+            iters_total += kdone + 1;
             ++conv_windows;
+            s += Mw;
+            w = min(W, 2 * w);
         } else {
             iters_total += ba.newton_max;
+            if (Mw > 1) {
+                w = max(1, Mw / 2);  // retry the same first level with a shorter window
+            } else {
+                s += 1;              // a single level that does not converge: go on
+                w = 1;
+            }
         }
-        base += (unsigned long long)ba.newton_max * Mw + 1;
         __syncthreads();
     }
     // final residual of the whole solution, all levels (needs the neighbours' last updates)

@@ -137,6 +137,19 @@ def evaluate(cfg: LearnedConfig, net, probs):
     return rows, U.view(p.M, -1).cpu().numpy()
 
 
+def train_flops_per_step(cfg: LearnedConfig) -> float:
+    """Tensor-core flops (FMA = 2) of one training step: forward, data gradients of all
+    layers but the input one, weight gradients of all layers (input channels padded to 16)."""
+    pix = cfg.batch * cfg.n * cfg.n
+    C, M = cfg.channels, cfg.M
+    fwd = [(16, C)] + [(C, C)] * (2 * cfg.blocks) + [(C, M)]
+    per = lambda ci, co: 2.0 * pix * co * 9 * ci
+    f = sum(per(ci, co) for ci, co in fwd)          # forward
+    f += sum(per(ci, co) for ci, co in fwd[1:])     # data gradients
+    f += sum(per(ci, co) for ci, co in fwd)         # weight gradients
+    return f
+
+
 def run(cfg: LearnedConfig) -> dict:
     import torch
     net = pit.pit_net_create(cfg.n, cfg.n, cfg.M, cfg.channels, cfg.blocks, max_batch=cfg.batch, seed=cfg.seed)
@@ -150,9 +163,11 @@ def run(cfg: LearnedConfig) -> dict:
     torch.cuda.synchronize()
     ok = [r for r in rows if r["plain_ok"] and r["learned_ok"]]
     dof = cfg.n * cfg.n * cfg.M
+    flops_step = train_flops_per_step(cfg)
     rep = {
         "config": {k: v for k, v in cfg.__dict__.items() if k != "extra"},
-        "generation_s": t_gen, "training_s": t_train, "train_steps": steps,
+        "generation_s": t_gen, "generation_dof_per_s": cfg.train * dof / t_gen, "training_s": t_train,
+        "train_steps": steps, "train_tflops": flops_step * steps / t_train / 1e12,
         "loss_first": losses[0] if losses else None, "loss_last": losses[-1] if losses else None,
         "held_out_converged_plain": sum(r["plain_ok"] for r in rows),
         "held_out_converged_learned": sum(r["learned_ok"] for r in rows),
