@@ -167,6 +167,24 @@ pit_status pit_set_data(pit_ctx* ctx, const double* u0_dev, const double* bc_dev
 /* Write the plain initial iterate u^n = u^0, n = 1..M, into U_dev [M][Ns]. */
 pit_status pit_fill_plain_guess(pit_ctx* ctx, double* U_dev);
 
+/* The paper's initial iterate (Sec. 4): solve the context's problem on a grid
+ * coarsened by cf >= 2 in both spatial directions and in time -- (nx+1)/cf - 1 by
+ * (ny+1)/cf - 1 interior nodes on the same domain, M/cf levels over the same end time --
+ * then interpolate the coarse solution to every fine node and level with natural cubic
+ * splines along x, y and t, and write it to U_dev [M][Ns].
+ * The coarse data are sampled from the context's data (pit_set_data): u^0 and sources
+ * bilinearly in space, Dirichlet data linearly along each edge, both linearly in time
+ * (exact injection where coarse and fine nodes coincide). The coarse problem is solved
+ * all at once with the context's options (team sizes re-chosen); its converged result
+ * is the sequential BDF1 solution on the coarse grid. coarse_info (may be NULL)
+ * receives that solve's report.
+ * Allocates and frees its temporaries (about (M/cf + 1) * Ns * 3 doubles) and
+ * synchronizes the context's stream before returning.
+ * PIT_EINVAL for cf < 2 or a grid too small to coarsen; a failed coarse solve returns
+ * its status (PIT_ENOCONV, PIT_EDIVERGED, ...) and leaves U_dev unwritten -- fall back
+ * to pit_fill_plain_guess. */
+pit_status pit_coarse_guess(pit_ctx* ctx, int cf, double* U_dev, pit_solve_info* coarse_info);
+
 /* Row (a1): the all-at-once residual of eq. 4-5 for all M levels at once,
  * R_dev[n] = -tau[(u^n - u^{n-1})/tau + F(u^n) - q^n] with F of eq. 3.
  * U_dev [M][Ns] in, R_dev [M][Ns] out (may not alias U_dev). If res_inf is not
@@ -296,6 +314,38 @@ pit_status pit_net_train_step(pit_net* net, const double* u0_dev, const float* l
                               int B, float lr, float* loss_out);
 const char* pit_net_last_error(const pit_net* net);
 void pit_net_destroy(pit_net* net);
+
+/* ---------------------------------------------------------------- literal product form
+ * The decoupled systems of Theorem 1 (eq. 8) exactly as the paper states them, built
+ * by the recursion of Sec. 5: P^1 = A_1, P^n = P^{n-1} A_n, r~^1 = r^1,
+ * r~^n = P^{n-1} r^n + r~^{n-1}; each P^n du^n = r~^n is scaled by diag(P^n) (the
+ * preconditioner of Sec. 7) and solved by banded LU without pivoting (the direct solver
+ * of Sec. 8), all levels in parallel. P^n has the 2n^2 + 2n + 1 diagonals of Remark 2
+ * and is stored by diagonal offset; memory grows like (2/3) M^3 Ns doubles for the
+ * products plus the dense bands (half width n nx) of the factorizations. The condition
+ * number of P^n grows like K^n (Sec. 7, eq. 15): beyond eq. 15's bound on M the result
+ * loses its digits, while pit_block_solve (nested form, same exact inverse) does not. */
+typedef struct {
+    int levels;           /* M */
+    long long diagonals;  /* stored diagonals of P^M: 2M^2 + 2M + 1 */
+    long long half_band;  /* half bandwidth of the factorization of P^M: M nx */
+    double min_pivot;     /* smallest |pivot| met by the LU of the scaled systems */
+    float ms_assemble, ms_products, ms_factor;  /* device time of the three stages */
+} pit_product_info;
+
+/* One product-form block solve: the Jacobians A_n at U_dev [M][Ns], right-hand sides
+ * R_dev [M][Ns] (the tau-scaled residual, as for pit_block_solve), solution dU_dev
+ * [M][Ns]. Allocates its workspace per call and synchronizes the stream.
+ * PIT_EUNSUPPORTED for M > 180; PIT_ENOMEM when the products do not fit half the
+ * free device memory; PIT_ECUDA when a band row of P^M does not fit shared memory. */
+pit_status pit_product_form_solve(pit_ctx* ctx, const double* U_dev, const double* R_dev, double* dU_dev,
+                                  pit_product_info* info);
+
+/* Newton on the all-at-once system with the product-form block solve in every
+ * iteration (the method as the paper states it), from the iterate in U_dev, until
+ * ||R||_inf <= tol_res or newton_max iterations (context options). info as for pit_solve
+ * (steps[k].ms_solve = products + factorization). */
+pit_status pit_solve_product(pit_ctx* ctx, double* U_dev, pit_solve_info* info);
 
 /* Limits of pit_block_solve_noalloc's built-in workspace. */
 #define PIT_NOALLOC_MAX_NX 512       /* interior nodes per grid row */

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "pit.h"
+#include "pit_internal.h"
 #include "pit_kernels.cuh"
 
 using namespace pit;
@@ -395,8 +396,16 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
         ctx->G = (ny + rows_per - 1) / rows_per;
         ctx->rows_base = ny / ctx->G;
         ctx->rows_rem = ny % ctx->G;
-        CK(cudaFuncSetAttribute(reinterpret_cast<const void*>(chain_kernel<kNT>),
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->chain_smem));
+        // The limit is a property of the kernel, shared by every context in the process:
+        // raise it to the device maximum (never lower it to this context's need, which
+        // would break the launches of a context created earlier with larger strips).
+        {
+            cudaFuncAttributes fa;
+            CK(cudaFuncGetAttributes(&fa, chain_kernel<kNT>));
+            CK(cudaFuncSetAttribute(reinterpret_cast<const void*>(chain_kernel<kNT>),
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(ctx->smem_optin - fa.sharedSizeBytes)));
+        }
         int per_sm = 0;
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chain_kernel<kNT>, kNT, ctx->chain_smem));
         if ((long long)per_sm * ctx->num_sms < ctx->G)
@@ -429,7 +438,7 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
                 }
             }
             if (ctx->K > 0) {
-                CK(cudaFuncSetAttribute(wf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->wave_smem));
+                CK(cudaFuncSetAttribute(wf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max));
                 int per = 0;
                 CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, wf, kNT, ctx->wave_smem));
                 if ((long long)per * ctx->num_sms < (long long)ctx->K * ctx->Gw) ctx->K = 0;  // fall back
@@ -525,6 +534,28 @@ extern "C" pit_status pit_set_data(pit_ctx* ctx, const double* u0_dev, const dou
     }
     ctx->has_q = q_dev != nullptr;
     return PIT_OK;
+}
+
+void pit_internal_view(const pit_ctx* ctx, PitProblemView* v) {
+    v->grid = ctx->grid;
+    v->M = ctx->M;
+    v->dt = ctx->dt;
+    v->params = ctx->params;
+    v->opt = ctx->opt;
+    v->u0 = ctx->u0;
+    v->bc = ctx->has_bc ? ctx->bc : nullptr;
+    v->q = ctx->has_q ? ctx->q : nullptr;
+    v->stream = ctx->stream;
+}
+
+pit_status pit_internal_fail(pit_ctx* ctx, pit_status s, const char* fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
 }
 
 extern "C" pit_status pit_fill_plain_guess(pit_ctx* ctx, double* U_dev) {

@@ -25,12 +25,13 @@ PIT_MAX_NEWTON = 64
 PIT_NOALLOC_MAX_NX, PIT_NOALLOC_MAX_TEAM, PIT_NOALLOC_MAX_LEVELS = 512, 160, 4096
 
 #: every symbol include/pit.h declares
-EXPORTS = ("pit_default_options", "pit_create", "pit_set_data", "pit_fill_plain_guess", "pit_residual",
-           "pit_assemble", "pit_block_solve", "pit_newton_step", "pit_solve", "pit_solve_host", "pit_last_error",
-           "pit_status_string", "pit_destroy", "pit_block_solve_noalloc", "pit_batch_create", "pit_batch_solve",
-           "pit_batch_result", "pit_batch_last_error", "pit_batch_destroy", "pit_net_param_count", "pit_net_create",
-           "pit_net_get_params", "pit_net_set_params", "pit_net_guess", "pit_net_make_target", "pit_net_gradients",
-           "pit_net_train_step", "pit_net_last_error", "pit_net_destroy")
+EXPORTS = ("pit_default_options", "pit_create", "pit_set_data", "pit_fill_plain_guess", "pit_coarse_guess",
+           "pit_residual", "pit_assemble", "pit_block_solve", "pit_newton_step", "pit_solve", "pit_solve_host",
+           "pit_last_error", "pit_status_string", "pit_destroy", "pit_block_solve_noalloc", "pit_batch_create",
+           "pit_batch_solve", "pit_batch_result", "pit_batch_last_error", "pit_batch_destroy", "pit_net_param_count",
+           "pit_net_create", "pit_net_get_params", "pit_net_set_params", "pit_net_guess", "pit_net_make_target",
+           "pit_net_gradients", "pit_net_train_step", "pit_net_last_error", "pit_net_destroy",
+           "pit_product_form_solve", "pit_solve_product")
 
 
 class pit_grid(ctypes.Structure):
@@ -93,6 +94,15 @@ class pit_batch_info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class pit_product_info(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("diagonals", ctypes.c_longlong), ("half_band", ctypes.c_longlong),
+                ("min_pivot", ctypes.c_double), ("ms_assemble", ctypes.c_float), ("ms_products", ctypes.c_float),
+                ("ms_factor", ctypes.c_float)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class pit_net_shape(ctypes.Structure):
     _fields_ = [("height", ctypes.c_int), ("width", ctypes.c_int), ("levels", ctypes.c_int),
                 ("channels", ctypes.c_int), ("blocks", ctypes.c_int), ("max_batch", ctypes.c_int)]
@@ -129,6 +139,8 @@ def lib():
             L.pit_set_data.restype = st
             L.pit_fill_plain_guess.argtypes = [P, V]
             L.pit_fill_plain_guess.restype = st
+            L.pit_coarse_guess.argtypes = [P, ctypes.c_int, V, ctypes.POINTER(pit_solve_info)]
+            L.pit_coarse_guess.restype = st
             L.pit_residual.argtypes = [P, V, V, D]
             L.pit_residual.restype = st
             L.pit_assemble.argtypes = [P, V, V]
@@ -184,6 +196,10 @@ def lib():
             L.pit_net_last_error.restype = ctypes.c_char_p
             L.pit_net_destroy.argtypes = [P]
             L.pit_net_destroy.restype = None
+            L.pit_product_form_solve.argtypes = [P, V, V, V, ctypes.POINTER(pit_product_info)]
+            L.pit_product_form_solve.restype = st
+            L.pit_solve_product.argtypes = [P, V, ctypes.POINTER(pit_solve_info)]
+            L.pit_solve_product.restype = st
             _lib = L
         return _lib
 
@@ -285,6 +301,16 @@ def pit_fill_plain_guess(ctx: Context, U):
     ctx._check(lib().pit_fill_plain_guess(ctx.handle, _dptr(U, "U", ctx.dof)))
 
 
+def pit_coarse_guess(ctx: Context, cf: int, U, check: bool = True):
+    """The paper's coarse-grid + cubic-spline initial iterate into U. Returns (status,
+    report of the coarse solve)."""
+    info = pit_solve_info()
+    s = lib().pit_coarse_guess(ctx.handle, int(cf), _dptr(U, "U", ctx.dof), ctypes.byref(info))
+    if check:
+        ctx._check(s)
+    return s, info.as_dict()
+
+
 def pit_residual(ctx: Context, U, R, want_norm: bool = True) -> Optional[float]:
     out = ctypes.c_double(0.0)
     ctx._check(lib().pit_residual(ctx.handle, _dptr(U, "U", ctx.dof), _dptr(R, "R", ctx.dof),
@@ -322,6 +348,26 @@ def pit_solve_host(ctx: Context, u0_host, U_host, check: bool = True):
     info = pit_solve_info()
     s = lib().pit_solve_host(ctx.handle, _hptr(u0_host, "u0_host", ctx.ns), _hptr(U_host, "U_host", ctx.dof),
                              ctypes.byref(info))
+    if check:
+        ctx._check(s)
+    return s, info.as_dict()
+
+
+def pit_product_form_solve(ctx: Context, U, R, dU, check: bool = True):
+    """The literal eq. 8 product form (P^n du^n = r~^n, diagonally scaled, banded LU).
+    Returns (status, info dict)."""
+    info = pit_product_info()
+    s = lib().pit_product_form_solve(ctx.handle, _dptr(U, "U", ctx.dof), _dptr(R, "R", ctx.dof),
+                                     _dptr(dU, "dU", ctx.dof), ctypes.byref(info))
+    if check:
+        ctx._check(s)
+    return s, info.as_dict()
+
+
+def pit_solve_product(ctx: Context, U, check: bool = True):
+    """Newton with the product-form block solve. Returns (status, info dict)."""
+    info = pit_solve_info()
+    s = lib().pit_solve_product(ctx.handle, _dptr(U, "U", ctx.dof), ctypes.byref(info))
     if check:
         ctx._check(s)
     return s, info.as_dict()

@@ -316,3 +316,21 @@ def test_windowed_solve_matches_oracle(window, teams, prec):
         Ug = U.cpu().numpy().reshape(p.M, -1)
     assert info["converged"] and info["windows"] == -(-p.M // window)
     assert np.abs(Ug - Uo).max() <= 1e-10 * np.abs(Uo).max()
+
+
+def test_a_smaller_context_does_not_break_a_larger_one():
+    # kernel launch limits are per kernel, not per context: creating a context for a
+    # small grid after a large one must leave the large one's launches valid
+    big = W.random_problem(21, 96, 96, 6, W.BURGERS)
+    small = W.random_problem(22, 6, 6, 3, W.HEAT)
+    Uo, _, _, _ = oracle.solve(big, tol=1e-13)
+    with pit.context_for(big) as cb:
+        with pit.context_for(small) as cs:
+            Us = torch.empty(small.dof, dtype=torch.float64, device="cuda")
+            pit.pit_fill_plain_guess(cs, Us)
+            pit.pit_solve(cs, Us)
+        U = torch.empty(big.dof, dtype=torch.float64, device="cuda")
+        pit.pit_fill_plain_guess(cb, U)
+        status, info = pit.pit_solve(cb, U)
+    assert info["converged"]
+    assert np.abs(U.cpu().numpy().reshape(big.M, -1) - Uo).max() <= 1e-10 * np.abs(Uo).max()

@@ -1,0 +1,108 @@
+"""f4: the literal product form of Theorem 1 (eq. 8) on the GPU -- the recursion of
+Sec. 5 in diagonal-offset storage, diag(P^n) scaling, banded LU without pivoting --
+against the oracle's dense product form and against the nested block inverse.
+
+Tolerance: the scaled product system of level n has condition ~K^n (eq. 15); both
+sides solve it with LU in FP64, so they agree to ~eps K^n. The cases below keep
+K^M below 1e4 (small mu tau / h^2), where 1e-10 relative is a safe bound; one case past
+the bound shows the loss of digits that the nested form avoids."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_00878_gb300 import pit
+from paper_2406_00878_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def _iterate(p, seed, amp=0.1):
+    rng = np.random.default_rng(seed)
+    return np.ascontiguousarray(p.plain_guess() + amp * rng.standard_normal((p.M, p.grid.ns)))
+
+
+def _gpu_product(p, U, R):
+    with pit.context_for(p) as ctx:
+        dU = torch.empty(p.dof, dtype=torch.float64, device="cuda")
+        st, info = pit.pit_product_form_solve(ctx, _dev(U), _dev(R), dU)
+        return dU.cpu().numpy().reshape(p.M, -1), info
+
+
+@pytest.mark.parametrize("seed,nx,ny,M,eq", [(0, 4, 3, 3, W.HEAT), (1, 5, 5, 4, W.BURGERS), (2, 6, 4, 5, W.BURGERS),
+                                             (3, 1, 6, 4, W.HEAT), (4, 6, 1, 3, W.BURGERS)])
+def test_product_form_matches_dense_oracle(seed, nx, ny, M, eq):
+    p = W.random_problem(seed, nx, ny, M, eq, with_bc=True, mu_a=0.02, mu_b=0.0, dt=1e-3)
+    U = _iterate(p, seed)
+    R = oracle.residual(p.grid, p.params, M, p.dt, p.u0, U, p.bc, p.q)
+    coef = oracle.jacobian(p.grid, p.params, M, p.dt, U, p.bc)
+    want = oracle.product_form_solve(nx, ny, M, coef, R, diag_precondition=True)
+    got, info = _gpu_product(p, U, R)
+    assert info["diagonals"] == 2 * M * M + 2 * M + 1 and info["half_band"] == M * nx
+    assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("seed,n,M,eq", [(5, 15, 8, W.BURGERS), (6, 24, 12, W.HEAT), (7, 31, 6, W.BURGERS)])
+def test_product_form_equals_nested_inverse(seed, n, M, eq):
+    # Theorem 1: the decoupled systems have the same solution as eq. 6
+    p = W.random_problem(seed, n, n + 3, M, eq, with_bc=True, with_q=True, mu_a=1e-3, mu_b=0.0, dt=1e-3)
+    U = _iterate(p, seed)
+    R = oracle.residual(p.grid, p.params, M, p.dt, p.u0, U, p.bc, p.q)
+    coef = oracle.jacobian(p.grid, p.params, M, p.dt, U, p.bc)
+    want = oracle.block_solve(n, n + 3, M, coef, R)
+    got, info = _gpu_product(p, U, R)
+    assert info["min_pivot"] > 0
+    assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+
+
+def _paper_burgers(n=63, M=12, nu=1e-3, v=0.5):
+    """The paper's Burgers test (Sec. 8): a viscous shock u = v/2 (1 - tanh(v (x + y - v t) / (4 nu)))
+    on [0,1]^2 (domain: a reading), N_x = N_y = 63 interior nodes, N_t = 12 levels, T = 1,
+    initial and Dirichlet data from the exact solution."""
+    g = W.Grid(n, n)
+    dt = 1.0 / M
+    ex = lambda x, y, t: 0.5 * v * (1.0 - np.tanh(v * (x + y - v * t) / (4 * nu)))
+    X, Y = g.nodes()
+    x = g.hx * np.arange(1, n + 1)
+    bc = np.array([np.concatenate([ex(x, 0.0, t), ex(x, 1.0, t), ex(0.0, x, t), ex(1.0, x, t)])
+                   for t in dt * np.arange(1, M + 1)])
+    return W.Problem("paper_burgers", g, W.Params(W.BURGERS, nu), M, dt, np.ascontiguousarray(ex(X, Y, 0.0).ravel()),
+                     bc)
+
+
+def test_newton_with_product_form_reaches_the_sequential_solution():
+    p = _paper_burgers()
+    Us, _ = oracle.sequential_bdf1(p.grid, p.params, p.M, p.dt, p.u0, p.bc)
+    with pit.context_for(p) as ctx:
+        U = torch.empty(p.dof, dtype=torch.float64, device="cuda")
+        pit.pit_fill_plain_guess(ctx, U)
+        st, info = pit.pit_solve_product(ctx, U)
+        Up = U.cpu().numpy().reshape(p.M, -1)
+        # the nested-form solver from the same start reaches the same solution
+        pit.pit_fill_plain_guess(ctx, U)
+        pit.pit_solve(ctx, U)
+        Un = U.cpu().numpy().reshape(p.M, -1)
+    assert info["converged"] and info["res_inf"][-1] <= 1e-12
+    assert np.abs(Up - Us).max() <= 1e-10 * np.abs(Us).max()
+    assert np.abs(Un - Us).max() <= 1e-10 * np.abs(Us).max()
+
+
+def test_product_form_loses_digits_past_the_condition_bound():
+    # heat with mu ~ 1 on 32^2 and tau = 1/64: K ~ 1e2 per level (eq. 15), so P^8 has
+    # condition ~1e16 -- the literal form's last level is wrong at O(1) while the nested
+    # inverse (same exact solution, Theorem 1) stays exact
+    p = W.heat32(0)
+    M = 8
+    p = W.truncated(p, M)
+    U = p.plain_guess()
+    R = oracle.residual(p.grid, p.params, M, p.dt, p.u0, U)
+    coef = oracle.jacobian(p.grid, p.params, M, p.dt, U)
+    want = oracle.block_solve(p.grid.nx, p.grid.ny, M, coef, R)
+    got, info = _gpu_product(p, U, R)
+    err = np.abs(got - want).max(axis=1) / np.abs(want).max()
+    assert err[0] <= 1e-12                # level 1 is a plain A_1 solve
+    assert not (err[-1] <= 1e-6), err     # the last level has lost many digits (or overflowed)
