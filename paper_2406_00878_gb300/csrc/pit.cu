@@ -63,6 +63,7 @@ struct pit_ctx {
     int K = 0, Gw = 0, w_rows_base = 0, w_rows_rem = 0, kcap = 0;
     size_t wave_smem = 0;
     double* w_pub = nullptr;
+    double* w_pub2 = nullptr;               // one-exchange SOR sweeps (rows_base >= 3), else nullptr
     double* w_red = nullptr;
     unsigned long long* w_sync = nullptr;  // flags[K*Gw], red_cnt[K*4], prog[K*Gw]
     int* w_ints = nullptr;                  // abort, status, stop[2]
@@ -447,6 +448,8 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
                 const int K = ctx->K, Gw = ctx->Gw;
                 ctx->kcap = std::max(1, o.newton_max);
                 CK(dalloc(&ctx->w_pub, (size_t)K * 2 * Gw * 2 * nx));
+                if (ctx->w_rows_base >= 3 && Gw >= 2)
+                    CK(dalloc(&ctx->w_pub2, (size_t)K * 2 * Gw * kDeepSlotRows * nx));
                 CK(dalloc(&ctx->w_red, (size_t)K * 4 * Gw * 4));
                 CK(dalloc(&ctx->w_sync, (size_t)K * Gw * 2 + (size_t)K * 4));
                 CK(dalloc(&ctx->w_ints, 4));
@@ -506,6 +509,7 @@ extern "C" void pit_destroy(pit_ctx* ctx) {
     cudaFree(ctx->cta_sumsq);
     cudaFree(ctx->timers);
     cudaFree(ctx->w_pub);
+    cudaFree(ctx->w_pub2);
     cudaFree(ctx->w_red);
     cudaFree(ctx->w_sync);
     cudaFree(ctx->w_ints);
@@ -657,6 +661,7 @@ static pit_status run_wave(pit_ctx* ctx, int s, int Mw, double* Uall, int k_begi
     a.max_iter = ctx->opt.lin_max_iter;
     a.wait_budget = ctx->opt.wait_budget;
     a.pub = ctx->w_pub;
+    a.pub2 = ctx->w_pub2;
     a.red_part = ctx->w_red;
     a.flags = ctx->w_sync;
     a.prog = ctx->w_sync + (size_t)K * Gw;

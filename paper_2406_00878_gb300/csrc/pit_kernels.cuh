@@ -343,6 +343,20 @@ __device__ __forceinline__ bool wait_geq(const TeamCtl& c, const unsigned long l
     return true;
 }
 
+// Thread 0: make this CTA's publication at `seq` visible (release), then wait until
+// both neighbours have published `seq` (acquire). Writes the outcome to *s_ok.
+__device__ __forceinline__ void publish_and_wait(const TeamCtl& c, Team& t, unsigned long long seq, int* s_ok) {
+    __threadfence();
+    st_release_u64(t.flags + t.b, seq);
+    const unsigned long long t0 = global_ns();
+    bool ok = true;
+    if (t.b > 0) ok = wait_geq(c, t.flags + t.b - 1, seq);
+    if (ok && t.b + 1 < t.G) ok = wait_geq(c, t.flags + t.b + 1, seq);
+    __threadfence();
+    *s_ok = ok ? 1 : 0;
+    t.t_halo += global_ns() - t0;
+}
+
 // Publish the first and last local rows of v for the neighbours; then fetch the
 // neighbours' rows published at the same step into haloS (row r0-1) and haloN
 // (row r0+nrows). Rows outside the domain are zero (the correction vanishes on
@@ -358,17 +372,7 @@ __device__ bool exchange_halo(const TeamCtl& c, Team& t, const T* v, T* haloS, T
         __stcg(mine + nx + i, v[(t.nrows - 1) * nx + i]);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        st_release_u64(t.flags + t.b, seq);
-        const unsigned long long t0 = global_ns();
-        bool ok = true;
-        if (t.b > 0) ok = wait_geq(c, t.flags + t.b - 1, seq);
-        if (ok && t.b + 1 < t.G) ok = wait_geq(c, t.flags + t.b + 1, seq);
-        __threadfence();
-        *s_ok = ok ? 1 : 0;
-        t.t_halo += global_ns() - t0;
-    }
+    if (threadIdx.x == 0) publish_and_wait(c, t, seq, s_ok);
     __syncthreads();
     if (!*s_ok) return false;
     const T* par = pubT + (size_t)(seq & 1) * t.G * 2 * nx;
@@ -383,6 +387,64 @@ __device__ bool exchange_halo(const TeamCtl& c, Team& t, const T* v, T* haloS, T
         for (int i = threadIdx.x; i < nx; i += NT) haloN[i] = __ldcg(hi + i);
     } else {
         for (int i = threadIdx.x; i < nx; i += NT) haloN[i] = T(0);
+    }
+    __syncthreads();
+    return true;
+}
+
+// Rows of the two neighbours that let red-black SOR run on one exchange per sweep: the
+// scaled couplings and rhs of rows r0-1 and r0+nrows (cS, cN: cw ce cs cn bs, exchanged
+// once per level) and the iterate two rows away (xS2, xN2). With these a CTA updates the
+// red points of its halo rows itself -- the same arithmetic on the same values as their
+// owner -- so the black half-sweep needs no second exchange. pub: the team's publication
+// area of kDeepSlotRows rows per CTA and buffer ([2][G][kDeepSlotRows][nx] doubles).
+constexpr int kDeepSlotRows = 16;
+template <typename T>
+struct Deep {
+    double* pub;
+    T* cS[5];
+    T* cN[5];
+    T* xS2;
+    T* xN2;
+};
+
+// Publish H rows for each neighbour -- lo[h] (this CTA's first rows) for the CTA below and
+// hi[h] (its last rows) for the CTA above -- then fetch the CTA below's hi rows into
+// fromS and the CTA above's lo rows into fromN (zeros off the domain).
+template <int NT, typename T, int H>
+__device__ bool exchange_rows(const TeamCtl& c, Team& t, double* pub, const T* const (&lo)[H],
+                              const T* const (&hi)[H], T* const (&fromS)[H], T* const (&fromN)[H], int* s_ok) {
+    static_assert(2 * H <= kDeepSlotRows, "slot too small");
+    const int nx = t.nx;
+    const unsigned long long seq = ++t.pub_seq;
+    T* const pubT = reinterpret_cast<T*>(pub);
+    const size_t slot = (size_t)kDeepSlotRows * nx;
+    T* mine = pubT + ((size_t)(seq & 1) * t.G + t.b) * slot;
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+        for (int i = threadIdx.x; i < nx; i += NT) {
+            __stcg(mine + (size_t)h * nx + i, lo[h][i]);
+            __stcg(mine + (size_t)(H + h) * nx + i, hi[h][i]);
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) publish_and_wait(c, t, seq, s_ok);
+    __syncthreads();
+    if (!*s_ok) return false;
+    const T* par = pubT + (size_t)(seq & 1) * t.G * slot;
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        if (t.b > 0) {
+            const T* src = par + (size_t)(t.b - 1) * slot + (size_t)(H + h) * nx;
+            for (int i = threadIdx.x; i < nx; i += NT) fromS[h][i] = __ldcg(src + i);
+        } else {
+            for (int i = threadIdx.x; i < nx; i += NT) fromS[h][i] = T(0);
+        }
+        if (t.b + 1 < t.G) {
+            const T* src = par + (size_t)(t.b + 1) * slot + (size_t)h * nx;
+            for (int i = threadIdx.x; i < nx; i += NT) fromN[h][i] = __ldcg(src + i);
+        } else {
+            for (int i = threadIdx.x; i < nx; i += NT) fromN[h][i] = T(0);
+        }
     }
     __syncthreads();
     return true;
@@ -507,27 +569,99 @@ __device__ __forceinline__ void local_spmv(const Team& t, const Smem<T>& m, cons
     }
 }
 
+// Order-preserving key of |x| in an integer (max on the integer pipe; NaN sorts above +Inf).
+__device__ __forceinline__ unsigned long long mag_key(double x) { return abs_key(x); }
+__device__ __forceinline__ unsigned long long mag_key(float x) {
+    return static_cast<unsigned long long>(__float_as_uint(fabsf(x)));
+}
+template <typename T>
+__device__ __forceinline__ double mag_val(unsigned long long k);
+template <>
+__device__ __forceinline__ double mag_val<double>(unsigned long long k) { return key_val(k); }
+template <>
+__device__ __forceinline__ double mag_val<float>(unsigned long long k) { return (double)__uint_as_float((unsigned)k); }
+
+// One SOR point update on the omega-scaled system (couplings and rhs multiplied by
+// omega): x' = (1 - omega) x + bs - (cw xW + ce xE + cs xS + cn xN). Shared by the owner
+// of a point and by a neighbour that recomputes it, so both get the same bits.
+template <typename T>
+__device__ __forceinline__ T sor_point(T xk, T bs, T cw, T ce, T cs, T cn, T xW, T xE, T xS, T xN, T om1) {
+    T acc = cw * xW;
+    acc = fma(ce, xE, acc);
+    acc = fma(cs, xS, acc);
+    acc = fma(cn, xN, acc);
+    return fma(om1, xk, bs) - acc;
+}
+
 // Red-black SOR on the scaled level system x + W x_W + E x_E + S x_S + N x_N = bs,
 // starting from x. Stops when the error estimate d_s rho / (1 - rho) <= tol, where
 // d_s is the largest change of a sweep and rho = max(d_s / d_{s-1}, omega - 1); the
 // global d_s is known one sweep late (lagged team reduction), so every CTA takes
 // the same decision at the same sweep. Threads walk the points of one colour only
 // (every lane of a warp does useful work). Scalar decisions are taken by thread 0
-// and broadcast. Returns the sweep count (< 0 on abort).
+// and broadcast. The couplings and rhs are scaled by omega in place first (they are
+// reloaded for every level). With deep rows (see Deep) a sweep takes one halo exchange,
+// otherwise two. Returns the sweep count (< 0 on abort).
 template <int NT, typename T>
-__device__ int level_sor(const TeamCtl& c, Team& t, const Smem<T>& m, double omega, double tol, int* s_ok) {
+__device__ int level_sor(const TeamCtl& c, Team& t, const Smem<T>& m, double omega, double tol, int* s_ok,
+                         const Deep<T>* deep = nullptr) {
     const int nx = t.nx;
     const int half = (nx + 1) >> 1;            // points of one colour per row, at most
     const int npts = t.nrows * half;
-    const T om = (T)omega;
+    const T om = (T)omega, om1 = (T)(1.0 - omega);
+    for (int k = threadIdx.x; k < t.nloc; k += NT) {
+        m.cw[k] *= om;
+        m.ce[k] *= om;
+        m.cs[k] *= om;
+        m.cn[k] *= om;
+        m.bs[k] *= om;
+    }
+    __syncthreads();
+    if (deep) {
+        // the neighbours' boundary rows of the (scaled) system, once per level
+        const int last = (t.nrows - 1) * nx;
+        const T* const lo[5] = {m.cw, m.ce, m.cs, m.cn, m.bs};
+        const T* const hi[5] = {m.cw + last, m.ce + last, m.cs + last, m.cn + last, m.bs + last};
+        T* const fS[5] = {deep->cS[0], deep->cS[1], deep->cS[2], deep->cS[3], deep->cS[4]};
+        T* const fN[5] = {deep->cN[0], deep->cN[1], deep->cN[2], deep->cN[3], deep->cN[4]};
+        if (!exchange_rows<NT, T, 5>(c, t, deep->pub, lo, hi, fS, fN, s_ok)) return -1;
+    }
     double prev = -1.0, prev2 = -1.0;          // global max change of sweeps s-1 and s-2 (thread 0)
     unsigned long long pending = 0;
     bool have_pending = false;
     int* s_flag = reinterpret_cast<int*>(m.red + 48);
+    const bool has_s = t.b > 0, has_n = t.b + 1 < t.G;
     for (int sweep = 1;; ++sweep) {
-        T dmax = T(0);
+        unsigned long long key = 0;
         for (int color = 0; color < 2; ++color) {
-            if (!exchange_halo<NT, T>(c, t, m.x, m.haloS, m.haloN, s_ok)) return -1;
+            if (deep) {
+                if (color == 0) {
+                    const int last = (t.nrows - 1) * nx;
+                    const T* const lo[2] = {m.x, m.x + nx};
+                    const T* const hi[2] = {m.x + last, m.x + last - nx};
+                    T* const fS[2] = {m.haloS, deep->xS2};
+                    T* const fN[2] = {m.haloN, deep->xN2};
+                    if (!exchange_rows<NT, T, 2>(c, t, deep->pub, lo, hi, fS, fN, s_ok)) return -1;
+                    // red points of the two halo rows, as their owners compute them
+                    const int r_s = t.r0 - 1, r_n = t.r0 + t.nrows;
+                    for (int q = threadIdx.x; q < 2 * half; q += NT) {
+                        const bool south = q < half;
+                        if (south ? !has_s : !has_n) continue;
+                        const int row = south ? r_s : r_n;
+                        const int i = (row & 1) + 2 * (south ? q : q - half);
+                        if (i >= nx) continue;
+                        T* h = south ? m.haloS : m.haloN;
+                        T* const* cc = south ? deep->cS : deep->cN;
+                        const T xS = south ? deep->xS2[i] : m.x[last + i];
+                        const T xN = south ? m.x[i] : deep->xN2[i];
+                        const T xW = i > 0 ? h[i - 1] : T(0);
+                        const T xE = i < nx - 1 ? h[i + 1] : T(0);
+                        h[i] = sor_point<T>(h[i], cc[4][i], cc[0][i], cc[1][i], cc[2][i], cc[3][i], xW, xE, xS, xN, om1);
+                    }
+                }
+            } else {
+                if (!exchange_halo<NT, T>(c, t, m.x, m.haloS, m.haloN, s_ok)) return -1;
+            }
             for (int q = threadIdx.x; q < npts; q += NT) {
                 const int jl = q / half;
                 const int i = ((t.r0 + jl + color) & 1) + 2 * (q - jl * half);
@@ -538,19 +672,19 @@ __device__ int level_sor(const TeamCtl& c, Team& t, const Smem<T>& m, double ome
                 const T xS = jl > 0 ? m.x[k - nx] : m.haloS[i];
                 const T xN = jl < t.nrows - 1 ? m.x[k + nx] : m.haloN[i];
                 const T xk = m.x[k];
-                const T resid = m.bs[k] - xk - (m.cw[k] * xW + m.ce[k] * xE + m.cs[k] * xS + m.cn[k] * xN);
-                const T dx = om * resid;
-                m.x[k] = xk + dx;
-                dmax = fmax(dmax, fabs(dx));
-                if (dx != dx) dmax = dx;
+                const T xn = sor_point<T>(xk, m.bs[k], m.cw[k], m.ce[k], m.cs[k], m.cn[k], xW, xE, xS, xN, om1);
+                m.x[k] = xn;
+                const unsigned long long kk = mag_key(xn - xk);
+                key = kk > key ? kk : key;
             }
             __syncthreads();
         }
         // this CTA's max change, then arrive at the team reduction of this sweep
         double v[1];
         {
-            unsigned long long key = block_max_u64<NT>(abs_key((double)dmax), reinterpret_cast<unsigned long long*>(m.red));
-            v[0] = key_val(key);
+            const unsigned long long bk = block_max_u64<NT>(abs_key(mag_val<T>(key)),
+                                                            reinterpret_cast<unsigned long long*>(m.red));
+            v[0] = key_val(bk);
         }
         const unsigned long long use = reduce_arrive<1>(t, v);
         if (have_pending) {
@@ -710,7 +844,7 @@ __device__ int level_bicgstab(const TeamCtl& c, Team& t, const Smem<T>& m, doubl
 template <int NT, typename T>
 __device__ __forceinline__ int level_solve(const TeamCtl& c, Team& t, const Smem<T>& m, int method, double sor_rho_max,
                                            double rho_g, bool nonsym, double sor_tol, double eta, double atol,
-                                           int* s_ok, int* used) {
+                                           int* s_ok, int* used, const Deep<T>* deep = nullptr) {
     const bool use_sor = method == 1 || (method == 0 && rho_g < sor_rho_max);
     *used = use_sor ? 1 : 2;
     if (use_sor) {
@@ -721,7 +855,7 @@ __device__ __forceinline__ int level_solve(const TeamCtl& c, Team& t, const Smem
             if (nonsym) omega = fmax(1.0, fmin(omega, 0.99 * 2.0 / (1.0 + rho_g)));
         }
         omega = bcast0(omega, m.red + 48);
-        return level_sor<NT, T>(c, t, m, omega, sor_tol, s_ok);
+        return level_sor<NT, T>(c, t, m, omega, sor_tol, s_ok, deep);
     }
     return level_bicgstab<NT, T>(c, t, m, eta, atol, s_ok);
 }
@@ -908,6 +1042,7 @@ struct WaveArgs {
     long long wait_budget;
     // workspace, zeroed by the host before the launch (stop[1] set to INT_MAX)
     double* pub;                        // [K][2][G][2][nx]
+    double* pub2;                       // [K][2][G][kDeepSlotRows][nx] for one-exchange SOR sweeps, or nullptr
     unsigned long long* flags;          // [K][G]
     double* red_part;                   // [K][4][G][4]
     unsigned long long* red_cnt;        // [K][4]
@@ -966,6 +1101,22 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
     double* slot = m.red + 48;
     // Burgers-type closures with constant viscosity have a constant diagonal 1 + 2 mu_a (vx + vy)
     const double dconst = 1.0 / (1.0 + 2.0 * oc.mu_a * (oc.vx + oc.vy));
+    // neighbour rows for one-exchange SOR sweeps: in the BiCGStab scratch r..t (5 cap values),
+    // which SOR leaves unused and u^n_k no longer needs once the level's system is formed.
+    // The conditions are the same on every CTA of the team (cap and rows_base are team-wide).
+    Deep<T> deep_rows;
+    const Deep<T>* deep = nullptr;
+    if (a.pub2 && a.G >= 2 && a.rows_base >= 2 && 12 * (size_t)nx <= 5 * (size_t)cap) {
+        T* d0 = m.r;
+        for (int h = 0; h < 5; ++h) {
+            deep_rows.cS[h] = d0 + (size_t)h * nx;
+            deep_rows.cN[h] = d0 + (size_t)(5 + h) * nx;
+        }
+        deep_rows.xS2 = d0 + (size_t)10 * nx;
+        deep_rows.xN2 = d0 + (size_t)11 * nx;
+        deep_rows.pub = a.pub2 + (size_t)team * 2 * a.G * kDeepSlotRows * nx;
+        deep = &deep_rows;
+    }
 
     for (int k = a.k_begin + team; k < a.k_end; k += a.K) {
         for (int i = threadIdx.x; i < nloc; i += NT) {
@@ -1129,7 +1280,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 sor_tol = bcast0(sor_tol, slot);
                 int used = 0;
                 const int iters = level_solve<NT, T>(c, t, m, a.method, a.sor_rho_max, g3[1], g3[2] != 0.0, sor_tol,
-                                                     eta, a.atol, &s_ok, &used);
+                                                     eta, a.atol, &s_ok, &used, deep);
                 if (iters < 0) return;  // aborted
                 // 6. U^n += du^n; du^n stays in x for the next level
                 double* Uw = a.U + (long long)n * Ns + off0;
