@@ -143,6 +143,9 @@ typedef struct {
     float us_halo_wait, us_reduce_wait;    /* first CTA of team 0: team synchronisation */
     int windows;                           /* windows of levels solved (1 without windowing) */
     int newton_iters_total;                /* Newton updates summed over the windows */
+    float us_setup;                        /* first CTA of team 0: forming level systems (residual, Jacobian) */
+    float us_level_solve;                  /* first CTA of team 0: level solves (includes halo/reduction waits) */
+    float us_update;                       /* first CTA of team 0: iterate updates and progress publication */
 } pit_solve_info;
 
 /* Fill *opt with the defaults listed above. */

@@ -71,7 +71,7 @@ struct pit_ctx {
     double* w_prefix = nullptr;             // [kcap][M]
     int* w_cell = nullptr;                  // [kcap][M]
     double* w_sumsq = nullptr;              // [kcap][Gw]
-    unsigned long long* w_timers = nullptr; // [K][4]
+    unsigned long long* w_timers = nullptr; // [K][8]
     std::vector<double> h_wres, h_wsumsq;
     std::vector<int> h_wcell;
     std::vector<unsigned long long> h_wtimers;
@@ -457,11 +457,11 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
                 CK(dalloc(&ctx->w_prefix, (size_t)ctx->kcap * M));
                 CK(dalloc(&ctx->w_cell, (size_t)ctx->kcap * M));
                 CK(dalloc(&ctx->w_sumsq, (size_t)ctx->kcap * Gw));
-                CK(dalloc(&ctx->w_timers, (size_t)K * 4));
+                CK(dalloc(&ctx->w_timers, (size_t)K * 8));
                 ctx->h_wres.assign(ctx->kcap, 0.0);
                 ctx->h_wcell.assign((size_t)ctx->kcap * M, 0);
                 ctx->h_wsumsq.assign((size_t)ctx->kcap * Gw, 0.0);
-                ctx->h_wtimers.assign((size_t)K * 4, 0);
+                ctx->h_wtimers.assign((size_t)K * 8, 0);
             }
         }
         CK(dalloc(&ctx->u0, ctx->Ns));
@@ -638,7 +638,7 @@ static pit_status run_wave(pit_ctx* ctx, int s, int Mw, double* Uall, int k_begi
     CK(cudaMemsetAsync(ctx->w_ints, 0, sizeof(int) * 3, ctx->stream));
     CK(cudaMemsetAsync(ctx->w_ints + 3, 0x7f, sizeof(int), ctx->stream));  // stop[1] = first converged k: large
     CK(cudaMemsetAsync(ctx->w_cell, 0, sizeof(int) * (size_t)ctx->kcap * M, ctx->stream));
-    CK(cudaMemsetAsync(ctx->w_timers, 0, sizeof(unsigned long long) * K * 4, ctx->stream));
+    CK(cudaMemsetAsync(ctx->w_timers, 0, sizeof(unsigned long long) * K * 8, ctx->stream));
     WaveArgs a{};
     a.c = ctx->oc;
     a.c.M = Mw;
@@ -688,7 +688,7 @@ static pit_status run_wave(pit_ctx* ctx, int s, int Mw, double* Uall, int k_begi
                        ctx->stream));
     CK(cudaMemcpyAsync(ctx->h_wsumsq.data(), ctx->w_sumsq, sizeof(double) * (size_t)ctx->kcap * Gw,
                        cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->h_wtimers.data(), ctx->w_timers, sizeof(unsigned long long) * K * 4,
+    CK(cudaMemcpyAsync(ctx->h_wtimers.data(), ctx->w_timers, sizeof(unsigned long long) * K * 8,
                        cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     float ms = 0.f;
@@ -698,6 +698,9 @@ static pit_status run_wave(pit_ctx* ctx, int s, int Mw, double* Uall, int k_begi
     inf->us_pred_wait += (float)(ctx->h_wtimers[2] * 1e-3);
     inf->us_halo_wait += (float)(ctx->h_wtimers[0] * 1e-3);
     inf->us_reduce_wait += (float)(ctx->h_wtimers[1] * 1e-3);
+    inf->us_setup += (float)(ctx->h_wtimers[4] * 1e-3);
+    inf->us_level_solve += (float)(ctx->h_wtimers[5] * 1e-3);
+    inf->us_update += (float)(ctx->h_wtimers[6] * 1e-3);
     *stopped = hi[2] != 0 && hi[3] < k_end;
     // completed iterations: every level of iteration k ran (cell statistics all set)
     int done = k_begin;

@@ -60,6 +60,31 @@ __device__ __forceinline__ unsigned long long abs_key(double x) {
 }
 __device__ __forceinline__ double key_val(unsigned long long k) { return __longlong_as_double((long long)k); }
 
+// x * y < 0 for nonzero finite x, y, decided on the sign and magnitude bits (integer pipe).
+__device__ __forceinline__ bool opposite_nonzero(double x, double y) {
+    const long long bx = __double_as_longlong(x), by = __double_as_longlong(y);
+    const long long mag = 0x7fffffffffffffffll;
+    return ((bx ^ by) < 0) && (bx & mag) != 0 && (by & mag) != 0;
+}
+
+// Maxima of four keys over the CTA, valid on thread 0 only (one barrier); red holds
+// NT/32 * 4 keys.
+template <int NT>
+__device__ __forceinline__ void block_max4_to0(unsigned long long (&k)[4], unsigned long long* red) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long w = __shfl_xor_sync(0xffffffffu, k[q], o);
+            k[q] = w > k[q] ? w : k[q];
+        }
+    if ((threadIdx.x & 31) == 0)
+        for (int q = 0; q < 4; ++q) red[(threadIdx.x >> 5) * 4 + q] = k[q];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < NT / 32; ++w)
+            for (int q = 0; q < 4; ++q) k[q] = red[w * 4 + q] > k[q] ? red[w * 4 + q] : k[q];
+}
+
 template <int NT>
 __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* red) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -679,36 +704,78 @@ __device__ int level_sor(const TeamCtl& c, Team& t, const Smem<T>& m, double ome
             }
             __syncthreads();
         }
-        // this CTA's max change, then arrive at the team reduction of this sweep
-        double v[1];
+        // this CTA's max change (warp maxima, folded by thread 0), then arrive at the team
+        // reduction of this sweep
+        const unsigned long long use = t.red_seq++;
         {
-            const unsigned long long bk = block_max_u64<NT>(abs_key(mag_val<T>(key)),
-                                                            reinterpret_cast<unsigned long long*>(m.red));
-            v[0] = key_val(bk);
-        }
-        const unsigned long long use = reduce_arrive<1>(t, v);
-        if (have_pending) {
-            double g[1];
-            if (!reduce_finish<1, true>(c, t, pending, g, m.red + 32, s_ok)) return -1;
+            unsigned long long* wred = reinterpret_cast<unsigned long long*>(m.red);
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long w = __shfl_xor_sync(0xffffffffu, key, o);
+                key = w > key ? w : key;
+            }
+            if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = key;
+            __syncthreads();
             if (threadIdx.x == 0) {
-                const double d = g[0];
-                int decision = 0;  // 0 continue, 1 converged / capped, 2 NaN
-                if (d != d) {
-                    decision = 2;
-                } else {
-                    prev2 = prev;
-                    prev = d;
-                    double rho = omega - 1.0;
-                    if (prev2 > 0.0) rho = fmax(rho, prev / prev2);
-                    if (prev == 0.0 || (prev2 > 0.0 && rho < 1.0 && prev * rho <= tol * (1.0 - rho)) ||
-                        sweep >= c.max_iter)
-                        decision = 1;
+                unsigned long long kmax = wred[0];
+                for (int w = 1; w < NT / 32; ++w) kmax = wred[w] > kmax ? wred[w] : kmax;
+                double* part = t.red_part + ((size_t)(use & 3) * t.G + t.b) * 4;
+                __stcg(part, mag_val<T>(kmax));
+                __threadfence();
+                atomicAdd(t.red_cnt + (use & 3), 1ull);
+            }
+        }
+        if (have_pending) {
+            // warp 0 finishes the previous sweep's reduction; thread 0 decides
+            if (threadIdx.x < 32) {
+                const int lane = threadIdx.x;
+                const int slot = (int)(pending & 3);
+                int ok = 1;
+                if (lane == 0) {
+                    const unsigned long long target = (unsigned long long)t.G * ((pending >> 2) + 1);
+                    const unsigned long long t0 = global_ns();
+                    ok = wait_geq(c, t.red_cnt + slot, target) ? 1 : 0;
+                    __threadfence();
+                    t.t_red += global_ns() - t0;
                 }
-                *s_flag = decision;
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                int decision = -1;  // -1 abort, 0 continue, 1 converged / capped, 2 NaN
+                if (ok) {
+                    const double* part = t.red_part + (size_t)slot * t.G * 4;
+                    double d = 0.0;
+                    bool nan = false;
+                    for (int b = lane; b < t.G; b += 32) {
+                        const double v = __ldcg(part + (size_t)b * 4);
+                        d = fmax(d, v);
+                        nan |= (v != v);
+                    }
+                    for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
+                    nan = __any_sync(0xffffffffu, nan);
+                    decision = 0;
+                    if (lane == 0) {
+                        if (nan) {
+                            decision = 2;
+                        } else {
+                            prev2 = prev;
+                            prev = d;
+                            double rho = omega - 1.0;
+                            if (prev2 > 0.0) rho = fmax(rho, prev / prev2);
+                            // d_{s-1} rho / (1 - rho) estimates the error after sweep s - 1; sweep s,
+                            // already done, shrinks it by rho once more
+                            if (prev == 0.0 || (prev2 > 0.0 && rho < 1.0 && prev * rho * rho <= tol * (1.0 - rho)) ||
+                                sweep >= c.max_iter)
+                                decision = 1;
+                        }
+                    }
+                }
+                if (lane == 0) *s_flag = decision;
             }
             __syncthreads();
+            // s_flag is written again only after the next sweep's barriers
             const int decision = *s_flag;
-            __syncthreads();
+            if (decision < 0) {
+                *s_ok = 0;
+                return -1;
+            }
             if (decision) {
                 if (decision == 2 && threadIdx.x == 0) atomicCAS(c.status, 0, ST_EDIVERGED);
                 // consume the outstanding reduction so the sequence stays aligned
@@ -1056,7 +1123,8 @@ struct WaveArgs {
     double* cell_prefix;                // [k_end][M] max_{j <= n} ||r^j_k||_inf (written by CTA 0 of the team)
     int* cell_iters;                    // [k_end][M] 1 + sweeps (SOR) or -(1 + iterations) (BiCGStab); 0 = not run
     double* cta_sumsq;                  // [k_end][G] sum of du_k^2 over the CTA's rows
-    unsigned long long* timers;         // [K][4] CTA 0 of each team: halo, reduction, predecessor waits, total
+    unsigned long long* timers;         // [K][8] CTA 0 of each team: halo, reduction, predecessor waits, total,
+                                        // level setup, level solves, update (ns)
 };
 
 // u^n_k with its halo rows ((cap + 2 nx) doubles) shares the BiCGStab scratch r..t
@@ -1084,7 +1152,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
     const int nx = oc.nx, ny = oc.ny, M = oc.M;
     TeamCtl c{a.abort_flag, a.status, a.wait_budget, a.max_iter};
     const unsigned long long t_start = global_ns();
-    unsigned long long t_pred = 0;
+    unsigned long long t_pred = 0, t_setup = 0, t_solve = 0, t_upd = 0, t_mark = 0;
     const int nloc = t.nloc;
     const int cap = (a.rows_base + (a.rows_rem ? 1 : 0)) * nx;
     const Smem<T> m = smem_layout<T>(smem, cap, nx);
@@ -1190,10 +1258,12 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 uprev_valid = true;
                 __syncthreads();
             }
+            if (threadIdx.x == 0) t_mark = global_ns();
             // 2. u^n_k: own rows and one halo row each side (Dirichlet data off the domain)
             const double* Un = a.U + (long long)n * Ns;
             const double* bnd = a.bc ? a.bc + (long long)n * nb : nullptr;
-            double rmax = 0.0, rs = 0.0, bmax = 0.0;
+            // maxima as integer keys (abs_key), so the bookkeeping stays off the FP64 pipe
+            unsigned long long krmax = 0, krs = 0, kbmax = 0;
             bool ns = false;
             if (!stop_local) {
                 for (int i = threadIdx.x; i < (t.nrows + 2) * nx; i += NT) {
@@ -1236,21 +1306,23 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                     m.bs[i] = (T)(d * bval);
                     m.x[i] = (T)bval;                        // SOR start
                     uprev[i] = uC;                           // u^n_k for the next level's time difference
-                    rmax = fmax(rmax, fabs(r));
-                    if (r != r) rmax = r;
-                    rs = fmax(rs, fabs(aW) + fabs(aE) + fabs(aS) + fabs(aN));
-                    ns |= (aW * aE < 0.0 || aS * aN < 0.0);
-                    bmax = fmax(bmax, fabs(bval));
+                    const unsigned long long kr = abs_key(r), kg = abs_key(fabs(aW) + fabs(aE) + fabs(aS) + fabs(aN)),
+                                             kb = abs_key(bval);
+                    krmax = kr > krmax ? kr : krmax;
+                    krs = kg > krs ? kg : krs;
+                    kbmax = kb > kbmax ? kb : kbmax;
+                    ns |= opposite_nonzero(aW, aE) || opposite_nonzero(aS, aN);
                 }
             }
             // 4. team reduction: max |r|, Gershgorin bound, 2 stop + nonsymmetric-row flag, max |rhs|
             //    (every CTA of the team takes the same decisions from these)
             const int flags_local = (stop_local ? 2 : 0) + (ns ? 1 : 0);
             double v3[4];
-            v3[0] = key_val(block_max_u64<NT>(abs_key(rmax), reinterpret_cast<unsigned long long*>(m.red)));
-            v3[1] = key_val(block_max_u64<NT>(abs_key(rs), reinterpret_cast<unsigned long long*>(m.red)));
-            v3[2] = key_val(block_max_u64<NT>(abs_key((double)flags_local), reinterpret_cast<unsigned long long*>(m.red)));
-            v3[3] = key_val(block_max_u64<NT>(abs_key(bmax), reinterpret_cast<unsigned long long*>(m.red)));
+            {
+                unsigned long long kk[4] = {krmax, krs, abs_key((double)flags_local), kbmax};
+                block_max4_to0<NT>(kk, reinterpret_cast<unsigned long long*>(m.red));
+                for (int q = 0; q < 4; ++q) v3[q] = key_val(kk[q]);  // meaningful on thread 0 only
+            }
             double g3[4];
             if (!reduce_finish<4, true>(c, t, reduce_arrive<4>(t, v3), g3, m.red + 32, &s_ok)) return;
             if (g3[2] >= 2.0) goto done;  // another iteration has converged (or the launch aborts)
@@ -1278,10 +1350,20 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 }
                 eta = bcast0(eta, slot);
                 sor_tol = bcast0(sor_tol, slot);
+                if (threadIdx.x == 0) {
+                    const unsigned long long now = global_ns();
+                    t_setup += now - t_mark;
+                    t_mark = now;
+                }
                 int used = 0;
                 const int iters = level_solve<NT, T>(c, t, m, a.method, a.sor_rho_max, g3[1], g3[2] != 0.0, sor_tol,
                                                      eta, a.atol, &s_ok, &used, deep);
                 if (iters < 0) return;  // aborted
+                if (threadIdx.x == 0) {
+                    const unsigned long long now = global_ns();
+                    t_solve += now - t_mark;
+                    t_mark = now;
+                }
                 // 6. U^n += du^n; du^n stays in x for the next level
                 double* Uw = a.U + (long long)n * Ns + off0;
                 for (int i = threadIdx.x; i < nloc; i += NT) {
@@ -1298,6 +1380,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                     __threadfence();
                     st_release_u64(my_prog + b, a.cell_base + (unsigned long long)k * M + n + 1);
                     if (iters >= c.max_iter) atomicCAS(a.status, 0, ST_ENOCONV);
+                    t_upd += global_ns() - t_mark;
                 }
             }
         }
@@ -1326,11 +1409,14 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
     }
 done:
     if (b == 0 && threadIdx.x == 0 && a.timers) {
-        unsigned long long* tm = a.timers + (size_t)team * 4;
+        unsigned long long* tm = a.timers + (size_t)team * 8;
         tm[0] = t.t_halo;
         tm[1] = t.t_red;
         tm[2] = t_pred;
         tm[3] = global_ns() - t_start;
+        tm[4] = t_setup;
+        tm[5] = t_solve;
+        tm[6] = t_upd;
     }
     __syncthreads();
 }
