@@ -43,6 +43,28 @@ FLOPS_PER_SOR_UPDATE = 11
 FLOPS_PER_BICGSTAB_ITER = 2 * 9 + 6 * 2 + 5 * 2
 # per node and Newton iteration, Burgers with constant viscosity: residual (convective
 # and viscous differences, time term) and the four scaled couplings
+# DRAM bytes (read + write) of one wavefront launch on this workload, from the ncu capture
+# summarised in profiles/wave_kernel_burgers256_full.md; valid only for the kernel sources it
+# was taken on (their SHA-256 below), reported as null once they change.
+WAVE_TRAFFIC_BYTES = 137.854976e6 + 128.570368e6
+WAVE_TRAFFIC_SOURCES = {
+    "paper_2406_00878_gb300/csrc/pit_kernels.cuh": "9a7f00e94f6f55af804c9c434406e04f9ea4a686298cefa7c80bdf3a8959f54e",
+    "paper_2406_00878_gb300/csrc/pit.cu": "8833ef47d13c3cd8c9d29f61dadc67538d05c6556abfdbb81ac3a44a151bc123",
+}
+
+
+def wave_traffic(levels: int):
+    import hashlib
+    if levels != 256:
+        return None
+    root = os.path.dirname(os.path.abspath(__file__))
+    for rel, digest in WAVE_TRAFFIC_SOURCES.items():
+        with open(os.path.join(root, rel), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != digest:
+                return None
+    return WAVE_TRAFFIC_BYTES
+
+
 FLOPS_PER_RESIDUAL = 18
 FLOPS_PER_JACOBIAN = 8
 
@@ -229,7 +251,9 @@ def run_ours(args, ws, rank, local):
                     "d2h_bytes_per_step": int(p.dof * 8)},
             "roofline": {"kernel": kernel_name, "bound": "alu",
                          "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                         "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                         "traffic": wave_traffic(args.levels) if wave else None,
+                         "traffic_unit": "bytes per launch (ncu dram read + write)",
                          "peak_source": "FP64 nominal 1.25 TFLOP/s (profiling recipe); FP64 not in MEASURED_PEAKS"},
             "clocks": clk.summary(),
         }
@@ -291,7 +315,94 @@ def variants(args):
         "precision": "fp32 level solves / fp64 newton", "converged": info["converged"], "max_res_inf_final": res,
         "graph_replay": bool(info["graph"]), "team_ctas": [info["min_team"], info["max_team"]],
         "autotune_ms": info["ms_tuning"], "schedule_estimate_ms": info["est_makespan_ms"]}
+    out.update(paper_variants(args))
+    if args.learned:
+        out["learned_guess"] = learned_variant(args)
     return out
+
+
+def _timed(stream, fn, steps):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        r = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps, r
+
+
+def paper_variants(args):
+    """The paper's own forms: its coarse-grid + spline initial iterate (c_f = 3) on the
+    bench workload, and Newton with the literal eq. 8 product form on its Burgers shock
+    (63^2 x 12), next to the nested inverse on the same problem."""
+    import torch
+    from paper_2406_00878_gb300 import pit
+    from paper_2406_00878_gb300 import workloads as W
+    out = {}
+    p = W.burgers256(seed=0, M=args.levels)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = pit.context_for(p, stream=stream)
+        U = torch.empty(p.dof, dtype=torch.float64, device="cuda")
+
+        def coarse_step():
+            _, cinfo = pit.pit_coarse_guess(ctx, 3, U)
+            _, info = pit.pit_solve(ctx, U)
+            return cinfo, info
+
+        _timed(stream, coarse_step, 1)
+        ms, (cinfo, info) = _timed(stream, coarse_step, 2)
+        ms_guess, _ = _timed(stream, lambda: pit.pit_coarse_guess(ctx, 3, U), 2)
+        ctx.close()
+    out["coarse_guess_cf3"] = {
+        "value": p.dof / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "ms_guess": ms_guess, "dof": p.dof,
+        "workload": p.name, "M": p.M, "precision": "fp64",
+        "guess": "coarse 84^2 x 85 solve + natural cubic splines in x, y, t (the paper's initial iterate, c_f = 3)",
+        "newton_iters": info["newton_iters"], "coarse_newton_iters": cinfo["newton_iters"],
+        "res_inf_first": info["res_inf"][0], "res_inf_final": info["res_inf"][-1]}
+    q = W.burgers_shock()
+    with torch.cuda.stream(stream):
+        ctx = pit.context_for(q, stream=stream)
+        U = torch.empty(q.dof, dtype=torch.float64, device="cuda")
+
+        def product_step():
+            pit.pit_fill_plain_guess(ctx, U)
+            return pit.pit_solve_product(ctx, U)[1]
+
+        def nested_step():
+            pit.pit_fill_plain_guess(ctx, U)
+            return pit.pit_solve(ctx, U)[1]
+
+        product_step()
+        ms_p, ip = _timed(stream, product_step, 2)
+        nested_step()
+        ms_n, inn = _timed(stream, nested_step, 5)
+        ctx.close()
+    out["product_form_burgers_shock63x12"] = {
+        "value": q.dof / (ms_p * 1e-3), "unit": UNIT, "ms_per_step": ms_p, "dof": q.dof, "workload": q.name,
+        "precision": "fp64", "solver": "literal eq. 8: P^n by the Sec. 5 recursion, diag(P^n) scaling, banded LU",
+        "newton_iters": ip["newton_iters"], "res_inf_final": ip["res_inf"][-1],
+        "nested_inverse_same_problem": {"value": q.dof / (ms_n * 1e-3), "ms_per_step": ms_n,
+                                        "newton_iters": inn["newton_iters"]}}
+    return out
+
+
+def learned_variant(args):
+    """The learned initial iterate on a bounded sample of its workload (128^2, M = 128 Burgers):
+    `--learned-train` generated training solutions, 8 epochs, 16 held-out problems."""
+    from paper_2406_00878_gb300 import learned
+    cfg = learned.LearnedConfig(train=args.learned_train, held_out=16, epochs=8)
+    rep = learned.run(cfg)
+    return {"value": rep["dof_per_s_learned"], "unit": UNIT, "plain_value": rep["dof_per_s_plain"],
+            "workload": "burgers 128^2 x 128, nu log-uniform [1e-3, 1e-1], sine-series u0",
+            "sample": f"{cfg.train} training solutions, {cfg.epochs} epochs, {cfg.held_out} held-out problems",
+            "newton_iters_plain": rep["newton_iters_plain_mean"],
+            "newton_iters_learned": rep["newton_iters_learned_mean"],
+            "converged_plain": rep["held_out_converged_plain"],
+            "converged_learned": rep["held_out_converged_learned"],
+            "train_tflops_bf16": rep["train_tflops"], "generation_dof_per_s": rep["generation_dof_per_s"],
+            "max_rel_diff_solutions": rep["max_rel_diff_solutions"]}
 
 
 def cpu_baseline(args, levels=None):
@@ -348,6 +459,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-check", dest="check", action="store_false")
     ap.add_argument("--no-variants", dest="variants", action="store_false")
+    ap.add_argument("--no-learned", dest="learned", action="store_false")
+    ap.add_argument("--learned-train", type=int, default=1024)
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
