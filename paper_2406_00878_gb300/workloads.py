@@ -117,8 +117,24 @@ def burgers512(seed: int = 0, M: int = 1024) -> Problem:
                    meta={"seed": seed})
 
 
+def burgers_shock(n: int = 63, M: int = 12, nu: float = 1e-3, v: float = 0.5, seed: int = 0) -> Problem:
+    """The paper's Burgers test (Sec. 8.2): the viscous shock u = v/2 (1 - tanh(v (x + y - v t) / (4 nu)))
+    on [0,1]^2 (domain: a reading), n x n interior nodes, M levels over T = 1, initial and Dirichlet
+    data from the exact solution (63^2 x 12 is the setting of the paper's Newton-history figure)."""
+    g = Grid(n, n)
+    dt = 1.0 / M
+    ex = lambda x, y, t: 0.5 * v * (1.0 - np.tanh(v * (x + y - v * t) / (4 * nu)))
+    X, Y = g.nodes()
+    x = g.hx * np.arange(1, n + 1)
+    bc = np.array([np.concatenate([ex(x, 0.0, t), ex(x, 1.0, t), ex(0.0, x, t), ex(1.0, x, t)])
+                   for t in dt * np.arange(1, M + 1)])
+    return Problem(f"burgers_shock{n}x{M}", g, Params(BURGERS, nu), M, dt, np.ascontiguousarray(ex(X, Y, 0.0).ravel()),
+                   np.ascontiguousarray(bc), meta={"seed": seed})
+
+
 def by_name(name: str, seed: int = 0, **kw) -> Problem:
-    return {"heat32": heat32, "burgers256": burgers256, "burgers512": burgers512}[name](seed=seed, **kw)
+    return {"heat32": heat32, "burgers256": burgers256, "burgers512": burgers512,
+            "burgers_shock": burgers_shock}[name](seed=seed, **kw)
 
 
 def truncated(problem: Problem, M: int) -> Problem:

@@ -59,23 +59,8 @@ def test_product_form_equals_nested_inverse(seed, n, M, eq):
     assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
 
 
-def _paper_burgers(n=63, M=12, nu=1e-3, v=0.5):
-    """The paper's Burgers test (Sec. 8): a viscous shock u = v/2 (1 - tanh(v (x + y - v t) / (4 nu)))
-    on [0,1]^2 (domain: a reading), N_x = N_y = 63 interior nodes, N_t = 12 levels, T = 1,
-    initial and Dirichlet data from the exact solution."""
-    g = W.Grid(n, n)
-    dt = 1.0 / M
-    ex = lambda x, y, t: 0.5 * v * (1.0 - np.tanh(v * (x + y - v * t) / (4 * nu)))
-    X, Y = g.nodes()
-    x = g.hx * np.arange(1, n + 1)
-    bc = np.array([np.concatenate([ex(x, 0.0, t), ex(x, 1.0, t), ex(0.0, x, t), ex(1.0, x, t)])
-                   for t in dt * np.arange(1, M + 1)])
-    return W.Problem("paper_burgers", g, W.Params(W.BURGERS, nu), M, dt, np.ascontiguousarray(ex(X, Y, 0.0).ravel()),
-                     bc)
-
-
 def test_newton_with_product_form_reaches_the_sequential_solution():
-    p = _paper_burgers()
+    p = W.burgers_shock()
     Us, _ = oracle.sequential_bdf1(p.grid, p.params, p.M, p.dt, p.u0, p.bc)
     with pit.context_for(p) as ctx:
         U = torch.empty(p.dof, dtype=torch.float64, device="cuda")
