@@ -63,7 +63,9 @@ struct pit_ctx {
     int K = 0, Gw = 0, w_rows_base = 0, w_rows_rem = 0, kcap = 0;
     size_t wave_smem = 0;
     double* w_pub = nullptr;
-    double* w_pub2 = nullptr;               // one-exchange SOR sweeps (rows_base >= 3), else nullptr
+    unsigned long long* w_tpub = nullptr;   // tagged publication words: one-exchange SOR sweeps (rows_base >= 3)
+    unsigned long long* w_tred = nullptr;   // tagged reduction words (with w_tpub)
+    size_t w_tpub_n = 0, w_tred_n = 0;
     double* w_red = nullptr;
     unsigned long long* w_sync = nullptr;  // flags[K*Gw], red_cnt[K*4], prog[K*Gw]
     int* w_ints = nullptr;                  // abort, status, stop[2]
@@ -448,8 +450,12 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
                 const int K = ctx->K, Gw = ctx->Gw;
                 ctx->kcap = std::max(1, o.newton_max);
                 CK(dalloc(&ctx->w_pub, (size_t)K * 2 * Gw * 2 * nx));
-                if (ctx->w_rows_base >= 3 && Gw >= 2)
-                    CK(dalloc(&ctx->w_pub2, (size_t)K * 2 * Gw * kDeepSlotRows * nx));
+                if (ctx->w_rows_base >= 3 && Gw >= 2) {
+                    ctx->w_tpub_n = (size_t)K * 2 * Gw * kDeepSlotRows * nx * 2;
+                    ctx->w_tred_n = (size_t)K * 4 * Gw * kTagRedWords;
+                    CK(dalloc(&ctx->w_tpub, ctx->w_tpub_n));
+                    CK(dalloc(&ctx->w_tred, ctx->w_tred_n));
+                }
                 CK(dalloc(&ctx->w_red, (size_t)K * 4 * Gw * 4));
                 CK(dalloc(&ctx->w_sync, (size_t)K * Gw * 2 + (size_t)K * 4));
                 CK(dalloc(&ctx->w_ints, 4));
@@ -509,7 +515,8 @@ extern "C" void pit_destroy(pit_ctx* ctx) {
     cudaFree(ctx->cta_sumsq);
     cudaFree(ctx->timers);
     cudaFree(ctx->w_pub);
-    cudaFree(ctx->w_pub2);
+    cudaFree(ctx->w_tpub);
+    cudaFree(ctx->w_tred);
     cudaFree(ctx->w_red);
     cudaFree(ctx->w_sync);
     cudaFree(ctx->w_ints);
@@ -639,6 +646,10 @@ static pit_status run_wave(pit_ctx* ctx, int s, int Mw, double* Uall, int k_begi
     CK(cudaMemsetAsync(ctx->w_ints + 3, 0x7f, sizeof(int), ctx->stream));  // stop[1] = first converged k: large
     CK(cudaMemsetAsync(ctx->w_cell, 0, sizeof(int) * (size_t)ctx->kcap * M, ctx->stream));
     CK(cudaMemsetAsync(ctx->w_timers, 0, sizeof(unsigned long long) * K * 8, ctx->stream));
+    if (ctx->w_tpub) {  // tag 0 is never published: stale words of an earlier launch cannot match
+        CK(cudaMemsetAsync(ctx->w_tpub, 0, sizeof(unsigned long long) * ctx->w_tpub_n, ctx->stream));
+        CK(cudaMemsetAsync(ctx->w_tred, 0, sizeof(unsigned long long) * ctx->w_tred_n, ctx->stream));
+    }
     WaveArgs a{};
     a.c = ctx->oc;
     a.c.M = Mw;
@@ -661,7 +672,8 @@ static pit_status run_wave(pit_ctx* ctx, int s, int Mw, double* Uall, int k_begi
     a.max_iter = ctx->opt.lin_max_iter;
     a.wait_budget = ctx->opt.wait_budget;
     a.pub = ctx->w_pub;
-    a.pub2 = ctx->w_pub2;
+    a.tpub = ctx->w_tpub;
+    a.tred = ctx->w_tred;
     a.red_part = ctx->w_red;
     a.flags = ctx->w_sync;
     a.prog = ctx->w_sync + (size_t)K * Gw;

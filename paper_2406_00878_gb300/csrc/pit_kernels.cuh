@@ -323,7 +323,8 @@ struct Team {
     double* red_part;
     unsigned long long* red_cnt;
     unsigned long long pub_seq;   // publications so far by this CTA
-    unsigned long long red_seq;   // reductions started so far
+    unsigned long long red_seq;   // counter-based reductions started so far
+    unsigned long long tag_seq;   // sequence-tagged reductions started so far
     unsigned long long t_halo;    // ns spent waiting for neighbours (thread 0)
     unsigned long long t_red;     // ns spent waiting for team reductions (thread 0)
 };
@@ -344,6 +345,7 @@ __device__ __forceinline__ void team_init(Team& t, int b, int G, int nx, int ny,
     t.red_cnt = red_cnt;
     t.pub_seq = 0;
     t.red_seq = 0;
+    t.tag_seq = 0;
     t.t_halo = 0;
     t.t_red = 0;
 }
@@ -421,58 +423,199 @@ __device__ bool exchange_halo(const TeamCtl& c, Team& t, const T* v, T* haloS, T
 // scaled couplings and rhs of rows r0-1 and r0+nrows (cS, cN: cw ce cs cn bs, exchanged
 // once per level) and the iterate two rows away (xS2, xN2). With these a CTA updates the
 // red points of its halo rows itself -- the same arithmetic on the same values as their
-// owner -- so the black half-sweep needs no second exchange. pub: the team's publication
-// area of kDeepSlotRows rows per CTA and buffer ([2][G][kDeepSlotRows][nx] doubles).
-constexpr int kDeepSlotRows = 16;
+// owner -- so the black half-sweep needs no second exchange.
+//
+// These exchanges, and the team reductions of the same launches, use sequence-tagged
+// words: every published 32-bit piece travels in a 64-bit word whose high half is the
+// sequence number of the publication (single-copy atomic), so a reader polls the data
+// itself -- no release/acquire flag and no fence on the critical path. tpub: the team's
+// publication words, [2][G][kDeepSlotRows][nx][words per value]; tred: the team's
+// reduction words, [4][G][kTagRedWords]; both zero before the launch (tag 0 is never used).
+constexpr int kDeepSlotRows = 10;
+constexpr int kTagRedWords = 8;
 template <typename T>
 struct Deep {
-    double* pub;
+    unsigned long long* tpub;
+    unsigned long long* tred;
     T* cS[5];
     T* cN[5];
     T* xS2;
     T* xN2;
 };
 
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long tagged(unsigned tag, unsigned payload) {
+    return ((unsigned long long)tag << 32) | payload;
+}
+
+// 32-bit pieces of a value (one for float, two for double).
+template <typename T>
+struct Pieces;
+template <>
+struct Pieces<float> {
+    static constexpr int n = 1;
+    __device__ static unsigned get(float v, int) { return __float_as_uint(v); }
+    __device__ static float make(const unsigned (&w)[2]) { return __uint_as_float(w[0]); }
+};
+template <>
+struct Pieces<double> {
+    static constexpr int n = 2;
+    __device__ static unsigned get(double v, int k) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        return k ? (unsigned)(b >> 32) : (unsigned)b;
+    }
+    __device__ static double make(const unsigned (&w)[2]) {
+        return __longlong_as_double((long long)(((unsigned long long)w[1] << 32) | w[0]));
+    }
+};
+
+// Complete a batch of N tagged words: the first loads are issued together (one L2 round
+// trip for the batch); words whose tag is not yet `tag` are polled again. false after the
+// wait budget or when the launch aborts (checked every 256 rounds).
+template <int N>
+__device__ __forceinline__ bool wait_tagged(const TeamCtl& c, const unsigned long long* const (&src)[N],
+                                            unsigned long long (&w)[N], unsigned tag) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) w[k] = src[k] ? ld_relaxed_u64(src[k]) : tagged(tag, 0u);
+    for (long long spins = 0;; ++spins) {
+        bool all = true;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            if ((unsigned)(w[k] >> 32) != tag) {
+                all = false;
+                w[k] = ld_relaxed_u64(src[k]);
+            }
+        if (all) return true;
+        if ((spins & 255) == 255 && ld_acquire_s32(c.abort_flag)) return false;
+        if (spins > c.wait_budget) return false;
+    }
+}
+
 // Publish H rows for each neighbour -- lo[h] (this CTA's first rows) for the CTA below and
-// hi[h] (its last rows) for the CTA above -- then fetch the CTA below's hi rows into
-// fromS and the CTA above's lo rows into fromN (zeros off the domain).
+// hi[h] (its last rows) for the CTA above -- then fetch the CTA below's hi rows into fromS
+// and the CTA above's lo rows into fromN (zeros off the domain). Returns false when a
+// wait timed out (the launch is then aborted) or the launch aborted.
 template <int NT, typename T, int H>
-__device__ bool exchange_rows(const TeamCtl& c, Team& t, double* pub, const T* const (&lo)[H],
-                              const T* const (&hi)[H], T* const (&fromS)[H], T* const (&fromN)[H], int* s_ok) {
+__device__ bool exchange_rows_tagged(const TeamCtl& c, Team& t, unsigned long long* tpub, const T* const (&lo)[H],
+                                     const T* const (&hi)[H], T* const (&fromS)[H], T* const (&fromN)[H]) {
     static_assert(2 * H <= kDeepSlotRows, "slot too small");
+    constexpr int P = Pieces<T>::n;
     const int nx = t.nx;
     const unsigned long long seq = ++t.pub_seq;
-    T* const pubT = reinterpret_cast<T*>(pub);
-    const size_t slot = (size_t)kDeepSlotRows * nx;
-    T* mine = pubT + ((size_t)(seq & 1) * t.G + t.b) * slot;
+    const unsigned tag = (unsigned)seq;
+    const size_t row_w = (size_t)nx * P, slot_w = (size_t)kDeepSlotRows * row_w;
+    unsigned long long* mine = tpub + ((size_t)(seq & 1) * t.G + t.b) * slot_w;
 #pragma unroll
     for (int h = 0; h < H; ++h)
-        for (int i = threadIdx.x; i < nx; i += NT) {
-            __stcg(mine + (size_t)h * nx + i, lo[h][i]);
-            __stcg(mine + (size_t)(H + h) * nx + i, hi[h][i]);
-        }
-    __syncthreads();
-    if (threadIdx.x == 0) publish_and_wait(c, t, seq, s_ok);
-    __syncthreads();
-    if (!*s_ok) return false;
-    const T* par = pubT + (size_t)(seq & 1) * t.G * slot;
+        for (int i = threadIdx.x; i < nx; i += NT)
 #pragma unroll
-    for (int h = 0; h < H; ++h) {
-        if (t.b > 0) {
-            const T* src = par + (size_t)(t.b - 1) * slot + (size_t)(H + h) * nx;
-            for (int i = threadIdx.x; i < nx; i += NT) fromS[h][i] = __ldcg(src + i);
-        } else {
-            for (int i = threadIdx.x; i < nx; i += NT) fromS[h][i] = T(0);
-        }
-        if (t.b + 1 < t.G) {
-            const T* src = par + (size_t)(t.b + 1) * slot + (size_t)h * nx;
-            for (int i = threadIdx.x; i < nx; i += NT) fromN[h][i] = __ldcg(src + i);
-        } else {
-            for (int i = threadIdx.x; i < nx; i += NT) fromN[h][i] = T(0);
+            for (int k = 0; k < P; ++k) {
+                st_relaxed_u64(mine + h * row_w + (size_t)i * P + k, tagged(tag, Pieces<T>::get(lo[h][i], k)));
+                st_relaxed_u64(mine + (H + h) * row_w + (size_t)i * P + k, tagged(tag, Pieces<T>::get(hi[h][i], k)));
+            }
+    const unsigned long long* par = tpub + (size_t)(seq & 1) * t.G * slot_w;
+    const unsigned long long* srcS = t.b > 0 ? par + (size_t)(t.b - 1) * slot_w + H * row_w : nullptr;
+    const unsigned long long* srcN = t.b + 1 < t.G ? par + (size_t)(t.b + 1) * slot_w : nullptr;
+    bool ok = true;
+    for (int i0 = 0; i0 < nx && ok; i0 += NT) {
+        const int i = i0 + threadIdx.x;
+        if (i >= nx) continue;
+        const unsigned long long* src[2 * H * P];
+        unsigned long long w[2 * H * P];
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                src[(h * P + k)] = srcS ? srcS + h * row_w + (size_t)i * P + k : nullptr;
+                src[(H + h) * P + k] = srcN ? srcN + h * row_w + (size_t)i * P + k : nullptr;
+            }
+        ok = wait_tagged<2 * H * P>(c, src, w, tag);
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            unsigned pS[2] = {0u, 0u}, pN[2] = {0u, 0u};
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                pS[k] = (unsigned)w[h * P + k];
+                pN[k] = (unsigned)w[(H + h) * P + k];
+            }
+            fromS[h][i] = srcS ? Pieces<T>::make(pS) : T(0);
+            fromN[h][i] = srcN ? Pieces<T>::make(pN) : T(0);
         }
     }
-    __syncthreads();
+    const bool failed = __syncthreads_or(!ok) != 0;
+    if (failed) {
+        if (threadIdx.x == 0 && !ld_acquire_s32(c.abort_flag)) team_fail(c, ST_ETIMEOUT);
+        return false;
+    }
     return true;
+}
+
+// Team reduction over sequence-tagged words. Arrive: thread 0 publishes this CTA's K
+// values for reduction `use` (slot use & 3, tag use + 1). Finish: warp 0 polls every
+// CTA's words, lanes fold in CTA order with a fixed shuffle tree (max or sum, NaN
+// propagates); the result goes to out on thread 0 (lane 0) only. A CTA publishes
+// reduction use + 1 only after finishing use - 1, which needs every CTA's arrival at
+// use - 1, so four slots are never overwritten while still being read.
+template <int K>
+__device__ __forceinline__ void tagged_arrive(Team& t, unsigned long long* tred, unsigned long long use,
+                                              const double (&vals)[K]) {
+    static_assert(2 * K <= kTagRedWords, "too many values");
+    unsigned long long* w = tred + ((size_t)(use & 3) * t.G + t.b) * kTagRedWords;
+    const unsigned tag = (unsigned)(use + 1);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        st_relaxed_u64(w + 2 * k, tagged(tag, Pieces<double>::get(vals[k], 0)));
+        st_relaxed_u64(w + 2 * k + 1, tagged(tag, Pieces<double>::get(vals[k], 1)));
+    }
+}
+
+// Warp 0 only. Returns false when a wait timed out or the launch aborted.
+template <int K, bool MAXOP>
+__device__ __forceinline__ bool tagged_finish(const TeamCtl& c, const Team& t, const unsigned long long* tred,
+                                              unsigned long long use, double (&out)[K]) {
+    const int lane = threadIdx.x & 31;
+    const unsigned tag = (unsigned)(use + 1);
+    const unsigned long long* base = tred + (size_t)(use & 3) * t.G * kTagRedWords;
+    double acc[K];
+    bool nan[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        acc[k] = 0.0;
+        nan[k] = false;
+    }
+    bool ok = true;
+    for (int b = lane; b < t.G && ok; b += 32) {
+        const unsigned long long* src[2 * K];
+        unsigned long long w[2 * K];
+#pragma unroll
+        for (int k = 0; k < 2 * K; ++k) src[k] = base + (size_t)b * kTagRedWords + k;
+        ok = wait_tagged<2 * K>(c, src, w, tag);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const unsigned pw[2] = {(unsigned)w[2 * k], (unsigned)w[2 * k + 1]};
+            const double v = Pieces<double>::make(pw);
+            acc[k] = MAXOP ? fmax(acc[k], v) : acc[k] + v;
+            nan[k] |= (v != v);
+        }
+    }
+    ok = __all_sync(0xffffffffu, ok);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_xor_sync(0xffffffffu, acc[k], o);
+            acc[k] = MAXOP ? fmax(acc[k], w) : acc[k] + w;
+        }
+        const bool any_nan = __any_sync(0xffffffffu, nan[k]);
+        out[k] = any_nan ? __longlong_as_double(0x7ff8000000000000ll) : acc[k];
+    }
+    return ok;
 }
 
 // Start a team reduction of K <= 4 values (this CTA's partials already block-reduced
@@ -649,7 +792,10 @@ __device__ int level_sor(const TeamCtl& c, Team& t, const Smem<T>& m, double ome
         const T* const hi[5] = {m.cw + last, m.ce + last, m.cs + last, m.cn + last, m.bs + last};
         T* const fS[5] = {deep->cS[0], deep->cS[1], deep->cS[2], deep->cS[3], deep->cS[4]};
         T* const fN[5] = {deep->cN[0], deep->cN[1], deep->cN[2], deep->cN[3], deep->cN[4]};
-        if (!exchange_rows<NT, T, 5>(c, t, deep->pub, lo, hi, fS, fN, s_ok)) return -1;
+        if (!exchange_rows_tagged<NT, T, 5>(c, t, deep->tpub, lo, hi, fS, fN)) {
+            *s_ok = 0;
+            return -1;
+        }
     }
     double prev = -1.0, prev2 = -1.0;          // global max change of sweeps s-1 and s-2 (thread 0)
     unsigned long long pending = 0;
@@ -666,7 +812,10 @@ __device__ int level_sor(const TeamCtl& c, Team& t, const Smem<T>& m, double ome
                     const T* const hi[2] = {m.x + last, m.x + last - nx};
                     T* const fS[2] = {m.haloS, deep->xS2};
                     T* const fN[2] = {m.haloN, deep->xN2};
-                    if (!exchange_rows<NT, T, 2>(c, t, deep->pub, lo, hi, fS, fN, s_ok)) return -1;
+                    if (!exchange_rows_tagged<NT, T, 2>(c, t, deep->tpub, lo, hi, fS, fN)) {
+                        *s_ok = 0;
+                        return -1;
+                    }
                     // red points of the two halo rows, as their owners compute them
                     const int r_s = t.r0 - 1, r_n = t.r0 + t.nrows;
                     for (int q = threadIdx.x; q < 2 * half; q += NT) {
@@ -706,7 +855,7 @@ __device__ int level_sor(const TeamCtl& c, Team& t, const Smem<T>& m, double ome
         }
         // this CTA's max change (warp maxima, folded by thread 0), then arrive at the team
         // reduction of this sweep
-        const unsigned long long use = t.red_seq++;
+        const unsigned long long use = deep ? t.tag_seq++ : t.red_seq++;
         {
             unsigned long long* wred = reinterpret_cast<unsigned long long*>(m.red);
             for (int o = 16; o > 0; o >>= 1) {
@@ -718,10 +867,15 @@ __device__ int level_sor(const TeamCtl& c, Team& t, const Smem<T>& m, double ome
             if (threadIdx.x == 0) {
                 unsigned long long kmax = wred[0];
                 for (int w = 1; w < NT / 32; ++w) kmax = wred[w] > kmax ? wred[w] : kmax;
-                double* part = t.red_part + ((size_t)(use & 3) * t.G + t.b) * 4;
-                __stcg(part, mag_val<T>(kmax));
-                __threadfence();
-                atomicAdd(t.red_cnt + (use & 3), 1ull);
+                if (deep) {
+                    const double v1[1] = {mag_val<T>(kmax)};
+                    tagged_arrive<1>(t, deep->tred, use, v1);
+                } else {
+                    double* part = t.red_part + ((size_t)(use & 3) * t.G + t.b) * 4;
+                    __stcg(part, mag_val<T>(kmax));
+                    __threadfence();
+                    atomicAdd(t.red_cnt + (use & 3), 1ull);
+                }
             }
         }
         if (have_pending) {
@@ -730,26 +884,35 @@ __device__ int level_sor(const TeamCtl& c, Team& t, const Smem<T>& m, double ome
                 const int lane = threadIdx.x;
                 const int slot = (int)(pending & 3);
                 int ok = 1;
-                if (lane == 0) {
-                    const unsigned long long target = (unsigned long long)t.G * ((pending >> 2) + 1);
-                    const unsigned long long t0 = global_ns();
-                    ok = wait_geq(c, t.red_cnt + slot, target) ? 1 : 0;
-                    __threadfence();
-                    t.t_red += global_ns() - t0;
+                double d = 0.0;
+                bool nan = false;
+                const unsigned long long t0 = lane == 0 ? global_ns() : 0ull;
+                if (deep) {
+                    double g1[1];
+                    ok = tagged_finish<1, true>(c, t, deep->tred, pending, g1) ? 1 : 0;
+                    d = g1[0];
+                    nan = d != d;
+                } else {
+                    if (lane == 0) {
+                        const unsigned long long target = (unsigned long long)t.G * ((pending >> 2) + 1);
+                        ok = wait_geq(c, t.red_cnt + slot, target) ? 1 : 0;
+                        __threadfence();
+                    }
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    if (ok) {
+                        const double* part = t.red_part + (size_t)slot * t.G * 4;
+                        for (int b = lane; b < t.G; b += 32) {
+                            const double v = __ldcg(part + (size_t)b * 4);
+                            d = fmax(d, v);
+                            nan |= (v != v);
+                        }
+                        for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
+                        nan = __any_sync(0xffffffffu, nan);
+                    }
                 }
-                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (lane == 0) t.t_red += global_ns() - t0;
                 int decision = -1;  // -1 abort, 0 continue, 1 converged / capped, 2 NaN
                 if (ok) {
-                    const double* part = t.red_part + (size_t)slot * t.G * 4;
-                    double d = 0.0;
-                    bool nan = false;
-                    for (int b = lane; b < t.G; b += 32) {
-                        const double v = __ldcg(part + (size_t)b * 4);
-                        d = fmax(d, v);
-                        nan |= (v != v);
-                    }
-                    for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
-                    nan = __any_sync(0xffffffffu, nan);
                     decision = 0;
                     if (lane == 0) {
                         if (nan) {
@@ -773,14 +936,17 @@ __device__ int level_sor(const TeamCtl& c, Team& t, const Smem<T>& m, double ome
             // s_flag is written again only after the next sweep's barriers
             const int decision = *s_flag;
             if (decision < 0) {
+                if (threadIdx.x == 0 && !ld_acquire_s32(c.abort_flag)) team_fail(c, ST_ETIMEOUT);
                 *s_ok = 0;
                 return -1;
             }
             if (decision) {
                 if (decision == 2 && threadIdx.x == 0) atomicCAS(c.status, 0, ST_EDIVERGED);
-                // consume the outstanding reduction so the sequence stays aligned
-                double h[1];
-                if (!reduce_finish<1, true>(c, t, use, h, m.red + 32, s_ok)) return -1;
+                if (!deep) {
+                    // consume the outstanding reduction so the counter sequence stays aligned
+                    double h[1];
+                    if (!reduce_finish<1, true>(c, t, use, h, m.red + 32, s_ok)) return -1;
+                }
                 return sweep;
             }
         }
@@ -1109,7 +1275,8 @@ struct WaveArgs {
     long long wait_budget;
     // workspace, zeroed by the host before the launch (stop[1] set to INT_MAX)
     double* pub;                        // [K][2][G][2][nx]
-    double* pub2;                       // [K][2][G][kDeepSlotRows][nx] for one-exchange SOR sweeps, or nullptr
+    unsigned long long* tpub;           // [K][2][G][kDeepSlotRows][nx][2] tagged words (one-exchange SOR), or nullptr
+    unsigned long long* tred;           // [K][4][G][kTagRedWords] tagged reduction words (with tpub)
     unsigned long long* flags;          // [K][G]
     double* red_part;                   // [K][4][G][4]
     unsigned long long* red_cnt;        // [K][4]
@@ -1174,7 +1341,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
     // The conditions are the same on every CTA of the team (cap and rows_base are team-wide).
     Deep<T> deep_rows;
     const Deep<T>* deep = nullptr;
-    if (a.pub2 && a.G >= 2 && a.rows_base >= 2 && 12 * (size_t)nx <= 5 * (size_t)cap) {
+    if (a.tpub && a.tred && a.G >= 2 && a.rows_base >= 2 && 12 * (size_t)nx <= 5 * (size_t)cap) {
         T* d0 = m.r;
         for (int h = 0; h < 5; ++h) {
             deep_rows.cS[h] = d0 + (size_t)h * nx;
@@ -1182,7 +1349,8 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
         }
         deep_rows.xS2 = d0 + (size_t)10 * nx;
         deep_rows.xN2 = d0 + (size_t)11 * nx;
-        deep_rows.pub = a.pub2 + (size_t)team * 2 * a.G * kDeepSlotRows * nx;
+        deep_rows.tpub = a.tpub + (size_t)team * 2 * a.G * kDeepSlotRows * nx * 2;
+        deep_rows.tred = a.tred + (size_t)team * 4 * a.G * kTagRedWords;
         deep = &deep_rows;
     }
 
@@ -1324,7 +1492,27 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 for (int q = 0; q < 4; ++q) v3[q] = key_val(kk[q]);  // meaningful on thread 0 only
             }
             double g3[4];
-            if (!reduce_finish<4, true>(c, t, reduce_arrive<4>(t, v3), g3, m.red + 32, &s_ok)) return;
+            if (deep) {
+                const unsigned long long use = t.tag_seq++;
+                if (threadIdx.x == 0) tagged_arrive<4>(t, deep->tred, use, v3);
+                if (threadIdx.x < 32) {
+                    const unsigned long long t0 = threadIdx.x == 0 ? global_ns() : 0ull;
+                    const bool okr = tagged_finish<4, true>(c, t, deep->tred, use, g3);
+                    if (threadIdx.x == 0) {
+                        t.t_red += global_ns() - t0;
+                        for (int q = 0; q < 4; ++q) m.red[32 + q] = g3[q];
+                        if (!okr && !ld_acquire_s32(c.abort_flag)) team_fail(c, ST_ETIMEOUT);
+                        s_ok = okr ? 1 : 0;
+                    }
+                }
+                __syncthreads();
+                for (int q = 0; q < 4; ++q) g3[q] = m.red[32 + q];
+                const bool okr = s_ok != 0;
+                __syncthreads();
+                if (!okr) return;
+            } else if (!reduce_finish<4, true>(c, t, reduce_arrive<4>(t, v3), g3, m.red + 32, &s_ok)) {
+                return;
+            }
             if (g3[2] >= 2.0) goto done;  // another iteration has converged (or the launch aborts)
             if (!(g3[0] < kDiverged)) {
                 // NaN/Inf or a runaway residual: Newton diverges on this range of levels. One
