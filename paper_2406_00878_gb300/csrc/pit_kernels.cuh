@@ -1336,6 +1336,9 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
     double* slot = m.red + 48;
     // Burgers-type closures with constant viscosity have a constant diagonal 1 + 2 mu_a (vx + vy)
     const double dconst = 1.0 / (1.0 + 2.0 * oc.mu_a * (oc.vx + oc.vy));
+    // their folded constants: viscous mu_a tau / h^2, and the scaled couplings
+    const double vmu_x = oc.mu_a * oc.vx, vmu_y = oc.mu_a * oc.vy;
+    const double sjx = oc.jx * dconst, sjy = oc.jy * dconst, svx = vmu_x * dconst, svy = vmu_y * dconst;
     // neighbour rows for one-exchange SOR sweeps: in the BiCGStab scratch r..t (5 cap values),
     // which SOR leaves unused and u^n_k no longer needs once the level's system is formed.
     // The conditions are the same on every CTA of the team (cap and rows_base are team-wide).
@@ -1453,19 +1456,34 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                     const double uE = ii < nx - 1 ? u[ku + 1] : (bnd ? bnd[2 * nx + ny + j] : 0.0);
                     const double uS = u[ku - nx];
                     const double uN = u[ku + nx];
-                    double r = (uprev[i] - uC) - tau_F<CONV, NLV>(oc, uC, uW, uE, uS, uN);
+                    double r, aW, aE, aS, aN, d;
+                    if (CONV && !NLV) {
+                        // Burgers with constant viscosity: eq. 3 and its Jacobian with the constants
+                        // folded (the diagonal 1/d is constant), fewer FP64 operations
+                        const double sEW = uE + uW, sNS = uN + uS;
+                        const double cv = fma(oc.cy, (uN - uS) * sNS, oc.cx * ((uE - uW) * sEW));
+                        const double vs = fma(vmu_y, fma(-2.0, uC, sNS), vmu_x * fma(-2.0, uC, sEW));
+                        r = (uprev[i] - uC) - (cv - vs);
+                        d = dconst;
+                        aE = fma(sjx, uE, -svx);
+                        aW = fma(-sjx, uW, -svx);
+                        aN = fma(sjy, uN, -svy);
+                        aS = fma(-sjy, uS, -svy);
+                    } else {
+                        r = (uprev[i] - uC) - tau_F<CONV, NLV>(oc, uC, uW, uE, uS, uN);
+                        double aC;
+                        jac_row<CONV, NLV>(oc, uC, uW, uE, uS, uN, aC, aW, aE, aS, aN);
+                        d = NLV ? 1.0 / aC : dconst;
+                        aW *= d;
+                        aE *= d;
+                        aS *= d;
+                        aN *= d;
+                    }
                     if (qn) r = fma(oc.dt, qn[i], r);
-                    double aC, aW, aE, aS, aN;
-                    jac_row<CONV, NLV>(oc, uC, uW, uE, uS, uN, aC, aW, aE, aS, aN);
                     if (ii == 0) aW = 0.0;
                     if (ii == nx - 1) aE = 0.0;
                     if (j == 0) aS = 0.0;
                     if (j == ny - 1) aN = 0.0;
-                    const double d = NLV ? 1.0 / aC : dconst;
-                    aW *= d;
-                    aE *= d;
-                    aS *= d;
-                    aN *= d;
                     m.cw[i] = (T)aW;
                     m.ce[i] = (T)aE;
                     m.cs[i] = (T)aS;
