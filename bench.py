@@ -70,10 +70,8 @@ FLOPS_PER_JACOBIAN = 8
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2406_00878_gb300 import dist
+    return dist.env()
 
 
 class ClockSampler:
@@ -133,6 +131,7 @@ class ClockSampler:
 
 def run_ours(args, ws, rank, local):
     import torch
+    from paper_2406_00878_gb300 import dist as D
     from paper_2406_00878_gb300 import pit
     from paper_2406_00878_gb300 import workloads as W
 
@@ -153,8 +152,7 @@ def run_ours(args, ws, rank, local):
         for _ in range(max(args.warmup, 0)):
             info = step()
         stream.synchronize()
-        if ws > 1:
-            torch.distributed.barrier()
+        D.barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         infos = []
@@ -165,13 +163,8 @@ def run_ours(args, ws, rank, local):
             e1.record(stream)
             e1.synchronize()
         torch.cuda.synchronize()
-        if ws > 1:
-            torch.distributed.barrier()
-        ms = e0.elapsed_time(e1) / args.steps
-        if ws > 1:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        D.barrier()
+        ms = D.max_over_ranks(e0.elapsed_time(e1) / args.steps, device="cuda")
         # accuracy of the timed result against the oracle's first levels (rank 0)
         Ug = U.cpu().numpy().reshape(p.M, -1)
 
@@ -183,11 +176,7 @@ def run_ours(args, ws, rank, local):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             pit.pit_solve_host(ctx, u0_h, U_h)
-        e2e_s = (time.perf_counter() - t0) / args.steps
-        if ws > 1:
-            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = D.max_over_ranks((time.perf_counter() - t0) / args.steps, device="cuda")
         ctx.close()
 
     last = infos[-1]
@@ -218,7 +207,7 @@ def run_ours(args, ws, rank, local):
     achieved_tflops = flops_per_launch / (kernel_ms * 1e-3) / 1e12
     out = None
     if rank == 0:
-        value = ws * p.dof / (ms * 1e-3)
+        value = D.job_throughput([p.dof] * ws, ms * 1e-3)
         err = None
         if args.check:
             import oracle
@@ -247,7 +236,7 @@ def run_ours(args, ws, rank, local):
                                                  "reduce_wait": round(last["us_reduce_wait"], 1)}} if wave else None,
                        "max_rel_err_first_levels_vs_oracle": err},
             "gpu_launches": launches * args.steps,
-            "e2e": {"value": ws * p.dof / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(p.grid.ns * 8),
+            "e2e": {"value": D.job_throughput([p.dof] * ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(p.grid.ns * 8),
                     "d2h_bytes_per_step": int(p.dof * 8)},
             "roofline": {"kernel": kernel_name, "bound": "alu",
                          "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
