@@ -46,10 +46,10 @@ FLOPS_PER_BICGSTAB_ITER = 2 * 9 + 6 * 2 + 5 * 2
 # DRAM bytes (read + write) of one wavefront launch on this workload, from the ncu capture
 # summarised in profiles/wave_kernel_burgers256_full.md; valid only for the kernel sources it
 # was taken on (their SHA-256 below), reported as null once they change.
-WAVE_TRAFFIC_BYTES = 137.854976e6 + 128.570368e6
+WAVE_TRAFFIC_BYTES = 145.605888e6 + 218.326272e6
 WAVE_TRAFFIC_SOURCES = {
-    "paper_2406_00878_gb300/csrc/pit_kernels.cuh": "9a7f00e94f6f55af804c9c434406e04f9ea4a686298cefa7c80bdf3a8959f54e",
-    "paper_2406_00878_gb300/csrc/pit.cu": "8833ef47d13c3cd8c9d29f61dadc67538d05c6556abfdbb81ac3a44a151bc123",
+    "paper_2406_00878_gb300/csrc/pit_kernels.cuh": "f223e1b2685f18c6d87fe537e28e97438798c2cd7fc7ad3ec071b8f77f935335",
+    "paper_2406_00878_gb300/csrc/pit.cu": "c29afa7e889a4a27971b213cd16bb2329ef6cd3eac8daf10e8ee0d39f57f37e6",
 }
 
 
