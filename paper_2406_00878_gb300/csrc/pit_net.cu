@@ -6,11 +6,12 @@
 //   out = conv(x)                                   (3x3 convs, zero padding, bias)
 //
 // Activations are BF16 NHWC, weights BF16 [Cout][9][Cin] with FP32 master copies,
-// products accumulate in FP32 on the tensor cores (mma.sync m16n8k16). The input has
-// 2 channels, padded to 16 for the tensor-core K step. Training: MSE loss, manual
-// backward (data gradients through the forward kernel on flipped, transposed
-// weights; weight gradients by a split-K tensor-core kernel with a deterministic
-// two-pass reduction), Adam on the FP32 masters.
+// products accumulate in FP32 on the tensor cores: the convolutions (forward, and data
+// gradients through the same kernel on flipped, transposed weights) are tcgen05 implicit
+// GEMMs with TMEM accumulators (pit_tc.cuh); weight gradients use a split-K kernel on
+// warp-level MMAs (mma.sync m16n8k16) with a deterministic two-pass reduction. The input
+// has 2 channels, padded to 16 for the tensor-core K step. Training: MSE loss, manual
+// backward, Adam on the FP32 masters.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -22,6 +23,7 @@
 #include <vector>
 
 #include "pit.h"
+#include "pit_tc.cuh"
 
 namespace {
 
@@ -42,98 +44,6 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// ---------------------------------------------------------------- forward conv
-//
-// CTA: 64 pixels of one image row (n, h, w0..w0+63) x 64 output channels. Per
-// 16-channel input chunk it stages the three input rows h-1..h+1 (66 columns, zero
-// outside the image) and the chunk's weights of all 9 taps in shared memory; each
-// of the 4 warps computes 16 pixels x 64 channels with one k16 mma per tap and
-// 8-wide output tile. Epilogue: bias, optional residual add, optional ReLU, BF16.
-constexpr int kAStride = 16 + 8;        // bf16 per staged pixel (padding against bank conflicts)
-constexpr int kBStride = 9 * 16 + 8;    // bf16 per staged output channel
-
-__global__ void __launch_bounds__(128) conv3x3_fwd_kernel(const bf16* __restrict__ X, const bf16* __restrict__ Wt,
-                                                          const float* __restrict__ bias,
-                                                          const bf16* __restrict__ residual, bf16* __restrict__ Y,
-                                                          int N, int H, int W, int Cin, int Cout, int relu) {
-    __shared__ __align__(16) bf16 sA[3][kPixTile + 2][kAStride];
-    __shared__ __align__(16) bf16 sB[kCoTile][kBStride];
-    const int tiles_w = (W + kPixTile - 1) / kPixTile;
-    const int row = blockIdx.x / tiles_w;          // n * H + h
-    const int w0 = (blockIdx.x - row * tiles_w) * kPixTile;
-    const int n = row / H, h = row - n * H;
-    const int co0 = blockIdx.y * kCoTile;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, q = lane & 3;
-    float acc[8][4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
-
-    for (int c0 = 0; c0 < Cin; c0 += 16) {
-        // stage input rows: 3 x 66 pixels x 16 channels, as 2 x 16-byte pieces
-        for (int t = threadIdx.x; t < 3 * (kPixTile + 2) * 2; t += blockDim.x) {
-            const int half = t & 1, pc = t >> 1;
-            const int r = pc / (kPixTile + 2), col = pc - r * (kPixTile + 2);
-            const int hh = h + r - 1, ww = w0 + col - 1;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (hh >= 0 && hh < H && ww >= 0 && ww < W)
-                v = *reinterpret_cast<const uint4*>(X + (((size_t)n * H + hh) * W + ww) * Cin + c0 + half * 8);
-            *reinterpret_cast<uint4*>(&sA[r][col][half * 8]) = v;
-        }
-        // stage weights: 64 output channels x 9 taps x 16 channels
-        for (int t = threadIdx.x; t < kCoTile * 9 * 2; t += blockDim.x) {
-            const int half = t & 1, ot = t >> 1;
-            const int o = ot / 9, tap = ot - o * 9;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (co0 + o < Cout)
-                v = *reinterpret_cast<const uint4*>(Wt + ((size_t)(co0 + o) * 9 + tap) * Cin + c0 + half * 8);
-            *reinterpret_cast<uint4*>(&sB[o][tap * 16 + half * 8]) = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-            const int r = tap / 3, s = tap - r * 3;
-            const int p = warp * 16 + g;  // pixel rows g and g + 8 of the warp's 16
-            unsigned a[4];
-            a[0] = *reinterpret_cast<const unsigned*>(&sA[r][p + s][q * 2]);
-            a[1] = *reinterpret_cast<const unsigned*>(&sA[r][p + 8 + s][q * 2]);
-            a[2] = *reinterpret_cast<const unsigned*>(&sA[r][p + s][q * 2 + 8]);
-            a[3] = *reinterpret_cast<const unsigned*>(&sA[r][p + 8 + s][q * 2 + 8]);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                unsigned bb[2];
-                bb[0] = *reinterpret_cast<const unsigned*>(&sB[j * 8 + g][tap * 16 + q * 2]);
-                bb[1] = *reinterpret_cast<const unsigned*>(&sB[j * 8 + g][tap * 16 + q * 2 + 8]);
-                mma_bf16(acc[j], a, bb);
-            }
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int co = co0 + j * 8 + q * 2;
-#pragma unroll
-        for (int hf = 0; hf < 2; ++hf) {
-            const int w = w0 + warp * 16 + g + hf * 8;
-            if (w >= W || co >= Cout) continue;
-            const size_t o = (((size_t)n * H + h) * W + w) * Cout + co;
-            float v0 = acc[j][hf * 2] + bias[co];
-            float v1 = co + 1 < Cout ? acc[j][hf * 2 + 1] + bias[co + 1] : 0.f;
-            if (residual) {
-                v0 += __bfloat162float(residual[o]);
-                if (co + 1 < Cout) v1 += __bfloat162float(residual[o + 1]);
-            }
-            if (relu) {
-                v0 = fmaxf(v0, 0.f);
-                v1 = fmaxf(v1, 0.f);
-            }
-            Y[o] = __float2bfloat16(v0);
-            if (co + 1 < Cout) Y[o + 1] = __float2bfloat16(v1);
-        }
-    }
-}
 
 // ----------------------------------------------------- weight gradient (split K)
 //
@@ -220,24 +130,57 @@ __global__ void __launch_bounds__(128) conv3x3_bwdw_kernel(const bf16* __restric
 __global__ void sum_partials_kernel(const float* __restrict__ part, float* __restrict__ out, int splits, size_t n) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         float s = 0.f;
-        for (int k = 0; k < splits; ++k) s += part[(size_t)k * n + i];
+#pragma unroll 8
+        for (int k = 0; k < splits; ++k) s += __ldg(part + (size_t)k * n + i);  // loads batched, adds in order
         out[i] = s;
     }
 }
 
-// db[o] = sum over pixels of dY[pix][o]: one CTA per channel block, fixed order.
-__global__ void bias_grad_kernel(const bf16* __restrict__ dY, float* __restrict__ db, size_t pixels, int Cout) {
+// out[c] = sum over k of part[k][c] for few columns c and many rows k: one CTA per column,
+// threads take rows in a fixed stride and fold in a fixed tree (deterministic).
+__global__ void __launch_bounds__(256) sum_rows_kernel(const float* __restrict__ part, float* __restrict__ out,
+                                                       int rows, int cols) {
     __shared__ float red[256];
-    const int o = blockIdx.x;
+    const int c = blockIdx.x;
     float s = 0.f;
-    for (size_t p = threadIdx.x; p < pixels; p += blockDim.x) s += __bfloat162float(dY[p * Cout + o]);
+#pragma unroll 4
+    for (int k = threadIdx.x; k < rows; k += 256) s += __ldg(part + (size_t)k * cols + c);
     red[threadIdx.x] = s;
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    for (int w = 128; w > 0; w >>= 1) {
         if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) db[o] = red[0];
+    if (threadIdx.x == 0) out[c] = red[0];
+}
+
+// Bias gradient, first pass: CTA b sums dY[pix][o] over its range of pixels for every
+// channel o (threads: pixel lanes x channels, so reads are coalesced), lanes folded in a
+// fixed order; part[b][o]. The second pass (sum_partials_kernel) adds the CTAs in order.
+constexpr int kBiasBlocks = 2048;
+__global__ void __launch_bounds__(256) bias_grad_partial_kernel(const bf16* __restrict__ dY, float* __restrict__ part,
+                                                                size_t pixels, int Cout, size_t per_block) {
+    __shared__ float red[256];
+    const size_t p0 = (size_t)blockIdx.x * per_block;
+    const size_t p1 = p0 + per_block < pixels ? p0 + per_block : pixels;
+    for (int c0 = 0; c0 < Cout; c0 += 256) {
+        const int cw = Cout - c0 < 256 ? Cout - c0 : 256;
+        const int lanes = 256 / cw;
+        const int c = threadIdx.x % cw, pl = threadIdx.x / cw;
+        float acc = 0.f;
+        if (pl < lanes) {
+#pragma unroll 8
+            for (size_t p = p0 + pl; p < p1; p += lanes) acc += __bfloat162float(dY[p * Cout + c0 + c]);
+        }
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        if (threadIdx.x < cw) {
+            float t = 0.f;
+            for (int l = 0; l < lanes; ++l) t += red[l * cw + threadIdx.x];
+            part[(size_t)blockIdx.x * Cout + c0 + threadIdx.x] = t;
+        }
+        __syncthreads();
+    }
 }
 
 // W'[c][8 - tap][o] = W[o][tap][c]: the weights of the data-gradient convolution.
@@ -376,6 +319,8 @@ struct pit_net {
     bf16* d2 = nullptr;
     bf16* dout = nullptr;
     float* lognu = nullptr;
+    int* tc_err = nullptr;   // raised by a tensor-core conv whose mbarrier wait timed out
+    float* bias_part = nullptr;  // [kBiasBlocks][max channels] bias-gradient partials
     char err[512] = "";
 };
 
@@ -403,13 +348,39 @@ extern "C" long long pit_net_param_count(const pit_net_shape* s) {
     return (C * 9 * 2 + C) + 2LL * s->blocks * (C * 9 * C + C) + (M * 9 * C + M);
 }
 
-static pit_status conv_fwd(pit_net* net, const bf16* X, const Layer& L, const bf16* res, bf16* Y, int B, int relu) {
+// Y = act(conv3x3(X; Wt) + bias (+ res)) on the tcgen05 tensor cores (pit_tc.cuh).
+static pit_status launch_conv_tc(pit_net* net, const bf16* X, const bf16* Wt, const float* bias, const bf16* res,
+                                 bf16* Y, int B, int Cin, int Cout, int relu) {
     const pit_net_shape& s = net->shape;
-    if (L.cin % 16 != 0 || L.cout % 16 != 0) return nfail(net, PIT_EINVAL, "conv channels must be multiples of 16");
-    dim3 grid((unsigned)(B * s.height * ((s.width + kPixTile - 1) / kPixTile)), (unsigned)((L.cout + kCoTile - 1) / kCoTile));
-    conv3x3_fwd_kernel<<<grid, 128, 0, net->stream>>>(X, net->wb + L.w_off, net->p + L.b_off, res, Y, B, s.height,
-                                                      s.width, L.cin, L.cout, relu);
+    if (Cin % 16 != 0 || Cout % 16 != 0) return nfail(net, PIT_EINVAL, "conv channels must be multiples of 16");
+    static bool attr_set = false;  // the limit belongs to the kernel; raising it again is harmless
+    if (!attr_set) {
+        NCK(cudaFuncSetAttribute(pit_tc::conv3x3_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 pit_tc::kSmemMax));
+        attr_set = true;
+    }
+    const int smem = pit_tc::smem_bytes(Cout < pit_tc::kNMax ? Cout : pit_tc::kNMax);
+    dim3 grid((unsigned)(B * ((s.height + pit_tc::kRows - 1) / pit_tc::kRows) * ((s.width + pit_tc::kM - 1) / pit_tc::kM)),
+              (unsigned)((Cout + pit_tc::kNMax - 1) / pit_tc::kNMax));
+    pit_tc::conv3x3_fwd_tc_kernel<<<grid, pit_tc::kThreads, smem, net->stream>>>(
+        X, Wt, bias, res, Y, B, s.height, s.width, Cin, Cout, relu, net->tc_err);
     NCK(cudaGetLastError());
+    return PIT_OK;
+}
+
+static pit_status conv_fwd(pit_net* net, const bf16* X, const Layer& L, const bf16* res, bf16* Y, int B, int relu) {
+    return launch_conv_tc(net, X, net->wb + L.w_off, net->p + L.b_off, res, Y, B, L.cin, L.cout, relu);
+}
+
+// A tensor-core conv that timed out on an mbarrier raises tc_err; report it (synchronises).
+static pit_status check_tc(pit_net* net) {
+    int flag = 0;
+    NCK(cudaMemcpyAsync(&flag, net->tc_err, sizeof(int), cudaMemcpyDeviceToHost, net->stream));
+    NCK(cudaStreamSynchronize(net->stream));
+    if (flag) {
+        NCK(cudaMemsetAsync(net->tc_err, 0, sizeof(int), net->stream));
+        return nfail(net, PIT_ETIMEOUT, "tensor-core convolution: an mbarrier wait timed out");
+    }
     return PIT_OK;
 }
 
@@ -432,13 +403,18 @@ static pit_status conv_bwd(pit_net* net, const bf16* X, const bf16* dY, const La
     NCK(cudaGetLastError());
     const size_t nw = (size_t)L.cout * 9 * L.cin;
     sum_partials_kernel<<<grid_for(nw), 256, 0, net->stream>>>(net->part, net->g + L.w_off, splits, nw);
-    bias_grad_kernel<<<L.cout, 256, 0, net->stream>>>(dY, net->g + L.b_off, (size_t)B * s.height * s.width, L.cout);
+    {
+        const size_t pixels = (size_t)B * s.height * s.width;
+        const size_t per = (pixels + kBiasBlocks - 1) / kBiasBlocks;
+        const int blocks = (int)((pixels + per - 1) / per);
+        bias_grad_partial_kernel<<<blocks, 256, 0, net->stream>>>(dY, net->bias_part, pixels, L.cout, per);
+        sum_rows_kernel<<<L.cout, 256, 0, net->stream>>>(net->bias_part, net->g + L.b_off, blocks, L.cout);
+    }
     if (dX) {
         flip_transpose_kernel<<<grid_for(nw), 256, 0, net->stream>>>(net->wb + L.w_off, net->wf, L.cout, L.cin);
-        dim3 g2((unsigned)(B * s.height * ((s.width + kPixTile - 1) / kPixTile)), (unsigned)((L.cin + kCoTile - 1) / kCoTile));
-        // zero bias for the data gradient: use the tail of the gradient buffer's zero area
-        conv3x3_fwd_kernel<<<g2, 128, 0, net->stream>>>(dY, net->wf, net->loss_part + 1024, nullptr, dX, B, s.height,
-                                                        s.width, L.cout, L.cin, 0);
+        // zero bias for the data gradient: the zero tail of the loss buffer
+        if (pit_status st = launch_conv_tc(net, dY, net->wf, net->loss_part + 1024, nullptr, dX, B, L.cout, L.cin, 0))
+            return st;
     }
     NCK(cudaGetLastError());
     return PIT_OK;
@@ -503,6 +479,9 @@ extern "C" pit_status pit_net_create(const pit_net_shape* shape, unsigned long l
         net->part_n = 128 * wmax;
         NCK(cudaMalloc(&net->part, sizeof(float) * net->part_n));
         NCK(cudaMalloc(&net->loss_part, sizeof(float) * (1024 + 4096)));
+        NCK(cudaMalloc(&net->tc_err, sizeof(int)));
+        NCK(cudaMalloc(&net->bias_part, sizeof(float) * kBiasBlocks * std::max<size_t>(C, M)));
+        NCK(cudaMemsetAsync(net->tc_err, 0, sizeof(int), net->stream));
         NCK(cudaMemsetAsync(net->loss_part, 0, sizeof(float) * (1024 + 4096), net->stream));
         NCK(cudaMalloc(&net->in, sizeof(bf16) * B * Ns * kCinPad0));
         for (int k = 0; k <= shape->blocks; ++k) {
@@ -568,6 +547,8 @@ extern "C" void pit_net_destroy(pit_net* net) {
     cudaFree(net->wf);
     cudaFree(net->part);
     cudaFree(net->loss_part);
+    cudaFree(net->tc_err);
+    cudaFree(net->bias_part);
     cudaFree(net->in);
     for (auto x : net->xs) cudaFree(x);
     for (auto x : net->hs) cudaFree(x);
@@ -638,7 +619,7 @@ extern "C" pit_status pit_net_guess(pit_net* net, const double* u0_dev, const fl
     output_kernel<<<grid_for((size_t)B * net->shape.levels * Ns), 256, 0, net->stream>>>(net->out, u0_dev, U_dev, B,
                                                                                        net->shape.levels, Ns);
     NCK(cudaGetLastError());
-    return PIT_OK;
+    return check_tc(net);
 }
 
 extern "C" pit_status pit_net_make_target(pit_net* net, const double* u0_dev, const double* U_dev, void* target_dev) {
@@ -693,6 +674,7 @@ extern "C" pit_status pit_net_gradients(pit_net* net, const double* u0_dev, cons
                                         const void* target_dev, int B, float* loss_out, float* grads_host) {
     if (!net || !u0_dev || !lognu_host || !target_dev || B < 1 || B > net->shape.max_batch) return PIT_EINVAL;
     if (pit_status st = loss_grad(net, u0_dev, lognu_host, target_dev, B, loss_out)) return st;
+    if (pit_status st = check_tc(net)) return st;
     if (grads_host) {
         std::vector<float> st(net->nparam);
         NCK(cudaMemcpyAsync(st.data(), net->g, sizeof(float) * net->nparam, cudaMemcpyDeviceToHost, net->stream));
@@ -714,5 +696,5 @@ extern "C" pit_status pit_net_train_step(pit_net* net, const double* u0_dev, con
                                                                 b2, 1e-8f, c1, c2);
     to_bf16_kernel<<<grid_for(net->nparam), 256, 0, net->stream>>>(net->p, net->wb, net->nparam);
     NCK(cudaGetLastError());
-    return PIT_OK;
+    return loss_out ? check_tc(net) : PIT_OK;
 }

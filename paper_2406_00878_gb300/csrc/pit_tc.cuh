@@ -1,0 +1,306 @@
+// pit_tc.cuh -- 3x3 convolution (NHWC, BF16) as an implicit GEMM on the 5th-generation
+// tensor cores: tcgen05.mma with the FP32 accumulator in tensor memory (TMEM).
+//
+// GEMM view: rows = 128 pixels of one image row (n, h, w0..w0+127), columns = up to 128
+// output channels, K = 9 taps x Cin input channels, taken 16 at a time (one tap, one
+// 16-channel chunk per MMA instruction: M = 128, N = nt, K = 16). A CTA computes kRows
+// consecutive output rows h0..h0+kRows-1 with one accumulator each in TMEM, so every
+// staged weight chunk serves kRows rows and every staged input row up to three.
+//
+// Operands sit in shared memory in the canonical K-major layout without swizzle: a core
+// matrix is 8 rows x 16 bytes (8 BF16 K values per row), rows 16 bytes apart. For each
+// 16-channel chunk the CTA stages the input rows h0-1..h0+kRows (130 columns, zeros
+// outside the image) as two planes of 8 channels each -- pixel c of a plane at 16 c
+// bytes -- so the A operand of tap (r, s) is simply the plane of row r starting at
+// column s: 8 consecutive pixels are always one core matrix (stride between core
+// matrices along M: 128 bytes; between the two K halves: the plane size). The weights
+// of the chunk (9 taps x nt channels) are staged the same way.
+//
+// Pipeline: two staging buffers. Every thread loads chunk c into buffer c & 1 while the
+// MMAs of chunk c - 1 run; thread 0 issues the 9 x kRows MMAs of a chunk and commits them
+// to the buffer's mbarrier, which the CTA waits on before refilling that buffer two
+// chunks later. After the last chunk the accumulators are read from TMEM (tcgen05.ld,
+// each warp its 32 lanes = 32 pixels) for the epilogue: bias, optional residual, optional
+// ReLU, BF16. Every mbarrier wait is bounded: on time-out the CTA raises *err, waits (bounded)
+// for its MMAs in flight, frees its TMEM and returns without writing.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cstdint>
+
+namespace pit_tc {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kM = 128;          // pixels per output row segment (TMEM lanes)
+constexpr int kNMax = 128;       // output channels per CTA
+constexpr int kRows = 4;         // output rows per CTA (accumulators: kRows x nt <= 512 TMEM columns)
+constexpr int kInRows = kRows + 2;
+constexpr int kCols = kM + 2;    // staged columns of an input row (one halo column each side)
+constexpr int kThreads = 128;
+constexpr long long kWaitPolls = 1ll << 22;
+
+// staging buffer: A [kInRows rows][2 halves][kCols][8] then B [9 taps][2 halves][nb][8], BF16,
+// nb = min(Cout, kNMax) rows per weight plane
+constexpr int kABytes = kInRows * 2 * kCols * 16;
+__host__ __device__ constexpr int buf_bytes(int nb) { return kABytes + 9 * 2 * nb * 16; }
+// Dynamic shared memory of a launch: two buffers, three mbarriers and the TMEM address
+// slot. When one CTA's accumulators take all 512 TMEM columns the request is raised so
+// that only one CTA fits on an SM (a second would wait in tcgen05.alloc).
+__host__ __device__ constexpr int smem_bytes(int nb) {
+    return (nb > 64 ? (2 * buf_bytes(nb) + 32 > 116 * 1024 ? 2 * buf_bytes(nb) + 32 : 116 * 1024)
+                    : 2 * buf_bytes(nb) + 32);
+}
+constexpr int kSmemMax = smem_bytes(kNMax);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Poll until the phase with the given parity has completed, at most kWaitPolls times.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (long long i = 0; i < kWaitPolls; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// 16-byte asynchronous copy global -> shared (zero-filled when `valid` is false), and the
+// wait for all of this thread's outstanding copies.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Whole warp: allocate ncols TMEM columns (power of two >= 32); the address goes to *slot.
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major without swizzle: start address, byte offset
+// between the core matrices adjacent in K (lbo) and in M/N (sbo), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo & 0x3FFFF) >> 4) << 16;
+    d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major,
+// N >> 3 and M >> 4.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive once on bar when every MMA issued so far by this thread has completed.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Y[n][h][w][co] = act(bias[co] + sum_{tap, ci} X[n][h+r-1][w+s-1][ci] W[co][tap][ci] (+ residual)).
+// Grid: x = N * ceil(H / kRows) * ceil(W / 128) row-group segments, y = ceil(Cout / 128);
+// 128 threads; kSmemBytes of dynamic shared memory. Cin and Cout are multiples of 16.
+__global__ void __launch_bounds__(kThreads) conv3x3_fwd_tc_kernel(const bf16* __restrict__ X,
+                                                                  const bf16* __restrict__ Wt,
+                                                                  const float* __restrict__ bias,
+                                                                  const bf16* __restrict__ residual,
+                                                                  bf16* __restrict__ Y, int N, int H, int W, int Cin,
+                                                                  int Cout, int relu, int* err) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    const int nb = Cout < kNMax ? Cout : kNMax;  // weight rows per staged plane
+    const int bufb = buf_bytes(nb);
+    unsigned char* buf[2] = {sm, sm + bufb};
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * bufb);  // [0], [1] buffers, [2] final
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 3);
+
+    const int tiles_w = (W + kM - 1) / kM;
+    const int groups_h = (H + kRows - 1) / kRows;
+    const int grp = blockIdx.x / tiles_w;  // n * groups_h + g
+    const int w0 = (blockIdx.x - grp * tiles_w) * kM;
+    const int n = grp / groups_h, h0 = (grp - n * groups_h) * kRows;
+    const int co0 = blockIdx.y * kNMax;
+    const int nt = Cout - co0 < kNMax ? Cout - co0 : kNMax;  // multiple of 16, <= nb
+    const int ntp = nt <= 32 ? 32 : (nt <= 64 ? 64 : 128);   // TMEM columns per accumulator
+    const uint32_t ncols = (uint32_t)(ntp * kRows);          // power of two, <= 512
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (warp == 0) tmem_alloc(tslot, ncols);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init(&bar[2], 1);
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = *tslot;
+    const uint32_t idesc = idesc_bf16(kM, nt);
+
+    // issue the copies of chunk c into buffer c & 1 (one cp.async group; zero fill outside the image)
+    auto stage = [&](int c) {
+        bf16* sA = reinterpret_cast<bf16*>(buf[c & 1]);
+        bf16* sB = reinterpret_cast<bf16*>(buf[c & 1] + kABytes);
+        const int ci0 = c * 16;
+        for (int t = threadIdx.x; t < kInRows * kCols * 2; t += kThreads) {
+            const int half = t & 1, pc = t >> 1;
+            const int r = pc / kCols, col = pc - r * kCols;
+            const int hh = h0 + r - 1, ww = w0 + col - 1;
+            const bool in = hh >= 0 && hh < H && ww >= 0 && ww < W;
+            const bf16* src = in ? X + (((size_t)n * H + hh) * W + ww) * Cin + ci0 + half * 8 : X;
+            cp_async16(sA + ((size_t)(r * 2 + half) * kCols + col) * 8, src, in);
+        }
+        for (int t = threadIdx.x; t < nt * 9 * 2; t += kThreads) {
+            const int half = t & 1, ot = t >> 1;
+            const int o = ot / 9, tap = ot - o * 9;
+            cp_async16(sB + ((size_t)(tap * 2 + half) * nb + o) * 8,
+                       Wt + ((size_t)(co0 + o) * 9 + tap) * Cin + ci0 + half * 8, true);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+
+    const int nchunks = Cin / 16;
+    bool ok = true;
+    stage(0);
+    for (int c = 0; c < nchunks; ++c) {
+        const int b = c & 1;
+        if (c + 1 < nchunks) {
+            if (c >= 1) {  // buffer (c + 1) & 1: the MMAs of chunk c - 1 have finished reading it
+                const bool got = mbar_wait(&bar[(c + 1) & 1], (uint32_t)(((c - 1) >> 1) & 1));
+                ok = __syncthreads_and(got) != 0;
+                if (!ok) break;
+            }
+            stage(c + 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");  // chunk c has landed
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        fence_async_smem();  // the copies feed the tensor cores (async proxy)
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(buf[b]), b0 = smem_u32(buf[b] + kABytes);
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const int r = tap / 3, s = tap - r * 3;
+                const uint64_t bd = smem_desc(b0 + (uint32_t)(tap * 2 * nb * 16), (uint32_t)(nb * 16), 128);
+#pragma unroll
+                for (int q = 0; q < kRows; ++q) {  // output row h0 + q reads input row h0 + q + r - 1
+                    const uint64_t ad =
+                        smem_desc(a0 + (uint32_t)(((q + r) * 2 * kCols + s) * 16), kCols * 16, 128);
+                    mma_bf16(taddr + (uint32_t)(q * ntp), ad, bd, idesc, (c > 0 || tap > 0) ? 1u : 0u);
+                }
+            }
+            mma_commit(&bar[b]);
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy left in flight (also after a time-out)
+    // every MMA issued has completed (also after a time-out: bounded)
+    if (threadIdx.x == 0) mma_commit(&bar[2]);
+    const bool fin = mbar_wait(&bar[2], 0);
+    ok = (__syncthreads_and(fin) != 0) && ok;
+    tc_fence_after();
+    if (ok) {
+        const int p = w0 + warp * 32 + lane;  // this thread's pixel = TMEM lane warp * 32 + lane
+        for (int q = 0; q < kRows; ++q) {
+            const int h = h0 + q;
+            const size_t ybase = (((size_t)n * H + h) * W + p) * Cout + co0;
+            for (int j0 = 0; j0 < nt; j0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * ntp + j0), r);
+                if (p < W && h < H) {
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]) + bias[co0 + j0 + j];
+                    if (residual) {
+                        const uint4* rs = reinterpret_cast<const uint4*>(residual + ybase + j0);
+#pragma unroll
+                        for (int e2 = 0; e2 < 2; ++e2) {
+                            const uint4 u = rs[e2];
+                            const unsigned uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                v[e2 * 8 + 2 * e] +=
+                                    __bfloat162float(__ushort_as_bfloat16((unsigned short)(uu[e] & 0xffff)));
+                                v[e2 * 8 + 2 * e + 1] +=
+                                    __bfloat162float(__ushort_as_bfloat16((unsigned short)(uu[e] >> 16)));
+                            }
+                        }
+                    }
+                    if (relu)
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
+                    uint32_t packed[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        packed[e] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(v[2 * e])) |
+                                    ((uint32_t)__bfloat16_as_ushort(__float2bfloat16(v[2 * e + 1])) << 16);
+                    uint4* out = reinterpret_cast<uint4*>(Y + ybase + j0);
+                    out[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                    out[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(taddr, ncols);
+}
+
+}  // namespace pit_tc
