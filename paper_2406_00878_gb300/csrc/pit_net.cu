@@ -7,9 +7,9 @@
 //
 // Activations are BF16 NHWC, weights BF16 [Cout][9][Cin] with FP32 master copies,
 // products accumulate in FP32 on the tensor cores: the convolutions (forward, and data
-// gradients through the same kernel on flipped, transposed weights) are tcgen05 implicit
-// GEMMs with TMEM accumulators (pit_tc.cuh); weight gradients use a split-K kernel on
-// warp-level MMAs (mma.sync m16n8k16) with a deterministic two-pass reduction. The input
+// gradients through the same kernel on flipped, transposed weights) and the weight
+// gradients (split over pixels, deterministic two-pass reduction) are tcgen05 GEMMs with
+// TMEM accumulators (pit_tc.cuh). The input
 // has 2 channels, padded to 16 for the tensor-core K step. Training: MSE loss, manual
 // backward, Adam on the FP32 masters.
 #include <cuda_bf16.h>
@@ -29,102 +29,7 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 constexpr int kCinPad0 = 16;   // input channels padded for the K step
-constexpr int kPixTile = 64;   // pixels of one image row per CTA
-constexpr int kCoTile = 64;    // output channels per CTA
-
-__device__ __forceinline__ unsigned pack2(bf16 lo, bf16 hi) {
-    return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-
-// ----------------------------------------------------- weight gradient (split K)
-//
-// dW[o][tap][c] = sum over pixels of dY[pix][o] * X[pix shifted by tap][c]. Grid:
-// x = pixel splits (rows_per_split image rows each), y = tap * (Cin / ct) + c-tile,
-// z = Cout / 64. Each of the 4 warps computes 16 output channels x ct input
-// channels with k16 mma steps over the pixels; partial sums go to
-// part[split][Cout][9][Cin] and a second kernel adds the splits in order.
-template <int CT>
-__global__ void __launch_bounds__(128) conv3x3_bwdw_kernel(const bf16* __restrict__ X, const bf16* __restrict__ dY,
-                                                           float* __restrict__ part, int N, int H, int W, int Cin,
-                                                           int Cout, int rows_per_split) {
-    __shared__ __align__(16) bf16 sY[kPixTile][kCoTile + 8];
-    __shared__ __align__(16) bf16 sX[kPixTile][CT + 8];
-    const int ctiles = Cin / CT;
-    const int tap = blockIdx.y / ctiles, ct = blockIdx.y - tap * ctiles;
-    const int r = tap / 3, s = tap - r * 3;
-    const int c0 = ct * CT, co0 = blockIdx.z * kCoTile;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, q = lane & 3;
-    constexpr int NT = CT / 8;
-    float acc[NT][4];
-#pragma unroll
-    for (int j = 0; j < NT; ++j)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
-    const int row_begin = blockIdx.x * rows_per_split, row_end = min(row_begin + rows_per_split, N * H);
-    for (int rowi = row_begin; rowi < row_end; ++rowi) {
-        const int n = rowi / H, h = rowi - n * H;
-        const int hh = h + r - 1;
-        for (int w0 = 0; w0 < W; w0 += kPixTile) {
-            for (int t = threadIdx.x; t < kPixTile * (kCoTile / 8); t += blockDim.x) {
-                const int p = t / (kCoTile / 8), piece = t - p * (kCoTile / 8);
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (w0 + p < W && co0 + piece * 8 < Cout)
-                    v = *reinterpret_cast<const uint4*>(dY + (((size_t)n * H + h) * W + w0 + p) * Cout + co0 + piece * 8);
-                *reinterpret_cast<uint4*>(&sY[p][piece * 8]) = v;
-            }
-            for (int t = threadIdx.x; t < kPixTile * (CT / 8); t += blockDim.x) {
-                const int p = t / (CT / 8), piece = t - p * (CT / 8);
-                const int ww = w0 + p + s - 1;
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (w0 + p < W && hh >= 0 && hh < H && ww >= 0 && ww < W)
-                    v = *reinterpret_cast<const uint4*>(X + (((size_t)n * H + hh) * W + ww) * Cin + c0 + piece * 8);
-                *reinterpret_cast<uint4*>(&sX[p][piece * 8]) = v;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int k0 = 0; k0 < kPixTile; k0 += 16) {
-                // A = dY^T: rows o (warp*16 + g, +8), columns pixels k0 + 2q (+1, +8, +9)
-                const int o = warp * 16 + g;
-                unsigned a[4];
-                a[0] = pack2(sY[k0 + q * 2][o], sY[k0 + q * 2 + 1][o]);
-                a[1] = pack2(sY[k0 + q * 2][o + 8], sY[k0 + q * 2 + 1][o + 8]);
-                a[2] = pack2(sY[k0 + q * 2 + 8][o], sY[k0 + q * 2 + 9][o]);
-                a[3] = pack2(sY[k0 + q * 2 + 8][o + 8], sY[k0 + q * 2 + 9][o + 8]);
-#pragma unroll
-                for (int j = 0; j < NT; ++j) {
-                    const int c = j * 8 + g;
-                    unsigned bb[2];
-                    bb[0] = pack2(sX[k0 + q * 2][c], sX[k0 + q * 2 + 1][c]);
-                    bb[1] = pack2(sX[k0 + q * 2 + 8][c], sX[k0 + q * 2 + 9][c]);
-                    mma_bf16(acc[j], a, bb);
-                }
-            }
-            __syncthreads();
-        }
-    }
-    float* P = part + (size_t)blockIdx.x * Cout * 9 * Cin;
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-        const int c = c0 + j * 8 + q * 2;
-#pragma unroll
-        for (int hf = 0; hf < 2; ++hf) {
-            const int o = co0 + warp * 16 + g + hf * 8;
-            if (o >= Cout) continue;
-            P[((size_t)o * 9 + tap) * Cin + c] = acc[j][hf * 2];
-            P[((size_t)o * 9 + tap) * Cin + c + 1] = acc[j][hf * 2 + 1];
-        }
-    }
-}
+constexpr int kMaxSplits = 160;  // pixel splits of the weight-gradient GEMMs, at most
 
 // Sum the split partials in split order (deterministic).
 __global__ void sum_partials_kernel(const float* __restrict__ part, float* __restrict__ out, int splits, size_t n) {
@@ -390,16 +295,21 @@ static pit_status conv_bwd(pit_net* net, const bf16* X, const bf16* dY, const La
     // the data-gradient convolution reads L.cout input channels in chunks of 16
     if (L.cin % 16 != 0 || L.cout % 16 != 0) return nfail(net, PIT_EINVAL, "conv channels must be multiples of 16");
     const int rows = B * s.height;
-    const int rows_per_split = std::max(1, (rows + 127) / 128);
+    // one CTA per split and channel tile pair, about one per SM
+    const int tiles = ((L.cin + pit_tc::kWCi - 1) / pit_tc::kWCi) * ((L.cout + pit_tc::kWCo - 1) / pit_tc::kWCo);
+    const int want = std::max(1, std::min(kMaxSplits, 148 / tiles));
+    const int rows_per_split = std::max(1, (rows + want - 1) / want);
     const int splits = (rows + rows_per_split - 1) / rows_per_split;
-    const int ct = L.cin >= 64 ? 64 : 16;
-    dim3 grid((unsigned)splits, (unsigned)(9 * (L.cin / ct)), (unsigned)((L.cout + kCoTile - 1) / kCoTile));
-    if (ct == 64)
-        conv3x3_bwdw_kernel<64><<<grid, 128, 0, net->stream>>>(X, dY, net->part, B, s.height, s.width, L.cin, L.cout,
-                                                              rows_per_split);
-    else
-        conv3x3_bwdw_kernel<16><<<grid, 128, 0, net->stream>>>(X, dY, net->part, B, s.height, s.width, L.cin, L.cout,
-                                                              rows_per_split);
+    static bool wattr_set = false;  // the limit belongs to the kernel; raising it again is harmless
+    if (!wattr_set) {
+        NCK(cudaFuncSetAttribute(pit_tc::conv3x3_bwdw_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 pit_tc::kWSmemBytes));
+        wattr_set = true;
+    }
+    dim3 grid((unsigned)splits, (unsigned)((L.cin + pit_tc::kWCi - 1) / pit_tc::kWCi),
+              (unsigned)((L.cout + pit_tc::kWCo - 1) / pit_tc::kWCo));
+    pit_tc::conv3x3_bwdw_tc_kernel<<<grid, pit_tc::kThreads, pit_tc::kWSmemBytes, net->stream>>>(
+        X, dY, net->part, B, s.height, s.width, L.cin, L.cout, rows_per_split, net->tc_err);
     NCK(cudaGetLastError());
     const size_t nw = (size_t)L.cout * 9 * L.cin;
     sum_partials_kernel<<<grid_for(nw), 256, 0, net->stream>>>(net->part, net->g + L.w_off, splits, nw);
@@ -476,7 +386,7 @@ extern "C" pit_status pit_net_create(const pit_net_shape* shape, unsigned long l
         size_t wmax = 0;
         for (auto& L : net->layers) wmax = std::max(wmax, (size_t)L.cout * 9 * L.cin);
         NCK(cudaMalloc(&net->wf, sizeof(bf16) * wmax));
-        net->part_n = 128 * wmax;
+        net->part_n = (size_t)kMaxSplits * wmax;
         NCK(cudaMalloc(&net->part, sizeof(float) * net->part_n));
         NCK(cudaMalloc(&net->loss_part, sizeof(float) * (1024 + 4096)));
         NCK(cudaMalloc(&net->tc_err, sizeof(int)));

@@ -37,7 +37,7 @@ constexpr int kNMax = 128;       // output channels per CTA
 constexpr int kRows = 4;         // output rows per CTA (accumulators: kRows x nt <= 512 TMEM columns)
 constexpr int kInRows = kRows + 2;
 constexpr int kCols = kM + 2;    // staged columns of an input row (one halo column each side)
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;   // 8 warps; warps w and w + 4 read the same TMEM lane quarter
 constexpr long long kWaitPolls = 1ll << 22;
 
 // staging buffer: A [kInRows rows][2 halves][kCols][8] then B [9 taps][2 halves][nb][8], BF16,
@@ -255,13 +255,14 @@ __global__ void __launch_bounds__(kThreads) conv3x3_fwd_tc_kernel(const bf16* __
     ok = (__syncthreads_and(fin) != 0) && ok;
     tc_fence_after();
     if (ok) {
-        const int p = w0 + warp * 32 + lane;  // this thread's pixel = TMEM lane warp * 32 + lane
-        for (int q = 0; q < kRows; ++q) {
+        const int quarter = warp & 3;             // TMEM lanes 32 quarter .. 32 quarter + 31
+        const int p = w0 + quarter * 32 + lane;   // this thread's pixel
+        for (int q = warp >> 2; q < kRows; q += kThreads / 128) {
             const int h = h0 + q;
             const size_t ybase = (((size_t)n * H + h) * W + p) * Cout + co0;
             for (int j0 = 0; j0 < nt; j0 += 16) {
                 uint32_t r[16];
-                tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * ntp + j0), r);
+                tmem_ld16(taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(q * ntp + j0), r);
                 if (p < W && h < H) {
                     float v[16];
 #pragma unroll
@@ -292,6 +293,258 @@ __global__ void __launch_bounds__(kThreads) conv3x3_fwd_tc_kernel(const bf16* __
                     uint4* out = reinterpret_cast<uint4*>(Y + ybase + j0);
                     out[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
                     out[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(taddr, ncols);
+}
+
+}  // namespace pit_tc
+
+namespace pit_tc {
+
+// ------------------------------------------------------------------ weight gradients
+//
+// dW[co][tap][ci] = sum over pixels p of X[p + tap][ci] dY[p][co] (zero outside the image),
+// as GEMMs on the tensor cores with dY as the shared operand: B = dY (N = 64 output
+// channels), K = pixels, 64 per staged segment of an image row (4 MMAs of K = 16). The
+// 128 rows of A hold two taps at once -- rows 0..63 the input channels of tap 2g shifted
+// by that tap, rows 64..127 those of tap 2g + 1 -- so five accumulators (taps 0-1, 2-3,
+// 4-5, 6-7, 8) cover all nine taps and every dY segment is staged once. A CTA covers a
+// 64 x 64 channel tile pair and a split of the image rows and writes FP32 partial sums;
+// a second pass adds them over the splits in a fixed order.
+//
+// Both operands come from NHWC activations, where channels are contiguous and pixels are
+// not; staging transposes them into the K-major core-matrix layout: a thread loads an
+// 8-pixel x 8-channel block (8 x 16 bytes), exchanges 16-bit halves between pixel pairs
+// (16 byte permutes), and after that the rows of the transposed block are a renaming of
+// the registers -- each is one 16-byte row of a core matrix (8 channels x 8 pixels, 128
+// contiguous bytes). Plane j of a staged operand holds pixels 8j..8j+7 of all its rows,
+// so MMA k reads planes 2k and 2k+1 (byte offset between K-adjacent core matrices: the
+// plane size; between row groups: 128 bytes).
+constexpr int kWK = 64;                            // pixels per staged segment
+constexpr int kWPlanes = kWK / 8;
+constexpr int kWCi = 64;                           // input channels per tap half of A
+constexpr int kWCo = 64;                           // output channels (N)
+constexpr int kWGroups = 5;                        // tap pairs
+constexpr int kWAGroupBytes = kWPlanes * 128 * 16;  // one group: 128 rows
+constexpr int kWABytes = kWGroups * kWAGroupBytes;
+constexpr int kWBBytes = kWPlanes * kWCo * 16;
+constexpr int kWBufBytes = kWABytes + kWBBytes;
+constexpr int kWSmemBytes = 2 * kWBufBytes + 32;
+constexpr int kWBlk = 3;                           // 8x8 blocks per thread and segment, at most (<= 640)
+
+// Transpose an 8 x 8 block of 16-bit values held as 8 rows of 4 words (row i = pixel i,
+// word k = channels 2k, 2k+1) into 8 rows of 4 words indexed by channel (word a = pixels
+// 2a, 2a+1).
+__device__ __forceinline__ void transpose8x8_b16(const uint32_t (&in)[8][4], uint32_t (&out)[8][4]) {
+    uint32_t w[8][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            w[2 * a][k] = __byte_perm(in[2 * a][k], in[2 * a + 1][k], 0x5410);      // channel 2k of pixels 2a, 2a+1
+            w[2 * a + 1][k] = __byte_perm(in[2 * a][k], in[2 * a + 1][k], 0x7632);  // channel 2k+1
+        }
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) out[c][a] = w[2 * a + (c & 1)][c >> 1];
+}
+
+// Grid: x = splits of the N*H image rows (rows_per_split each), y = ceil(Cin / 64),
+// z = ceil(Cout / 64); 128 threads; kWSmemBytes of dynamic shared memory.
+// part[split][co][tap][ci] receives the CTA's sums. Cin and Cout are multiples of 16.
+__global__ void __launch_bounds__(kThreads) conv3x3_bwdw_tc_kernel(const bf16* __restrict__ X,
+                                                                   const bf16* __restrict__ dY,
+                                                                   float* __restrict__ part, int N, int H, int W,
+                                                                   int Cin, int Cout, int rows_per_split, int* err) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    const int ci0 = blockIdx.y * kWCi, co0 = blockIdx.z * kWCo;
+    const int cw = Cin - ci0 < kWCi ? Cin - ci0 : kWCi;   // real rows per tap half (multiple of 16)
+    const int nco = Cout - co0 < kWCo ? Cout - co0 : kWCo; // N (multiple of 16)
+    unsigned char* buf[2] = {sm, sm + kWBufBytes};
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * kWBufBytes);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 3);
+    const int ntp = nco <= 32 ? 32 : 64;                    // TMEM columns per accumulator
+    const uint32_t ncols = ntp * kWGroups <= 256 ? 256u : 512u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // A rows that never receive data stay zero in both buffers: rows cw..63 of every tap
+    // half, and the upper half of the last group (there is no tenth tap)
+    for (int b = 0; b < 2; ++b)
+        for (int t = threadIdx.x; t < kWGroups * kWPlanes * 128; t += kThreads) {
+            const int row = t & 127, gp = t >> 7;  // gp = group * kWPlanes + plane
+            const int grp = gp / kWPlanes;
+            const bool empty = (row & 63) >= cw || (grp == kWGroups - 1 && row >= 64);
+            if (empty) *reinterpret_cast<uint4*>(buf[b] + (size_t)gp * 128 * 16 + (size_t)row * 16) = make_uint4(0, 0, 0, 0);
+        }
+    if (warp == 0) tmem_alloc(tslot, ncols);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init(&bar[2], 1);
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = *tslot;
+    const uint32_t idesc = idesc_bf16(kM, nco);
+
+    const int row_begin = blockIdx.x * rows_per_split;
+    const int row_end = min(row_begin + rows_per_split, N * H);
+    const int segs_w = (W + kWK - 1) / kWK;
+    const int nseg = (row_end > row_begin ? row_end - row_begin : 0) * segs_w;
+    // 8x8 blocks per segment: A, 9 taps x cw/8 channel groups x 8 planes; B, nco/8 x 8
+    const int cg8 = cw / 8, nA = 9 * cg8 * kWPlanes, nB = (nco / 8) * kWPlanes;
+
+    uint4 in[kWBlk][8];
+    auto load = [&](int sg) {
+        const int rowi = row_begin + sg / segs_w;
+        const int w0 = (sg % segs_w) * kWK;
+        const int n = rowi / H, h = rowi - n * H;
+#pragma unroll
+        for (int u = 0; u < kWBlk; ++u) {
+            const int blk = threadIdx.x + u * kThreads;
+            const bool isA = blk < nA;
+            int tap = 0, cg, j;
+            if (isA) {
+                tap = blk / (cg8 * kWPlanes);
+                const int q = blk - tap * cg8 * kWPlanes;
+                j = q / cg8;
+                cg = q - j * cg8;
+            } else {
+                const int q = blk - nA;
+                j = q / (nco / 8);
+                cg = q - j * (nco / 8);
+            }
+            const int r = tap / 3, s = tap - r * 3, hh = h + r - 1;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int w = w0 + j * 8 + i;
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (blk < nA + nB && w < W) {
+                    if (isA) {
+                        const int ww = w + s - 1;
+                        if (hh >= 0 && hh < H && ww >= 0 && ww < W)
+                            v = *reinterpret_cast<const uint4*>(X + (((size_t)n * H + hh) * W + ww) * Cin + ci0 + cg * 8);
+                    } else {
+                        v = *reinterpret_cast<const uint4*>(dY + (((size_t)n * H + h) * W + w) * Cout + co0 + cg * 8);
+                    }
+                }
+                in[u][i] = v;
+            }
+        }
+    };
+    auto store = [&](unsigned char* sA, unsigned char* sB) {
+#pragma unroll
+        for (int u = 0; u < kWBlk; ++u) {
+            const int blk = threadIdx.x + u * kThreads;
+            if (blk >= nA + nB) continue;
+            const bool isA = blk < nA;
+            int tap = 0, cg, j;
+            if (isA) {
+                tap = blk / (cg8 * kWPlanes);
+                const int q = blk - tap * cg8 * kWPlanes;
+                j = q / cg8;
+                cg = q - j * cg8;
+            } else {
+                const int q = blk - nA;
+                j = q / (nco / 8);
+                cg = q - j * (nco / 8);
+            }
+            uint32_t w8[8][4], out[8][4];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                w8[i][0] = in[u][i].x;
+                w8[i][1] = in[u][i].y;
+                w8[i][2] = in[u][i].z;
+                w8[i][3] = in[u][i].w;
+            }
+            transpose8x8_b16(w8, out);
+            unsigned char* dst = isA ? sA + (size_t)((tap >> 1) * kWPlanes + j) * 128 * 16 +
+                                           (size_t)((tap & 1) * 64 + cg * 8) * 16
+                                     : sB + (size_t)j * kWCo * 16 + (size_t)cg * 128;
+            // Core matrices of neighbouring threads sit 128 bytes apart, i.e. on the same four
+            // banks: thread-dependent row order (rotated by rot) spreads one store instruction
+            // of a warp over all 32 banks. The rotation is done on registers in three steps.
+            const int rot = (cg + j) & 7;
+#pragma unroll
+            for (int st = 1; st < 8; st <<= 1) {
+                if (rot & st) {
+                    uint32_t tmp[8][4];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) tmp[c][a] = out[(c + st) & 7][a];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) out[c][a] = tmp[c][a];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c)  // out[c] now holds transposed row (c + rot) & 7
+                *reinterpret_cast<uint4*>(dst + ((c + rot) & 7) * 16) =
+                    make_uint4(out[c][0], out[c][1], out[c][2], out[c][3]);
+        }
+    };
+
+    bool ok = true;
+    if (nseg > 0) load(0);
+    for (int sg = 0; sg < nseg; ++sg) {
+        const int b = sg & 1;
+        if (sg >= 2) {
+            const bool got = mbar_wait(&bar[b], (uint32_t)(((sg - 2) >> 1) & 1));
+            ok = __syncthreads_and(got) != 0;
+            if (!ok) break;
+        }
+        unsigned char* sA = buf[b];
+        unsigned char* sB = buf[b] + kWABytes;
+        store(sA, sB);
+        if (sg + 1 < nseg) load(sg + 1);
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll
+            for (int k = 0; k < kWPlanes / 2; ++k) {
+                const uint64_t bd = smem_desc(b0 + (uint32_t)(2 * k * kWCo * 16), kWCo * 16, 128);
+#pragma unroll
+                for (int g = 0; g < kWGroups; ++g) {
+                    const uint64_t ad =
+                        smem_desc(a0 + (uint32_t)((g * kWPlanes + 2 * k) * 128 * 16), 128 * 16, 128);
+                    mma_bf16(taddr + (uint32_t)(g * ntp), ad, bd, idesc, (sg > 0 || k > 0) ? 1u : 0u);
+                }
+            }
+            mma_commit(&bar[b]);
+        }
+    }
+    if (threadIdx.x == 0) mma_commit(&bar[2]);
+    const bool fin = mbar_wait(&bar[2], 0);
+    ok = (__syncthreads_and(fin) != 0) && ok;
+    tc_fence_after();
+    if (ok) {
+        // TMEM lane = A row: rows 0..63 tap 2g, rows 64..127 tap 2g + 1; column = output channel
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane, ci = ci0 + (row & 63);
+        float* P = part + (size_t)blockIdx.x * Cout * 9 * Cin;
+        for (int g = warp >> 2; g < kWGroups; g += kThreads / 128) {
+            const int tap = 2 * g + (row >> 6);
+            for (int j0 = 0; j0 < nco; j0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(g * ntp + j0), v);
+                if (tap < 9 && (row & 63) < cw) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        P[((size_t)(co0 + j0 + j) * 9 + tap) * Cin + ci] = nseg > 0 ? __uint_as_float(v[j]) : 0.f;
                 }
             }
         }
