@@ -103,9 +103,14 @@ static size_t team_smem(bool fp32, int nx, int ny, int G) {
 struct WsSize {
     size_t sync, data;
 };
+static size_t tagged_words(int G, int nx) {
+    return (size_t)2 * G * kDeepSlotRows * nx * 2 + (size_t)4 * G * kTagRedWords;
+}
 static WsSize ws_size(int G, int nx, int newton_max, int window) {
     WsSize w;
-    w.sync = align_up(sizeof(unsigned long long) * ((size_t)G * 2 + 4) + sizeof(int) * 4, 256);
+    // flags, prog, red_cnt, kconv, then the tagged words (all zeroed before each launch)
+    w.sync = align_up(sizeof(unsigned long long) * ((size_t)G * 2 + 4) + sizeof(int) * 4, 256) +
+             align_up(sizeof(unsigned long long) * tagged_words(G, nx), 256);
     w.data = align_up(sizeof(double) * ((size_t)2 * G * 2 * nx + (size_t)4 * G * 4 + (size_t)newton_max * window), 256);
     return w;
 }
@@ -179,6 +184,10 @@ static pit_status build_launch(pit_batch* b, const std::vector<pit_instance>& in
         ws[q].prog = sw + G;
         ws[q].red_cnt = sw + 2 * G;
         ws[q].kconv = reinterpret_cast<int*>(sw + 2 * G + 4);
+        unsigned long long* tw = reinterpret_cast<unsigned long long*>(
+            b->pool + so + align_up(sizeof(unsigned long long) * ((size_t)G * 2 + 4) + sizeof(int) * 4, 256));
+        ws[q].tpub = tw;
+        ws[q].tred = tw + (size_t)2 * G * kDeepSlotRows * nx * 2;
         so += wss[q].sync;
         double* dw = reinterpret_cast<double*>(b->pool + dof);
         ws[q].pub = dw;

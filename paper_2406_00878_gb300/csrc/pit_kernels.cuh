@@ -1671,6 +1671,8 @@ struct BatchTeamWs {
     unsigned long long* prog;           // [G]
     double* cell_prefix;                // [newton_max][window]
     int* kconv;                         // converged iteration of the current window (CTA 0 only)
+    unsigned long long* tpub;           // [2][G][kDeepSlotRows][nx][2] tagged words (zeroed per launch)
+    unsigned long long* tred;           // [4][G][kTagRedWords] tagged reduction words (zeroed per launch)
 };
 
 struct BatchArgs {
@@ -1751,6 +1753,8 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
         a.max_iter = ba.max_iter;
         a.wait_budget = ba.wait_budget;
         a.pub = ws.pub;
+        a.tpub = ws.tpub;  // one-exchange sweeps and tagged reductions when the strips allow
+        a.tred = ws.tred;
         a.flags = ws.flags;
         a.red_part = ws.red_part;
         a.red_cnt = ws.red_cnt;
