@@ -1753,8 +1753,10 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
         a.max_iter = ba.max_iter;
         a.wait_budget = ba.wait_budget;
         a.pub = ws.pub;
-        a.tpub = ws.tpub;  // one-exchange sweeps and tagged reductions when the strips allow
-        a.tred = ws.tred;
+        // one-exchange sweeps and tagged reductions for wide teams; small teams (thick
+        // strips, little halo traffic) measured faster with the flag protocol
+        a.tpub = G >= 8 ? ws.tpub : nullptr;
+        a.tred = G >= 8 ? ws.tred : nullptr;
         a.flags = ws.flags;
         a.red_part = ws.red_part;
         a.red_cnt = ws.red_cnt;

@@ -203,6 +203,31 @@ def test_errors_are_reported():
             pit.pit_residual(ctx, U, U)
 
 
+def test_device_wait_timeout_is_reported_and_the_device_stays_usable():
+    # a wait budget of one poll: the first team wait that is not satisfied at once gives up,
+    # raises the abort flag for the other CTAs and the launch ends with PIT_ETIMEOUT (no
+    # fault, no hang); a fresh context on the same device then solves normally
+    p = W.random_problem(16, 64, 48, 4, W.BURGERS, with_bc=True)
+    for teams in (-1, 0):                       # per-stage launches (chain kernel) and the wavefront
+        opt = pit.pit_default_options()
+        opt.wait_budget = 1
+        opt.team_ctas = 8
+        opt.wave_teams = teams
+        with pit.context_for(p, opt) as ctx:
+            U = torch.empty(p.dof, dtype=torch.float64, device="cuda")
+            pit.pit_fill_plain_guess(ctx, U)
+            status, info = pit.pit_solve(ctx, U, check=False)
+            assert status == pit.PIT_ETIMEOUT, status
+            assert "budget" in pit.lib().pit_last_error(ctx.handle).decode()
+    Uo, _, _, _ = oracle.solve(p, tol=1e-13)
+    with pit.context_for(p) as ctx:
+        U = torch.empty(p.dof, dtype=torch.float64, device="cuda")
+        pit.pit_fill_plain_guess(ctx, U)
+        status, info = pit.pit_solve(ctx, U)
+        assert info["converged"]
+        assert np.abs(U.cpu().numpy().reshape(p.M, -1) - Uo).max() <= 1e-10 * np.abs(Uo).max()
+
+
 WAVE_CASES = [
     (lambda: W.heat32(1), "heat32s1"),
     (lambda: W.random_problem(31, 37, 45, 7, W.BURGERS, with_bc=True, with_q=True), "burg37x45"),
