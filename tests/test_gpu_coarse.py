@@ -98,3 +98,12 @@ def test_invalid_factors_are_rejected():
             assert st == pit.PIT_EINVAL
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("nx,ny,M,cf", [(3, 5, 2, 2), (5, 5, 3, 3), (7, 4, 9, 2)])
+def test_smallest_coarse_grids(nx, ny, M, cf):
+    # one coarse node in a direction, a single coarse level, ragged sizes
+    p = W.random_problem(40 + nx, nx, ny, M, W.BURGERS, with_bc=True, with_q=True)
+    U, info = _gpu_guess(p, cf)
+    Uo, _, _ = C.coarse_guess(p.grid, p.params, M, p.dt, p.u0, p.bc, p.q, cf=cf)
+    assert np.abs(U - Uo).max() <= 1e-10 * np.abs(Uo).max()

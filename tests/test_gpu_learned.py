@@ -113,3 +113,36 @@ def test_invalid_shapes_are_rejected():
         pit.pit_net_create(8, 8, 8, 16, 1)      # levels not a multiple of 16
     with pytest.raises(pit.PitError):
         pit.pit_net_create(8, 8, 16, 24, 1)     # channels not a multiple of 16
+
+
+@pytest.mark.parametrize("C,M,B,H,Wd", [(80, 144, 2, 5, 9), (16, 32, 3, 7, 130)])
+def test_multi_tile_convolutions_match_oracle(C, M, B, H, Wd):
+    # channel counts that split into several tensor-core tiles (80 input channels: 64 + 16;
+    # 144 levels: 128 + 16 output channels) and an image row longer than one 128-pixel segment
+    rng = np.random.default_rng(11)
+    shapes = CN.layer_shapes(C, 1, M)
+    theta = np.concatenate([np.concatenate([0.2 * rng.standard_normal(co * 9 * ci), 0.05 * rng.standard_normal(co)])
+                            for co, ci in shapes]).astype(np.float32)
+    u0 = rng.standard_normal((B, H * Wd))
+    lognu = rng.uniform(-3, -1, B).astype(np.float32)
+    target = rng.standard_normal((B, H, Wd, M)) * 0.5
+    net = pit.pit_net_create(H, Wd, M, C, 1, max_batch=B, seed=1)
+    pit.pit_net_set_params(net, theta)
+    params = CN.unflatten(theta.astype(np.float64), shapes)
+    inp = CN.net_input(_bf16_round(u0).reshape(B, H, Wd), _bf16_round(lognu))
+    with net:
+        U = torch.empty((B, M, H * Wd), dtype=torch.float64, device="cuda")
+        pit.pit_net_guess(net, torch.as_tensor(u0, device="cuda"), lognu, U)
+        corr = (U.cpu().numpy() - u0[:, None, :]).reshape(B, M, H, Wd).transpose(0, 2, 3, 1)
+        tgt = torch.as_tensor(target, dtype=torch.float32).to(torch.bfloat16).cuda().contiguous()
+        loss, g = pit.pit_net_gradients(net, torch.as_tensor(u0, device="cuda"), lognu, tgt)
+    ref = CN.forward(params, inp)
+    assert np.linalg.norm(corr - ref) / np.linalg.norm(ref) < 3e-2
+    lref, grads = CN.loss_and_grad(params, inp, tgt.float().cpu().numpy().astype(np.float64))
+    o = 0
+    for (Wr, br) in grads:
+        for ref_g in (Wr.ravel(), br.ravel()):
+            got = g[o:o + ref_g.size].astype(np.float64)
+            o += ref_g.size
+            cos = got @ ref_g / (np.linalg.norm(got) * np.linalg.norm(ref_g) + 1e-300)
+            assert cos > 0.995, cos

@@ -91,3 +91,28 @@ def test_product_form_loses_digits_past_the_condition_bound():
     err = np.abs(got - want).max(axis=1) / np.abs(want).max()
     assert err[0] <= 1e-12                # level 1 is a plain A_1 solve
     assert not (err[-1] <= 1e-6), err     # the last level has lost many digits (or overflowed)
+
+
+@pytest.mark.parametrize("seed,nx,ny,M", [(8, 7, 5, 1), (9, 1, 9, 3), (10, 9, 1, 4)])
+def test_product_form_edge_shapes(seed, nx, ny, M):
+    # M = 1 (P^1 = A_1: a plain level solve) and one-dimensional grids
+    p = W.random_problem(seed, nx, ny, M, W.BURGERS, with_bc=True, mu_a=0.01, mu_b=0.0, dt=1e-3)
+    U = _iterate(p, seed)
+    R = oracle.residual(p.grid, p.params, M, p.dt, p.u0, U, p.bc, p.q)
+    coef = oracle.jacobian(p.grid, p.params, M, p.dt, U, p.bc)
+    want = oracle.block_solve(nx, ny, M, coef, R)
+    got, info = _gpu_product(p, U, R)
+    assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+
+
+def test_newton_with_product_form_on_heat_with_sources():
+    # heat with Dirichlet data and sources, within the conditioning bound (small mu tau / h^2)
+    p = W.random_problem(12, 12, 10, 5, W.HEAT, with_bc=True, with_q=True, mu_a=0.05, mu_b=0.05, dt=1e-3)
+    Us, _ = oracle.sequential_bdf1(p.grid, p.params, p.M, p.dt, p.u0, p.bc, p.q)
+    with pit.context_for(p) as ctx:
+        U = torch.empty(p.dof, dtype=torch.float64, device="cuda")
+        pit.pit_fill_plain_guess(ctx, U)
+        st, info = pit.pit_solve_product(ctx, U)
+        Ug = U.cpu().numpy().reshape(p.M, -1)
+    assert info["converged"]
+    assert np.abs(Ug - Us).max() <= 1e-10 * np.abs(Us).max()
