@@ -17,7 +17,7 @@
 // Solve: every row of P^n and of r~^n is divided by the diagonal entry of P^n (the
 // diagonal preconditioner of Sec. 7), the result is scattered into a dense band of
 // half width n * nx and factored by banded LU without pivoting (the direct solver of
-// Sec. 8), one CTA per level, levels in parallel. The product's condition number grows
+// Sec. 8), a team of CTAs per level, levels in parallel. The product's condition number grows
 // like K^n with the per-level condition K (eq. 15): past the bound of eq. 15 the
 // computed du^n loses its digits, which is why the library's main path applies the
 // same inverse in nested form (eq. 7) instead.
@@ -152,57 +152,101 @@ __global__ void scatter_kernel(const double* __restrict__ Pall, const long long*
     }
 }
 
-// Banded LU without pivoting and the two triangular solves, one CTA per level:
+// Banded LU without pivoting and the two triangular solves of every level of a batch:
 // the rhs is overwritten by the solution, which goes to dU[n - 1].
-__global__ void __launch_bounds__(kLuThreads) band_lu_solve_kernel(double* __restrict__ band,
-                                                                   const long long* __restrict__ bbase,
-                                                                   double* __restrict__ rhs, double* __restrict__ dU,
-                                                                   double* __restrict__ min_pivot, int n0, int nx,
-                                                                   int ny) {
-    extern __shared__ double urow[];  // row k of U beyond the diagonal, b entries
+// Team version: G CTAs per level share the elimination. Rows are dealt out cyclically
+// (row k + 1 + t to CTA t mod G), every step ends with a team barrier (the pivot row and
+// rhs entry of the next step are then final), and the back substitution runs the same
+// way. Barriers are counters in global memory with bounded waits and an abort flag: a
+// time-out raises *status and ends every CTA of the launch.
+__device__ __forceinline__ unsigned long long lu_ld_acquire(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int lu_ld_acquire_s32(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ bool lu_team_sync(unsigned long long* cnt, unsigned long long target, int* abort,
+                                             int* status, long long budget, int* s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(cnt, 1ull);
+        int ok = 1;
+        long long spins = 0;
+        while (lu_ld_acquire(cnt) < target) {
+            if (lu_ld_acquire_s32(abort)) {
+                ok = 0;
+                break;
+            }
+            if (++spins > budget) {
+                atomicCAS(status, 0, 1);
+                atomicExch(abort, 1);
+                ok = 0;
+                break;
+            }
+            if (spins > 1024) __nanosleep(32);
+        }
+        __threadfence();
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+__global__ void __launch_bounds__(kLuThreads) band_lu_team_kernel(double* __restrict__ band,
+                                                                  const long long* __restrict__ bbase,
+                                                                  double* __restrict__ rhs, double* __restrict__ dU,
+                                                                  double* __restrict__ min_pivot, int n0, int nx,
+                                                                  int ny, int G, unsigned long long* cnt, int* abort,
+                                                                  int* status, long long budget) {
+    __shared__ int s_flag;
     const size_t Ns = (size_t)nx * ny;
-    const int n = n0 + blockIdx.x;
+    const int lvl = blockIdx.x / G, g = blockIdx.x - lvl * G;
+    const int n = n0 + lvl;
     const int b = n * nx;
     const size_t W = 2 * (size_t)b + 1;
-    double* B = band + bbase[blockIdx.x];
-    double* r = rhs + (size_t)blockIdx.x * Ns;
+    double* B = band + bbase[lvl];
+    double* r = rhs + (size_t)lvl * Ns;
+    unsigned long long* c = cnt + lvl;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    unsigned long long sync = 0;
     double pmin = INFINITY;
     for (size_t k = 0; k < Ns; ++k) {
+        const double* prow = B + k * W + b + 1;  // prow[jj] = B(k, k + 1 + jj)
         const double piv = B[k * W + b];
         const int span = (int)((size_t)b < Ns - 1 - k ? (size_t)b : Ns - 1 - k);
         if (threadIdx.x == 0) pmin = fmin(pmin, fabs(piv));
         const double inv = 1.0 / piv;
-        // multipliers l_i = B(i, k) / piv into column k; row k of U into shared memory
-        for (int t = threadIdx.x; t < span; t += blockDim.x) {
-            const size_t i = k + 1 + t;
-            B[i * W + (b - 1 - t)] *= inv;  // B(i, k): column offset k - i = -1 - t
-            urow[t] = B[k * W + b + 1 + t];  // B(k, k + 1 + t)
-        }
-        __syncthreads();
         const double rk = r[k];
-        for (int t = warp; t < span; t += nwarps) {
+        for (int t = g + warp * G; t < span; t += nwarps * G) {
             const size_t i = k + 1 + t;
-            double* row = B + i * W + (b - 1 - t);  // row[jj] = B(i, k + 1 + jj)
-            const double l = B[i * W + (b - 1 - t)];
-            for (int jj = lane; jj < span; jj += 32) row[jj + 1] = fma(-l, urow[jj], row[jj + 1]);
-            if (lane == 0) r[i] = fma(-l, rk, r[i]);
+            double* row = B + i * W + (b - 1 - t);  // row[0] = B(i, k), row[1 + jj] = B(i, k + 1 + jj)
+            const double l = row[0] * inv;
+            __syncwarp();
+            for (int jj = lane; jj < span; jj += 32) row[jj + 1] = fma(-l, prow[jj], row[jj + 1]);
+            if (lane == 0) {
+                row[0] = l;
+                r[i] = fma(-l, rk, r[i]);
+            }
         }
-        __syncthreads();
+        if (!lu_team_sync(c, (unsigned long long)G * ++sync, abort, status, budget, &s_flag)) return;
     }
     // back substitution U x = y
     for (size_t kk = Ns; kk-- > 0;) {
         const double xk = r[kk] / B[kk * W + b];
         const int span = (int)((size_t)b < kk ? (size_t)b : kk);
-        __syncthreads();
-        for (int t = threadIdx.x; t < span; t += blockDim.x) {
+        for (int t = g + (int)threadIdx.x * G; t < span; t += (int)blockDim.x * G) {
             const size_t i = kk - 1 - t;
             r[i] = fma(-B[i * W + (b + 1 + t)], xk, r[i]);  // B(i, kk): column offset kk - i = 1 + t
         }
-        if (threadIdx.x == 0) dU[(size_t)(n - 1) * Ns + kk] = xk;
-        __syncthreads();
+        if (g == 0 && threadIdx.x == 0) dU[(size_t)(n - 1) * Ns + kk] = xk;
+        if (!lu_team_sync(c, (unsigned long long)G * ++sync, abort, status, budget, &s_flag)) return;
     }
-    if (threadIdx.x == 0) min_pivot[n - 1] = pmin;
+    if (g == 0 && threadIdx.x == 0) min_pivot[n - 1] = pmin;
 }
 
 __global__ void axpy_kernel(double* __restrict__ U, const double* __restrict__ dU, size_t N, double* sumsq) {
@@ -233,13 +277,16 @@ struct ProductWs {
     long long* d_bbase = nullptr;   // per batch slot
     double* rhs = nullptr;          // [batch][Ns]
     double* pmin = nullptr;         // [M]
+    unsigned long long* lu_cnt = nullptr;  // [batch] team barrier counters of the LU launch
+    int* lu_flags = nullptr;        // [2] abort, status
+    int lu_G = 1;                   // CTAs per level in the LU launch
     int batch = 0;
     size_t band_doubles = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 
     ~ProductWs() {
         for (void* p : {(void*)P, (void*)rt, (void*)coef, (void*)d_pbase, (void*)band, (void*)d_bbase, (void*)rhs,
-                        (void*)pmin})
+                        (void*)pmin, (void*)lu_cnt, (void*)lu_flags})
             cudaFree(p);
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
@@ -286,6 +333,13 @@ pit_status ws_init(pit_ctx* ctx, const PitProblemView& v, ProductWs& w) {
     if (e == cudaSuccess) e = al((void**)&w.d_bbase, sizeof(long long) * w.batch);
     if (e == cudaSuccess) e = al((void**)&w.rhs, sizeof(double) * w.batch * w.Ns);
     if (e == cudaSuccess) e = al((void**)&w.pmin, sizeof(double) * w.M);
+    if (e == cudaSuccess) e = al((void**)&w.lu_cnt, sizeof(unsigned long long) * w.batch);
+    if (e == cudaSuccess) e = al((void**)&w.lu_flags, sizeof(int) * 2);
+    {   // CTAs per level: the batch's levels side by side on (about) one CTA per SM each
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            w.lu_G = std::max(1, std::min(32, (sms - 4) / std::max(1, w.batch)));
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(w.d_pbase, w.pbase.data(), sizeof(long long) * (w.M + 2), cudaMemcpyHostToDevice,
                             v.stream);
@@ -340,17 +394,27 @@ pit_status product_solve(pit_ctx* ctx, const PitProblemView& v, ProductWs& w, co
         if (e != cudaSuccess) break;
         scatter_kernel<<<dim3(std::min<unsigned>(grid_for(Ns), 64u), count), kT, 0, st>>>(
             w.P, w.d_pbase, w.rt, w.band, w.d_bbase, w.rhs, n0, w.nx, w.ny);
-        const size_t smem = sizeof(double) * std::max(1, hi * w.nx);
-        {  // the limit is shared by all callers of the kernel: only ever raise it
-            cudaFuncAttributes fa;
-            e = cudaFuncGetAttributes(&fa, band_lu_solve_kernel);
-            if (e == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < smem)
-                e = cudaFuncSetAttribute(band_lu_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.lu_cnt, 0, sizeof(unsigned long long) * count, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.lu_flags, 0, sizeof(int) * 2, st);
         if (e != cudaSuccess) break;
-        band_lu_solve_kernel<<<count, kLuThreads, smem, st>>>(w.band, w.d_bbase, w.rhs, dU, w.pmin, n0, w.nx, w.ny);
-        e = cudaGetLastError();
+        {
+            int G = w.lu_G;
+            const long long budget = v.opt.wait_budget;
+            int* abort_flag = w.lu_flags;
+            int* status = w.lu_flags + 1;
+            void* args[] = {&w.band, &w.d_bbase, &w.rhs, &dU, &w.pmin, (void*)&n0, &w.nx, &w.ny, &G, &w.lu_cnt,
+                            &abort_flag, &status, (void*)&budget};
+            e = cudaLaunchCooperativeKernel((const void*)band_lu_team_kernel, dim3(count * G), dim3(kLuThreads), args, 0,
+                                            st);
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // bbase is a host temporary reused by the next batch
+        if (e == cudaSuccess) {
+            int fl[2] = {0, 0};
+            e = cudaMemcpy(fl, w.lu_flags, sizeof(fl), cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && fl[1])
+                return pit_internal_fail(ctx, PIT_ETIMEOUT, "product form: a team barrier of the LU ran out of budget");
+        }
         hi = n0 - 1;
     }
     if (e == cudaSuccess) e = cudaEventRecord(w.ev[3], st);
