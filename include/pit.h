@@ -110,6 +110,11 @@ typedef struct {
                                diverges (residual not finite or above 1e10) or does not converge
                                is halved and restarted from the plain guess, and grows back
                                after a success */
+    int batch_solo_nodes;   /* pit_batch_create: a problem with nx*ny >= batch_solo_nodes is solved on
+                               its own by the wavefront path of pit_solve (several Newton iterations
+                               in flight on the whole GPU), one such problem after another; the rest
+                               share the persistent launch. <= 0 = every problem in the persistent
+                               launch (default 65536, a 256 x 256 grid) */
 } pit_options;
 
 enum { PIT_FP64 = 0, PIT_FP32_INNER = 1 };
@@ -146,6 +151,7 @@ typedef struct {
     float us_setup;                        /* first CTA of team 0: forming level systems (residual, Jacobian) */
     float us_level_solve;                  /* first CTA of team 0: level solves (includes halo/reduction waits) */
     float us_update;                       /* first CTA of team 0: iterate updates and progress publication */
+    int windows_converged;                 /* windows whose Newton reached tol_res (windows minus restarts) */
 } pit_solve_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -233,17 +239,22 @@ pit_status pit_solve_host(pit_ctx* ctx, const double* u0_host, double* U_host, p
 
 /* ----------------------------------------------------------- batched solves
  * Many independent problems (grids, level counts, closures and viscosities may
- * all differ) solved in ONE persistent cooperative launch. Each problem is solved
- * by a team of CTAs (the level chain of eq. 7 with Newton iterations until its
- * residual is <= tol_res, in windows of opt->window levels, default 32); teams of
- * different sizes run side by side on the GPU. pit_batch_create picks every
- * problem's team size with an autotuner (short timed runs of each distinct grid
- * size at candidate team sizes; opt->team_ctas > 0 fixes it instead) and
- * list-schedules the teams over the SMs, longest first. pit_batch_solve replays
- * the launch as a captured CUDA graph after its first call; the batch works on a
- * stream of its own, ordered after the caller's `stream` at every solve, and
- * returns when the solve is complete. Level solves follow opt->precision
- * (PIT_FP32_INNER is the intended use). */
+ * all differ). Problems on grids of at least opt->batch_solo_nodes nodes are
+ * solved one after another, each alone on the GPU by the wavefront path of
+ * pit_solve (windows of opt->window levels); the batch holds a context for each
+ * (about 56 bytes per unknown; a problem whose context does not fit in memory
+ * joins the persistent launch instead). All other problems are solved in ONE
+ * persistent cooperative launch: each by a team of CTAs (the level chain of eq. 7
+ * with Newton iterations until its residual is <= tol_res, in windows of
+ * opt->window levels, default 32); teams of different sizes run side by side on
+ * the GPU. pit_batch_create picks every packed problem's team size with an
+ * autotuner (short timed runs of each distinct grid size at candidate team sizes;
+ * opt->team_ctas > 0 fixes it instead) and list-schedules the teams over the
+ * SMs, longest first. pit_batch_solve replays that launch as a captured CUDA
+ * graph after its first call; the batch works on a stream of its own, ordered
+ * after the caller's `stream` at every solve, and returns when the solve is
+ * complete. Level solves follow opt->precision (PIT_FP32_INNER is the intended
+ * use). */
 typedef struct pit_batch pit_batch;
 
 typedef struct {
@@ -265,18 +276,29 @@ typedef struct {
     int min_team, max_team; /* team sizes chosen */
     int converged;          /* problems whose final ||R||_inf <= tol_res */
     int graph;              /* 1 when the launch was replayed from a CUDA graph */
-    double ms;              /* device time of the launch */
+    double ms;              /* time of the whole solve on the batch's stream (solo problems and the
+                               persistent launch, with the gaps between the solo windows) */
     double est_makespan_ms; /* the schedule's estimate from the autotuner's timings */
-    double ms_tuning;       /* host time spent in pit_batch_create's autotuner */
+    double ms_tuning;       /* host time spent in pit_batch_create (contexts and autotuner) */
+    int solo;               /* problems solved alone by the wavefront path */
+    double ms_solo;         /* their time, summed */
+    double ms_packed;       /* time of the persistent launch (0 when every problem is solo) */
 } pit_batch_info;
 
 pit_status pit_batch_create(const pit_instance* inst, int count, const pit_options* opt, void* stream,
                             pit_batch** out);
 pit_status pit_batch_solve(pit_batch* batch, pit_batch_info* info);
 /* Results of problem i after pit_batch_solve: final ||R||_inf of U (FP64), Newton
- * updates summed over windows, and the number of windows that converged. */
+ * updates summed over windows, the number of windows that converged, and the CTAs
+ * of the team that solved it (per Newton iteration in flight for a solo problem;
+ * see pit_batch_placement). */
 pit_status pit_batch_result(const pit_batch* batch, int i, double* res_inf, int* newton_iters, int* windows_converged,
                             int* team_ctas);
+/* Where problem i runs: *solo = 1 for the wavefront path, with *teams Newton
+ * iterations in flight of *team_ctas CTAs each (*teams = 0 when the context fell
+ * back to one launch per stage); *solo = 0 for the persistent launch, one team of
+ * *team_ctas CTAs (*teams = 1). Any pointer may be NULL. */
+pit_status pit_batch_placement(const pit_batch* batch, int i, int* solo, int* teams, int* team_ctas);
 const char* pit_batch_last_error(const pit_batch* batch);
 void pit_batch_destroy(pit_batch* batch);
 

@@ -139,6 +139,7 @@ extern "C" void pit_default_options(pit_options* o) {
     o->wave_teams = 0;
     o->precision = PIT_FP64;
     o->window = 0;
+    o->batch_solo_nodes = 65536;
 }
 
 extern "C" const char* pit_status_string(pit_status s) {
@@ -557,6 +558,8 @@ void pit_internal_view(const pit_ctx* ctx, PitProblemView* v) {
     v->bc = ctx->has_bc ? ctx->bc : nullptr;
     v->q = ctx->has_q ? ctx->q : nullptr;
     v->stream = ctx->stream;
+    v->wave_teams = ctx->K;
+    v->wave_team_ctas = ctx->Gw;
 }
 
 pit_status pit_internal_fail(pit_ctx* ctx, pit_status s, const char* fmt, ...) {
@@ -802,6 +805,7 @@ static pit_status solve_wave(pit_ctx* ctx, double* U_dev, pit_solve_info* inf) {
         inf->newton_iters_total += iters;
         inf->newton_iters = std::max(inf->newton_iters, iters);
         if (st == PIT_OK) {
+            inf->windows_converged += 1;
             s += Mw;
             w = std::min(Wn, 2 * w);
         } else if ((st == PIT_ENOCONV || st == PIT_EDIVERGED) && Mw > 1) {
@@ -878,6 +882,9 @@ extern "C" pit_status pit_solve(pit_ctx* ctx, double* U_dev, pit_solve_info* inf
         if (st == PIT_ENOCONV) st = PIT_OK;  // a capped level solve: Newton carries on
         if (st != PIT_OK) break;
     }
+    inf->windows = 1;
+    inf->windows_converged = inf->converged;
+    inf->newton_iters_total = inf->newton_iters;
     CK(cudaEventRecord(t1, ctx->stream));
     CK(cudaEventSynchronize(t1));
     float ms = 0.f;

@@ -1,11 +1,16 @@
-// pit_batch.cu -- many independent problems in one persistent cooperative launch.
+// pit_batch.cu -- many independent problems: large grids one after another through
+// the wavefront path, the rest in one persistent cooperative launch.
 //
-// Each problem gets a team of CTAs that runs the level chain (nested block inverse
-// of eq. 7) with Newton iterations per window of levels until the window's residual
-// is below tol_res, then a final FP64 residual pass (batch_kernel in pit_kernels.cuh).
-// Here: the autotuner that picks a team size per problem from short timed runs, the
-// list schedule that places the teams on the SMs, the workspace pools, and the
-// launch, which is captured once into a CUDA graph and replayed.
+// A large problem fills the GPU by itself: the wavefront kernel keeps several Newton
+// iterations of it in flight, which a single team of the persistent launch cannot.
+// Each such problem gets a context of its own and is solved by pit_solve in windows.
+// In the persistent launch each problem gets a team of CTAs that runs the level chain
+// (nested block inverse of eq. 7) with Newton iterations per window of levels until
+// the window's residual is below tol_res, then a final FP64 residual pass
+// (batch_kernel in pit_kernels.cuh). Here: the routing, the autotuner that picks a
+// team size per packed problem from short timed runs, the list schedule that places
+// the teams on the SMs, the workspace pools, and the launch, which is captured once
+// into a CUDA graph and replayed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,6 +24,7 @@
 #include <vector>
 
 #include "pit.h"
+#include "pit_internal.h"
 #include "pit_kernels.cuh"
 
 using namespace pit;
@@ -38,7 +44,18 @@ struct pit_batch {
     size_t dyn_max = 0;
     bool fp32 = false;
     std::vector<pit_instance> in;
-    std::vector<int> team_of;          // team size per problem
+    std::vector<int> team_of;          // team size per problem (CTAs per wavefront team when solo)
+    // problems solved alone by the wavefront path
+    std::vector<int> solo_of;          // per problem: index into the solo lists, or -1
+    std::vector<int> solo_idx;         // problem of each solo entry
+    std::vector<pit_ctx*> solo_ctx;
+    std::vector<int> solo_K;           // Newton iterations in flight (0: per-stage launches)
+    std::vector<double> solo_res;      // results of the last solve
+    std::vector<int> solo_iters, solo_wconv;
+    std::vector<int> packed_idx;       // problems of the persistent launch
+    double* d_scratch = nullptr;       // residual scratch for a solo problem that stopped early
+    size_t scratch_n = 0;
+    cudaEvent_t ea = nullptr, eb = nullptr;  // around a whole solve
     // device data
     BatchInstance* d_inst = nullptr;
     BatchJob* d_jobs = nullptr;
@@ -121,10 +138,11 @@ struct Job {
     std::vector<int> ctas;
 };
 
-// Build jobs, workspace and device descriptors for team sizes `team` (per problem)
-// and problems `which` (calibration runs use a subset with truncated levels).
+// Build jobs, workspace and device descriptors for problems `in` with team sizes
+// `team`; problem i reports into result slot gid[i] (calibration runs use one
+// problem with truncated levels and slot 0).
 static pit_status build_launch(pit_batch* b, const std::vector<pit_instance>& in, const std::vector<int>& team,
-                               const std::vector<double>& cost) {
+                               const std::vector<double>& cost, const std::vector<int>& gid) {
     const int n = (int)in.size();
     const int P = b->num_sms;
     // list schedule, longest first: each team takes the G CTAs that free up earliest
@@ -228,9 +246,9 @@ static pit_status build_launch(pit_batch* b, const std::vector<pit_instance>& in
         bi[i].bc = I.bc_dev;
         bi[i].q = I.q_dev;
         bi[i].U = I.U_dev;
-        bi[i].res_inf = b->d_res + i;
-        bi[i].newton_iters = b->d_iters + i;
-        bi[i].converged_windows = b->d_iters + b->count + i;
+        bi[i].res_inf = b->d_res + gid[i];
+        bi[i].newton_iters = b->d_iters + gid[i];
+        bi[i].converged_windows = b->d_iters + b->count + gid[i];
         smem = std::max(smem, team_smem(b->fp32, I.grid.nx, I.grid.ny, team[i]));
     }
     b->smem = smem;
@@ -349,35 +367,73 @@ extern "C" pit_status pit_batch_create(const pit_instance* inst, int count, cons
         BCK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
         BCK(cudaEventRecord(b->ev_user, b->user_stream));
         BCK(cudaStreamWaitEvent(b->stream, b->ev_user, 0));
-        // smallest team whose strips fit in shared memory, per problem
-        std::vector<int> gmin(count);
+        BCK(cudaEventCreate(&b->ea));
+        BCK(cudaEventCreate(&b->eb));
+        // routing: a large grid is solved alone through the wavefront path when its
+        // context can be created (memory); everything else joins the persistent launch
+        b->solo_of.assign(count, -1);
+        b->team_of.assign(count, 0);
         for (int i = 0; i < count; ++i) {
             const pit_instance& I = inst[i];
+            const long long nodes = (long long)I.grid.nx * I.grid.ny;
+            bool solo = b->opt.batch_solo_nodes > 0 && nodes >= b->opt.batch_solo_nodes;
+            if (solo) {
+                pit_options so = b->opt;
+                so.team_ctas = 0;  // the wavefront picks its own team size
+                pit_ctx* ctx = nullptr;
+                if (pit_create(&I.grid, I.M, I.dt, &I.params, &so, b->stream, &ctx) != PIT_OK) {
+                    cudaGetLastError();  // e.g. out of memory: the persistent launch takes it
+                    solo = false;
+                } else {
+                    PitProblemView v;
+                    pit_internal_view(ctx, &v);
+                    b->solo_of[i] = (int)b->solo_ctx.size();
+                    b->solo_idx.push_back(i);
+                    b->solo_ctx.push_back(ctx);
+                    b->solo_K.push_back(v.wave_teams);
+                    b->team_of[i] = v.wave_team_ctas;
+                }
+            }
+            if (!solo) b->packed_idx.push_back(i);
+        }
+        const size_t ns = b->solo_ctx.size();
+        b->solo_res.assign(ns, 0.0);
+        b->solo_iters.assign(ns, 0);
+        b->solo_wconv.assign(ns, 0);
+        const int np = (int)b->packed_idx.size();
+        if (np == 0) return PIT_OK;
+        std::vector<pit_instance> pk(np);
+        for (int j = 0; j < np; ++j) pk[j] = inst[b->packed_idx[j]];
+        // smallest team whose strips fit in shared memory, per packed problem
+        std::vector<int> gmin(np);
+        for (int j = 0; j < np; ++j) {
+            const pit_instance& I = pk[j];
             int g = 1;
             while (g <= std::min(I.grid.ny, kMaxTeam) && team_smem(b->fp32, I.grid.nx, I.grid.ny, g) > b->dyn_max) ++g;
             if (g > std::min(I.grid.ny, std::min(kMaxTeam, b->num_sms)))
-                return bfail(b, PIT_EUNSUPPORTED, "problem %d: a level strip does not fit in shared memory", i);
-            gmin[i] = g;
+                return bfail(b, PIT_EUNSUPPORTED, "problem %d: a level strip does not fit in shared memory",
+                             b->packed_idx[j]);
+            gmin[j] = g;
         }
-        std::vector<int> team(count);
-        std::vector<double> cost(count, 1.0);
+        std::vector<int> team(np);
+        std::vector<double> cost(np, 1.0);
         if (b->opt.team_ctas > 0) {
-            for (int i = 0; i < count; ++i)
-                team[i] = std::max(gmin[i], std::min({b->opt.team_ctas, inst[i].grid.ny, b->num_sms}));
-            for (int i = 0; i < count; ++i) cost[i] = (double)inst[i].M * inst[i].grid.nx * inst[i].grid.ny / team[i];
+            for (int j = 0; j < np; ++j)
+                team[j] = std::max(gmin[j], std::min({b->opt.team_ctas, pk[j].grid.ny, b->num_sms}));
+            for (int j = 0; j < np; ++j) cost[j] = (double)pk[j].M * pk[j].grid.nx * pk[j].grid.ny / team[j];
         } else {
             // autotuner: per distinct grid, time candidate team sizes on the first problem of
             // that grid truncated to a few levels; per-level time t(G) -> cost = t(G) * M
             std::map<std::pair<int, int>, int> rep;
-            for (int i = 0; i < count; ++i) rep.emplace(std::make_pair(inst[i].grid.nx, inst[i].grid.ny), i);
+            for (int j = 0; j < np; ++j) rep.emplace(std::make_pair(pk[j].grid.nx, pk[j].grid.ny), j);
             std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> table;
             for (auto& kv : rep) {
-                const int i = kv.second;
-                const pit_instance& I = inst[i];
+                const int j = kv.second;
+                const pit_instance& I = pk[j];
                 std::vector<int> cands;
                 const int gmax = std::min({I.grid.ny, kMaxTeam, b->num_sms});
                 for (double f : {1.0, 1.5, 2.0, 3.0, 4.0, 6.0}) {
-                    const int g = std::min(gmax, std::max(gmin[i], (int)std::lround(gmin[i] * f)));
+                    const int g = std::min(gmax, std::max(gmin[j], (int)std::lround(gmin[j] * f)));
                     if (std::find(cands.begin(), cands.end(), g) == cands.end()) cands.push_back(g);
                 }
                 pit_instance cal = I;
@@ -385,7 +441,7 @@ extern "C" pit_status pit_batch_create(const pit_instance* inst, int count, cons
                 for (int g : cands) {
                     std::vector<pit_instance> one{cal};
                     double best = 1e300;
-                    BRET(build_launch(b, one, std::vector<int>{g}, std::vector<double>{1.0}));
+                    BRET(build_launch(b, one, std::vector<int>{g}, std::vector<double>{1.0}, std::vector<int>{0}));
                     // results land in slot 0 of the real arrays; harmless before the real solve
                     for (int rep2 = 0; rep2 < 2; ++rep2) {
                         double ms = 0.0;
@@ -397,34 +453,34 @@ extern "C" pit_status pit_batch_create(const pit_instance* inst, int count, cons
             }
             // per problem: the team size with the least SM time (t * G), then give the
             // longest problems more CTAs while they bound the makespan
-            for (int i = 0; i < count; ++i) {
-                const auto& tb = table[std::make_pair(inst[i].grid.nx, inst[i].grid.ny)];
+            for (int j = 0; j < np; ++j) {
+                const auto& tb = table[std::make_pair(pk[j].grid.nx, pk[j].grid.ny)];
                 double bestv = 1e300;
                 for (auto& e : tb) {
                     if (e.second * e.first < bestv) {
                         bestv = e.second * e.first;
-                        team[i] = e.first;
-                        cost[i] = e.second * inst[i].M;
+                        team[j] = e.first;
+                        cost[j] = e.second * pk[j].M;
                     }
                 }
             }
             for (int round = 0; round < 64; ++round) {
                 double total = 0.0, worst = 0.0;
                 int wi = 0;
-                for (int i = 0; i < count; ++i) {
-                    total += cost[i] * team[i];
-                    if (cost[i] > worst) {
-                        worst = cost[i];
-                        wi = i;
+                for (int j = 0; j < np; ++j) {
+                    total += cost[j] * team[j];
+                    if (cost[j] > worst) {
+                        worst = cost[j];
+                        wi = j;
                     }
                 }
                 if (worst <= total / b->num_sms) break;
-                const auto& tb = table[std::make_pair(inst[wi].grid.nx, inst[wi].grid.ny)];
+                const auto& tb = table[std::make_pair(pk[wi].grid.nx, pk[wi].grid.ny)];
                 bool grew = false;
                 for (auto& e : tb) {
-                    if (e.first > team[wi] && e.second * inst[wi].M < cost[wi]) {
+                    if (e.first > team[wi] && e.second * pk[wi].M < cost[wi]) {
                         team[wi] = e.first;
-                        cost[wi] = e.second * inst[wi].M;
+                        cost[wi] = e.second * pk[wi].M;
                         grew = true;
                         break;
                     }
@@ -432,8 +488,8 @@ extern "C" pit_status pit_batch_create(const pit_instance* inst, int count, cons
                 if (!grew) break;
             }
         }
-        b->team_of = team;
-        BRET(build_launch(b, b->in, team, cost));
+        for (int j = 0; j < np; ++j) b->team_of[b->packed_idx[j]] = team[j];
+        BRET(build_launch(b, pk, team, cost, b->packed_idx));
         return PIT_OK;
     };
     pit_status st = setup();
@@ -447,13 +503,44 @@ extern "C" pit_status pit_batch_create(const pit_instance* inst, int count, cons
     return PIT_OK;
 }
 
-extern "C" pit_status pit_batch_solve(pit_batch* b, pit_batch_info* info) {
-    if (!b) return PIT_EINVAL;
-    double ms = 0.0;
-    bool used_graph = false;
-    // the caller's stream may hold the producers of the problems' data
-    BCK(cudaEventRecord(b->ev_user, b->user_stream));
-    BCK(cudaStreamWaitEvent(b->stream, b->ev_user, 0));
+// Problem solo_idx[j] alone through the wavefront path (fresh data, plain guess, then
+// pit_solve in windows). A problem that does not converge is recorded, as in the
+// persistent launch; a device wait that ran out or a non-finite residual fails the batch.
+static pit_status solve_solo(pit_batch* b, size_t j) {
+    const int i = b->solo_idx[j];
+    pit_ctx* ctx = b->solo_ctx[j];
+    const pit_instance& I = b->in[i];
+    pit_status s = pit_set_data(ctx, I.u0_dev, I.bc_dev, I.q_dev);
+    if (s == PIT_OK) s = pit_fill_plain_guess(ctx, I.U_dev);
+    if (s != PIT_OK) return bfail(b, s, "problem %d: %s", i, pit_last_error(ctx));
+    pit_solve_info inf;
+    s = pit_solve(ctx, I.U_dev, &inf);
+    if (s == PIT_ETIMEOUT) return bfail(b, s, "problem %d (wavefront): a device wait ran out of budget", i);
+    if (s == PIT_EDIVERGED) return bfail(b, s, "problem %d (wavefront): NaN/Inf in a residual or solve", i);
+    if (s != PIT_OK && s != PIT_ENOCONV) return bfail(b, s, "problem %d: %s", i, pit_last_error(ctx));
+    double res = inf.res_inf[inf.newton_iters];
+    if (s == PIT_ENOCONV) {
+        // a window of one level may have stopped the solve before the final residual:
+        // take it over all levels
+        const size_t dof = (size_t)I.M * I.grid.nx * I.grid.ny;
+        if (b->scratch_n < dof) {
+            cudaFree(b->d_scratch);
+            b->d_scratch = nullptr;
+            b->scratch_n = 0;
+            BCK(cudaMalloc(&b->d_scratch, sizeof(double) * dof));
+            b->scratch_n = dof;
+        }
+        s = pit_residual(ctx, I.U_dev, b->d_scratch, &res);
+        if (s != PIT_OK) return bfail(b, s, "problem %d: %s", i, pit_last_error(ctx));
+    }
+    b->solo_res[j] = res;
+    b->solo_iters[j] = inf.newton_iters_total;
+    b->solo_wconv[j] = inf.windows_converged;
+    return PIT_OK;
+}
+
+// The persistent launch of the packed problems (graph replay after the first call).
+static pit_status solve_packed(pit_batch* b, bool* used_graph) {
     if (b->graph_ok && !b->exec) {
         // capture the launch sequence once
         cudaStreamCaptureStatus cs;
@@ -481,14 +568,47 @@ extern "C" pit_status pit_batch_solve(pit_batch* b, pit_batch_info* info) {
         BCK(cudaGraphLaunch(b->exec, b->stream));
         BCK(cudaEventRecord(b->e1, b->stream));
         BCK(cudaStreamSynchronize(b->stream));
-        float f = 0.f;
-        BCK(cudaEventElapsedTime(&f, b->e0, b->e1));
-        ms = f;
-        used_graph = true;
+        *used_graph = true;
         if (b->h_ctl[1] == ST_ETIMEOUT) return bfail(b, PIT_ETIMEOUT, "batch kernel: a device wait ran out of budget");
         if (b->h_ctl[1] == ST_EDIVERGED) return bfail(b, PIT_EDIVERGED, "batch kernel: NaN/Inf in a problem");
-    } else {
-        BRET(run_direct(b, &ms));
+        return PIT_OK;
+    }
+    double ms = 0.0;
+    return run_direct(b, &ms);
+}
+
+extern "C" pit_status pit_batch_solve(pit_batch* b, pit_batch_info* info) {
+    if (!b) return PIT_EINVAL;
+    bool used_graph = false;
+    // the caller's stream may hold the producers of the problems' data
+    BCK(cudaEventRecord(b->ev_user, b->user_stream));
+    BCK(cudaStreamWaitEvent(b->stream, b->ev_user, 0));
+    BCK(cudaEventRecord(b->ea, b->stream));
+    double ms_solo = 0.0, ms_packed = 0.0;
+    for (size_t j = 0; j < b->solo_ctx.size(); ++j) {
+        BCK(cudaEventRecord(b->e0, b->stream));
+        BRET(solve_solo(b, j));
+        BCK(cudaEventRecord(b->e1, b->stream));
+        BCK(cudaEventSynchronize(b->e1));
+        float f = 0.f;
+        BCK(cudaEventElapsedTime(&f, b->e0, b->e1));
+        ms_solo += f;
+    }
+    if (!b->packed_idx.empty()) {
+        BRET(solve_packed(b, &used_graph));
+        float f = 0.f;
+        BCK(cudaEventElapsedTime(&f, b->e0, b->e1));
+        ms_packed = f;
+    }
+    BCK(cudaEventRecord(b->eb, b->stream));
+    BCK(cudaEventSynchronize(b->eb));
+    float fall = 0.f;
+    BCK(cudaEventElapsedTime(&fall, b->ea, b->eb));
+    for (size_t j = 0; j < b->solo_idx.size(); ++j) {
+        const int i = b->solo_idx[j];
+        b->h_res[i] = b->solo_res[j];
+        b->h_iters[i] = b->solo_iters[j];
+        b->h_iters[b->count + i] = b->solo_wconv[j];
     }
     int conv = 0;
     for (int i = 0; i < b->count; ++i) conv += (b->h_res[i] <= b->opt.tol_res);
@@ -500,9 +620,12 @@ extern "C" pit_status pit_batch_solve(pit_batch* b, pit_batch_info* info) {
         info->max_team = b->max_team;
         info->converged = conv;
         info->graph = used_graph ? 1 : 0;
-        info->ms = ms;
+        info->ms = fall;
         info->est_makespan_ms = b->est_ms;
         info->ms_tuning = b->ms_tuning;
+        info->solo = (int)b->solo_idx.size();
+        info->ms_solo = ms_solo;
+        info->ms_packed = ms_packed;
     }
     if (conv < b->count) return bfail(b, PIT_ENOCONV, "%d of %d problems did not reach tol_res", b->count - conv, b->count);
     return PIT_OK;
@@ -518,10 +641,23 @@ extern "C" pit_status pit_batch_result(const pit_batch* b, int i, double* res_in
     return PIT_OK;
 }
 
+extern "C" pit_status pit_batch_placement(const pit_batch* b, int i, int* solo, int* teams, int* team_ctas) {
+    if (!b || i < 0 || i >= b->count) return PIT_EINVAL;
+    const int j = b->solo_of.empty() ? -1 : b->solo_of[i];
+    if (solo) *solo = j >= 0;
+    if (teams) *teams = j >= 0 ? b->solo_K[j] : 1;
+    if (team_ctas) *team_ctas = b->team_of.empty() ? 0 : b->team_of[i];
+    return PIT_OK;
+}
+
 extern "C" const char* pit_batch_last_error(const pit_batch* b) { return b ? b->err : "null batch"; }
 
 extern "C" void pit_batch_destroy(pit_batch* b) {
     if (!b) return;
+    for (pit_ctx* c : b->solo_ctx) pit_destroy(c);
+    cudaFree(b->d_scratch);
+    if (b->ea) cudaEventDestroy(b->ea);
+    if (b->eb) cudaEventDestroy(b->eb);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     cudaFree(b->d_inst);

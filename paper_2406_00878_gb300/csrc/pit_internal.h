@@ -15,6 +15,8 @@ struct PitProblemView {
     const double* bc;  // [M][2nx+2ny] device, or nullptr for zero Dirichlet data
     const double* q;   // [M][Ns] device, or nullptr for no source
     cudaStream_t stream;
+    int wave_teams;      // Newton iterations in flight in pit_solve's wavefront (0: per-stage launches)
+    int wave_team_ctas;  // CTAs per wavefront team
 };
 
 __attribute__((visibility("hidden"))) void pit_internal_view(const pit_ctx* ctx, PitProblemView* v);

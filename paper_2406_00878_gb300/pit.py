@@ -28,7 +28,7 @@ PIT_NOALLOC_MAX_NX, PIT_NOALLOC_MAX_TEAM, PIT_NOALLOC_MAX_LEVELS = 512, 160, 409
 EXPORTS = ("pit_default_options", "pit_create", "pit_set_data", "pit_fill_plain_guess", "pit_coarse_guess",
            "pit_residual", "pit_assemble", "pit_block_solve", "pit_newton_step", "pit_solve", "pit_solve_host",
            "pit_last_error", "pit_status_string", "pit_destroy", "pit_block_solve_noalloc", "pit_batch_create",
-           "pit_batch_solve", "pit_batch_result", "pit_batch_last_error", "pit_batch_destroy", "pit_net_param_count",
+           "pit_batch_solve", "pit_batch_result", "pit_batch_placement", "pit_batch_last_error", "pit_batch_destroy", "pit_net_param_count",
            "pit_net_create", "pit_net_get_params", "pit_net_set_params", "pit_net_guess", "pit_net_make_target",
            "pit_net_gradients", "pit_net_train_step", "pit_net_last_error", "pit_net_destroy",
            "pit_product_form_solve", "pit_solve_product")
@@ -48,7 +48,7 @@ class pit_options(ctypes.Structure):
                 ("eta_max", ctypes.c_double), ("eta_gamma", ctypes.c_double), ("lin_atol", ctypes.c_double),
                 ("lin_max_iter", ctypes.c_int), ("sor_rho_max", ctypes.c_double), ("team_ctas", ctypes.c_int),
                 ("wait_budget", ctypes.c_longlong), ("wave_teams", ctypes.c_int), ("precision", ctypes.c_int),
-                ("window", ctypes.c_int)]
+                ("window", ctypes.c_int), ("batch_solo_nodes", ctypes.c_int)]
 
 
 class pit_step_info(ctypes.Structure):
@@ -68,7 +68,7 @@ class pit_solve_info(ctypes.Structure):
                 ("wave_launches", ctypes.c_int), ("ms_wave", ctypes.c_float), ("us_pred_wait", ctypes.c_float),
                 ("us_halo_wait", ctypes.c_float), ("us_reduce_wait", ctypes.c_float), ("windows", ctypes.c_int),
                 ("newton_iters_total", ctypes.c_int), ("us_setup", ctypes.c_float), ("us_level_solve", ctypes.c_float),
-                ("us_update", ctypes.c_float)]
+                ("us_update", ctypes.c_float), ("windows_converged", ctypes.c_int)]
 
     def as_dict(self):
         k = self.newton_iters
@@ -90,7 +90,8 @@ class pit_instance(ctypes.Structure):
 class pit_batch_info(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int), ("ctas", ctypes.c_int), ("teams", ctypes.c_int), ("min_team", ctypes.c_int),
                 ("max_team", ctypes.c_int), ("converged", ctypes.c_int), ("graph", ctypes.c_int),
-                ("ms", ctypes.c_double), ("est_makespan_ms", ctypes.c_double), ("ms_tuning", ctypes.c_double)]
+                ("ms", ctypes.c_double), ("est_makespan_ms", ctypes.c_double), ("ms_tuning", ctypes.c_double),
+                ("solo", ctypes.c_int), ("ms_solo", ctypes.c_double), ("ms_packed", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -172,6 +173,9 @@ def lib():
             L.pit_batch_result.argtypes = [P, ctypes.c_int, D, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
             L.pit_batch_result.restype = st
+            L.pit_batch_placement.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+            L.pit_batch_placement.restype = st
             L.pit_batch_last_error.argtypes = [P]
             L.pit_batch_last_error.restype = ctypes.c_char_p
             L.pit_batch_destroy.argtypes = [P]
@@ -492,6 +496,15 @@ def pit_batch_result(batch: Batch, i: int) -> dict:
     batch._check(lib().pit_batch_result(batch.handle, int(i), ctypes.byref(r), ctypes.byref(it), ctypes.byref(wc),
                                         ctypes.byref(tc)))
     return {"res_inf": r.value, "newton_iters": it.value, "windows_converged": wc.value, "team_ctas": tc.value}
+
+
+def pit_batch_placement(batch: Batch, i: int) -> dict:
+    """Where problem i runs: alone through the wavefront path (solo, with `teams` Newton
+    iterations in flight of `team_ctas` CTAs each) or in the persistent launch."""
+    so, te, tc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    batch._check(lib().pit_batch_placement(batch.handle, int(i), ctypes.byref(so), ctypes.byref(te),
+                                           ctypes.byref(tc)))
+    return {"solo": bool(so.value), "teams": te.value, "team_ctas": tc.value}
 
 
 def pit_batch_destroy(batch: Batch):

@@ -72,3 +72,32 @@ def test_null_context_calls_return_einval():
     assert L.pit_solve(None, None, None) == pit.PIT_EINVAL
     assert L.pit_last_error(None) == b"null context"
     L.pit_destroy(None)
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding mirrors has the header's size and field offsets (a C
+    program built against include/pit.h prints them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [c for c in vars(pit).values()
+               if isinstance(c, type) and issubclass(c, ctypes.Structure) and c.__name__.startswith("pit_")]
+    assert {"pit_options", "pit_solve_info", "pit_batch_info", "pit_instance"} <= {c.__name__ for c in structs}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "pit.h"', "int main(void) {"]
+    for c in structs:
+        lines.append(f'  printf("{c.__name__} size %zu\\n", sizeof({c.__name__}));')
+        for f, _ in c._fields_:
+            lines.append(f'  printf("{c.__name__} {f} %zu\\n", offsetof({c.__name__}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_layout = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for c in structs:
+        assert c_layout[(c.__name__, "size")] == ctypes.sizeof(c), c.__name__
+        for f, _ in c._fields_:
+            assert c_layout[(c.__name__, f)] == getattr(c, f).offset, (c.__name__, f)

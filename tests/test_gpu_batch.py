@@ -23,18 +23,29 @@ def _problems():
     ]
 
 
-@pytest.mark.parametrize("prec,team,window", [(0, 0, 0), (1, 0, 0), (0, 3, 2), (1, 5, 4)])
-def test_batch_matches_oracle_per_problem(prec, team, window):
+# solo = batch_solo_nodes: 65536 (default) sends the 256 x 256 problem through the
+# wavefront path and packs the rest; 0 packs every problem; 1 solves every one alone
+@pytest.mark.parametrize("prec,team,window,solo", [(0, 0, 0, 65536), (1, 0, 0, 0), (0, 3, 2, 0), (1, 5, 4, 65536),
+                                                   (1, 0, 4, 1), (0, 0, 2, 1)])
+def test_batch_matches_oracle_per_problem(prec, team, window, solo):
     probs = _problems()
     opt = pit.pit_default_options()
-    opt.precision, opt.team_ctas, opt.window = prec, team, window
+    assert opt.batch_solo_nodes == 65536
+    opt.precision, opt.team_ctas, opt.window, opt.batch_solo_nodes = prec, team, window, solo
     with pit.pit_batch_create(probs, opt) as batch:
+        for i, p in enumerate(probs):
+            where = pit.pit_batch_placement(batch, i)
+            assert where["solo"] == (solo > 0 and p.grid.nx * p.grid.ny >= solo), (i, where)
+            assert where["team_ctas"] >= 1 and where["teams"] >= 1
         results = []
         for rep in range(2):  # the second solve replays the captured graph
             status, info = pit.pit_batch_solve(batch)
             assert info["converged"] == len(probs)
             results.append([t["U"].cpu().numpy().copy() for t in batch.tensors])
-        assert info["graph"] == 1
+        n_solo = sum(solo > 0 and p.grid.nx * p.grid.ny >= solo for p in probs)
+        assert info["solo"] == n_solo
+        assert info["graph"] == (1 if n_solo < len(probs) else 0)
+        assert info["ms"] >= info["ms_solo"] + info["ms_packed"] - 1e-3
         for i, p in enumerate(probs):
             r = pit.pit_batch_result(batch, i)
             assert r["res_inf"] <= 1e-12
@@ -42,3 +53,22 @@ def test_batch_matches_oracle_per_problem(prec, team, window):
             Ug = results[-1][i].reshape(p.M, -1)
             assert np.abs(Ug - Uo).max() <= 1e-10 * np.abs(Uo).max(), (i, p.name)
             np.testing.assert_array_equal(results[0][i], results[1][i])
+
+
+@pytest.mark.parametrize("solo", [0, 1])
+def test_batch_unconverged_problems_report_their_true_residual(solo):
+    """With one Newton update allowed, no problem converges: the batch says so, and the
+    residual it reports for each is the oracle's residual of the U it returned (for a
+    solo problem that stopped early, taken over all levels)."""
+    probs = _problems()[:4]
+    opt = pit.pit_default_options()
+    opt.newton_max, opt.batch_solo_nodes, opt.window = 1, solo, 4
+    with pit.pit_batch_create(probs, opt) as batch:
+        status, info = pit.pit_batch_solve(batch, check=False)
+        assert status == pit.PIT_ENOCONV and info["converged"] < len(probs)
+        for i, p in enumerate(probs):
+            r = pit.pit_batch_result(batch, i)
+            U = batch.tensors[i]["U"].cpu().numpy().reshape(p.M, -1)
+            R = oracle.residual(p.grid, p.params, p.M, p.dt, p.u0, U, p.bc, p.q)
+            ro = float(np.abs(R).max())
+            assert abs(r["res_inf"] - ro) <= 1e-9 * ro + 1e-15, (i, r["res_inf"], ro)
