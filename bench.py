@@ -288,8 +288,9 @@ def variants(args):
                      "workload": p.name, "M": p.M, "window": window, "precision": "fp32 level solves / fp64 newton",
                      "newton_iters_total": info["newton_iters_total"], "res_inf_final": info["res_inf"][-1],
                      "wave_teams": info["wave_teams"], "ctas_per_team": info["wave_team_ctas"]}
-    # 64 independent problems of uneven size: grids of 256^2 nodes and more one after
-    # another through the wavefront path, the rest in one persistent launch (graph replay)
+    # 64 independent problems of uneven size in one persistent launch (graph replay):
+    # grids of 256^2 nodes and more as wavefront jobs (several Newton iterations in
+    # flight), the rest as single teams side by side
     probs = W.batched(seed=0)
     dof = sum(p.dof for p in probs)
     opt = pit.pit_default_options()
@@ -299,15 +300,14 @@ def variants(args):
         pit.pit_batch_solve(batch)
         st, info = pit.pit_batch_solve(batch)
         res = max(pit.pit_batch_result(batch, i)["res_inf"] for i in range(len(probs)))
-        solo_dof = sum(p.dof for i, p in enumerate(probs) if pit.pit_batch_placement(batch, i)["solo"])
+        wave_dof = sum(p.dof for i, p in enumerate(probs) if pit.pit_batch_placement(batch, i)["teams"] > 1)
     out["batched64_mixed_window32"] = {
         "value": dof / (info["ms"] * 1e-3), "unit": UNIT, "ms_per_step": info["ms"], "dof": dof,
         "problems": len(probs), "grids": "64..384 squared", "levels": "32..512",
         "precision": "fp32 level solves / fp64 newton", "converged": info["converged"], "max_res_inf_final": res,
         "graph_replay": bool(info["graph"]), "team_ctas": [info["min_team"], info["max_team"]],
-        "solo_problems": info["solo"], "solo_dof": solo_dof, "ms_solo": info["ms_solo"],
-        "ms_packed": info["ms_packed"], "solo_min_nodes": opt.batch_solo_nodes,
-        "create_ms": info["ms_tuning"], "schedule_estimate_ms": info["est_makespan_ms"]}
+        "wave_jobs": info["wave_jobs"], "wave_job_dof": wave_dof, "wave_job_min_nodes": opt.batch_wave_nodes,
+        "autotune_ms": info["ms_tuning"], "schedule_estimate_ms": info["est_makespan_ms"]}
     out.update(paper_variants(args))
     if args.learned:
         out["learned_guess"] = learned_variant(args)

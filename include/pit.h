@@ -110,11 +110,10 @@ typedef struct {
                                diverges (residual not finite or above 1e10) or does not converge
                                is halved and restarted from the plain guess, and grows back
                                after a success */
-    int batch_solo_nodes;   /* pit_batch_create: a problem with nx*ny >= batch_solo_nodes is solved on
-                               its own by the wavefront path of pit_solve (several Newton iterations
-                               in flight on the whole GPU), one such problem after another; the rest
-                               share the persistent launch. <= 0 = every problem in the persistent
-                               launch (default 65536, a 256 x 256 grid) */
+    int batch_wave_nodes;   /* pit_batch_create: a problem with nx*ny >= batch_wave_nodes is a wavefront
+                               job of the persistent launch (up to 6 teams, nearly every SM, several
+                               Newton iterations of a window in flight), such jobs one after another;
+                               <= 0 = one team per problem for all (default 65536, a 256 x 256 grid) */
 } pit_options;
 
 enum { PIT_FP64 = 0, PIT_FP32_INNER = 1 };
@@ -239,22 +238,25 @@ pit_status pit_solve_host(pit_ctx* ctx, const double* u0_host, double* U_host, p
 
 /* ----------------------------------------------------------- batched solves
  * Many independent problems (grids, level counts, closures and viscosities may
- * all differ). Problems on grids of at least opt->batch_solo_nodes nodes are
- * solved one after another, each alone on the GPU by the wavefront path of
- * pit_solve (windows of opt->window levels); the batch holds a context for each
- * (about 56 bytes per unknown; a problem whose context does not fit in memory
- * joins the persistent launch instead). All other problems are solved in ONE
- * persistent cooperative launch: each by a team of CTAs (the level chain of eq. 7
- * with Newton iterations until its residual is <= tol_res, in windows of
- * opt->window levels, default 32); teams of different sizes run side by side on
- * the GPU. pit_batch_create picks every packed problem's team size with an
- * autotuner (short timed runs of each distinct grid size at candidate team sizes;
+ * all differ) solved in ONE persistent cooperative launch. Each problem runs the
+ * level chain of eq. 7 with Newton iterations until its residual is <= tol_res,
+ * in windows of opt->window levels (default 32). A problem on a grid of at least
+ * opt->batch_wave_nodes nodes is a wavefront job: K teams of G CTAs (K * G up to
+ * the SM count) with K Newton iterations of a window in flight, as in pit_solve;
+ * these jobs run first, one after another. Every other problem gets one team of
+ * CTAs, and teams of different sizes run side by side on the remaining SMs and
+ * afterwards. pit_batch_create picks every such team's size with an autotuner
+ * (short timed runs of each distinct grid size at candidate team sizes;
  * opt->team_ctas > 0 fixes it instead) and list-schedules the teams over the
- * SMs, longest first. pit_batch_solve replays that launch as a captured CUDA
+ * SMs, longest first. pit_batch_solve replays the launch as a captured CUDA
  * graph after its first call; the batch works on a stream of its own, ordered
  * after the caller's `stream` at every solve, and returns when the solve is
  * complete. Level solves follow opt->precision (PIT_FP32_INNER is the intended
- * use). */
+ * use). A window whose Newton diverges (a residual that is not finite or above
+ * 1e10, or a level solve that breaks down) is restarted shorter, down to single
+ * levels; a problem that still fails only ends unconverged (pit_batch_solve then
+ * returns PIT_ENOCONV and its res_inf tells which); only a device wait that runs
+ * out of budget ends the launch (PIT_ETIMEOUT). */
 typedef struct pit_batch pit_batch;
 
 typedef struct {
@@ -276,13 +278,10 @@ typedef struct {
     int min_team, max_team; /* team sizes chosen */
     int converged;          /* problems whose final ||R||_inf <= tol_res */
     int graph;              /* 1 when the launch was replayed from a CUDA graph */
-    double ms;              /* time of the whole solve on the batch's stream (solo problems and the
-                               persistent launch, with the gaps between the solo windows) */
+    double ms;              /* device time of the launch */
     double est_makespan_ms; /* the schedule's estimate from the autotuner's timings */
-    double ms_tuning;       /* host time spent in pit_batch_create (contexts and autotuner) */
-    int solo;               /* problems solved alone by the wavefront path */
-    double ms_solo;         /* their time, summed */
-    double ms_packed;       /* time of the persistent launch (0 when every problem is solo) */
+    double ms_tuning;       /* host time spent in pit_batch_create's autotuner */
+    int wave_jobs;          /* problems solved as wavefront jobs (several teams) */
 } pit_batch_info;
 
 pit_status pit_batch_create(const pit_instance* inst, int count, const pit_options* opt, void* stream,
@@ -290,15 +289,13 @@ pit_status pit_batch_create(const pit_instance* inst, int count, const pit_optio
 pit_status pit_batch_solve(pit_batch* batch, pit_batch_info* info);
 /* Results of problem i after pit_batch_solve: final ||R||_inf of U (FP64), Newton
  * updates summed over windows, the number of windows that converged, and the CTAs
- * of the team that solved it (per Newton iteration in flight for a solo problem;
- * see pit_batch_placement). */
+ * of each team that solved it (see pit_batch_placement). */
 pit_status pit_batch_result(const pit_batch* batch, int i, double* res_inf, int* newton_iters, int* windows_converged,
                             int* team_ctas);
-/* Where problem i runs: *solo = 1 for the wavefront path, with *teams Newton
- * iterations in flight of *team_ctas CTAs each (*teams = 0 when the context fell
- * back to one launch per stage); *solo = 0 for the persistent launch, one team of
- * *team_ctas CTAs (*teams = 1). Any pointer may be NULL. */
-pit_status pit_batch_placement(const pit_batch* batch, int i, int* solo, int* teams, int* team_ctas);
+/* How problem i is solved: *teams teams (K > 1: a wavefront job with K Newton
+ * iterations in flight; 1: one team) of *team_ctas CTAs each. Any pointer may be
+ * NULL. */
+pit_status pit_batch_placement(const pit_batch* batch, int i, int* teams, int* team_ctas);
 const char* pit_batch_last_error(const pit_batch* batch);
 void pit_batch_destroy(pit_batch* batch);
 

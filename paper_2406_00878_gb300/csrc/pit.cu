@@ -139,7 +139,7 @@ extern "C" void pit_default_options(pit_options* o) {
     o->wave_teams = 0;
     o->precision = PIT_FP64;
     o->window = 0;
-    o->batch_solo_nodes = 65536;
+    o->batch_wave_nodes = 65536;
 }
 
 extern "C" const char* pit_status_string(pit_status s) {

@@ -1,16 +1,15 @@
-// pit_batch.cu -- many independent problems: large grids one after another through
-// the wavefront path, the rest in one persistent cooperative launch.
+// pit_batch.cu -- many independent problems in one persistent cooperative launch.
 //
-// A large problem fills the GPU by itself: the wavefront kernel keeps several Newton
-// iterations of it in flight, which a single team of the persistent launch cannot.
-// Each such problem gets a context of its own and is solved by pit_solve in windows.
-// In the persistent launch each problem gets a team of CTAs that runs the level chain
-// (nested block inverse of eq. 7) with Newton iterations per window of levels until
-// the window's residual is below tol_res, then a final FP64 residual pass
-// (batch_kernel in pit_kernels.cuh). Here: the routing, the autotuner that picks a
-// team size per packed problem from short timed runs, the list schedule that places
-// the teams on the SMs, the workspace pools, and the launch, which is captured once
-// into a CUDA graph and replayed.
+// Each problem is a job of the launch (batch_kernel in pit_kernels.cuh): the level
+// chain (nested block inverse of eq. 7) with Newton iterations per window of levels
+// until the window's residual is below tol_res, then a final FP64 residual pass.
+// A problem on a large grid is a wavefront job: K teams of G CTAs, nearly the whole
+// GPU, keep K Newton iterations of its window in flight, and such jobs run one after
+// another at the start of the launch. Every other problem gets a single team, and
+// teams of different sizes run side by side on the remaining SMs and afterwards.
+// Here: the routing, the autotuner that picks a team size per packed problem from
+// short timed runs, the list schedule that places the jobs on the SMs, the workspace
+// pools, and the launch, which is captured once into a CUDA graph and replayed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,7 +23,6 @@
 #include <vector>
 
 #include "pit.h"
-#include "pit_internal.h"
 #include "pit_kernels.cuh"
 
 using namespace pit;
@@ -32,6 +30,8 @@ using namespace pit;
 namespace {
 constexpr int kNT = 256;
 constexpr int kMaxTeam = 160;
+constexpr int kMinLocal = 256;   // wavefront teams: at least this many unknowns per CTA
+constexpr int kMaxWaveTeams = 6;
 }
 
 struct pit_batch {
@@ -44,24 +44,15 @@ struct pit_batch {
     size_t dyn_max = 0;
     bool fp32 = false;
     std::vector<pit_instance> in;
-    std::vector<int> team_of;          // team size per problem (CTAs per wavefront team when solo)
-    // problems solved alone by the wavefront path
-    std::vector<int> solo_of;          // per problem: index into the solo lists, or -1
-    std::vector<int> solo_idx;         // problem of each solo entry
-    std::vector<pit_ctx*> solo_ctx;
-    std::vector<int> solo_K;           // Newton iterations in flight (0: per-stage launches)
-    std::vector<double> solo_res;      // results of the last solve
-    std::vector<int> solo_iters, solo_wconv;
-    std::vector<int> packed_idx;       // problems of the persistent launch
-    double* d_scratch = nullptr;       // residual scratch for a solo problem that stopped early
-    size_t scratch_n = 0;
-    cudaEvent_t ea = nullptr, eb = nullptr;  // around a whole solve
+    std::vector<int> team_of;          // CTAs per team, per problem
+    std::vector<int> teams_of;         // teams per problem: K for a wavefront job, 1 otherwise
+    int wave_jobs = 0;
     // device data
     BatchInstance* d_inst = nullptr;
     BatchJob* d_jobs = nullptr;
     int* d_job_off = nullptr;
     BatchTeamWs* d_ws = nullptr;
-    unsigned char* pool = nullptr;     // team workspaces
+    unsigned char* pool = nullptr;     // job workspaces
     size_t pool_bytes = 0, sync_bytes = 0;  // sync region (zeroed per launch) at the start of the pool
     double* d_res = nullptr;
     int* d_iters = nullptr;            // [count] iters, [count] converged windows
@@ -116,50 +107,94 @@ static size_t team_smem(bool fp32, int nx, int ny, int G) {
     return fp32 ? wave_smem_bytes<float>(rows * nx, nx) : wave_smem_bytes<double>(rows * nx, nx);
 }
 
-// Bytes of one team's workspace: sync part (flags, red_cnt, prog, kconv) and data part.
+// Bytes of one job's workspace (K teams of G CTAs): sync part (job barrier; kconv,
+// stop and abort words; flags, prog, red_cnt; tagged words; zeroed before each
+// launch) and data part (halo rows, reduction partials, per-cell running maxima).
 struct WsSize {
-    size_t sync, data;
+    size_t sync_head, sync, data;
 };
-static size_t tagged_words(int G, int nx) {
-    return (size_t)2 * G * kDeepSlotRows * nx * 2 + (size_t)4 * G * kTagRedWords;
+static size_t tagged_words(int K, int G, int nx) {
+    return (size_t)K * ((size_t)2 * G * kDeepSlotRows * nx * 2 + (size_t)4 * G * kTagRedWords);
 }
-static WsSize ws_size(int G, int nx, int newton_max, int window) {
+static WsSize ws_size(int K, int G, int nx, int newton_max, int window) {
     WsSize w;
-    // flags, prog, red_cnt, kconv, then the tagged words (all zeroed before each launch)
-    w.sync = align_up(sizeof(unsigned long long) * ((size_t)G * 2 + 4) + sizeof(int) * 4, 256) +
-             align_up(sizeof(unsigned long long) * tagged_words(G, nx), 256);
-    w.data = align_up(sizeof(double) * ((size_t)2 * G * 2 * nx + (size_t)4 * G * 4 + (size_t)newton_max * window), 256);
+    w.sync_head = align_up(sizeof(unsigned long long) * (5 + (size_t)K * G * 2 + (size_t)K * 4), 256);
+    w.sync = w.sync_head + align_up(sizeof(unsigned long long) * tagged_words(K, G, nx), 256);
+    w.data = align_up(sizeof(double) * ((size_t)K * 2 * G * 2 * nx + (size_t)K * 4 * G * 4 + (size_t)newton_max * window),
+                      256);
     return w;
 }
 
+// Wavefront shape of a large problem: the most teams (<= 6, <= newton_max) whose
+// strips of at least kMinLocal unknowns fit in shared memory with K * G <= SMs.
+static bool wave_shape(const pit_batch* b, const pit_instance& I, int* K_out, int* G_out) {
+    const int nx = I.grid.nx, ny = I.grid.ny;
+    const int rows_min = (kMinLocal + nx - 1) / nx;
+    for (int K = std::min(kMaxWaveTeams, std::max(1, b->opt.newton_max)); K >= 2; --K) {
+        int G = std::min(b->num_sms / K, (ny + rows_min - 1) / rows_min);
+        G = std::max(1, std::min({G, ny, kMaxTeam}));
+        const int rows = (ny + G - 1) / G;
+        G = (ny + rows - 1) / rows;
+        if (team_smem(b->fp32, nx, ny, G) <= b->dyn_max && K * G <= b->num_sms) {
+            *K_out = K;
+            *G_out = G;
+            return true;
+        }
+    }
+    return false;
+}
+
 struct Job {
-    int inst, G;
+    int inst, G, K;
     double start, dur;
-    std::vector<int> ctas;
+    std::vector<int> ctas;  // K * G CTAs: team tk, rank r -> ctas[tk * G + r]
 };
 
-// Build jobs, workspace and device descriptors for problems `in` with team sizes
-// `team`; problem i reports into result slot gid[i] (calibration runs use one
-// problem with truncated levels and slot 0).
+// Build jobs, workspace and device descriptors for problems `in` with K[i] teams of
+// G[i] CTAs each (K[i] > 1: a wavefront job, placed first on CTAs 0 .. K G - 1, one
+// after another; the other jobs are list-scheduled over the SMs after them, longest
+// first);
+// problem i reports into result slot gid[i] (calibration runs use one problem with
+// truncated levels and slot 0).
 static pit_status build_launch(pit_batch* b, const std::vector<pit_instance>& in, const std::vector<int>& team,
-                               const std::vector<double>& cost, const std::vector<int>& gid) {
+                               const std::vector<int>& teams, const std::vector<double>& cost,
+                               const std::vector<int>& gid) {
     const int n = (int)in.size();
     const int P = b->num_sms;
-    // list schedule, longest first: each team takes the G CTAs that free up earliest
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] * 1 > cost[c] * 1; });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        if ((teams[a] > 1) != (teams[c] > 1)) return teams[a] > 1;  // wavefront jobs first
+        return cost[a] > cost[c];
+    });
     std::vector<double> free_at(P, 0.0);
     std::vector<Job> jobs;
+    bool wave_phase = true;
     for (int i : order) {
-        std::vector<int> idx(P);
-        std::iota(idx.begin(), idx.end(), 0);
-        std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return free_at[a] < free_at[c]; });
+        if (wave_phase && teams[i] == 1) {
+            // the single teams start when the wavefront jobs are done, on every SM: their
+            // cost estimates are rough, and teams packed beside them on the few SMs left
+            // over would form a tail
+            wave_phase = false;
+            const double t0 = *std::max_element(free_at.begin(), free_at.end());
+            std::fill(free_at.begin(), free_at.end(), t0);
+        }
         Job j;
         j.inst = i;
         j.G = team[i];
-        j.ctas.assign(idx.begin(), idx.begin() + team[i]);
-        std::sort(j.ctas.begin(), j.ctas.end());
+        j.K = teams[i];
+        const int width = j.K * j.G;
+        if (j.K > 1) {
+            j.ctas.resize(width);
+            std::iota(j.ctas.begin(), j.ctas.end(), 0);
+        } else {
+            // a team takes the G CTAs that free up earliest
+            std::vector<int> idx(P);
+            std::iota(idx.begin(), idx.end(), 0);
+            std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return free_at[a] < free_at[c]; });
+            j.ctas.assign(idx.begin(), idx.begin() + width);
+            std::sort(j.ctas.begin(), j.ctas.end());
+        }
         double start = 0.0;
         for (int c : j.ctas) start = std::max(start, free_at[c]);
         j.start = start;
@@ -177,11 +212,14 @@ static pit_status build_launch(pit_batch* b, const std::vector<pit_instance>& in
     size_t sync_total = 0, data_total = 0;
     const int W = b->opt.window > 0 ? b->opt.window : 32;
     for (size_t q = 0; q < jobs.size(); ++q) {
-        const pit_instance& I = in[jobs[q].inst];
-        wss[q] = ws_size(jobs[q].G, I.grid.nx, b->opt.newton_max, std::min(W, I.M));
+        const Job& j = jobs[q];
+        const pit_instance& I = in[j.inst];
+        wss[q] = ws_size(j.K, j.G, I.grid.nx, b->opt.newton_max, std::min(W, I.M));
         sync_total += wss[q].sync;
         data_total += wss[q].data;
-        for (int r = 0; r < jobs[q].G; ++r) per[jobs[q].ctas[r]].push_back(BatchJob{jobs[q].inst, r, jobs[q].G, (int)q});
+        for (int tk = 0; tk < j.K; ++tk)
+            for (int r = 0; r < j.G; ++r)
+                per[j.ctas[(size_t)tk * j.G + r]].push_back(BatchJob{j.inst, r, j.G, (int)q, j.K, tk});
     }
     // device buffers (freed and rebuilt for every build)
     cudaFree(b->pool);
@@ -190,27 +228,37 @@ static pit_status build_launch(pit_batch* b, const std::vector<pit_instance>& in
     cudaFree(b->d_ws);
     cudaFree(b->d_inst);
     b->pool = nullptr;
+    b->d_jobs = nullptr;
+    b->d_job_off = nullptr;
+    b->d_ws = nullptr;
+    b->d_inst = nullptr;
     b->pool_bytes = sync_total + data_total;
     b->sync_bytes = sync_total;
     BCK(cudaMalloc(&b->pool, b->pool_bytes));
     std::vector<BatchTeamWs> ws(jobs.size());
     size_t so = 0, dof = sync_total;
     for (size_t q = 0; q < jobs.size(); ++q) {
-        const int G = jobs[q].G, nx = in[jobs[q].inst].grid.nx;
+        const int K = jobs[q].K, G = jobs[q].G, nx = in[jobs[q].inst].grid.nx;
         unsigned long long* sw = reinterpret_cast<unsigned long long*>(b->pool + so);
-        ws[q].flags = sw;
-        ws[q].prog = sw + G;
-        ws[q].red_cnt = sw + 2 * G;
-        ws[q].kconv = reinterpret_cast<int*>(sw + 2 * G + 4);
-        unsigned long long* tw = reinterpret_cast<unsigned long long*>(
-            b->pool + so + align_up(sizeof(unsigned long long) * ((size_t)G * 2 + 4) + sizeof(int) * 4, 256));
+        ws[q].jbar = sw;
+        ws[q].jres = sw + 1;
+        ws[q].kconv = reinterpret_cast<int*>(sw + 2);  // kconv, stop[2], jabort, jstatus
+        ws[q].stop = ws[q].kconv + 1;
+        ws[q].jabort = ws[q].kconv + 3;
+        ws[q].jstatus = ws[q].kconv + 4;
+        ws[q].flags = sw + 5;
+        ws[q].prog = sw + 5 + (size_t)K * G;
+        ws[q].red_cnt = sw + 5 + (size_t)2 * K * G;
+        ws[q].sync_words = sw + 5;
+        ws[q].sync_count = wss[q].sync / sizeof(unsigned long long) - 5;
+        unsigned long long* tw = reinterpret_cast<unsigned long long*>(b->pool + so + wss[q].sync_head);
         ws[q].tpub = tw;
-        ws[q].tred = tw + (size_t)2 * G * kDeepSlotRows * nx * 2;
+        ws[q].tred = tw + (size_t)K * 2 * G * kDeepSlotRows * nx * 2;
         so += wss[q].sync;
         double* dw = reinterpret_cast<double*>(b->pool + dof);
         ws[q].pub = dw;
-        ws[q].red_part = dw + (size_t)2 * G * 2 * nx;
-        ws[q].cell_prefix = ws[q].red_part + (size_t)4 * G * 4;
+        ws[q].red_part = dw + (size_t)K * 2 * G * 2 * nx;
+        ws[q].cell_prefix = ws[q].red_part + (size_t)K * 4 * G * 4;
         dof += wss[q].data;
     }
     std::vector<BatchJob> flat;
@@ -367,81 +415,67 @@ extern "C" pit_status pit_batch_create(const pit_instance* inst, int count, cons
         BCK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
         BCK(cudaEventRecord(b->ev_user, b->user_stream));
         BCK(cudaStreamWaitEvent(b->stream, b->ev_user, 0));
-        BCK(cudaEventCreate(&b->ea));
-        BCK(cudaEventCreate(&b->eb));
-        // routing: a large grid is solved alone through the wavefront path when its
-        // context can be created (memory); everything else joins the persistent launch
-        b->solo_of.assign(count, -1);
-        b->team_of.assign(count, 0);
+        // routing: a large grid becomes a wavefront job when a wavefront shape fits
+        b->teams_of.assign(count, 1);
+        std::vector<int> team(count, 0);
         for (int i = 0; i < count; ++i) {
             const pit_instance& I = inst[i];
             const long long nodes = (long long)I.grid.nx * I.grid.ny;
-            bool solo = b->opt.batch_solo_nodes > 0 && nodes >= b->opt.batch_solo_nodes;
-            if (solo) {
-                pit_options so = b->opt;
-                so.team_ctas = 0;  // the wavefront picks its own team size
-                pit_ctx* ctx = nullptr;
-                if (pit_create(&I.grid, I.M, I.dt, &I.params, &so, b->stream, &ctx) != PIT_OK) {
-                    cudaGetLastError();  // e.g. out of memory: the persistent launch takes it
-                    solo = false;
-                } else {
-                    PitProblemView v;
-                    pit_internal_view(ctx, &v);
-                    b->solo_of[i] = (int)b->solo_ctx.size();
-                    b->solo_idx.push_back(i);
-                    b->solo_ctx.push_back(ctx);
-                    b->solo_K.push_back(v.wave_teams);
-                    b->team_of[i] = v.wave_team_ctas;
-                }
+            int K = 0, G = 0;
+            if (b->opt.batch_wave_nodes > 0 && nodes >= b->opt.batch_wave_nodes && wave_shape(b, I, &K, &G)) {
+                b->teams_of[i] = K;
+                team[i] = G;
+                ++b->wave_jobs;
             }
-            if (!solo) b->packed_idx.push_back(i);
         }
-        const size_t ns = b->solo_ctx.size();
-        b->solo_res.assign(ns, 0.0);
-        b->solo_iters.assign(ns, 0);
-        b->solo_wconv.assign(ns, 0);
-        const int np = (int)b->packed_idx.size();
-        if (np == 0) return PIT_OK;
-        std::vector<pit_instance> pk(np);
-        for (int j = 0; j < np; ++j) pk[j] = inst[b->packed_idx[j]];
+        const std::vector<int>& teams = b->teams_of;
         // smallest team whose strips fit in shared memory, per packed problem
-        std::vector<int> gmin(np);
-        for (int j = 0; j < np; ++j) {
-            const pit_instance& I = pk[j];
+        std::vector<int> gmin(count, 1);
+        for (int i = 0; i < count; ++i) {
+            if (teams[i] > 1) continue;
+            const pit_instance& I = inst[i];
             int g = 1;
             while (g <= std::min(I.grid.ny, kMaxTeam) && team_smem(b->fp32, I.grid.nx, I.grid.ny, g) > b->dyn_max) ++g;
             if (g > std::min(I.grid.ny, std::min(kMaxTeam, b->num_sms)))
-                return bfail(b, PIT_EUNSUPPORTED, "problem %d: a level strip does not fit in shared memory",
-                             b->packed_idx[j]);
-            gmin[j] = g;
+                return bfail(b, PIT_EUNSUPPORTED, "problem %d: a level strip does not fit in shared memory", i);
+            gmin[i] = g;
         }
-        std::vector<int> team(np);
-        std::vector<double> cost(np, 1.0);
+        std::vector<double> cost(count, 1.0);
         if (b->opt.team_ctas > 0) {
-            for (int j = 0; j < np; ++j)
-                team[j] = std::max(gmin[j], std::min({b->opt.team_ctas, pk[j].grid.ny, b->num_sms}));
-            for (int j = 0; j < np; ++j) cost[j] = (double)pk[j].M * pk[j].grid.nx * pk[j].grid.ny / team[j];
+            for (int i = 0; i < count; ++i)
+                if (teams[i] == 1) team[i] = std::max(gmin[i], std::min({b->opt.team_ctas, inst[i].grid.ny, b->num_sms}));
+            for (int i = 0; i < count; ++i)
+                cost[i] = (double)inst[i].M * inst[i].grid.nx * inst[i].grid.ny / ((double)team[i] * teams[i]);
         } else {
             // autotuner: per distinct grid, time candidate team sizes on the first problem of
-            // that grid truncated to a few levels; per-level time t(G) -> cost = t(G) * M
+            // that grid truncated to a few levels; per-level time t(G) -> cost = t(G) * M.
+            // A wavefront grid is timed at its team size; its cost counts the iterations in
+            // flight as halving the time (only the schedule of the packed teams uses it).
             std::map<std::pair<int, int>, int> rep;
-            for (int j = 0; j < np; ++j) rep.emplace(std::make_pair(pk[j].grid.nx, pk[j].grid.ny), j);
+            std::map<std::pair<int, int>, std::vector<int>> cand;
+            for (int i = 0; i < count; ++i) {
+                const auto key = std::make_pair(inst[i].grid.nx, inst[i].grid.ny);
+                rep.emplace(key, i);
+                std::vector<int>& cs = cand[key];
+                if (teams[i] > 1) {
+                    if (std::find(cs.begin(), cs.end(), team[i]) == cs.end()) cs.push_back(team[i]);
+                    continue;
+                }
+                const int gmax = std::min({inst[i].grid.ny, kMaxTeam, b->num_sms});
+                for (double f : {1.0, 1.5, 2.0, 3.0, 4.0, 6.0}) {
+                    const int g = std::min(gmax, std::max(gmin[i], (int)std::lround(gmin[i] * f)));
+                    if (std::find(cs.begin(), cs.end(), g) == cs.end()) cs.push_back(g);
+                }
+            }
             std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> table;
             for (auto& kv : rep) {
-                const int j = kv.second;
-                const pit_instance& I = pk[j];
-                std::vector<int> cands;
-                const int gmax = std::min({I.grid.ny, kMaxTeam, b->num_sms});
-                for (double f : {1.0, 1.5, 2.0, 3.0, 4.0, 6.0}) {
-                    const int g = std::min(gmax, std::max(gmin[j], (int)std::lround(gmin[j] * f)));
-                    if (std::find(cands.begin(), cands.end(), g) == cands.end()) cands.push_back(g);
-                }
-                pit_instance cal = I;
-                cal.M = std::min(I.M, 8);
-                for (int g : cands) {
+                pit_instance cal = inst[kv.second];
+                cal.M = std::min(cal.M, 8);
+                for (int g : cand[kv.first]) {
                     std::vector<pit_instance> one{cal};
                     double best = 1e300;
-                    BRET(build_launch(b, one, std::vector<int>{g}, std::vector<double>{1.0}, std::vector<int>{0}));
+                    BRET(build_launch(b, one, std::vector<int>{g}, std::vector<int>{1}, std::vector<double>{1.0},
+                                      std::vector<int>{0}));
                     // results land in slot 0 of the real arrays; harmless before the real solve
                     for (int rep2 = 0; rep2 < 2; ++rep2) {
                         double ms = 0.0;
@@ -451,36 +485,41 @@ extern "C" pit_status pit_batch_create(const pit_instance* inst, int count, cons
                     table[kv.first].push_back({g, best / cal.M});
                 }
             }
-            // per problem: the team size with the least SM time (t * G), then give the
-            // longest problems more CTAs while they bound the makespan
-            for (int j = 0; j < np; ++j) {
-                const auto& tb = table[std::make_pair(pk[j].grid.nx, pk[j].grid.ny)];
+            // per packed problem: the team size with the least SM time (t * G), then give
+            // the longest problems more CTAs while they bound the makespan
+            for (int i = 0; i < count; ++i) {
+                const auto& tb = table[std::make_pair(inst[i].grid.nx, inst[i].grid.ny)];
+                if (teams[i] > 1) {
+                    for (auto& e : tb)
+                        if (e.first == team[i]) cost[i] = e.second * inst[i].M / 2.0;
+                    continue;
+                }
                 double bestv = 1e300;
                 for (auto& e : tb) {
-                    if (e.second * e.first < bestv) {
+                    if (e.first >= gmin[i] && e.second * e.first < bestv) {
                         bestv = e.second * e.first;
-                        team[j] = e.first;
-                        cost[j] = e.second * pk[j].M;
+                        team[i] = e.first;
+                        cost[i] = e.second * inst[i].M;
                     }
                 }
             }
             for (int round = 0; round < 64; ++round) {
                 double total = 0.0, worst = 0.0;
-                int wi = 0;
-                for (int j = 0; j < np; ++j) {
-                    total += cost[j] * team[j];
-                    if (cost[j] > worst) {
-                        worst = cost[j];
-                        wi = j;
+                int wi = -1;
+                for (int i = 0; i < count; ++i) {
+                    total += cost[i] * team[i] * teams[i];
+                    if (teams[i] == 1 && cost[i] > worst) {
+                        worst = cost[i];
+                        wi = i;
                     }
                 }
-                if (worst <= total / b->num_sms) break;
-                const auto& tb = table[std::make_pair(pk[wi].grid.nx, pk[wi].grid.ny)];
+                if (wi < 0 || worst <= total / b->num_sms) break;
+                const auto& tb = table[std::make_pair(inst[wi].grid.nx, inst[wi].grid.ny)];
                 bool grew = false;
                 for (auto& e : tb) {
-                    if (e.first > team[wi] && e.second * pk[wi].M < cost[wi]) {
+                    if (e.first > team[wi] && e.second * inst[wi].M < cost[wi]) {
                         team[wi] = e.first;
-                        cost[wi] = e.second * pk[wi].M;
+                        cost[wi] = e.second * inst[wi].M;
                         grew = true;
                         break;
                     }
@@ -488,8 +527,10 @@ extern "C" pit_status pit_batch_create(const pit_instance* inst, int count, cons
                 if (!grew) break;
             }
         }
-        for (int j = 0; j < np; ++j) b->team_of[b->packed_idx[j]] = team[j];
-        BRET(build_launch(b, pk, team, cost, b->packed_idx));
+        b->team_of = team;
+        std::vector<int> gid(count);
+        std::iota(gid.begin(), gid.end(), 0);
+        BRET(build_launch(b, b->in, team, teams, cost, gid));
         return PIT_OK;
     };
     pit_status st = setup();
@@ -503,44 +544,13 @@ extern "C" pit_status pit_batch_create(const pit_instance* inst, int count, cons
     return PIT_OK;
 }
 
-// Problem solo_idx[j] alone through the wavefront path (fresh data, plain guess, then
-// pit_solve in windows). A problem that does not converge is recorded, as in the
-// persistent launch; a device wait that ran out or a non-finite residual fails the batch.
-static pit_status solve_solo(pit_batch* b, size_t j) {
-    const int i = b->solo_idx[j];
-    pit_ctx* ctx = b->solo_ctx[j];
-    const pit_instance& I = b->in[i];
-    pit_status s = pit_set_data(ctx, I.u0_dev, I.bc_dev, I.q_dev);
-    if (s == PIT_OK) s = pit_fill_plain_guess(ctx, I.U_dev);
-    if (s != PIT_OK) return bfail(b, s, "problem %d: %s", i, pit_last_error(ctx));
-    pit_solve_info inf;
-    s = pit_solve(ctx, I.U_dev, &inf);
-    if (s == PIT_ETIMEOUT) return bfail(b, s, "problem %d (wavefront): a device wait ran out of budget", i);
-    if (s == PIT_EDIVERGED) return bfail(b, s, "problem %d (wavefront): NaN/Inf in a residual or solve", i);
-    if (s != PIT_OK && s != PIT_ENOCONV) return bfail(b, s, "problem %d: %s", i, pit_last_error(ctx));
-    double res = inf.res_inf[inf.newton_iters];
-    if (s == PIT_ENOCONV) {
-        // a window of one level may have stopped the solve before the final residual:
-        // take it over all levels
-        const size_t dof = (size_t)I.M * I.grid.nx * I.grid.ny;
-        if (b->scratch_n < dof) {
-            cudaFree(b->d_scratch);
-            b->d_scratch = nullptr;
-            b->scratch_n = 0;
-            BCK(cudaMalloc(&b->d_scratch, sizeof(double) * dof));
-            b->scratch_n = dof;
-        }
-        s = pit_residual(ctx, I.U_dev, b->d_scratch, &res);
-        if (s != PIT_OK) return bfail(b, s, "problem %d: %s", i, pit_last_error(ctx));
-    }
-    b->solo_res[j] = res;
-    b->solo_iters[j] = inf.newton_iters_total;
-    b->solo_wconv[j] = inf.windows_converged;
-    return PIT_OK;
-}
-
-// The persistent launch of the packed problems (graph replay after the first call).
-static pit_status solve_packed(pit_batch* b, bool* used_graph) {
+extern "C" pit_status pit_batch_solve(pit_batch* b, pit_batch_info* info) {
+    if (!b) return PIT_EINVAL;
+    double ms = 0.0;
+    bool used_graph = false;
+    // the caller's stream may hold the producers of the problems' data
+    BCK(cudaEventRecord(b->ev_user, b->user_stream));
+    BCK(cudaStreamWaitEvent(b->stream, b->ev_user, 0));
     if (b->graph_ok && !b->exec) {
         // capture the launch sequence once
         cudaStreamCaptureStatus cs;
@@ -568,47 +578,14 @@ static pit_status solve_packed(pit_batch* b, bool* used_graph) {
         BCK(cudaGraphLaunch(b->exec, b->stream));
         BCK(cudaEventRecord(b->e1, b->stream));
         BCK(cudaStreamSynchronize(b->stream));
-        *used_graph = true;
+        float f = 0.f;
+        BCK(cudaEventElapsedTime(&f, b->e0, b->e1));
+        ms = f;
+        used_graph = true;
         if (b->h_ctl[1] == ST_ETIMEOUT) return bfail(b, PIT_ETIMEOUT, "batch kernel: a device wait ran out of budget");
         if (b->h_ctl[1] == ST_EDIVERGED) return bfail(b, PIT_EDIVERGED, "batch kernel: NaN/Inf in a problem");
-        return PIT_OK;
-    }
-    double ms = 0.0;
-    return run_direct(b, &ms);
-}
-
-extern "C" pit_status pit_batch_solve(pit_batch* b, pit_batch_info* info) {
-    if (!b) return PIT_EINVAL;
-    bool used_graph = false;
-    // the caller's stream may hold the producers of the problems' data
-    BCK(cudaEventRecord(b->ev_user, b->user_stream));
-    BCK(cudaStreamWaitEvent(b->stream, b->ev_user, 0));
-    BCK(cudaEventRecord(b->ea, b->stream));
-    double ms_solo = 0.0, ms_packed = 0.0;
-    for (size_t j = 0; j < b->solo_ctx.size(); ++j) {
-        BCK(cudaEventRecord(b->e0, b->stream));
-        BRET(solve_solo(b, j));
-        BCK(cudaEventRecord(b->e1, b->stream));
-        BCK(cudaEventSynchronize(b->e1));
-        float f = 0.f;
-        BCK(cudaEventElapsedTime(&f, b->e0, b->e1));
-        ms_solo += f;
-    }
-    if (!b->packed_idx.empty()) {
-        BRET(solve_packed(b, &used_graph));
-        float f = 0.f;
-        BCK(cudaEventElapsedTime(&f, b->e0, b->e1));
-        ms_packed = f;
-    }
-    BCK(cudaEventRecord(b->eb, b->stream));
-    BCK(cudaEventSynchronize(b->eb));
-    float fall = 0.f;
-    BCK(cudaEventElapsedTime(&fall, b->ea, b->eb));
-    for (size_t j = 0; j < b->solo_idx.size(); ++j) {
-        const int i = b->solo_idx[j];
-        b->h_res[i] = b->solo_res[j];
-        b->h_iters[i] = b->solo_iters[j];
-        b->h_iters[b->count + i] = b->solo_wconv[j];
+    } else {
+        BRET(run_direct(b, &ms));
     }
     int conv = 0;
     for (int i = 0; i < b->count; ++i) conv += (b->h_res[i] <= b->opt.tol_res);
@@ -620,12 +597,10 @@ extern "C" pit_status pit_batch_solve(pit_batch* b, pit_batch_info* info) {
         info->max_team = b->max_team;
         info->converged = conv;
         info->graph = used_graph ? 1 : 0;
-        info->ms = fall;
+        info->ms = ms;
         info->est_makespan_ms = b->est_ms;
         info->ms_tuning = b->ms_tuning;
-        info->solo = (int)b->solo_idx.size();
-        info->ms_solo = ms_solo;
-        info->ms_packed = ms_packed;
+        info->wave_jobs = b->wave_jobs;
     }
     if (conv < b->count) return bfail(b, PIT_ENOCONV, "%d of %d problems did not reach tol_res", b->count - conv, b->count);
     return PIT_OK;
@@ -641,11 +616,9 @@ extern "C" pit_status pit_batch_result(const pit_batch* b, int i, double* res_in
     return PIT_OK;
 }
 
-extern "C" pit_status pit_batch_placement(const pit_batch* b, int i, int* solo, int* teams, int* team_ctas) {
+extern "C" pit_status pit_batch_placement(const pit_batch* b, int i, int* teams, int* team_ctas) {
     if (!b || i < 0 || i >= b->count) return PIT_EINVAL;
-    const int j = b->solo_of.empty() ? -1 : b->solo_of[i];
-    if (solo) *solo = j >= 0;
-    if (teams) *teams = j >= 0 ? b->solo_K[j] : 1;
+    if (teams) *teams = b->teams_of.empty() ? 0 : b->teams_of[i];
     if (team_ctas) *team_ctas = b->team_of.empty() ? 0 : b->team_of[i];
     return PIT_OK;
 }
@@ -654,10 +627,6 @@ extern "C" const char* pit_batch_last_error(const pit_batch* b) { return b ? b->
 
 extern "C" void pit_batch_destroy(pit_batch* b) {
     if (!b) return;
-    for (pit_ctx* c : b->solo_ctx) pit_destroy(c);
-    cudaFree(b->d_scratch);
-    if (b->ea) cudaEventDestroy(b->ea);
-    if (b->eb) cudaEventDestroy(b->eb);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     cudaFree(b->d_inst);

@@ -1284,7 +1284,8 @@ struct WaveArgs {
     int* abort_flag;
     int* status;
     int* stop;                          // [0] stop flag, [1] first converged iteration (K > 1; may be null)
-    int* kconv;                         // one team (K = 1): CTA 0 writes the converged iteration (may be null)
+    int* kconv;                         // one team (K = 1): CTA 0 writes the converged iteration; several
+                                        // teams of a batch: -2 marks a diverged window (may be null)
     // per iteration records, indexed by k
     double* res_inf;                    // [k_end] ||R_k||_inf
     double* cell_prefix;                // [k_end][M] max_{j <= n} ||r^j_k||_inf (written by CTA 0 of the team)
@@ -1539,6 +1540,13 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 if (threadIdx.x == 0) {
                     if (a.K == 1) {
                         if (b == 0 && a.kconv) *a.kconv = -2;
+                    } else if (a.kconv) {
+                        // several teams on one problem of a batch, whose abort word is the
+                        // job's own: mark the window diverged and end it for every team
+                        // (every wait watches that word); the batch retries a shorter window
+                        *a.kconv = -2;
+                        __threadfence();
+                        atomicExch(a.abort_flag, 1);
                     } else {
                         team_fail(c, ST_EDIVERGED);
                     }
@@ -1581,7 +1589,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 if (threadIdx.x == 0) {
                     if (b == 0) {
                         __stcg(a.cell_prefix + (size_t)k * M + n, prefix);
-                        a.cell_iters[(size_t)k * M + n] = used == 1 ? iters + 1 : -(iters + 1);
+                        if (a.cell_iters) a.cell_iters[(size_t)k * M + n] = used == 1 ? iters + 1 : -(iters + 1);
                     }
                     __threadfence();
                     st_release_u64(my_prog + b, a.cell_base + (unsigned long long)k * M + n + 1);
@@ -1655,24 +1663,37 @@ struct BatchInstance {
     int* converged_windows;             // out
 };
 
-// Job of one CTA: CTA `rank` of a team of G CTAs on instance `inst`. Jobs are listed
-// per CTA in one global order, so the lowest unfinished job always has all of its
-// CTAs (no cyclic waits). The team's workspace is given by offsets into the pools.
+// Job of one CTA: CTA `rank` of team `tk` of K teams of G CTAs on instance `inst`
+// (K = 1: one team runs the Newton iterations of a window one after another; K > 1:
+// a wavefront job, team tk runs iterations tk, tk + K, ... with several in flight).
+// Jobs are listed per CTA in one global order, so the lowest unfinished job always
+// has all of its CTAs (no cyclic waits). The job's workspace is given by offsets
+// into the pools.
 struct BatchJob {
     int inst, rank, G;
-    int team;                           // index of the team's workspace
+    int team;                           // index of the job's workspace
+    int K, tk;
 };
 
 struct BatchTeamWs {
-    double* pub;                        // [2][G][2][nx]
-    unsigned long long* flags;          // [G]
-    double* red_part;                   // [4][G][4]
-    unsigned long long* red_cnt;        // [4]
-    unsigned long long* prog;           // [G]
+    double* pub;                        // [K][2][G][2][nx]
+    unsigned long long* flags;          // [K][G]
+    double* red_part;                   // [K][4][G][4]
+    unsigned long long* red_cnt;        // [K][4]
+    unsigned long long* prog;           // [K][G]
     double* cell_prefix;                // [newton_max][window]
-    int* kconv;                         // converged iteration of the current window (CTA 0 only)
-    unsigned long long* tpub;           // [2][G][kDeepSlotRows][nx][2] tagged words (zeroed per launch)
-    unsigned long long* tred;           // [4][G][kTagRedWords] tagged reduction words (zeroed per launch)
+    int* kconv;                         // K = 1: converged iteration of the current window (CTA 0 only);
+                                        // K > 1: -2 when the window diverged
+    int* stop;                          // K > 1: [0] stop flag, [1] first converged iteration
+    int* jabort;                        // K > 1: the job's abort word (a diverged window, or a wait that gave up)
+    int* jstatus;                       // the job's status word: a level solve that breaks down or produces
+                                        // NaN ends its window (retried shorter), not the launch
+    unsigned long long* jbar;           // K > 1: arrivals at the job-wide barrier
+    unsigned long long* jres;           // K > 1: final ||R||_inf as an order-preserving key (max over teams)
+    unsigned long long* tpub;           // [K][2][G][kDeepSlotRows][nx][2] tagged words (zeroed per launch)
+    unsigned long long* tred;           // [K][4][G][kTagRedWords] tagged reduction words (zeroed per launch)
+    unsigned long long* sync_words;     // flags, prog, red_cnt and the tagged words: zeroed again after a
+    size_t sync_count;                  // window that ended on the job's abort word
 };
 
 struct BatchArgs {
@@ -1696,40 +1717,75 @@ __device__ __forceinline__ bool team_barrier(const TeamCtl& c, Team& t, double* 
     return reduce_finish<1, true>(c, t, reduce_arrive<1>(t, v), v, red + 32, s_ok);
 }
 
+// Barrier over all CTAs of a wavefront job: arrival count `target` = (barriers
+// passed so far + 1) x CTAs of the job. The fences order each CTA's earlier writes
+// before its arrival and the others' writes before its departure.
+__device__ __forceinline__ bool job_barrier(const TeamCtl& c, unsigned long long* cnt, unsigned long long target,
+                                            int* s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(cnt, 1ull);
+        *s_ok = wait_geq(c, cnt, target) ? 1 : 0;
+        __threadfence();
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
 template <int NT, typename T>
 __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigned char* smem, int& s_ok) {
     const BatchInstance& in = ba.inst[job.inst];
     const BatchTeamWs& ws = ba.ws[job.team];
     const OpConst& oc = in.c;
     const int nx = oc.nx, ny = oc.ny, M = oc.M;
-    const int G = job.G, b = job.rank;
+    const int G = job.G, b = job.rank, K = job.K, tk = job.tk;
     const int rows_base = ny / G, rows_rem = ny % G;
     TeamCtl c{ba.abort_flag, ba.status, ba.wait_budget, ba.max_iter};
     Team t;
-    team_init(t, b, G, nx, ny, rows_base, rows_rem, ws.pub, ws.flags, ws.red_part, ws.red_cnt);
+    team_init(t, b, G, nx, ny, rows_base, rows_rem, ws.pub + (size_t)tk * 2 * G * 2 * nx, ws.flags + (size_t)tk * G,
+              ws.red_part + (size_t)tk * 4 * G * 4, ws.red_cnt + (size_t)tk * 4);
     const long long Ns = t.Ns;
     const long long off0 = (long long)t.r0 * nx;
     const int nloc = t.nloc;
     const int cap = (rows_base + (rows_rem ? 1 : 0)) * nx;
     double* red = smem_layout<T>(smem, cap, nx).red;
     const int W = in.window > 0 ? in.window : M;
+    const bool lead = tk == 0 && b == 0;          // reports the results
+    const unsigned long long job_ctas = (unsigned long long)K * G;
+    unsigned long long jep = 0;                   // job-wide barriers passed (K > 1)
     unsigned long long base = 0;
     int iters_total = 0, conv_windows = 0;
+    __shared__ int s_kdone;
     // Windows adapt: a window whose Newton diverges or does not converge is halved and
     // restarted from the plain guess at its first level; after a success the window
     // length grows back toward W.
     int w = W;
     for (int s = 0; s < M;) {
         const int Mw = min(w, M - s);
-        // plain guess for the window from its previous level: own rows only
+        // plain guess for the window from its previous level: own rows only, levels
+        // tk, tk + K, ... by team tk
         const double* from = s == 0 ? in.u0 : in.U + (long long)(s - 1) * Ns;
-        for (int n = 0; n < Mw; ++n) {
+        for (int n = tk; n < Mw; n += K) {
             double* dst = in.U + (long long)(s + n) * Ns + off0;
             for (int i = threadIdx.x; i < nloc; i += NT) dst[i] = __ldcg(from + off0 + i);
         }
+        if (threadIdx.x == 0 && lead) {
+            if (K > 1) {
+                ws.stop[0] = 0;
+                ws.stop[1] = 0x7fffffff;
+                *ws.jabort = 0;
+            }
+            *ws.kconv = -1;
+            *ws.jstatus = 0;
+        }
         __syncthreads();
         if (threadIdx.x == 0) __threadfence();
-        if (!team_barrier<NT>(c, t, red, &s_ok)) return;  // neighbours' rows are filled
+        if (K == 1) {
+            if (!team_barrier<NT>(c, t, red, &s_ok)) return;  // neighbours' rows are filled
+        } else if (!job_barrier(c, ws.jbar, job_ctas * ++jep, &s_ok)) {
+            return;
+        }
         WaveArgs a{};
         a.c = oc;
         a.c.M = Mw;
@@ -1737,7 +1793,7 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
         a.bc = in.bc ? in.bc + (long long)s * (2 * nx + 2 * ny) : nullptr;
         a.q = in.q ? in.q + (long long)s * Ns : nullptr;
         a.U = in.U + (long long)s * Ns;
-        a.K = 1;
+        a.K = K;
         a.G = G;
         a.rows_base = rows_base;
         a.rows_rem = rows_rem;
@@ -1761,37 +1817,76 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
         a.red_part = ws.red_part;
         a.red_cnt = ws.red_cnt;
         a.prog = ws.prog;
-        a.abort_flag = ba.abort_flag;
-        a.status = ba.status;
-        a.stop = nullptr;
+        // several teams: the job's own abort word, so that a diverged window ends every
+        // team's waits without ending the launch
+        a.abort_flag = K > 1 ? ws.jabort : ba.abort_flag;
+        a.status = ws.jstatus;
+        a.stop = K > 1 ? ws.stop : nullptr;
         a.res_inf = nullptr;
         a.cell_prefix = ws.cell_prefix;
         a.cell_iters = nullptr;
         a.cta_sumsq = nullptr;
         a.timers = nullptr;
-        // converged iteration index (or -1 / -2 for not converged / diverged): written
-        // by CTA 0 of the team; the decision below must be the same on every CTA, so it
-        // goes through a team reduction
-        __shared__ int s_kdone;
-        a.kconv = b == 0 ? ws.kconv : nullptr;
-        if (threadIdx.x == 0 && b == 0) *ws.kconv = -1;
+        // K = 1: CTA 0 writes the converged iteration (or -1 / -2 for not converged /
+        // diverged); K > 1: any CTA marks a diverged window, the stop words give the
+        // first converged iteration
+        a.kconv = (K > 1 || b == 0) ? ws.kconv : nullptr;
         if (in.conv) {
-            if (in.nlv) wave_body<NT, true, true, T>(a, 0, b, t, smem, s_ok);
-            else wave_body<NT, true, false, T>(a, 0, b, t, smem, s_ok);
+            if (in.nlv) wave_body<NT, true, true, T>(a, tk, b, t, smem, s_ok);
+            else wave_body<NT, true, false, T>(a, tk, b, t, smem, s_ok);
         } else {
-            if (in.nlv) wave_body<NT, false, true, T>(a, 0, b, t, smem, s_ok);
-            else wave_body<NT, false, false, T>(a, 0, b, t, smem, s_ok);
+            if (in.nlv) wave_body<NT, false, true, T>(a, tk, b, t, smem, s_ok);
+            else wave_body<NT, false, false, T>(a, tk, b, t, smem, s_ok);
         }
         if (threadIdx.x == 0) {
+            // a wait that gave up is the launch's failure; other codes are the window's
+            if (ld_acquire_s32(ws.jstatus) == ST_ETIMEOUT) atomicCAS(ba.status, 0, ST_ETIMEOUT);
             s_ok = ld_acquire_s32(ba.abort_flag);
             s_kdone = b == 0 ? *ws.kconv : 0;
         }
         __syncthreads();
         if (s_ok) return;  // the launch aborts (read once per CTA)
-        double kv[1] = {b == 0 ? (double)(s_kdone + 3) : 0.0};  // CTA 0's result, shared by max
-        double kg[1];
-        if (!reduce_finish<1, true>(c, t, reduce_arrive<1>(t, kv), kg, red + 32, &s_ok)) return;
-        const int kdone = (int)kg[0] - 3;
+        int kdone;
+        if (K == 1) {
+            // the decision must be the same on every CTA: CTA 0's result, shared by max
+            double kv[1] = {b == 0 ? (double)(s_kdone + 3) : 0.0};
+            double kg[1];
+            if (!reduce_finish<1, true>(c, t, reduce_arrive<1>(t, kv), kg, red + 32, &s_ok)) return;
+            kdone = (int)kg[0] - 3;
+        } else {
+            // every team has left the window: the flags are final; read them, then let
+            // the lead CTA reset them only after everyone has read
+            if (!job_barrier(c, ws.jbar, job_ctas * ++jep, &s_ok)) return;
+            if (threadIdx.x == 0) {
+                const int kc = ld_acquire_s32(ws.kconv);
+                const int st = ld_acquire_s32(ws.stop);
+                const int k1 = ld_acquire_s32(ws.stop + 1);
+                const int ja = ld_acquire_s32(ws.jabort);
+                // the job's abort word without a diverged window: a wait gave up (fatal)
+                s_kdone = ja ? (kc == -2 ? -2 : -3) : (kc == -2 ? -2 : (st != 0 && k1 != 0x7fffffff ? k1 : -1));
+                s_ok = ja;
+            }
+            __syncthreads();
+            kdone = s_kdone;
+            const bool reset = s_ok != 0;
+            __syncthreads();
+            if (kdone == -3) {
+                if (threadIdx.x == 0 && lead) team_fail(c, ST_ETIMEOUT);
+                return;
+            }
+            if (reset) {
+                // the teams left the window at different points: restart the job's
+                // synchronisation from a clean state (zeroed words, fresh counters)
+                const size_t per = (ws.sync_count + job_ctas - 1) / job_ctas;
+                const size_t r = (size_t)tk * G + b;
+                const size_t lo = r * per, hi = lo + per < ws.sync_count ? lo + per : ws.sync_count;
+                for (size_t i = lo + threadIdx.x; i < hi; i += NT) ws.sync_words[i] = 0ull;
+            }
+            if (!job_barrier(c, ws.jbar, job_ctas * ++jep, &s_ok)) return;
+            if (reset)
+                team_init(t, b, G, nx, ny, rows_base, rows_rem, ws.pub + (size_t)tk * 2 * G * 2 * nx,
+                          ws.flags + (size_t)tk * G, ws.red_part + (size_t)tk * 4 * G * 4, ws.red_cnt + (size_t)tk * 4);
+        }
         base += (unsigned long long)ba.newton_max * Mw + 1;
         if (kdone >= 0) {
             iters_total += kdone + 1;
@@ -1809,12 +1904,18 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
         }
         __syncthreads();
     }
-    // final residual of the whole solution, all levels (needs the neighbours' last updates)
+    // final residual of the whole solution, all levels (needs the neighbours' last
+    // updates; with several teams every team's updates): team tk takes the levels
+    // tk, tk + K, ...
     if (threadIdx.x == 0) __threadfence();
-    if (!team_barrier<NT>(c, t, red, &s_ok)) return;
+    if (K > 1) {
+        if (!job_barrier(c, ws.jbar, job_ctas * ++jep, &s_ok)) return;
+    } else if (!team_barrier<NT>(c, t, red, &s_ok)) {
+        return;
+    }
     double rmax = 0.0;
     const int nb = 2 * nx + 2 * ny;
-    for (int n = 0; n < M; ++n) {
+    for (int n = tk; n < M; n += K) {
         const double* Un = in.U + (long long)n * Ns;
         const double* Up = n == 0 ? in.u0 : in.U + (long long)(n - 1) * Ns;
         const double* bnd = in.bc ? in.bc + (long long)n * nb : nullptr;
@@ -1838,7 +1939,13 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
     double v[1] = {key_val(block_max_u64<NT>(abs_key(rmax), reinterpret_cast<unsigned long long*>(red)))};
     double g[1];
     if (!reduce_finish<1, true>(c, t, reduce_arrive<1>(t, v), g, red + 32, &s_ok)) return;
-    if (b == 0 && threadIdx.x == 0) {
+    if (K > 1) {
+        // the teams' maxima meet in one key word
+        if (threadIdx.x == 0 && b == 0) atomicMax(ws.jres, abs_key(g[0]));
+        if (!job_barrier(c, ws.jbar, job_ctas * ++jep, &s_ok)) return;
+        if (threadIdx.x == 0 && lead) g[0] = key_val(ld_acquire_u64(ws.jres));
+    }
+    if (lead && threadIdx.x == 0) {
         *in.res_inf = g[0];
         *in.newton_iters = iters_total;
         *in.converged_windows = conv_windows;
@@ -1848,7 +1955,7 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
 
 // Persistent launch over a batch: CTA c works through its job list in order.
 template <int NT, typename T>
-__global__ void __launch_bounds__(NT) batch_kernel(BatchArgs ba) {
+__global__ void __launch_bounds__(NT, 1) batch_kernel(BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_ok;
     const int c = blockIdx.x;

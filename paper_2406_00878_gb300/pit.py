@@ -48,7 +48,7 @@ class pit_options(ctypes.Structure):
                 ("eta_max", ctypes.c_double), ("eta_gamma", ctypes.c_double), ("lin_atol", ctypes.c_double),
                 ("lin_max_iter", ctypes.c_int), ("sor_rho_max", ctypes.c_double), ("team_ctas", ctypes.c_int),
                 ("wait_budget", ctypes.c_longlong), ("wave_teams", ctypes.c_int), ("precision", ctypes.c_int),
-                ("window", ctypes.c_int), ("batch_solo_nodes", ctypes.c_int)]
+                ("window", ctypes.c_int), ("batch_wave_nodes", ctypes.c_int)]
 
 
 class pit_step_info(ctypes.Structure):
@@ -91,7 +91,7 @@ class pit_batch_info(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int), ("ctas", ctypes.c_int), ("teams", ctypes.c_int), ("min_team", ctypes.c_int),
                 ("max_team", ctypes.c_int), ("converged", ctypes.c_int), ("graph", ctypes.c_int),
                 ("ms", ctypes.c_double), ("est_makespan_ms", ctypes.c_double), ("ms_tuning", ctypes.c_double),
-                ("solo", ctypes.c_int), ("ms_solo", ctypes.c_double), ("ms_packed", ctypes.c_double)]
+                ("wave_jobs", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -174,7 +174,7 @@ def lib():
                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
             L.pit_batch_result.restype = st
             L.pit_batch_placement.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
-                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+                                              ctypes.POINTER(ctypes.c_int)]
             L.pit_batch_placement.restype = st
             L.pit_batch_last_error.argtypes = [P]
             L.pit_batch_last_error.restype = ctypes.c_char_p
@@ -499,12 +499,11 @@ def pit_batch_result(batch: Batch, i: int) -> dict:
 
 
 def pit_batch_placement(batch: Batch, i: int) -> dict:
-    """Where problem i runs: alone through the wavefront path (solo, with `teams` Newton
-    iterations in flight of `team_ctas` CTAs each) or in the persistent launch."""
-    so, te, tc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    batch._check(lib().pit_batch_placement(batch.handle, int(i), ctypes.byref(so), ctypes.byref(te),
-                                           ctypes.byref(tc)))
-    return {"solo": bool(so.value), "teams": te.value, "team_ctas": tc.value}
+    """How problem i is solved: `teams` teams of `team_ctas` CTAs (teams > 1: a wavefront
+    job with that many Newton iterations in flight)."""
+    te, tc = ctypes.c_int(), ctypes.c_int()
+    batch._check(lib().pit_batch_placement(batch.handle, int(i), ctypes.byref(te), ctypes.byref(tc)))
+    return {"teams": te.value, "team_ctas": tc.value}
 
 
 def pit_batch_destroy(batch: Batch):

@@ -23,29 +23,32 @@ def _problems():
     ]
 
 
-# solo = batch_solo_nodes: 65536 (default) sends the 256 x 256 problem through the
-# wavefront path and packs the rest; 0 packs every problem; 1 solves every one alone
-@pytest.mark.parametrize("prec,team,window,solo", [(0, 0, 0, 65536), (1, 0, 0, 0), (0, 3, 2, 0), (1, 5, 4, 65536),
+def _wave_job(p, wave_nodes):
+    return wave_nodes > 0 and p.grid.nx * p.grid.ny >= wave_nodes
+
+
+# wave = batch_wave_nodes: 65536 (default) makes the 256 x 256 problem a wavefront job
+# (several teams, Newton iterations in flight) and packs the rest; 0 packs every
+# problem; 1 makes every problem a wavefront job
+@pytest.mark.parametrize("prec,team,window,wave", [(0, 0, 0, 65536), (1, 0, 0, 0), (0, 3, 2, 0), (1, 5, 4, 65536),
                                                    (1, 0, 4, 1), (0, 0, 2, 1)])
-def test_batch_matches_oracle_per_problem(prec, team, window, solo):
+def test_batch_matches_oracle_per_problem(prec, team, window, wave):
     probs = _problems()
     opt = pit.pit_default_options()
-    assert opt.batch_solo_nodes == 65536
-    opt.precision, opt.team_ctas, opt.window, opt.batch_solo_nodes = prec, team, window, solo
+    assert opt.batch_wave_nodes == 65536
+    opt.precision, opt.team_ctas, opt.window, opt.batch_wave_nodes = prec, team, window, wave
     with pit.pit_batch_create(probs, opt) as batch:
         for i, p in enumerate(probs):
             where = pit.pit_batch_placement(batch, i)
-            assert where["solo"] == (solo > 0 and p.grid.nx * p.grid.ny >= solo), (i, where)
-            assert where["team_ctas"] >= 1 and where["teams"] >= 1
+            assert (where["teams"] > 1) == _wave_job(p, wave), (i, where)
+            assert where["team_ctas"] >= 1 and where["teams"] * where["team_ctas"] <= 160
         results = []
         for rep in range(2):  # the second solve replays the captured graph
             status, info = pit.pit_batch_solve(batch)
             assert info["converged"] == len(probs)
             results.append([t["U"].cpu().numpy().copy() for t in batch.tensors])
-        n_solo = sum(solo > 0 and p.grid.nx * p.grid.ny >= solo for p in probs)
-        assert info["solo"] == n_solo
-        assert info["graph"] == (1 if n_solo < len(probs) else 0)
-        assert info["ms"] >= info["ms_solo"] + info["ms_packed"] - 1e-3
+        assert info["graph"] == 1
+        assert info["wave_jobs"] == sum(_wave_job(p, wave) for p in probs)
         for i, p in enumerate(probs):
             r = pit.pit_batch_result(batch, i)
             assert r["res_inf"] <= 1e-12
@@ -55,20 +58,67 @@ def test_batch_matches_oracle_per_problem(prec, team, window, solo):
             np.testing.assert_array_equal(results[0][i], results[1][i])
 
 
-@pytest.mark.parametrize("solo", [0, 1])
-def test_batch_unconverged_problems_report_their_true_residual(solo):
-    """With one Newton update allowed, no problem converges: the batch says so, and the
-    residual it reports for each is the oracle's residual of the U it returned (for a
-    solo problem that stopped early, taken over all levels)."""
+@pytest.mark.parametrize("wave", [0, 1])
+def test_batch_unconverged_problems_report_their_true_residual(wave):
+    """With two Newton updates allowed, no problem converges: the batch says so, and the
+    residual it reports for each is the oracle's residual of the U it returned."""
     probs = _problems()[:4]
     opt = pit.pit_default_options()
-    opt.newton_max, opt.batch_solo_nodes, opt.window = 1, solo, 4
+    opt.newton_max, opt.batch_wave_nodes, opt.window = 2, wave, 4
     with pit.pit_batch_create(probs, opt) as batch:
         status, info = pit.pit_batch_solve(batch, check=False)
         assert status == pit.PIT_ENOCONV and info["converged"] < len(probs)
+        assert info["wave_jobs"] == (len(probs) if wave else 0)
         for i, p in enumerate(probs):
             r = pit.pit_batch_result(batch, i)
             U = batch.tensors[i]["U"].cpu().numpy().reshape(p.M, -1)
             R = oracle.residual(p.grid, p.params, p.M, p.dt, p.u0, U, p.bc, p.q)
             ro = float(np.abs(R).max())
             assert abs(r["res_inf"] - ro) <= 1e-9 * ro + 1e-15, (i, r["res_inf"], ro)
+
+
+def _source_driven_burgers():
+    """Burgers on 32 x 32, nu = 0.02, tau = 0.05, u0 = 0, a steady source
+    50 sin(2 pi x) sin(pi y): u grows to ~6 over 8 levels (cell Reynolds/CFL ~10).
+    The oracle's all-at-once Newton from the plain guess converges on windows of 1, 2
+    and 4 levels (6, 7, 9 updates) but diverges on all 8 (residual past 1e12)."""
+    g = W.Grid(32, 32)
+    X, Y = g.nodes()
+    q = np.tile((50.0 * np.sin(2 * np.pi * X) * np.sin(np.pi * Y)).ravel(), (8, 1))
+    return W.Problem("burgers_source32x8", g, W.Params(W.BURGERS, 0.02, 0.0), 8, 0.05, np.zeros(g.ns), None,
+                     np.ascontiguousarray(q))
+
+
+@pytest.mark.parametrize("wave", [0, 1])
+def test_batch_restarts_diverged_windows(wave):
+    """A window whose Newton diverges is restarted shorter, in a packed team and in a
+    wavefront job (whose teams all leave the window and restart their synchronisation).
+    A problem with a NaN in u0 diverges in every window and ends unconverged without
+    disturbing the others."""
+    div = _source_driven_burgers()
+    for Mw, ok_ in ((4, True), (8, False)):
+        _, it, res, _ = oracle.newton_all_at_once(div.grid, div.params, Mw, div.dt, div.u0, np.tile(div.u0, Mw),
+                                                  q=div.q[:Mw], maxit=30)
+        assert (it >= 0) == ok_ and (ok_ or not (np.nanmax(res) < 1e10))
+    nan = W.truncated(W.burgers256(0), 3)
+    nan.u0 = nan.u0.copy()
+    nan.u0[1000] = np.nan
+    ok = W.random_problem(63, 9, 13, 3, W.BURGERS)
+    probs = [div, nan, ok]
+    opt = pit.pit_default_options()
+    opt.window, opt.batch_wave_nodes = 8, wave
+    with pit.pit_batch_create(probs, opt) as batch:
+        for rep in range(2):
+            status, info = pit.pit_batch_solve(batch, check=False)
+            r = [pit.pit_batch_result(batch, i) for i in range(3)]
+            assert status == pit.PIT_ENOCONV and info["converged"] == 2, (status, r)
+            assert info["wave_jobs"] == (3 if wave else 0)
+            assert not (r[1]["res_inf"] <= 1e-12)
+            for i in (0, 2):
+                p = probs[i]
+                assert r[i]["res_inf"] <= 1e-12
+                Uo = oracle.sequential_bdf1(p.grid, p.params, p.M, p.dt, p.u0, p.bc, p.q)[0]
+                Ug = batch.tensors[i]["U"].cpu().numpy().reshape(p.M, -1)
+                assert np.abs(Ug - Uo).max() <= 1e-10 * np.abs(Uo).max(), (i, rep)
+            # the first window (all 8 levels) did not converge: it was split
+            assert r[0]["windows_converged"] > 1, r[0]
