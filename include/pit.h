@@ -91,7 +91,8 @@ typedef struct {
     double lin_atol;        /* absolute floor of SOR's error tolerance (default 1e-15); BiCGStab stops
                                relative to its Jacobi-scaled rhs */
     int lin_max_iter;       /* cap on sweeps / iterations per level solve (default 4000) */
-    double sor_rho_max;     /* AUTO uses SOR below this Gershgorin bound (default 0.99) */
+    double sor_rho_max;     /* AUTO uses SOR below this Gershgorin bound (default 0.999; below 1 SOR
+                               converges: symmetric levels are SPD, nonsymmetric ones get omega <= ~1) */
     int team_ctas;          /* CTAs that share one level in the chain kernel (0 = auto) */
     long long wait_budget;  /* spin iterations before a device wait gives up (default 1<<26) */
     int wave_teams;         /* pit_solve: Newton iterations in flight in the wavefront kernel

@@ -133,7 +133,7 @@ extern "C" void pit_default_options(pit_options* o) {
     o->eta_gamma = 1.0;
     o->lin_atol = 1e-15;
     o->lin_max_iter = 4000;
-    o->sor_rho_max = 0.99;
+    o->sor_rho_max = 0.999;
     o->team_ctas = 0;
     o->wait_budget = 1ll << 26;
     o->wave_teams = 0;
