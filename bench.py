@@ -75,7 +75,9 @@ def _dist():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms from before the warm-up
+    (the tool takes a while to start); only samples that arrive between region_start()
+    and region_end() describe the timed region."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
@@ -83,12 +85,13 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
-        self.lines = []
+        self.lines = []          # (arrival time, line)
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.dev), "-lms", "200"], stdout=subprocess.PIPE,
+                                          "-i", str(self.dev), "-lms", "50"], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -98,7 +101,13 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def region_start(self):
+        self.t0 = time.monotonic()
+
+    def region_end(self):
+        self.t1 = time.monotonic()
 
     def __exit__(self, *exc):
         if self.proc:
@@ -111,7 +120,8 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        inside = [ln for t, ln in self.lines if self.t0 is not None and self.t0 <= t <= (self.t1 or t) + 0.05]
+        for ln in inside:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -149,19 +159,21 @@ def run_ours(args, ws, rank, local):
             pit.pit_fill_plain_guess(ctx, U)
             return pit.pit_solve(ctx, U)[1]
 
-        for _ in range(max(args.warmup, 0)):
-            info = step()
-        stream.synchronize()
-        D.barrier()
-        torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         infos = []
         with ClockSampler(local) as clk:
+            for _ in range(max(args.warmup, 0)):
+                info = step()
+            stream.synchronize()
+            D.barrier()
+            torch.cuda.synchronize()
+            clk.region_start()
             e0.record(stream)
             for _ in range(args.steps):
                 infos.append(step())
             e1.record(stream)
             e1.synchronize()
+            clk.region_end()
         torch.cuda.synchronize()
         D.barrier()
         ms = D.max_over_ranks(e0.elapsed_time(e1) / args.steps, device="cuda")
@@ -443,7 +455,7 @@ def run_reference(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--levels", type=int, default=256)

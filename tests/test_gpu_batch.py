@@ -122,3 +122,25 @@ def test_batch_restarts_diverged_windows(wave):
                 assert np.abs(Ug - Uo).max() <= 1e-10 * np.abs(Uo).max(), (i, rep)
             # the first window (all 8 levels) did not converge: it was split
             assert r[0]["windows_converged"] > 1, r[0]
+
+
+@pytest.mark.parametrize("wave", [0, 1])
+def test_batch_wait_timeout_is_reported_and_the_device_stays_usable(wave):
+    """A wait budget of one poll: the first team or job wait that is not satisfied at
+    once gives up, the launch ends with PIT_ETIMEOUT (no fault, no hang), and a fresh
+    batch on the same device then solves to the oracle's solution."""
+    probs = _problems()[:3]
+    opt = pit.pit_default_options()
+    opt.wait_budget, opt.team_ctas, opt.batch_wave_nodes = 1, 4, wave  # fixed teams: no autotuner runs
+    with pit.pit_batch_create(probs, opt) as batch:
+        status, _ = pit.pit_batch_solve(batch, check=False)
+        assert status == pit.PIT_ETIMEOUT, status
+        assert "budget" in pit.lib().pit_batch_last_error(batch.handle).decode()
+    opt = pit.pit_default_options()
+    opt.batch_wave_nodes = wave
+    with pit.pit_batch_create(probs[:1], opt) as batch:
+        status, info = pit.pit_batch_solve(batch)
+        assert info["converged"] == 1
+        Uo, _, _, _ = oracle.solve(probs[0], tol=1e-13)
+        Ug = batch.tensors[0]["U"].cpu().numpy().reshape(probs[0].M, -1)
+        assert np.abs(Ug - Uo).max() <= 1e-10 * np.abs(Uo).max()
