@@ -14,12 +14,26 @@ LIB = os.path.join(OUT_DIR, "libpit.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
+# compiled once per level-solve precision and closure set (see that file)
+BATCH_KERNELS = "pit_batch_kernels.cu"
+
+
 def sources():
-    return [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith(".cu")]
+    return [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith(".cu") and f != BATCH_KERNELS]
+
+
+def units():
+    """(source, extra flags, object tag) of every compilation, the slowest first."""
+    out = [(s, [], os.path.basename(s)[:-3]) for s in sources()]
+    bk = os.path.join(CSRC, BATCH_KERNELS)
+    sets = sorted(range(1, 16), key=lambda c: -bin(c).count("1"))  # more closures compile longer
+    out[1:1] = [(bk, [f"-DPIT_BK_FP32={f}", f"-DPIT_BK_CLOSURES={c}"], f"bk_{f}_{c}") for c in sets for f in (0, 1)]
+    return out
 
 
 def _deps():
-    deps = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    deps = sources() + [os.path.join(CSRC, BATCH_KERNELS)]
+    deps += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     deps += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     return deps
 
@@ -32,19 +46,38 @@ def nvcc() -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every csrc/*.cu into paper_2406_00878_gb300/_build/libpit.so (skipped when up to date)."""
+    """Compile every csrc/*.cu into paper_2406_00878_gb300/_build/libpit.so (skipped when up to date).
+    The compilations run in parallel (one nvcc each, at most one per CPU), then one nvcc call links."""
     os.makedirs(OUT_DIR, exist_ok=True)
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in _deps()):
             return LIB
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-shared",
-           f"-I{INCLUDE}", f"-I{CSRC}", "-o", tmp, *sources()]
+    tag = f"{os.getpid()}"
+    flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O2", f"-I{INCLUDE}", f"-I{CSRC}"]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
+        flags.insert(0, "-Xptxas=-v")
+    jobs = units()
+    objs = [os.path.join(OUT_DIR, f"{name}.{tag}.o") for _, _, name in jobs]
+
+    def compile_one(i):
+        src, extra, _ = jobs[i]
+        return subprocess.run([nvcc(), *flags, *extra, "-c", src, "-o", objs[i]]).returncode
+
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=max(1, os.cpu_count() or 1)) as pool:
+        codes = list(pool.map(compile_one, range(len(jobs))))
+    try:
+        for (src, extra, _), c in zip(jobs, codes):
+            if c != 0:
+                raise subprocess.CalledProcessError(c, f"nvcc -c {src} {' '.join(extra)}")
+        tmp = LIB + f".{tag}.tmp"
+        subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs], check=True)
+        os.replace(tmp, LIB)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 

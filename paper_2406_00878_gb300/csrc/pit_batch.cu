@@ -28,7 +28,7 @@
 using namespace pit;
 
 namespace {
-constexpr int kNT = 256;
+constexpr int kNT = kBatchThreads;
 constexpr int kMaxTeam = 160;
 constexpr int kMinLocal = 256;   // wavefront teams: at least this many unknowns per CTA
 constexpr int kMaxWaveTeams = 6;
@@ -47,6 +47,8 @@ struct pit_batch {
     std::vector<int> team_of;          // CTAs per team, per problem
     std::vector<int> teams_of;         // teams per problem: K for a wavefront job, 1 otherwise
     int wave_jobs = 0;
+    int closures = 0;                  // set of the problems' closures (closure_bit)
+    const void* kfn = nullptr;         // the batched kernel compiled for that set
     // device data
     BatchInstance* d_inst = nullptr;
     BatchJob* d_jobs = nullptr;
@@ -97,9 +99,19 @@ static pit_status bfail(pit_batch* b, pit_status s, const char* fmt, ...) {
         if (s_ != PIT_OK) return s_; \
     } while (0)
 
-static const void* batch_fn(bool fp32) {
-    return fp32 ? reinterpret_cast<const void*>(batch_kernel<kNT, float>)
-                : reinterpret_cast<const void*>(batch_kernel<kNT, double>);
+// The batched kernel of every precision and closure set, one per compilation of
+// pit_batch_kernels.cu: pit_batch_kernel_<fp32>_<set>().
+#define PIT_BK_SETS(X, f) \
+    X(f, 1) X(f, 2) X(f, 3) X(f, 4) X(f, 5) X(f, 6) X(f, 7) X(f, 8) X(f, 9) X(f, 10) X(f, 11) X(f, 12) X(f, 13) X(f, 14) X(f, 15)
+#define PIT_BK_DECL(f, c) __attribute__((visibility("hidden"))) const void* pit_batch_kernel_##f##_##c();
+#define PIT_BK_ENTRY(f, c) pit_batch_kernel_##f##_##c,
+PIT_BK_SETS(PIT_BK_DECL, 0)
+PIT_BK_SETS(PIT_BK_DECL, 1)
+
+static const void* batch_fn(bool fp32, int closures) {
+    using Getter = const void* (*)();
+    static const Getter table[2][16] = {{nullptr, PIT_BK_SETS(PIT_BK_ENTRY, 0)}, {nullptr, PIT_BK_SETS(PIT_BK_ENTRY, 1)}};
+    return closures >= 1 && closures <= 15 ? table[fp32 ? 1 : 0][closures]() : nullptr;
 }
 
 static size_t team_smem(bool fp32, int nx, int ny, int G) {
@@ -344,8 +356,7 @@ static pit_status enqueue_launch(pit_batch* b, bool timed) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (timed) BCK(cudaEventRecord(b->e0, b->stream));
-    if (b->fp32) BCK(cudaLaunchKernelEx(&cfg, batch_kernel<kNT, float>, a));
-    else BCK(cudaLaunchKernelEx(&cfg, batch_kernel<kNT, double>, a));
+    BCK(cudaLaunchKernelEx(&cfg, reinterpret_cast<void (*)(BatchArgs)>(const_cast<void*>(b->kfn)), a));
     if (timed) BCK(cudaEventRecord(b->e1, b->stream));
     BCK(cudaMemcpyAsync(b->h_res, b->d_res, sizeof(double) * b->count, cudaMemcpyDeviceToHost, b->stream));
     BCK(cudaMemcpyAsync(b->h_iters, b->d_iters, sizeof(int) * 2 * b->count, cudaMemcpyDeviceToHost, b->stream));
@@ -396,12 +407,17 @@ extern "C" pit_status pit_batch_create(const pit_instance* inst, int count, cons
         BCK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         BCK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         if (!coop) return bfail(b, PIT_EUNSUPPORTED, "device lacks cooperative launch");
+        // the kernel compiled for exactly this batch's closures
+        for (int i = 0; i < count; ++i)
+            b->closures |= closure_bit(inst[i].params.equation == PIT_BURGERS, inst[i].params.mu_b != 0.0);
+        b->kfn = batch_fn(b->fp32, b->closures);
+        if (!b->kfn) return bfail(b, PIT_EUNSUPPORTED, "no batched kernel for closure set %d", b->closures);
         cudaFuncAttributes fa;
-        BCK(cudaFuncGetAttributes(&fa, batch_fn(b->fp32)));
+        BCK(cudaFuncGetAttributes(&fa, b->kfn));
         b->dyn_max = (size_t)optin - fa.sharedSizeBytes;
-        BCK(cudaFuncSetAttribute(batch_fn(b->fp32), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->dyn_max));
+        BCK(cudaFuncSetAttribute(b->kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->dyn_max));
         int per = 0;
-        BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_fn(b->fp32), kNT, b->dyn_max));
+        BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, b->kfn, kNT, b->dyn_max));
         if (per < 1) return bfail(b, PIT_EUNSUPPORTED, "batch kernel does not fit on an SM");
         BCK(cudaMalloc(&b->d_res, sizeof(double) * count));
         BCK(cudaMalloc(&b->d_iters, sizeof(int) * 2 * count));

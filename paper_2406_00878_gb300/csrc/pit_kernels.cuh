@@ -1733,7 +1733,27 @@ __device__ __forceinline__ bool job_barrier(const TeamCtl& c, unsigned long long
     return *s_ok != 0;
 }
 
-template <int NT, typename T>
+// Closures of a batched launch as a set: bit (2 conv + nlv). A batched kernel is compiled
+// for one set and holds only those closures' wave bodies: holding all four made every
+// job's code measurably slower than the dedicated wavefront kernel's (a heat problem:
+// 99.6 ms with all four, 81.3 ms with its own only, 78.0 ms in the wavefront kernel).
+__host__ __device__ constexpr int closure_bit(bool conv, bool nlv) { return 1 << ((conv ? 2 : 0) + (nlv ? 1 : 0)); }
+constexpr int kBatchThreads = 256;  // threads per CTA of every batched kernel
+
+template <int NT, int CLOSURES, typename T>
+__device__ __forceinline__ void wave_body_of(const WaveArgs& a, int bit, int team, int b, Team& t, unsigned char* smem,
+                                             int& s_ok) {
+    if constexpr ((CLOSURES & closure_bit(true, true)) != 0)
+        if (bit == closure_bit(true, true)) return wave_body<NT, true, true, T>(a, team, b, t, smem, s_ok);
+    if constexpr ((CLOSURES & closure_bit(true, false)) != 0)
+        if (bit == closure_bit(true, false)) return wave_body<NT, true, false, T>(a, team, b, t, smem, s_ok);
+    if constexpr ((CLOSURES & closure_bit(false, true)) != 0)
+        if (bit == closure_bit(false, true)) return wave_body<NT, false, true, T>(a, team, b, t, smem, s_ok);
+    if constexpr ((CLOSURES & closure_bit(false, false)) != 0)
+        if (bit == closure_bit(false, false)) return wave_body<NT, false, false, T>(a, team, b, t, smem, s_ok);
+}
+
+template <int NT, int CLOSURES, typename T>
 __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigned char* smem, int& s_ok) {
     const BatchInstance& in = ba.inst[job.inst];
     const BatchTeamWs& ws = ba.ws[job.team];
@@ -1831,13 +1851,8 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
         // diverged); K > 1: any CTA marks a diverged window, the stop words give the
         // first converged iteration
         a.kconv = (K > 1 || b == 0) ? ws.kconv : nullptr;
-        if (in.conv) {
-            if (in.nlv) wave_body<NT, true, true, T>(a, tk, b, t, smem, s_ok);
-            else wave_body<NT, true, false, T>(a, tk, b, t, smem, s_ok);
-        } else {
-            if (in.nlv) wave_body<NT, false, true, T>(a, tk, b, t, smem, s_ok);
-            else wave_body<NT, false, false, T>(a, tk, b, t, smem, s_ok);
-        }
+        // the host launches a kernel whose set holds every problem's closure
+        wave_body_of<NT, CLOSURES, T>(a, closure_bit(in.conv != 0, in.nlv != 0), tk, b, t, smem, s_ok);
         if (threadIdx.x == 0) {
             // a wait that gave up is the launch's failure; other codes are the window's
             if (ld_acquire_s32(ws.jstatus) == ST_ETIMEOUT) atomicCAS(ba.status, 0, ST_ETIMEOUT);
@@ -1953,15 +1968,16 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
     __syncthreads();
 }
 
-// Persistent launch over a batch: CTA c works through its job list in order.
-template <int NT, typename T>
+// Persistent launch over a batch: CTA c works through its job list in order. CLOSURES is
+// the set of closures (closure_bit) this instance can run.
+template <int NT, typename T, int CLOSURES>
 __global__ void __launch_bounds__(NT, 1) batch_kernel(BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_ok;
     const int c = blockIdx.x;
     for (int j = ba.job_off[c]; j < ba.job_off[c + 1]; ++j) {
         const BatchJob job = ba.jobs[j];
-        batch_instance<NT, T>(ba, job, smem, s_ok);
+        batch_instance<NT, CLOSURES, T>(ba, job, smem, s_ok);
         __syncthreads();
         if (threadIdx.x == 0) s_ok = ld_acquire_s32(ba.abort_flag);
         __syncthreads();

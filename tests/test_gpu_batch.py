@@ -144,3 +144,29 @@ def test_batch_wait_timeout_is_reported_and_the_device_stays_usable(wave):
         Uo, _, _, _ = oracle.solve(probs[0], tol=1e-13)
         Ug = batch.tensors[0]["U"].cpu().numpy().reshape(probs[0].M, -1)
         assert np.abs(Ug - Uo).max() <= 1e-10 * np.abs(Uo).max()
+
+
+def _closure_problem(bit, seed):
+    """A small problem of one closure: bit = closure index 2 conv + nlv."""
+    conv, nlv = bool(bit & 2), bool(bit & 1)
+    eq = W.BURGERS if conv else W.HEAT
+    return W.random_problem(seed, 11, 9, 3, eq, with_bc=bool(seed & 1), mu_a=0.05 if conv else 0.5,
+                            mu_b=(0.3 if nlv else 0.0))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_every_closure_set_has_its_kernel(prec):
+    """Each of the 15 non-empty sets of closures (Burgers/heat x constant/variable
+    viscosity) is solved by the batched kernel compiled for that set, per precision:
+    one problem of every closure in the set, each equal to the oracle's solution."""
+    for closures in range(1, 16):
+        probs = [_closure_problem(c, 100 + 4 * closures + c) for c in range(4) if closures >> c & 1]
+        opt = pit.pit_default_options()
+        opt.precision, opt.team_ctas, opt.batch_wave_nodes = prec, 2, 0
+        with pit.pit_batch_create(probs, opt) as batch:
+            status, info = pit.pit_batch_solve(batch)
+            assert info["converged"] == len(probs), closures
+            for i, p in enumerate(probs):
+                Uo, _, _, _ = oracle.solve(p, tol=1e-13)
+                Ug = batch.tensors[i]["U"].cpu().numpy().reshape(p.M, -1)
+                assert np.abs(Ug - Uo).max() <= 1e-10 * np.abs(Uo).max(), (closures, i)
