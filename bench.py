@@ -46,9 +46,9 @@ FLOPS_PER_BICGSTAB_ITER = 2 * 9 + 6 * 2 + 5 * 2
 # DRAM bytes (read + write) of one wavefront launch on this workload, from the ncu capture
 # summarised in profiles/wave_kernel_burgers256_full.md (traffic line); valid only for the kernel sources it
 # was taken on (their SHA-256 below), reported as null once they change.
-WAVE_TRAFFIC_BYTES = 145.633024e6 + 217.626624e6
+WAVE_TRAFFIC_BYTES = 150.245888e6 + 218.036480e6
 WAVE_TRAFFIC_SOURCES = {
-    "paper_2406_00878_gb300/csrc/pit_kernels.cuh": "4f3e875c026c4a22762306e45a22531dc081be08d8b20230955e99e75ee2715e",
+    "paper_2406_00878_gb300/csrc/pit_kernels.cuh": "d0c0755bdf6dcd374cde29a4a72450395dc7d97ed41aff712996a82f6b7c5bc6",
     "paper_2406_00878_gb300/csrc/pit.cu": "f27dee5af53374b9f63d06fefaead4dde0fb18186b383d6f3e4aeb8dc85a2a9e",
 }
 

@@ -1449,6 +1449,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 __syncthreads();
                 // 3. residual r^n_k, scaled couplings, rhs; uprev <- u^n_k
                 const double* qn = a.q ? a.q + (long long)n * Ns + off0 : nullptr;
+#pragma unroll 2
                 for (int i = threadIdx.x; i < nloc; i += NT) {
                     const int jl = i / nx, ii = i - jl * nx, j = t.r0 + jl;
                     const int ku = (jl + 1) * nx + ii;
