@@ -115,9 +115,17 @@ typedef struct {
                                job of the persistent launch (up to 6 teams, nearly every SM, several
                                Newton iterations of a window in flight), such jobs one after another;
                                <= 0 = one team per problem for all (default 65536, a 256 x 256 grid) */
+    int window_start;       /* where a window's Newton iteration starts (pit_solve with window > 0, and
+                               pit_batch_solve): PIT_START_PLAIN (default) = the plain guess
+                               u^n = u^{s-1} for every level of the window; PIT_START_GIVEN = the
+                               iterate the caller left in U_dev for those levels (a learned or
+                               coarse-grid guess). A window that is retried after a failure starts
+                               from the plain guess, as do later windows whose levels the failed
+                               attempt overwrote */
 } pit_options;
 
 enum { PIT_FP64 = 0, PIT_FP32_INNER = 1 };
+enum { PIT_START_PLAIN = 0, PIT_START_GIVEN = 1 };
 
 #define PIT_MAX_NEWTON 64
 
@@ -268,7 +276,8 @@ typedef struct {
     const double* u0_dev;   /* [Ns] initial data (required) */
     const double* bc_dev;   /* [M][2nx+2ny] Dirichlet data or NULL */
     const double* q_dev;    /* [M][Ns] source or NULL */
-    double* U_dev;          /* [M][Ns] out: the solution (its input content is ignored; every
+    double* U_dev;          /* [M][Ns] out: the solution; in: the starting iterate when
+                               opt->window_start = PIT_START_GIVEN (ignored otherwise: every
                                window starts from the plain guess at its first level) */
 } pit_instance;             /* all pointers caller-owned, valid until pit_batch_destroy */
 
@@ -338,6 +347,20 @@ pit_status pit_net_train_step(pit_net* net, const double* u0_dev, const float* l
 const char* pit_net_last_error(const pit_net* net);
 void pit_net_destroy(pit_net* net);
 
+/* One layer of the network above, without a network: the same tensor-core kernels on
+ * the caller's operands (for layer-by-layer checks, or nets of other shapes). NHWC BF16
+ * activations X [B][H][W][Cin], weights W [Cout][3][3][Cin] BF16, bias FP32 [Cout];
+ * Cin and Cout multiples of 16 (at most 4096).
+ * Forward: Y [B][H][W][Cout] = act(conv3x3(X, W) + bias (+ res)), zero padding, FP32
+ * accumulation, BF16 output; res (may be NULL) [B][H][W][Cout]; act = ReLU when relu != 0.
+ * Backward, for the loss L = sum(dY * conv3x3(X, W)): dX [B][H][W][Cin] BF16 (may be NULL),
+ * dW [Cout][3][3][Cin] FP32 and db [Cout] FP32 (device pointers).
+ * Both allocate their temporaries per call and synchronise `stream`. */
+pit_status pit_conv3x3_forward(const void* X_dev, const void* W_dev, const float* bias_dev, const void* res_dev,
+                               void* Y_dev, int B, int H, int W, int Cin, int Cout, int relu, void* stream);
+pit_status pit_conv3x3_backward(const void* X_dev, const void* W_dev, const void* dY_dev, void* dX_dev,
+                                float* dW_dev, float* db_dev, int B, int H, int W, int Cin, int Cout, void* stream);
+
 /* ---------------------------------------------------------------- literal product form
  * The decoupled systems of Theorem 1 (eq. 8) exactly as the paper states them, built
  * by the recursion of Sec. 5: P^1 = A_1, P^n = P^{n-1} A_n, r~^1 = r^1,
@@ -381,12 +404,14 @@ pit_status pit_solve_product(pit_ctx* ctx, double* U_dev, pit_solve_info* info);
  * synchronisation, or an embedding that owns all GPU memory itself. It needs no
  * context and allocates nothing: the caller passes the raw Jacobian entries
  * coef_dev [5][M][Ns] (C, W, E, S, N of every A_n, e.g. from pit_assemble) and
- * R_dev [M][Ns]; dU_dev [M][Ns] receives the nested block inverse of eq. 7 as in
- * pit_block_solve (level tolerance eta, solver choice from opt, NULL = defaults).
+ * R_dev [M][Ns]; dU_dev [M][Ns] receives the same block solve as pit_block_solve
+ * (level tolerance eta, solver choice from opt, NULL = defaults).
  * The level chain's team workspace is a static device array of about 2.7 MB in
  * this library, held by every GPU that loads it until the process exits. The
  * first call on a device looks up that array's device address (with the device
- * current); make that first call before any stream capture. Sizes beyond the
+ * current). Every call reads its status back and synchronises `stream`, so it must
+ * never be made while `stream` is being captured into a CUDA graph: such a call
+ * returns PIT_EUNSUPPORTED without doing anything. Sizes beyond the
  * workspace (nx > PIT_NOALLOC_MAX_NX, M > PIT_NOALLOC_MAX_LEVELS, a team larger
  * than PIT_NOALLOC_MAX_TEAM) return PIT_EUNSUPPORTED. All calls on a device share
  * the workspace: it is re-initialised at the start of each call, and calls that
@@ -396,6 +421,14 @@ pit_status pit_solve_product(pit_ctx* ctx, double* U_dev, pit_solve_info* info);
 pit_status pit_block_solve_noalloc(int nx, int ny, int M, const double* coef_dev, const double* R_dev,
                                    double* dU_dev, double eta, const pit_options* opt, void* stream, char* err,
                                    int err_len);
+
+/* Measurement helper, no counterpart in the paper: the fused multiply-add rate of
+ * this GPU in TFLOP/s (FMA = 2 flops), precision 0 = FP64, 1 = FP32. A full-occupancy
+ * grid runs eight independent FMA chains per thread; the best of five launches of
+ * about 40 ms, timed with CUDA events on `stream`, is written to *tflops. It is the
+ * peak that the FP64-bound level-chain kernels are compared against. Allocates a
+ * small output buffer and synchronises `stream`. PIT_EINVAL for another precision. */
+pit_status pit_probe_fma_peak(int precision, void* stream, double* tflops);
 
 /* Message for the last failing call on ctx (never NULL). */
 const char* pit_last_error(const pit_ctx* ctx);

@@ -34,8 +34,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pit_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "libpit_oracle.so")
+_OMP_PATH = os.path.join(_OUT_DIR, "libpit_oracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
+_use_omp = False
 
 HEAT, BURGERS = 0, 1
 SOLVER_AUTO, SOLVER_BAND_LU, SOLVER_BICGSTAB = 0, 1, 2
@@ -50,24 +52,45 @@ class _OgParams(ctypes.Structure):
     _fields_ = [("equation", ctypes.c_int), ("mu_a", ctypes.c_double), ("mu_b", ctypes.c_double)]
 
 
-def build(force: bool = False) -> str:
-    """Compile pit_oracle.c with gcc into oracle/_build/libpit_oracle.so."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile pit_oracle.c with gcc into oracle/_build/libpit_oracle.so (single-threaded,
+    the tested build) or, with openmp, libpit_oracle_omp.so (the timing build: the same
+    arithmetic with the element-independent loops spread over threads)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC,
-           "-lm"]
+    path = _OMP_PATH if openmp else _LIB_PATH
+    if not force and os.path.exists(path) and os.path.getmtime(path) >= os.path.getmtime(_SRC):
+        return path
+    tmp = path + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+    cmd += ["-fopenmp"] if openmp else []
+    cmd += ["-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
+
+
+def use_threads(n: int) -> int:
+    """Run the oracle's element-independent loops on n host threads (n > 1 loads the
+    OpenMP timing build; n <= 1 the single-threaded build). Results are bitwise the
+    same in both builds. Returns the thread count in use."""
+    global _use_omp
+    with _lock:
+        _use_omp = n > 1
+    if n > 1:
+        return int(_L().oracle_set_threads(int(n)))
+    return 1
 
 
 def _L():
-    global _lib
+    return _load(_use_omp)
+
+
+def _load(openmp: bool):
     with _lock:
+        _lib = _libs.get(openmp)
         if _lib is None:
-            _lib = ctypes.CDLL(build())
+            _lib = ctypes.CDLL(build(openmp=openmp))
+            _libs[openmp] = _lib
             D = ctypes.POINTER(ctypes.c_double)
             I = ctypes.POINTER(ctypes.c_int)
             G = ctypes.POINTER(_OgGrid)
@@ -87,6 +110,7 @@ def _L():
                 "oracle_newton_all_at_once": (c_int, [G, P, c_int, c_dbl, D, D, D, D, c_dbl, c_int, c_int, c_dbl, D,
                                                       D]),
                 "oracle_sequential_bdf1": (c_int, [G, P, c_int, c_dbl, D, D, D, D, c_dbl, c_int, c_int, c_dbl, I]),
+                "oracle_set_threads": (c_int, [c_int]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(_lib, name)

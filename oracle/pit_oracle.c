@@ -7,8 +7,12 @@
  * library: only the tests, the smoke check and the benchmark's CPU-baseline leg
  * load it.  It shares no code, header, table or helper with the CUDA path.
  *
- * Everything is IEEE FP64, single-threaded, written as plain loops in the order
- * and notation of the paper:
+ * Everything is IEEE FP64, written as plain loops in the order and notation of
+ * the paper. The default build is single-threaded; the timing build (-fopenmp)
+ * spreads only loops whose iterations are independent element by element -- the
+ * levels of the residual and the Jacobian, the rows of a matrix-vector product,
+ * the entries of a vector update -- so both builds return the same bits (dot
+ * products, norms and the level chain stay sequential):
  *   - eq. 3  spatial operator F (central convective fluxes, conservative viscous
  *            fluxes with mid-point viscosities) and the BDF1 time difference;
  *   - eq. 4  the all-at-once system over all time levels n = 1..N_t;
@@ -43,6 +47,21 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the timing build (no effect in the single-threaded build); returns the
+ * number of threads the parallel loops will use. */
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 typedef struct {
     int nx, ny;
@@ -122,6 +141,7 @@ void oracle_level_residual(const og_grid* g, const og_params* p, double dt, cons
 void oracle_residual(const og_grid* g, const og_params* p, int M, double dt, const double* u0,
                      const double* bc, const double* q, const double* U, double* R) {
     int Ns = g->nx * g->ny, nb = 2 * g->nx + 2 * g->ny;
+#pragma omp parallel for schedule(static)
     for (int n = 1; n <= M; ++n) {
         const double* u_prev = (n == 1) ? u0 : U + (size_t)(n - 2) * Ns;
         oracle_level_residual(g, p, dt, u_prev, U + (size_t)(n - 1) * Ns, bc ? bc + (size_t)(n - 1) * nb : NULL,
@@ -173,6 +193,7 @@ void oracle_jacobian(const og_grid* g, const og_params* p, int M, double dt, con
                      double* coef) {
     size_t Ns = (size_t)g->nx * g->ny, plane = (size_t)M * Ns;
     int nb = 2 * g->nx + 2 * g->ny;
+#pragma omp parallel for schedule(static)
     for (int n = 1; n <= M; ++n) {
         size_t o = (size_t)(n - 1) * Ns;
         oracle_level_jacobian(g, p, dt, U + o, bc ? bc + (size_t)(n - 1) * nb : NULL, coef + o, coef + plane + o,
@@ -183,6 +204,7 @@ void oracle_jacobian(const og_grid* g, const og_params* p, int M, double dt, con
 /* y = A x for one level's 5-point block; coefficient c of the level at cf[c*stride]. */
 void oracle_apply_A(int nx, int ny, const double* cf, size_t stride, const double* x, double* y) {
     const double *cC = cf, *cW = cf + stride, *cE = cf + 2 * stride, *cS = cf + 3 * stride, *cN = cf + 4 * stride;
+#pragma omp parallel for schedule(static) if (nx * ny >= 16384)
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             int k = j * nx + i;
@@ -277,25 +299,33 @@ int oracle_bicgstab(int nx, int ny, const double* cf, size_t stride, const doubl
         double rho = dot(rh, r, N);
         if (rho == 0.0) break;
         double beta = (rho / rho_old) * (alpha / omega);
-        for (int k = 0; k < N; ++k) pv[k] = r[k] + beta * (pv[k] - omega * v[k]);
-        for (int k = 0; k < N; ++k) ph[k] = pv[k] / diag[k];
+#pragma omp parallel for schedule(static) if (N >= 16384)
+        for (int k = 0; k < N; ++k) {
+            pv[k] = r[k] + beta * (pv[k] - omega * v[k]);
+            ph[k] = pv[k] / diag[k];
+        }
         oracle_apply_A(nx, ny, cf, stride, ph, v);
         double rv = dot(rh, v, N);
         if (rv == 0.0) break;
         alpha = rho / rv;
+#pragma omp parallel for schedule(static) if (N >= 16384)
         for (int k = 0; k < N; ++k) s[k] = r[k] - alpha * v[k];
         if (sqrt(dot(s, s, N)) <= rtol * bnorm) {
             for (int k = 0; k < N; ++k) x[k] += alpha * ph[k];
             ok = 1;
             break;
         }
+#pragma omp parallel for schedule(static) if (N >= 16384)
         for (int k = 0; k < N; ++k) sh[k] = s[k] / diag[k];
         oracle_apply_A(nx, ny, cf, stride, sh, t);
         double tt = dot(t, t, N);
         if (tt == 0.0) break;
         omega = dot(t, s, N) / tt;
-        for (int k = 0; k < N; ++k) x[k] += alpha * ph[k] + omega * sh[k];
-        for (int k = 0; k < N; ++k) r[k] = s[k] - omega * t[k];
+#pragma omp parallel for schedule(static) if (N >= 16384)
+        for (int k = 0; k < N; ++k) {
+            x[k] += alpha * ph[k] + omega * sh[k];
+            r[k] = s[k] - omega * t[k];
+        }
         if (sqrt(dot(r, r, N)) <= rtol * bnorm) ok = 1;
         if (omega == 0.0) break;
         rho_old = rho;

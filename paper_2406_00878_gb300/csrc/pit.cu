@@ -140,6 +140,7 @@ extern "C" void pit_default_options(pit_options* o) {
     o->precision = PIT_FP64;
     o->window = 0;
     o->batch_wave_nodes = 65536;
+    o->window_start = PIT_START_PLAIN;
 }
 
 extern "C" const char* pit_status_string(pit_status s) {
@@ -339,7 +340,8 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
     if (o.newton_max < 0 || o.newton_max > PIT_MAX_NEWTON || !(o.tol_res >= 0.0) || o.lin_solver < 0 ||
         o.lin_solver > 2 || !(o.eta_max > 0.0) || !(o.eta_gamma >= 0.0) || !(o.lin_atol >= 0.0) ||
         o.lin_max_iter < 1 || !(o.sor_rho_max > 0.0) || o.team_ctas < 0 || o.wait_budget < 1 || o.wave_teams < -1 ||
-        o.wave_teams > 64 || (o.precision != PIT_FP64 && o.precision != PIT_FP32_INNER) || o.window < 0) {
+        o.wave_teams > 64 || (o.precision != PIT_FP64 && o.precision != PIT_FP32_INNER) || o.window < 0 ||
+        (o.window_start != PIT_START_PLAIN && o.window_start != PIT_START_GIVEN)) {
         delete ctx;
         return PIT_EINVAL;
     }
@@ -794,13 +796,16 @@ static pit_status solve_wave(pit_ctx* ctx, double* U_dev, pit_solve_info* inf) {
     const int M = ctx->M;
     const int Wn = ctx->opt.window > 0 ? std::min(ctx->opt.window, M) : M;
     int w = Wn;
-    bool caller_iterate = Wn == M;  // the first attempt over all levels starts from the caller's U
+    // the caller's iterate is the start of the first attempt over all levels, and of every
+    // window with PIT_START_GIVEN, except on levels a failed attempt has overwritten
+    const bool given = Wn == M || ctx->opt.window_start == PIT_START_GIVEN;
+    int clean_from = 0;  // levels >= clean_from still hold the caller's iterate
     for (int s = 0; s < M;) {
         const int Mw = std::min(w, M - s);
-        if (!caller_iterate) CHECK_RET(fill_window_guess(ctx, U_dev, s, Mw));
-        caller_iterate = false;
+        if (!(given && s >= clean_from)) CHECK_RET(fill_window_guess(ctx, U_dev, s, Mw));
         int iters = 0;
         const pit_status st = solve_window(ctx, U_dev, s, Mw, inf, &iters);
+        if (st != PIT_OK) clean_from = std::max(clean_from, s + Mw);
         inf->windows += 1;
         inf->newton_iters_total += iters;
         inf->newton_iters = std::max(inf->newton_iters, iters);

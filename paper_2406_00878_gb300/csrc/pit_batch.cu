@@ -72,6 +72,7 @@ struct pit_batch {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     double est_ms = 0.0, ms_tuning = 0.0;
     int min_team = 0, max_team = 0;
+    bool calibrating = false;          // autotuner runs: plain starts on scratch iterates
     char err[512] = "";
 };
 
@@ -345,6 +346,7 @@ static pit_status enqueue_launch(pit_batch* b, bool timed) {
     a.method = b->opt.lin_solver;
     a.max_iter = b->opt.lin_max_iter;
     a.wait_budget = b->opt.wait_budget;
+    a.start_given = b->opt.window_start == PIT_START_GIVEN && !b->calibrating;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(b->ctas);
     cfg.blockDim = dim3(kNT);
@@ -385,6 +387,10 @@ extern "C" pit_status pit_batch_create(const pit_instance* inst, int count, cons
     pit_default_options(&b->opt);
     if (opt) b->opt = *opt;
     if (b->opt.window <= 0) b->opt.window = 32;
+    if (b->opt.window_start != PIT_START_PLAIN && b->opt.window_start != PIT_START_GIVEN) {
+        delete b;
+        return PIT_EINVAL;
+    }
     b->count = count;
     b->user_stream = static_cast<cudaStream_t>(stream);
     b->fp32 = b->opt.precision == PIT_FP32_INNER;
@@ -484,9 +490,25 @@ extern "C" pit_status pit_batch_create(const pit_instance* inst, int count, cons
                 }
             }
             std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> table;
+            // the calibration runs solve on a scratch iterate, so the problems' U_dev (which
+            // may hold the caller's starting iterate) stay untouched
+            size_t cal_n = 0;
+            for (auto& kv : rep) cal_n = std::max(cal_n, (size_t)std::min(inst[kv.second].M, 8) * kv.first.first * kv.first.second);
+            double* cal_U = nullptr;
+            BCK(cudaMalloc(&cal_U, sizeof(double) * std::max<size_t>(cal_n, 1)));
+            struct CalGuard {
+                pit_batch* b;
+                double* p;
+                ~CalGuard() {
+                    cudaFree(p);
+                    b->calibrating = false;
+                }
+            } guard{b, cal_U};
+            b->calibrating = true;
             for (auto& kv : rep) {
                 pit_instance cal = inst[kv.second];
                 cal.M = std::min(cal.M, 8);
+                cal.U_dev = cal_U;
                 for (int g : cand[kv.first]) {
                     std::vector<pit_instance> one{cal};
                     double best = 1e300;

@@ -1177,7 +1177,9 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
             rho_g = key_val(a.rho_key[n]);
             nonsym = a.rho_key[a.M + n] != 0ull;
         } else {
-            double rs = 0.0;
+            // row sums folded as order-preserving keys: a NaN entry gives a NaN bound
+            // (above +Inf), so the level goes to BiCGStab, which reports it
+            unsigned long long rs = 0ull;
             bool ns = false;
             for (int k = threadIdx.x; k < nloc; k += NT) {
                 const double d = 1.0 / cd[k];
@@ -1190,11 +1192,12 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
                 const double b = a.R[lo + k] + m.x[k];
                 m.bs[k] = d * b;
                 m.x[k] = b;
-                rs = fmax(rs, fabs(w) + fabs(e) + fabs(sv) + fabs(nv));
+                const unsigned long long kr = abs_key(fabs(w) + fabs(e) + fabs(sv) + fabs(nv));
+                rs = kr > rs ? kr : rs;
                 ns |= (w * e < 0.0 || sv * nv < 0.0);
             }
             double v[2];
-            v[0] = key_val(block_max_u64<NT>(abs_key(rs), reinterpret_cast<unsigned long long*>(m.red)));
+            v[0] = key_val(block_max_u64<NT>(rs, reinterpret_cast<unsigned long long*>(m.red)));
             v[1] = key_val(block_max_u64<NT>(ns ? abs_key(1.0) : 0ull, reinterpret_cast<unsigned long long*>(m.red)));
             double g[2];
             if (!reduce_finish<2, true>(c, t, reduce_arrive<2>(t, v), g, m.red + 32, &s_ok)) return;
@@ -1708,6 +1711,7 @@ struct BatchArgs {
     double tol_res, eta_max, eta_gamma, atol, sor_rho_max;
     int method, max_iter;
     long long wait_budget;
+    int start_given;                    // windows start from the iterate already in U (else the plain guess)
 };
 
 // A team-wide barrier built on the team reduction (every CTA of the team passes it
@@ -1782,14 +1786,18 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
     // restarted from the plain guess at its first level; after a success the window
     // length grows back toward W.
     int w = W;
+    int clean_from = 0;                           // levels >= clean_from still hold the caller's iterate
     for (int s = 0; s < M;) {
         const int Mw = min(w, M - s);
-        // plain guess for the window from its previous level: own rows only, levels
-        // tk, tk + K, ... by team tk
         const double* from = s == 0 ? in.u0 : in.U + (long long)(s - 1) * Ns;
-        for (int n = tk; n < Mw; n += K) {
-            double* dst = in.U + (long long)(s + n) * Ns + off0;
-            for (int i = threadIdx.x; i < nloc; i += NT) dst[i] = __ldcg(from + off0 + i);
+        // the same decision on every CTA of the job (s and clean_from are job-wide)
+        if (!(ba.start_given && s >= clean_from)) {
+            // plain guess for the window from its previous level: own rows only, levels
+            // tk, tk + K, ... by team tk
+            for (int n = tk; n < Mw; n += K) {
+                double* dst = in.U + (long long)(s + n) * Ns + off0;
+                for (int i = threadIdx.x; i < nloc; i += NT) dst[i] = __ldcg(from + off0 + i);
+            }
         }
         if (threadIdx.x == 0 && lead) {
             if (K > 1) {
@@ -1904,6 +1912,7 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
                           ws.flags + (size_t)tk * G, ws.red_part + (size_t)tk * 4 * G * 4, ws.red_cnt + (size_t)tk * 4);
         }
         base += (unsigned long long)ba.newton_max * Mw + 1;
+        if (kdone < 0) clean_from = max(clean_from, s + Mw);  // the failed attempt overwrote these levels
         if (kdone >= 0) {
             iters_total += kdone + 1;
             ++conv_windows;

@@ -608,3 +608,80 @@ extern "C" pit_status pit_net_train_step(pit_net* net, const double* u0_dev, con
     NCK(cudaGetLastError());
     return loss_out ? check_tc(net) : PIT_OK;
 }
+
+// ------------------------------------------------- one convolution layer, context-free
+//
+// The network's own tensor-core convolution kernels (the forward conv, the weight
+// gradient and the data gradient through the flipped weights), run on one layer's
+// operands. A scratch pit_net carries the shape, the stream and the temporaries of
+// the calls above; it owns nothing of the caller's.
+
+namespace {
+struct ScratchNet {
+    pit_net n;
+    ~ScratchNet() {
+        cudaFree(n.wf);
+        cudaFree(n.part);
+        cudaFree(n.g);
+        cudaFree(n.bias_part);
+        cudaFree(n.loss_part);
+        cudaFree(n.tc_err);
+    }
+};
+
+bool conv_args_ok(int B, int H, int Wd, int Cin, int Cout) {
+    return B >= 1 && H >= 1 && Wd >= 1 && Cin >= 16 && Cout >= 16 && Cin % 16 == 0 && Cout % 16 == 0 &&
+           Cin <= 4096 && Cout <= 4096;
+}
+}  // namespace
+
+extern "C" pit_status pit_conv3x3_forward(const void* X_dev, const void* W_dev, const float* bias_dev,
+                                          const void* res_dev, void* Y_dev, int B, int H, int Wd, int Cin, int Cout,
+                                          int relu, void* stream) {
+    if (!X_dev || !W_dev || !bias_dev || !Y_dev || !conv_args_ok(B, H, Wd, Cin, Cout)) return PIT_EINVAL;
+    ScratchNet s;
+    pit_net* net = &s.n;
+    net->shape.height = H;
+    net->shape.width = Wd;
+    net->stream = static_cast<cudaStream_t>(stream);
+    NCK(cudaMalloc(&net->tc_err, sizeof(int)));
+    NCK(cudaMemsetAsync(net->tc_err, 0, sizeof(int), net->stream));
+    if (pit_status st = launch_conv_tc(net, static_cast<const bf16*>(X_dev), static_cast<const bf16*>(W_dev), bias_dev,
+                                       static_cast<const bf16*>(res_dev), static_cast<bf16*>(Y_dev), B, Cin, Cout,
+                                       relu ? 1 : 0))
+        return st;
+    return check_tc(net);
+}
+
+extern "C" pit_status pit_conv3x3_backward(const void* X_dev, const void* W_dev, const void* dY_dev, void* dX_dev,
+                                           float* dW_dev, float* db_dev, int B, int H, int Wd, int Cin, int Cout,
+                                           void* stream) {
+    if (!X_dev || !W_dev || !dY_dev || !dW_dev || !db_dev || !conv_args_ok(B, H, Wd, Cin, Cout)) return PIT_EINVAL;
+    ScratchNet s;
+    pit_net* net = &s.n;
+    net->shape.height = H;
+    net->shape.width = Wd;
+    net->stream = static_cast<cudaStream_t>(stream);
+    const size_t nw = (size_t)Cout * 9 * Cin;
+    NCK(cudaMalloc(&net->tc_err, sizeof(int)));
+    NCK(cudaMalloc(&net->wf, sizeof(bf16) * nw));
+    NCK(cudaMalloc(&net->part, sizeof(float) * kMaxSplits * nw));
+    NCK(cudaMalloc(&net->g, sizeof(float) * (nw + Cout)));
+    NCK(cudaMalloc(&net->bias_part, sizeof(float) * kBiasBlocks * (size_t)Cout));
+    NCK(cudaMalloc(&net->loss_part, sizeof(float) * (1024 + 4096)));  // zero bias of the data gradient at +1024
+    NCK(cudaMemsetAsync(net->tc_err, 0, sizeof(int), net->stream));
+    NCK(cudaMemsetAsync(net->loss_part, 0, sizeof(float) * (1024 + 4096), net->stream));
+    net->wb = const_cast<bf16*>(static_cast<const bf16*>(W_dev));  // read only
+    Layer L;
+    L.cin = Cin;
+    L.cout = Cout;
+    L.cin_public = Cin;
+    L.w_off = 0;
+    L.b_off = nw;
+    if (pit_status st = conv_bwd(net, static_cast<const bf16*>(X_dev), static_cast<const bf16*>(dY_dev), L,
+                                 static_cast<bf16*>(dX_dev), B))
+        return st;
+    NCK(cudaMemcpyAsync(dW_dev, net->g, sizeof(float) * nw, cudaMemcpyDeviceToDevice, net->stream));
+    NCK(cudaMemcpyAsync(db_dev, net->g + nw, sizeof(float) * Cout, cudaMemcpyDeviceToDevice, net->stream));
+    return check_tc(net);
+}

@@ -14,7 +14,9 @@
 // exits. In host code its name is only a host-side stand-in, not a device
 // address, so the device address is fetched with cudaGetSymbolAddress once per
 // device, with that device current, the first time the entry point runs there.
-// Make that first call outside any stream capture. Every call on a device shares
+// Every call reads its status back into host memory and synchronises the stream,
+// so no call may be made while the stream is being captured into a CUDA graph:
+// such a call is refused with PIT_EUNSUPPORTED. Every call on a device shares
 // the one array and it keeps the last call's contents: the counters that must
 // start at zero are cleared at the start of each call, on the caller's stream.
 // Calls that overlap on the GPU (other streams, other host threads) race on the
@@ -95,6 +97,15 @@ extern "C" pit_status pit_block_solve_noalloc(int nx, int ny, int M, const doubl
         o.team_ctas < 0 || !(o.sor_rho_max > 0.0))
         return report(err, err_len, PIT_EINVAL, "invalid options");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    {
+        // the status read-back and the synchronisation below are illegal in a capture
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        const cudaError_t e = cudaStreamIsCapturing(st, &cap);
+        if (e != cudaSuccess) return report(err, err_len, PIT_ECUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(e));
+        if (cap != cudaStreamCaptureStatusNone)
+            return report(err, err_len, PIT_EUNSUPPORTED,
+                          "the stream is being captured: this call reads its status back and synchronises");
+    }
 
 #define NA_CK(call)                                                                                            \
     do {                                                                                                       \

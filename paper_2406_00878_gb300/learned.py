@@ -39,7 +39,8 @@ class LearnedConfig:
     lr: float = 1e-3
     seed: int = 0
     gen_window: int = 32          # windows for generating training solutions (robust Newton)
-    solve_window: int = 0         # windows for the evaluation solves (0 = all levels at once)
+    solve_window: int = 0         # windows for the per-problem evaluation solves (0 = all levels at once)
+    batch_window: int = 32        # windows of the batched evaluation forms
     chunk: int = 512              # problems per generation batch
     extra: dict = field(default_factory=dict)
 
@@ -106,35 +107,98 @@ def train(cfg: LearnedConfig, net, u0, lognu, targets):
     return losses, steps, time.perf_counter() - t0
 
 
-def evaluate(cfg: LearnedConfig, net, probs):
-    """Newton from the plain guess and from the learned guess for every problem."""
+def infer(cfg: LearnedConfig, net, probs, out):
+    """The network's starting iterates of all problems, cfg.batch at a time, into out
+    [S, M * Ns] (FP64, CUDA). Returns the device time in ms."""
     import torch
+    S, Ns = len(probs), cfg.n * cfg.n
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    u0 = torch.as_tensor(np.stack([np.ascontiguousarray(p.u0) for p in probs]), dtype=torch.float64, device="cuda")
+    lognu = np.array([np.log10(p.params.mu_a) for p in probs], dtype=np.float32)
+    ev0.record()
+    for b0 in range(0, S, cfg.batch):
+        B = min(cfg.batch, S - b0)
+        pit.pit_net_guess(net, u0[b0:b0 + B], lognu[b0:b0 + B], out[b0:b0 + B].view(B, cfg.M, Ns))
+    ev1.record()
+    ev1.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
+def _max_rel_diff(A, B, ok):
+    """max over problems i with ok[i] of max|A_i - B_i| / max|B_i| (CUDA tensors [S, DOF])."""
+    worst = 0.0
+    for i in range(A.shape[0]):
+        if ok[i]:
+            worst = max(worst, float((A[i] - B[i]).abs().max() / B[i].abs().max()))
+    return worst
+
+
+def evaluate(cfg: LearnedConfig, net, probs):
+    """Four forms of the solve on the same held-out problems, each to ||R||_inf <= 1e-12:
+
+      plain     pit_solve per problem, FP64 level solves, plain guess u^n = u^0;
+      learned   pit_solve per problem, FP64, from the network's guess (inference timed);
+      batched   one pit_batch launch for all problems, FP32 level solves inside FP64 Newton,
+                windows of cfg.batch_window levels from the plain guess;
+      combined  the network's guesses for all problems, then one pit_batch launch, FP32
+                level solves, every window starting from the guess (PIT_START_GIVEN)
+                (inference and the launch both timed).
+
+    Returns (rows, forms, solutions): per-problem records of the per-problem forms, a
+    summary per form, and the solutions of every form as CUDA tensors [S, M * Ns]."""
+    import torch
+    S, dof = len(probs), cfg.M * cfg.n * cfg.n
+    sol = {k: torch.empty((S, dof), dtype=torch.float64, device="cuda")
+           for k in ("plain", "learned", "batched", "combined")}
+    guess = torch.empty((S, dof), dtype=torch.float64, device="cuda")
+    infer(cfg, net, probs, guess)  # warm-up
+    ms_net = infer(cfg, net, probs, guess)
     opt = pit.pit_default_options()
     opt.window = cfg.solve_window
     rows = []
-    for p in probs:
+    for i, p in enumerate(probs):
         ctx = pit.context_for(p, opt)
-        U = torch.empty((1, p.M, p.grid.ns), dtype=torch.float64, device="cuda")
-        u0 = torch.as_tensor(np.ascontiguousarray(p.u0), device="cuda").reshape(1, -1)
-        # plain guess
-        pit.pit_fill_plain_guess(ctx, U.view(-1))
-        st_p, info_p = pit.pit_solve(ctx, U.view(-1), check=False)
-        U_plain = U.clone()
-        # learned guess: network inference is part of the timed work
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record()
-        pit.pit_net_guess(net, u0, np.array([np.log10(p.params.mu_a)], dtype=np.float32), U)
-        ev1.record()
-        ev1.synchronize()
-        ms_net = ev0.elapsed_time(ev1)
-        st_l, info_l = pit.pit_solve(ctx, U.view(-1), check=False)
-        diff = float((U - U_plain).abs().max() / U_plain.abs().max()) if st_p == 0 and st_l == 0 else float("nan")
+        U = sol["plain"][i]
+        pit.pit_fill_plain_guess(ctx, U)
+        st_p, info_p = pit.pit_solve(ctx, U, check=False)
+        U = sol["learned"][i]
+        U.copy_(guess[i])
+        st_l, info_l = pit.pit_solve(ctx, U, check=False)
         rows.append({"plain_ok": st_p == 0, "learned_ok": st_l == 0, "it_plain": info_p["newton_iters"],
                      "it_learned": info_l["newton_iters"], "ms_plain": info_p["ms_total"],
-                     "ms_learned": info_l["ms_total"] + ms_net, "ms_net": ms_net, "diff": diff,
+                     "ms_learned": info_l["ms_total"] + ms_net / S, "ms_net": ms_net / S,
                      "res0_plain": info_p["res_inf"][0], "res0_learned": info_l["res_inf"][0]})
         ctx.close()
-    return rows, U.view(p.M, -1).cpu().numpy()
+    ok = [r["plain_ok"] for r in rows]
+    forms = {}
+    n_ok = sum(ok)
+    forms["plain"] = {"ms": sum(r["ms_plain"] for r in rows), "converged": n_ok,
+                      "newton_iters_mean": float(np.mean([r["it_plain"] for r in rows]))}
+    forms["learned"] = {"ms": sum(r["ms_learned"] for r in rows), "converged": sum(r["learned_ok"] for r in rows),
+                        "newton_iters_mean": float(np.mean([r["it_learned"] for r in rows])), "ms_net": ms_net,
+                        "max_rel_diff_vs_plain": _max_rel_diff(sol["learned"], sol["plain"], ok)}
+    bopt = pit.pit_default_options()
+    bopt.precision = pit.PIT_FP32_INNER
+    bopt.window = cfg.batch_window
+    for name, start in (("batched", pit.PIT_START_PLAIN), ("combined", pit.PIT_START_GIVEN)):
+        bopt.window_start = start
+        Ub = sol[name]
+        if start == pit.PIT_START_GIVEN:
+            Ub.copy_(guess)
+        with pit.pit_batch_create(probs, bopt, U=list(Ub)) as batch:
+            # first solve: the launch is captured into a graph; time the replay after it
+            ms_guess = infer(cfg, net, probs, Ub) if start == pit.PIT_START_GIVEN else 0.0
+            pit.pit_batch_solve(batch, check=False)
+            ms_guess = infer(cfg, net, probs, Ub) if start == pit.PIT_START_GIVEN else 0.0
+            st, info = pit.pit_batch_solve(batch, check=False)
+            its = [pit.pit_batch_result(batch, i)["newton_iters"] for i in range(S)]
+        forms[name] = {"ms": info["ms"] + ms_guess, "ms_launch": info["ms"], "ms_net": ms_guess,
+                       "converged": info["converged"], "graph_replay": bool(info["graph"]),
+                       "newton_iters_mean": float(np.mean(its)), "window": cfg.batch_window,
+                       "max_rel_diff_vs_plain": _max_rel_diff(Ub, sol["plain"], ok)}
+    for f in forms.values():
+        f["dof_per_s"] = dof * S / (f["ms"] * 1e-3) if f["ms"] > 0 else None
+    return rows, forms, sol
 
 
 def train_flops_per_step(cfg: LearnedConfig) -> float:
@@ -150,15 +214,15 @@ def train_flops_per_step(cfg: LearnedConfig) -> float:
     return f
 
 
-def run(cfg: LearnedConfig) -> dict:
+def run(cfg: LearnedConfig, keep_solutions: bool = False) -> dict:
     import torch
     net = pit.pit_net_create(cfg.n, cfg.n, cfg.M, cfg.channels, cfg.blocks, max_batch=cfg.batch, seed=cfg.seed)
     train_probs = problems(cfg, 0, cfg.train)
     held = problems(cfg, 10_000_000, cfg.held_out)
     u0, lognu, targets, t_gen = generate(cfg, net, train_probs)
     losses, steps, t_train = train(cfg, net, u0, lognu, targets)
-    rows, last_U = evaluate(cfg, net, held)
-    del targets
+    del targets, u0
+    rows, forms, sol = evaluate(cfg, net, held)
     net.close()
     torch.cuda.synchronize()
     ok = [r for r in rows if r["plain_ok"] and r["learned_ok"]]
@@ -178,9 +242,13 @@ def run(cfg: LearnedConfig) -> dict:
         "dof_per_s_plain": dof * len(ok) / (sum(r["ms_plain"] for r in ok) * 1e-3) if ok else None,
         "dof_per_s_learned": dof * len(ok) / (sum(r["ms_learned"] for r in ok) * 1e-3) if ok else None,
         "ms_net_mean": float(np.mean([r["ms_net"] for r in rows])),
-        "max_rel_diff_solutions": max([r["diff"] for r in ok]) if ok else None,
-        "check_problem": held[-1], "check_solution": last_U,
+        "max_rel_diff_solutions": forms["learned"]["max_rel_diff_vs_plain"],
+        "forms": forms,
+        "check_problem": held[-1], "check_solution": sol["learned"][-1].view(cfg.M, -1).cpu().numpy(),
     }
+    if keep_solutions:
+        rep["held_out"] = held
+        rep["solutions"] = sol
     return rep
 
 

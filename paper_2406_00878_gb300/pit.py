@@ -21,6 +21,7 @@ PIT_OK, PIT_EINVAL, PIT_ECUDA, PIT_ENOMEM, PIT_ENOCONV, PIT_EDIVERGED, PIT_ETIME
 PIT_HEAT, PIT_BURGERS = 0, 1
 PIT_LIN_AUTO, PIT_LIN_SOR, PIT_LIN_BICGSTAB = 0, 1, 2
 PIT_FP64, PIT_FP32_INNER = 0, 1
+PIT_START_PLAIN, PIT_START_GIVEN = 0, 1
 PIT_MAX_NEWTON = 64
 PIT_NOALLOC_MAX_NX, PIT_NOALLOC_MAX_TEAM, PIT_NOALLOC_MAX_LEVELS = 512, 160, 4096
 
@@ -31,7 +32,8 @@ EXPORTS = ("pit_default_options", "pit_create", "pit_set_data", "pit_fill_plain_
            "pit_batch_solve", "pit_batch_result", "pit_batch_placement", "pit_batch_last_error", "pit_batch_destroy", "pit_net_param_count",
            "pit_net_create", "pit_net_get_params", "pit_net_set_params", "pit_net_guess", "pit_net_make_target",
            "pit_net_gradients", "pit_net_train_step", "pit_net_last_error", "pit_net_destroy",
-           "pit_product_form_solve", "pit_solve_product")
+           "pit_product_form_solve", "pit_solve_product", "pit_probe_fma_peak", "pit_conv3x3_forward",
+           "pit_conv3x3_backward")
 
 
 class pit_grid(ctypes.Structure):
@@ -48,7 +50,7 @@ class pit_options(ctypes.Structure):
                 ("eta_max", ctypes.c_double), ("eta_gamma", ctypes.c_double), ("lin_atol", ctypes.c_double),
                 ("lin_max_iter", ctypes.c_int), ("sor_rho_max", ctypes.c_double), ("team_ctas", ctypes.c_int),
                 ("wait_budget", ctypes.c_longlong), ("wave_teams", ctypes.c_int), ("precision", ctypes.c_int),
-                ("window", ctypes.c_int), ("batch_wave_nodes", ctypes.c_int)]
+                ("window", ctypes.c_int), ("batch_wave_nodes", ctypes.c_int), ("window_start", ctypes.c_int)]
 
 
 class pit_step_info(ctypes.Structure):
@@ -78,7 +80,8 @@ class pit_solve_info(ctypes.Structure):
                 "wave_launches": self.wave_launches, "ms_wave": self.ms_wave, "us_pred_wait": self.us_pred_wait,
                 "us_halo_wait": self.us_halo_wait, "us_reduce_wait": self.us_reduce_wait, "windows": self.windows,
                 "newton_iters_total": self.newton_iters_total, "us_setup": self.us_setup,
-                "us_level_solve": self.us_level_solve, "us_update": self.us_update}
+                "us_level_solve": self.us_level_solve, "us_update": self.us_update,
+                "windows_converged": self.windows_converged}
 
 
 class pit_instance(ctypes.Structure):
@@ -165,6 +168,8 @@ def lib():
             L.pit_block_solve_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, V, V, V, ctypes.c_double,
                                                   ctypes.POINTER(pit_options), V, ctypes.c_char_p, ctypes.c_int]
             L.pit_block_solve_noalloc.restype = st
+            L.pit_probe_fma_peak.argtypes = [ctypes.c_int, V, D]
+            L.pit_probe_fma_peak.restype = st
             L.pit_batch_create.argtypes = [ctypes.POINTER(pit_instance), ctypes.c_int, ctypes.POINTER(pit_options), V,
                                            ctypes.POINTER(P)]
             L.pit_batch_create.restype = st
@@ -202,6 +207,11 @@ def lib():
             L.pit_net_last_error.restype = ctypes.c_char_p
             L.pit_net_destroy.argtypes = [P]
             L.pit_net_destroy.restype = None
+            I = ctypes.c_int
+            L.pit_conv3x3_forward.argtypes = [V, V, V, V, V, I, I, I, I, I, I, V]
+            L.pit_conv3x3_forward.restype = st
+            L.pit_conv3x3_backward.argtypes = [V, V, V, V, V, V, I, I, I, I, I, V]
+            L.pit_conv3x3_backward.restype = st
             L.pit_product_form_solve.argtypes = [P, V, V, V, ctypes.POINTER(pit_product_info)]
             L.pit_product_form_solve.restype = st
             L.pit_solve_product.argtypes = [P, V, ctypes.POINTER(pit_solve_info)]
@@ -404,6 +414,20 @@ def pit_block_solve_noalloc(nx: int, ny: int, M: int, coef, R, dU, eta: float = 
     return s, msg
 
 
+def pit_probe_fma_peak(precision: int = 0, stream=None) -> float:
+    """Measured FMA rate of this GPU in TFLOP/s (precision 0 = FP64, 1 = FP32)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif not isinstance(stream, int):
+        stream = stream.cuda_stream
+    out = ctypes.c_double(0.0)
+    s = lib().pit_probe_fma_peak(int(precision), ctypes.c_void_p(stream), ctypes.byref(out))
+    if s != PIT_OK:
+        raise PitError(s, "pit_probe_fma_peak failed")
+    return float(out.value)
+
+
 # ------------------------------------------------------------- convenience
 
 def context_for(problem, opt: Optional[pit_options] = None, stream=None) -> Context:
@@ -449,8 +473,11 @@ class Batch:
             pass
 
 
-def pit_batch_create(problems, opt: Optional[pit_options] = None, stream=None) -> Batch:
-    """Upload a list of workloads.Problem and create a batch (runs the autotuner)."""
+def pit_batch_create(problems, opt: Optional[pit_options] = None, stream=None, U=None) -> Batch:
+    """Upload a list of workloads.Problem and create a batch (runs the autotuner).
+    U (optional): per problem a contiguous float64 CUDA tensor of M * Ns values that the
+    batch solves into (and starts from, with window_start = PIT_START_GIVEN); by default
+    the batch allocates them."""
     import torch
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
@@ -459,10 +486,12 @@ def pit_batch_create(problems, opt: Optional[pit_options] = None, stream=None) -
     arr = (pit_instance * len(problems))()
     tensors = []
     for i, p in enumerate(problems):
+        Ui = U[i] if U is not None else torch.empty(p.dof, dtype=torch.float64, device="cuda")
+        _dptr(Ui, f"U[{i}]", p.dof)
         t = {"u0": torch.as_tensor(np.ascontiguousarray(p.u0), dtype=torch.float64, device="cuda"),
              "bc": None if p.bc is None else torch.as_tensor(np.ascontiguousarray(p.bc), device="cuda"),
              "q": None if p.q is None else torch.as_tensor(np.ascontiguousarray(p.q), device="cuda"),
-             "U": torch.empty(p.dof, dtype=torch.float64, device="cuda")}
+             "U": Ui}
         tensors.append(t)
         g = p.grid
         arr[i].grid = pit_grid(int(g.nx), int(g.ny), float(g.xl), float(g.xr), float(g.yl), float(g.yr))
@@ -608,3 +637,49 @@ def pit_net_train_step(net: Net, u0, lognu, target, lr, want_loss=False):
 
 def pit_net_destroy(net: Net):
     net.close()
+
+
+def _tptr(t, name: str, dtype, numel: int):
+    """Device pointer of a contiguous CUDA tensor of the given dtype and size (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous {dtype} CUDA tensor")
+    if t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_of(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def pit_conv3x3_forward(X, Wt, bias, res, Y, B, H, Wd, Cin, Cout, relu, stream=None):
+    """One tensor-core conv layer: Y = act(conv3x3(X, Wt) + bias (+ res)), NHWC BF16."""
+    import torch
+    bf = torch.bfloat16
+    n = B * H * Wd
+    s = lib().pit_conv3x3_forward(_tptr(X, "X", bf, n * Cin), _tptr(Wt, "W", bf, Cout * 9 * Cin),
+                                  _tptr(bias, "bias", torch.float32, Cout), _tptr(res, "res", bf, n * Cout),
+                                  _tptr(Y, "Y", bf, n * Cout), B, H, Wd, Cin, Cout, int(bool(relu)),
+                                  ctypes.c_void_p(_stream_of(stream)))
+    if s != PIT_OK:
+        raise PitError(s, "pit_conv3x3_forward failed")
+
+
+def pit_conv3x3_backward(X, Wt, dY, dX, dW, db, B, H, Wd, Cin, Cout, stream=None):
+    """Gradients of sum(dY * conv3x3(X, Wt)): dX (BF16, may be None), dW and db (FP32)."""
+    import torch
+    bf = torch.bfloat16
+    n = B * H * Wd
+    s = lib().pit_conv3x3_backward(_tptr(X, "X", bf, n * Cin), _tptr(Wt, "W", bf, Cout * 9 * Cin),
+                                   _tptr(dY, "dY", bf, n * Cout), _tptr(dX, "dX", bf, n * Cin),
+                                   _tptr(dW, "dW", torch.float32, Cout * 9 * Cin),
+                                   _tptr(db, "db", torch.float32, Cout), B, H, Wd, Cin, Cout,
+                                   ctypes.c_void_p(_stream_of(stream)))
+    if s != PIT_OK:
+        raise PitError(s, "pit_conv3x3_backward failed")

@@ -30,10 +30,18 @@ def test_clock_record_keeps_the_timed_region_only():
 
 
 def test_traffic_is_withheld_for_other_sources(monkeypatch):
+    import hashlib
     assert bench.wave_traffic(128) is None                   # another workload size
     got = bench.wave_traffic(256)
     assert got is None or got == bench.WAVE_TRAFFIC_BYTES
-    monkeypatch.setitem(bench.WAVE_TRAFFIC_SOURCES, next(iter(bench.WAVE_TRAFFIC_SOURCES)), "0" * 64)
+    # a figure taken on the current sources is reported; one taken on other sources is not
+    rel = "paper_2406_00878_gb300/csrc/pit_kernels.cuh"
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        digest = hashlib.sha256(f.read()).hexdigest()
+    monkeypatch.setattr(bench, "WAVE_TRAFFIC_BYTES", 1.0e8)
+    monkeypatch.setattr(bench, "WAVE_TRAFFIC_SOURCES", {rel: digest})
+    assert bench.wave_traffic(256) == 1.0e8
+    monkeypatch.setattr(bench, "WAVE_TRAFFIC_SOURCES", {rel: "0" * 64})
     assert bench.wave_traffic(256) is None
 
 

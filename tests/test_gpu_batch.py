@@ -170,3 +170,62 @@ def test_every_closure_set_has_its_kernel(prec):
                 Uo, _, _, _ = oracle.solve(p, tol=1e-13)
                 Ug = batch.tensors[i]["U"].cpu().numpy().reshape(p.M, -1)
                 assert np.abs(Ug - Uo).max() <= 1e-10 * np.abs(Uo).max(), (closures, i)
+
+
+def test_full_size_batched_workload_every_problem_against_the_oracle():
+    # the 64-problem batched workload at full size, in the configuration the benchmark
+    # times (FP32 level solves, windows of 32, grids of 256^2 and up as wavefront jobs):
+    # for EVERY problem the oracle's residual of the returned solution at every level,
+    # and its first two levels against the oracle's own solve of those levels
+    import os
+    probs = W.batched(0)
+    opt = pit.pit_default_options()
+    opt.precision = pit.PIT_FP32_INNER
+    opt.window = 32
+    with pit.pit_batch_create(probs, opt) as batch:
+        status, info = pit.pit_batch_solve(batch)
+        assert info["converged"] == len(probs)
+        sols = [t["U"].cpu().numpy().reshape(p.M, -1) for t, p in zip(batch.tensors, probs)]
+    oracle.use_threads(len(os.sched_getaffinity(0)))   # bitwise the single-threaded oracle
+    try:
+        for i, (p, Ug) in enumerate(zip(probs, sols)):
+            R = oracle.residual(p.grid, p.params, p.M, p.dt, p.u0, Ug, p.bc, p.q)
+            assert np.isfinite(R).all() and np.abs(R).max() <= 2e-12, (i, float(np.abs(R).max()))
+            Uo, _, _, _ = oracle.solve(W.truncated(p, 2), tol=1e-13)
+            assert np.abs(Ug[:2] - Uo).max() <= 1e-10 * np.abs(Uo).max(), (i, p.name)
+    finally:
+        oracle.use_threads(1)
+
+
+@pytest.mark.parametrize("wave", [0, 1])
+def test_batch_starts_windows_from_the_given_iterate(wave):
+    # window_start = PIT_START_GIVEN: each window starts from the iterate the caller left in
+    # U. From a slightly perturbed solution Newton needs fewer updates than from the plain
+    # guess and reaches the same solution; from a wild start on one problem the window
+    # diverges, is retried from the plain guess, and still reaches the oracle's solution.
+    probs = _problems()[:4]
+    opt = pit.pit_default_options()
+    opt.window, opt.batch_wave_nodes = 3, wave
+    with pit.pit_batch_create(probs, opt) as batch:
+        pit.pit_batch_solve(batch)
+        exact = [t["U"].clone() for t in batch.tensors]
+        plain_iters = [pit.pit_batch_result(batch, i)["newton_iters"] for i in range(len(probs))]
+    opt.window_start = pit.PIT_START_GIVEN
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    starts = [u + 1e-7 * u.abs().max() * torch.randn(u.shape, generator=gen, device="cuda", dtype=torch.float64)
+              for u in exact]
+    starts[2] = 1e3 * torch.randn(exact[2].shape, generator=gen, device="cuda", dtype=torch.float64)
+    Us = [s.clone() for s in starts]
+    with pit.pit_batch_create(probs, opt, U=Us) as batch:
+        # the autotuner's calibration runs must leave the given iterates alone
+        for u, s in zip(Us, starts):
+            assert torch.equal(u, s)
+        status, info = pit.pit_batch_solve(batch)
+        assert info["converged"] == len(probs)
+        given_iters = [pit.pit_batch_result(batch, i)["newton_iters"] for i in range(len(probs))]
+        for i, p in enumerate(probs):
+            Uo, _, _, _ = oracle.solve(p, tol=1e-13)
+            Ug = Us[i].cpu().numpy().reshape(p.M, -1)
+            assert np.abs(Ug - Uo).max() <= 1e-10 * np.abs(Uo).max(), (i, p.name)
+    for i in (0, 1, 3):
+        assert given_iters[i] < plain_iters[i], (i, given_iters, plain_iters)

@@ -308,22 +308,36 @@ def test_fp32_inner_solves_reach_the_fp64_solution(make, name):
 
 def test_fp32_inner_full_size_burgers512():
     # the mixed-precision workload at full size (512 x 512, M = 1024, windows of 32
-    # levels): first levels against the oracle, and the oracle's residual on level
-    # windows across the range
+    # levels, the launch configuration the benchmark times): the first levels against
+    # the oracle's solution, the oracle's residual of the GPU solution at EVERY level
+    # (268 M unknowns; the all-at-once system has a bounded inverse, so a residual at
+    # round-off certifies the solution), and the whole solution against the FP64 GPU
+    # solve of the same problem
+    import os
     p = W.burgers512(0)
-    opt = pit.pit_default_options()
-    opt.precision = pit.PIT_FP32_INNER
-    opt.window = 32
-    with pit.context_for(p, opt) as ctx:
-        U = torch.empty(p.dof, dtype=torch.float64, device="cuda")
-        pit.pit_fill_plain_guess(ctx, U)
-        status, info = pit.pit_solve(ctx, U)
-        Ug = U.cpu().numpy().reshape(p.M, -1)
-    assert info["converged"]
+    sols = {}
+    for prec in (pit.PIT_FP32_INNER, pit.PIT_FP64):
+        opt = pit.pit_default_options()
+        opt.precision = prec
+        opt.window = 32
+        with pit.context_for(p, opt) as ctx:
+            U = torch.empty(p.dof, dtype=torch.float64, device="cuda")
+            pit.pit_fill_plain_guess(ctx, U)
+            status, info = pit.pit_solve(ctx, U)
+            assert info["converged"]
+            sols[prec] = U.cpu().numpy().reshape(p.M, -1)
+    Ug = sols[pit.PIT_FP32_INNER]
     Uo, _, _, _ = oracle.solve(W.truncated(p, 2), tol=1e-13)
     assert np.abs(Ug[:2] - Uo).max() <= 1e-10 * np.abs(Uo).max()
-    for start in (0, 511, 1020):
-        assert np.abs(_window_residual(p, Ug, start, 4)).max() <= 2e-12
+    oracle.use_threads(len(os.sched_getaffinity(0)))   # bitwise the single-threaded oracle
+    try:
+        R = oracle.residual(p.grid, p.params, p.M, p.dt, p.u0, Ug)
+    finally:
+        oracle.use_threads(1)
+    assert np.isfinite(R).all() and np.abs(R).max() <= 2e-12
+    del R
+    U64 = sols[pit.PIT_FP64]
+    assert np.abs(Ug - U64).max() <= 1e-10 * np.abs(U64).max()
 
 
 @pytest.mark.parametrize("window,teams,prec", [(1, 0, 0), (3, 2, 0), (4, 0, 1), (7, 3, 1)])
@@ -359,3 +373,39 @@ def test_a_smaller_context_does_not_break_a_larger_one():
         status, info = pit.pit_solve(cb, U)
     assert info["converged"]
     assert np.abs(U.cpu().numpy().reshape(big.M, -1) - Uo).max() <= 1e-10 * np.abs(Uo).max()
+
+
+def test_windowed_solve_starts_from_the_given_iterate():
+    # pit_solve with windows and PIT_START_GIVEN: a near-solution start saves Newton
+    # updates; a wild start diverges in its window, which restarts from the plain guess;
+    # both reach the oracle's solution
+    p = W.random_problem(52, 27, 31, 9, W.BURGERS, with_bc=True, with_q=True)
+    Uo, _, _, _ = oracle.solve(p, tol=1e-13)
+    opt = pit.pit_default_options()
+    opt.window = 3
+    with pit.context_for(p, opt) as ctx:
+        U = torch.empty(p.dof, dtype=torch.float64, device="cuda")
+        pit.pit_fill_plain_guess(ctx, U)
+        _, info_plain = pit.pit_solve(ctx, U)
+    opt.window_start = pit.PIT_START_GIVEN
+    rng = np.random.default_rng(52)
+    for start, fewer in ((Uo + 1e-8 * rng.standard_normal(Uo.shape), True),
+                         (1e3 * rng.standard_normal(Uo.shape), False)):
+        with pit.context_for(p, opt) as ctx:
+            U = _dev(start)
+            status, info = pit.pit_solve(ctx, U)
+            Ug = U.cpu().numpy().reshape(p.M, -1)
+        assert info["converged"]
+        assert np.abs(Ug - Uo).max() <= 1e-10 * np.abs(Uo).max()
+        if fewer:
+            assert info["newton_iters_total"] < info_plain["newton_iters_total"]
+        else:
+            assert info["windows"] > info["windows_converged"]  # the wild window was retried
+
+
+def test_fma_probe_measures_a_plausible_rate():
+    # GB300 runs FP64 at a small fraction of its FP32 rate; the probe must see both in range
+    f64 = pit.pit_probe_fma_peak(0)
+    f32 = pit.pit_probe_fma_peak(1)
+    assert 0.3 < f64 < 3.0, f64
+    assert 10.0 < f32 < 200.0 and f32 > 20 * f64, (f32, f64)

@@ -47,3 +47,40 @@ def test_noalloc_rejects_sizes_beyond_its_workspace():
     s, msg = pit.pit_block_solve_noalloc(1, 1, 4097, t.repeat(4097), t[:1].repeat(4097), t[:1].repeat(4097),
                                          check=False)
     assert s == pit.PIT_EUNSUPPORTED and "PIT_NOALLOC_MAX_LEVELS" in msg
+
+
+def test_noalloc_reports_a_nan_coefficient_as_diverged():
+    # a NaN entry must reach the caller as PIT_EDIVERGED, both with the automatic
+    # solver choice (the level's bound is then NaN) and with SOR forced
+    p = W.random_problem(24, 31, 27, 3, W.BURGERS)
+    U = _dev(p.plain_guess())
+    R = _dev(np.random.default_rng(24).standard_normal((3, p.grid.ns)))
+    with pit.context_for(p) as ctx:
+        coef = torch.empty(5 * p.dof, dtype=torch.float64, device="cuda")
+        pit.pit_assemble(ctx, U, coef)
+    coef[3 * p.dof + p.grid.ns + 17] = float("nan")  # an S entry of level 2
+    for solver in (pit.PIT_LIN_AUTO, pit.PIT_LIN_SOR):
+        opt = pit.pit_default_options()
+        opt.lin_solver = solver
+        dU = torch.zeros(p.dof, dtype=torch.float64, device="cuda")
+        status, msg = pit.pit_block_solve_noalloc(31, 27, 3, coef, R, dU, eta=1e-14, opt=opt, check=False)
+        assert status == pit.PIT_EDIVERGED, (solver, status, msg)
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    # every call reads its status back and synchronises, which a graph capture forbids
+    p = W.random_problem(25, 16, 16, 2, W.HEAT)
+    t = torch.zeros(5 * p.dof, dtype=torch.float64, device="cuda")
+    R = torch.zeros(p.dof, dtype=torch.float64, device="cuda")
+    dU = torch.zeros(p.dof, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    out = {}
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        try:
+            out["r"] = pit.pit_block_solve_noalloc(16, 16, 2, t, R, dU, eta=1e-14, stream=s, check=False)
+        finally:
+            g.capture_end()
+    status, msg = out["r"]
+    assert status == pit.PIT_EUNSUPPORTED and "captured" in msg
