@@ -230,6 +230,15 @@ pit_status pit_block_solve(pit_ctx* ctx, const double* U_dev, const double* R_de
  * the update U += dU. info (may be NULL) receives norms and statistics. */
 pit_status pit_newton_step(pit_ctx* ctx, double* U_dev, pit_step_info* info);
 
+/* Phase timers of the last wavefront launch of pit_solve, for performance analysis:
+ * for every team t of the launch (Newton iterations t, t + K, ...), 12 values from its
+ * first CTA, out[12 t + j]: 0 halo waits (flag protocol), 1 team-reduction waits,
+ * 2 waits for the previous Newton iteration, 3 total, 4 level setup, 5 level solves,
+ * 6 updates, 7 setup: loading u^n_k, 8 setup: team reduction and boundary-row exchange
+ * (nanoseconds), 9 cells solved, 10 sweeps or iterations (counts). Copies up to n values
+ * and returns how many there are (12 K), or -1 for a NULL argument. */
+int pit_wave_timers(const pit_ctx* ctx, unsigned long long* out, int n);
+
 /* Row (a4): Newton from the iterate in U_dev until ||R||_inf <= tol_res or
  * newton_max updates (PIT_ENOCONV; U_dev holds the last iterate). By default all
  * Newton iterations run in one cooperative wavefront launch: iteration k works on

@@ -73,7 +73,7 @@ struct pit_ctx {
     double* w_prefix = nullptr;             // [kcap][M]
     int* w_cell = nullptr;                  // [kcap][M]
     double* w_sumsq = nullptr;              // [kcap][Gw]
-    unsigned long long* w_timers = nullptr; // [K][8]
+    unsigned long long* w_timers = nullptr; // [K][kWaveTimers]
     std::vector<double> h_wres, h_wsumsq;
     std::vector<int> h_wcell;
     std::vector<unsigned long long> h_wtimers;
@@ -466,11 +466,11 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
                 CK(dalloc(&ctx->w_prefix, (size_t)ctx->kcap * M));
                 CK(dalloc(&ctx->w_cell, (size_t)ctx->kcap * M));
                 CK(dalloc(&ctx->w_sumsq, (size_t)ctx->kcap * Gw));
-                CK(dalloc(&ctx->w_timers, (size_t)K * 8));
+                CK(dalloc(&ctx->w_timers, (size_t)K * kWaveTimers));
                 ctx->h_wres.assign(ctx->kcap, 0.0);
                 ctx->h_wcell.assign((size_t)ctx->kcap * M, 0);
                 ctx->h_wsumsq.assign((size_t)ctx->kcap * Gw, 0.0);
-                ctx->h_wtimers.assign((size_t)K * 8, 0);
+                ctx->h_wtimers.assign((size_t)K * kWaveTimers, 0);
             }
         }
         CK(dalloc(&ctx->u0, ctx->Ns));
@@ -650,7 +650,7 @@ static pit_status run_wave(pit_ctx* ctx, int s, int Mw, double* Uall, int k_begi
     CK(cudaMemsetAsync(ctx->w_ints, 0, sizeof(int) * 3, ctx->stream));
     CK(cudaMemsetAsync(ctx->w_ints + 3, 0x7f, sizeof(int), ctx->stream));  // stop[1] = first converged k: large
     CK(cudaMemsetAsync(ctx->w_cell, 0, sizeof(int) * (size_t)ctx->kcap * M, ctx->stream));
-    CK(cudaMemsetAsync(ctx->w_timers, 0, sizeof(unsigned long long) * K * 8, ctx->stream));
+    CK(cudaMemsetAsync(ctx->w_timers, 0, sizeof(unsigned long long) * K * kWaveTimers, ctx->stream));
     if (ctx->w_tpub) {  // tag 0 is never published: stale words of an earlier launch cannot match
         CK(cudaMemsetAsync(ctx->w_tpub, 0, sizeof(unsigned long long) * ctx->w_tpub_n, ctx->stream));
         CK(cudaMemsetAsync(ctx->w_tred, 0, sizeof(unsigned long long) * ctx->w_tred_n, ctx->stream));
@@ -705,7 +705,7 @@ static pit_status run_wave(pit_ctx* ctx, int s, int Mw, double* Uall, int k_begi
                        ctx->stream));
     CK(cudaMemcpyAsync(ctx->h_wsumsq.data(), ctx->w_sumsq, sizeof(double) * (size_t)ctx->kcap * Gw,
                        cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->h_wtimers.data(), ctx->w_timers, sizeof(unsigned long long) * K * 8,
+    CK(cudaMemcpyAsync(ctx->h_wtimers.data(), ctx->w_timers, sizeof(unsigned long long) * K * kWaveTimers,
                        cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     float ms = 0.f;
@@ -898,6 +898,13 @@ extern "C" pit_status pit_solve(pit_ctx* ctx, double* U_dev, pit_solve_info* inf
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     return st;
+}
+
+extern "C" int pit_wave_timers(const pit_ctx* ctx, unsigned long long* out, int n) {
+    if (!ctx || !out || n < 0) return -1;
+    const int have = (int)ctx->h_wtimers.size();
+    for (int i = 0; i < n && i < have; ++i) out[i] = ctx->h_wtimers[i];
+    return have;
 }
 
 extern "C" pit_status pit_solve_host(pit_ctx* ctx, const double* u0_host, double* U_host, pit_solve_info* info) {

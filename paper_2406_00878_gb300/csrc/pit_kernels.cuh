@@ -54,9 +54,10 @@ __device__ __forceinline__ int ld_acquire_s32(const int* p) {
 }
 
 // |x| as an order-preserving key: non-negative doubles compare like their bits,
-// and NaN (after fabs, 0x7ff8...) sorts above +Inf so it propagates through max.
+// and NaN (sign cleared, 0x7ff8...) sorts above +Inf so it propagates through max.
+// The sign bit is masked on the integer pipe (GB300's FP64 pipe is the scarce one).
 __device__ __forceinline__ unsigned long long abs_key(double x) {
-    return static_cast<unsigned long long>(__double_as_longlong(fabs(x)));
+    return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7fffffffffffffffull;
 }
 __device__ __forceinline__ double key_val(unsigned long long k) { return __longlong_as_double((long long)k); }
 
@@ -499,12 +500,12 @@ __device__ __forceinline__ bool wait_tagged(const TeamCtl& c, const unsigned lon
 }
 
 // Publish H rows for each neighbour -- lo[h] (this CTA's first rows) for the CTA below and
-// hi[h] (its last rows) for the CTA above -- then fetch the CTA below's hi rows into fromS
-// and the CTA above's lo rows into fromN (zeros off the domain). Returns false when a
-// wait timed out (the launch is then aborted) or the launch aborted.
+// hi[h] (its last rows) for the CTA above -- as sequence-tagged words. Returns the
+// publication's sequence number, which fetch_rows_tagged takes. No barrier: the caller
+// makes the rows final before (a __syncthreads) and may compute on until it fetches.
 template <int NT, typename T, int H>
-__device__ bool exchange_rows_tagged(const TeamCtl& c, Team& t, unsigned long long* tpub, const T* const (&lo)[H],
-                                     const T* const (&hi)[H], T* const (&fromS)[H], T* const (&fromN)[H]) {
+__device__ __forceinline__ unsigned long long publish_rows_tagged(Team& t, unsigned long long* tpub,
+                                                                  const T* const (&lo)[H], const T* const (&hi)[H]) {
     static_assert(2 * H <= kDeepSlotRows, "slot too small");
     constexpr int P = Pieces<T>::n;
     const int nx = t.nx;
@@ -520,6 +521,19 @@ __device__ bool exchange_rows_tagged(const TeamCtl& c, Team& t, unsigned long lo
                 st_relaxed_u64(mine + h * row_w + (size_t)i * P + k, tagged(tag, Pieces<T>::get(lo[h][i], k)));
                 st_relaxed_u64(mine + (H + h) * row_w + (size_t)i * P + k, tagged(tag, Pieces<T>::get(hi[h][i], k)));
             }
+    return seq;
+}
+
+// Fetch the CTA below's hi rows of publication `seq` into fromS and the CTA above's lo rows
+// into fromN (zeros off the domain); ends with a barrier. Returns false when a wait timed
+// out (the launch is then aborted) or the launch aborted.
+template <int NT, typename T, int H>
+__device__ bool fetch_rows_tagged(const TeamCtl& c, const Team& t, const unsigned long long* tpub,
+                                  unsigned long long seq, T* const (&fromS)[H], T* const (&fromN)[H]) {
+    constexpr int P = Pieces<T>::n;
+    const int nx = t.nx;
+    const unsigned tag = (unsigned)seq;
+    const size_t row_w = (size_t)nx * P, slot_w = (size_t)kDeepSlotRows * row_w;
     const unsigned long long* par = tpub + (size_t)(seq & 1) * t.G * slot_w;
     const unsigned long long* srcS = t.b > 0 ? par + (size_t)(t.b - 1) * slot_w + H * row_w : nullptr;
     const unsigned long long* srcN = t.b + 1 < t.G ? par + (size_t)(t.b + 1) * slot_w : nullptr;
@@ -557,6 +571,14 @@ __device__ bool exchange_rows_tagged(const TeamCtl& c, Team& t, unsigned long lo
     return true;
 }
 
+// Publish, then fetch at once (no work in between).
+template <int NT, typename T, int H>
+__device__ bool exchange_rows_tagged(const TeamCtl& c, Team& t, unsigned long long* tpub, const T* const (&lo)[H],
+                                     const T* const (&hi)[H], T* const (&fromS)[H], T* const (&fromN)[H]) {
+    const unsigned long long seq = publish_rows_tagged<NT, T, H>(t, tpub, lo, hi);
+    return fetch_rows_tagged<NT, T, H>(c, t, tpub, seq, fromS, fromN);
+}
+
 // Team reduction over sequence-tagged words. Arrive: thread 0 publishes this CTA's K
 // values for reduction `use` (slot use & 3, tag use + 1). Finish: warp 0 polls every
 // CTA's words, lanes fold in CTA order with a fixed shuffle tree (max or sum, NaN
@@ -576,7 +598,9 @@ __device__ __forceinline__ void tagged_arrive(Team& t, unsigned long long* tred,
     }
 }
 
-// Warp 0 only. Returns false when a wait timed out or the launch aborted.
+// Warp 0 only. Returns false when a wait timed out or the launch aborted. MAXOP is for
+// non-negative values (magnitudes and flags, NaN included): their bit patterns order
+// like the values, so the maximum is taken on the integer pipe (NaN, above +Inf, wins).
 template <int K, bool MAXOP>
 __device__ __forceinline__ bool tagged_finish(const TeamCtl& c, const Team& t, const unsigned long long* tred,
                                               unsigned long long use, double (&out)[K]) {
@@ -584,10 +608,12 @@ __device__ __forceinline__ bool tagged_finish(const TeamCtl& c, const Team& t, c
     const unsigned tag = (unsigned)(use + 1);
     const unsigned long long* base = tred + (size_t)(use & 3) * t.G * kTagRedWords;
     double acc[K];
+    unsigned long long kmax[K];
     bool nan[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         acc[k] = 0.0;
+        kmax[k] = 0ull;
         nan[k] = false;
     }
     bool ok = true;
@@ -599,21 +625,31 @@ __device__ __forceinline__ bool tagged_finish(const TeamCtl& c, const Team& t, c
         ok = wait_tagged<2 * K>(c, src, w, tag);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const unsigned pw[2] = {(unsigned)w[2 * k], (unsigned)w[2 * k + 1]};
-            const double v = Pieces<double>::make(pw);
-            acc[k] = MAXOP ? fmax(acc[k], v) : acc[k] + v;
-            nan[k] |= (v != v);
+            if (MAXOP) {
+                const unsigned long long bits = ((w[2 * k + 1] & 0xffffffffull) << 32) | (w[2 * k] & 0xffffffffull);
+                kmax[k] = bits > kmax[k] ? bits : kmax[k];
+            } else {
+                const unsigned pw[2] = {(unsigned)w[2 * k], (unsigned)w[2 * k + 1]};
+                const double v = Pieces<double>::make(pw);
+                acc[k] += v;
+                nan[k] |= (v != v);
+            }
         }
     }
     ok = __all_sync(0xffffffffu, ok);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        for (int o = 16; o > 0; o >>= 1) {
-            const double w = __shfl_xor_sync(0xffffffffu, acc[k], o);
-            acc[k] = MAXOP ? fmax(acc[k], w) : acc[k] + w;
+        if (MAXOP) {
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long w = __shfl_xor_sync(0xffffffffu, kmax[k], o);
+                kmax[k] = w > kmax[k] ? w : kmax[k];
+            }
+            out[k] = key_val(kmax[k]);
+        } else {
+            for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+            const bool any_nan = __any_sync(0xffffffffu, nan[k]);
+            out[k] = any_nan ? __longlong_as_double(0x7ff8000000000000ll) : acc[k];
         }
-        const bool any_nan = __any_sync(0xffffffffu, nan[k]);
-        out[k] = any_nan ? __longlong_as_double(0x7ff8000000000000ll) : acc[k];
     }
     return ok;
 }
@@ -740,7 +776,7 @@ __device__ __forceinline__ void local_spmv(const Team& t, const Smem<T>& m, cons
 // Order-preserving key of |x| in an integer (max on the integer pipe; NaN sorts above +Inf).
 __device__ __forceinline__ unsigned long long mag_key(double x) { return abs_key(x); }
 __device__ __forceinline__ unsigned long long mag_key(float x) {
-    return static_cast<unsigned long long>(__float_as_uint(fabsf(x)));
+    return static_cast<unsigned long long>(__float_as_uint(x) & 0x7fffffffu);
 }
 template <typename T>
 __device__ __forceinline__ double mag_val(unsigned long long k);
@@ -749,16 +785,40 @@ __device__ __forceinline__ double mag_val<double>(unsigned long long k) { return
 template <>
 __device__ __forceinline__ double mag_val<float>(unsigned long long k) { return (double)__uint_as_float((unsigned)k); }
 
-// One SOR point update on the omega-scaled system (couplings and rhs multiplied by
-// omega): x' = (1 - omega) x + bs - (cw xW + ce xE + cs xS + cn xN). Shared by the owner
-// of a point and by a neighbour that recomputes it, so both get the same bits.
+// One SOR point update on the Jacobi-scaled level system
+// x + cw xW + ce xE + cs xS + cn xN = bs: t = x - bs + (cw xW + ce xE + cs xS + cn xN) is
+// minus the point's residual and x' = x - omega t, so the point moves by omega |t|. Six FP64
+// operations and no per-level scaling of the couplings. Shared by the owner of a point
+// and by a neighbour that recomputes it, so both get the same bits.
 template <typename T>
-__device__ __forceinline__ T sor_point(T xk, T bs, T cw, T ce, T cs, T cn, T xW, T xE, T xS, T xN, T om1) {
-    T acc = cw * xW;
+__device__ __forceinline__ T sor_point(T xk, T bs, T cw, T ce, T cs, T cn, T xW, T xE, T xS, T xN, T om, T& t) {
+    T acc = xk - bs;
+    acc = fma(cw, xW, acc);
     acc = fma(ce, xE, acc);
     acc = fma(cs, xS, acc);
     acc = fma(cn, xN, acc);
-    return fma(om1, xk, bs) - acc;
+    t = acc;
+    return fma(-om, acc, xk);
+}
+
+// Thread 0's stopping decision after sweep `sweep`, given d = the team's largest change
+// of sweep - 1 (NaN flagged in nan): -1 abort, 0 continue, 1 converged or capped, 2 NaN.
+// prev / prev2 carry the largest changes of the two sweeps before. With
+// rho = max(omega - 1, d_{s-1} / d_{s-2}), d_{s-1} rho / (1 - rho) estimates the error after
+// sweep s - 1, and sweep s, already done, shrinks it by rho once more: stop when
+// d_{s-1} rho^2 <= tol (1 - rho). Written with A = rho d_{s-2} so that it needs no FP64
+// division (a long dependent chain on GB300, while the other warps wait at a barrier):
+// rho < 1 <=> A < d_{s-2}, and the test <=> d_{s-1} A^2 <= tol d_{s-2} (d_{s-2} - A).
+// All changes may be scaled by one factor f > 0 if tol is divided by f.
+__device__ __forceinline__ int sor_decision(bool nan, double d, double omega, double tol, int sweep, int max_iter,
+                                            double& prev, double& prev2) {
+    if (nan) return 2;
+    prev2 = prev;
+    prev = d;
+    if (prev == 0.0 || sweep >= max_iter) return 1;
+    if (!(prev2 > 0.0)) return 0;
+    const double A = fmax((omega - 1.0) * prev2, prev);
+    return (A < prev2 && prev * A * A <= tol * prev2 * (prev2 - A)) ? 1 : 0;
 }
 
 // Red-black SOR on the scaled level system x + W x_W + E x_E + S x_S + N x_N = bs,
@@ -767,75 +827,24 @@ __device__ __forceinline__ T sor_point(T xk, T bs, T cw, T ce, T cs, T cn, T xW,
 // global d_s is known one sweep late (lagged team reduction), so every CTA takes
 // the same decision at the same sweep. Threads walk the points of one colour only
 // (every lane of a warp does useful work). Scalar decisions are taken by thread 0
-// and broadcast. The couplings and rhs are scaled by omega in place first (they are
-// reloaded for every level). With deep rows (see Deep) a sweep takes one halo exchange,
-// otherwise two. Returns the sweep count (< 0 on abort).
+// and broadcast. The largest change of a sweep is omega times the largest |t| of its
+// point updates (see sor_point). This form exchanges the halo before each half-sweep
+// (flag protocol); teams with deep rows use level_sor_deep. Returns the sweep count
+// (< 0 on abort).
 template <int NT, typename T>
-__device__ int level_sor(const TeamCtl& c, Team& t, const Smem<T>& m, double omega, double tol, int* s_ok,
-                         const Deep<T>* deep = nullptr) {
+__device__ int level_sor(const TeamCtl& c, Team& t, const Smem<T>& m, double omega, double tol, int* s_ok) {
     const int nx = t.nx;
     const int half = (nx + 1) >> 1;            // points of one colour per row, at most
     const int npts = t.nrows * half;
-    const T om = (T)omega, om1 = (T)(1.0 - omega);
-    for (int k = threadIdx.x; k < t.nloc; k += NT) {
-        m.cw[k] *= om;
-        m.ce[k] *= om;
-        m.cs[k] *= om;
-        m.cn[k] *= om;
-        m.bs[k] *= om;
-    }
-    __syncthreads();
-    if (deep) {
-        // the neighbours' boundary rows of the (scaled) system, once per level
-        const int last = (t.nrows - 1) * nx;
-        const T* const lo[5] = {m.cw, m.ce, m.cs, m.cn, m.bs};
-        const T* const hi[5] = {m.cw + last, m.ce + last, m.cs + last, m.cn + last, m.bs + last};
-        T* const fS[5] = {deep->cS[0], deep->cS[1], deep->cS[2], deep->cS[3], deep->cS[4]};
-        T* const fN[5] = {deep->cN[0], deep->cN[1], deep->cN[2], deep->cN[3], deep->cN[4]};
-        if (!exchange_rows_tagged<NT, T, 5>(c, t, deep->tpub, lo, hi, fS, fN)) {
-            *s_ok = 0;
-            return -1;
-        }
-    }
+    const T om = (T)omega;
     double prev = -1.0, prev2 = -1.0;          // global max change of sweeps s-1 and s-2 (thread 0)
     unsigned long long pending = 0;
     bool have_pending = false;
     int* s_flag = reinterpret_cast<int*>(m.red + 48);
-    const bool has_s = t.b > 0, has_n = t.b + 1 < t.G;
     for (int sweep = 1;; ++sweep) {
         unsigned long long key = 0;
         for (int color = 0; color < 2; ++color) {
-            if (deep) {
-                if (color == 0) {
-                    const int last = (t.nrows - 1) * nx;
-                    const T* const lo[2] = {m.x, m.x + nx};
-                    const T* const hi[2] = {m.x + last, m.x + last - nx};
-                    T* const fS[2] = {m.haloS, deep->xS2};
-                    T* const fN[2] = {m.haloN, deep->xN2};
-                    if (!exchange_rows_tagged<NT, T, 2>(c, t, deep->tpub, lo, hi, fS, fN)) {
-                        *s_ok = 0;
-                        return -1;
-                    }
-                    // red points of the two halo rows, as their owners compute them
-                    const int r_s = t.r0 - 1, r_n = t.r0 + t.nrows;
-                    for (int q = threadIdx.x; q < 2 * half; q += NT) {
-                        const bool south = q < half;
-                        if (south ? !has_s : !has_n) continue;
-                        const int row = south ? r_s : r_n;
-                        const int i = (row & 1) + 2 * (south ? q : q - half);
-                        if (i >= nx) continue;
-                        T* h = south ? m.haloS : m.haloN;
-                        T* const* cc = south ? deep->cS : deep->cN;
-                        const T xS = south ? deep->xS2[i] : m.x[last + i];
-                        const T xN = south ? m.x[i] : deep->xN2[i];
-                        const T xW = i > 0 ? h[i - 1] : T(0);
-                        const T xE = i < nx - 1 ? h[i + 1] : T(0);
-                        h[i] = sor_point<T>(h[i], cc[4][i], cc[0][i], cc[1][i], cc[2][i], cc[3][i], xW, xE, xS, xN, om1);
-                    }
-                }
-            } else {
-                if (!exchange_halo<NT, T>(c, t, m.x, m.haloS, m.haloN, s_ok)) return -1;
-            }
+            if (!exchange_halo<NT, T>(c, t, m.x, m.haloS, m.haloN, s_ok)) return -1;
             for (int q = threadIdx.x; q < npts; q += NT) {
                 const int jl = q / half;
                 const int i = ((t.r0 + jl + color) & 1) + 2 * (q - jl * half);
@@ -845,17 +854,16 @@ __device__ int level_sor(const TeamCtl& c, Team& t, const Smem<T>& m, double ome
                 const T xE = i < nx - 1 ? m.x[k + 1] : T(0);
                 const T xS = jl > 0 ? m.x[k - nx] : m.haloS[i];
                 const T xN = jl < t.nrows - 1 ? m.x[k + nx] : m.haloN[i];
-                const T xk = m.x[k];
-                const T xn = sor_point<T>(xk, m.bs[k], m.cw[k], m.ce[k], m.cs[k], m.cn[k], xW, xE, xS, xN, om1);
-                m.x[k] = xn;
-                const unsigned long long kk = mag_key(xn - xk);
+                T tk;
+                m.x[k] = sor_point<T>(m.x[k], m.bs[k], m.cw[k], m.ce[k], m.cs[k], m.cn[k], xW, xE, xS, xN, om, tk);
+                const unsigned long long kk = mag_key(tk);
                 key = kk > key ? kk : key;
             }
             __syncthreads();
         }
         // this CTA's max change (warp maxima, folded by thread 0), then arrive at the team
         // reduction of this sweep
-        const unsigned long long use = deep ? t.tag_seq++ : t.red_seq++;
+        const unsigned long long use = t.red_seq++;
         {
             unsigned long long* wred = reinterpret_cast<unsigned long long*>(m.red);
             for (int o = 16; o > 0; o >>= 1) {
@@ -867,15 +875,10 @@ __device__ int level_sor(const TeamCtl& c, Team& t, const Smem<T>& m, double ome
             if (threadIdx.x == 0) {
                 unsigned long long kmax = wred[0];
                 for (int w = 1; w < NT / 32; ++w) kmax = wred[w] > kmax ? wred[w] : kmax;
-                if (deep) {
-                    const double v1[1] = {mag_val<T>(kmax)};
-                    tagged_arrive<1>(t, deep->tred, use, v1);
-                } else {
-                    double* part = t.red_part + ((size_t)(use & 3) * t.G + t.b) * 4;
-                    __stcg(part, mag_val<T>(kmax));
-                    __threadfence();
-                    atomicAdd(t.red_cnt + (use & 3), 1ull);
-                }
+                double* part = t.red_part + ((size_t)(use & 3) * t.G + t.b) * 4;
+                __stcg(part, mag_val<T>(kmax) * omega);
+                __threadfence();
+                atomicAdd(t.red_cnt + (use & 3), 1ull);
             }
         }
         if (have_pending) {
@@ -887,48 +890,27 @@ __device__ int level_sor(const TeamCtl& c, Team& t, const Smem<T>& m, double ome
                 double d = 0.0;
                 bool nan = false;
                 const unsigned long long t0 = lane == 0 ? global_ns() : 0ull;
-                if (deep) {
-                    double g1[1];
-                    ok = tagged_finish<1, true>(c, t, deep->tred, pending, g1) ? 1 : 0;
-                    d = g1[0];
-                    nan = d != d;
-                } else {
-                    if (lane == 0) {
-                        const unsigned long long target = (unsigned long long)t.G * ((pending >> 2) + 1);
-                        ok = wait_geq(c, t.red_cnt + slot, target) ? 1 : 0;
-                        __threadfence();
+                if (lane == 0) {
+                    const unsigned long long target = (unsigned long long)t.G * ((pending >> 2) + 1);
+                    ok = wait_geq(c, t.red_cnt + slot, target) ? 1 : 0;
+                    __threadfence();
+                }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (ok) {
+                    const double* part = t.red_part + (size_t)slot * t.G * 4;
+                    for (int b = lane; b < t.G; b += 32) {
+                        const double v = __ldcg(part + (size_t)b * 4);
+                        d = fmax(d, v);
+                        nan |= (v != v);
                     }
-                    ok = __shfl_sync(0xffffffffu, ok, 0);
-                    if (ok) {
-                        const double* part = t.red_part + (size_t)slot * t.G * 4;
-                        for (int b = lane; b < t.G; b += 32) {
-                            const double v = __ldcg(part + (size_t)b * 4);
-                            d = fmax(d, v);
-                            nan |= (v != v);
-                        }
-                        for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
-                        nan = __any_sync(0xffffffffu, nan);
-                    }
+                    for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
+                    nan = __any_sync(0xffffffffu, nan);
                 }
                 if (lane == 0) t.t_red += global_ns() - t0;
                 int decision = -1;  // -1 abort, 0 continue, 1 converged / capped, 2 NaN
                 if (ok) {
                     decision = 0;
-                    if (lane == 0) {
-                        if (nan) {
-                            decision = 2;
-                        } else {
-                            prev2 = prev;
-                            prev = d;
-                            double rho = omega - 1.0;
-                            if (prev2 > 0.0) rho = fmax(rho, prev / prev2);
-                            // d_{s-1} rho / (1 - rho) estimates the error after sweep s - 1; sweep s,
-                            // already done, shrinks it by rho once more
-                            if (prev == 0.0 || (prev2 > 0.0 && rho < 1.0 && prev * rho * rho <= tol * (1.0 - rho)) ||
-                                sweep >= c.max_iter)
-                                decision = 1;
-                        }
-                    }
+                    if (lane == 0) decision = sor_decision(nan, d, omega, tol, sweep, c.max_iter, prev, prev2);
                 }
                 if (lane == 0) *s_flag = decision;
             }
@@ -942,11 +924,178 @@ __device__ int level_sor(const TeamCtl& c, Team& t, const Smem<T>& m, double ome
             }
             if (decision) {
                 if (decision == 2 && threadIdx.x == 0) atomicCAS(c.status, 0, ST_EDIVERGED);
-                if (!deep) {
-                    // consume the outstanding reduction so the counter sequence stays aligned
-                    double h[1];
-                    if (!reduce_finish<1, true>(c, t, use, h, m.red + 32, s_ok)) return -1;
+                // consume the outstanding reduction so the counter sequence stays aligned
+                double h[1];
+                if (!reduce_finish<1, true>(c, t, use, h, m.red + 32, s_ok)) return -1;
+                return sweep;
+            }
+        }
+        pending = use;
+        have_pending = true;
+    }
+}
+
+// Red-black SOR for a team with deep rows (see Deep), the same iteration and stopping
+// rule as level_sor with one exchange per sweep, arranged so that the team's latencies
+// overlap arithmetic:
+//   1. the CTA publishes its first two and last two rows (as of the start of the sweep),
+//   2. warp 0 issues the loads of the previous sweep's reduction words,
+//   3. colour 0 on the interior rows, which need no halo, while both are in flight,
+//   4. the neighbours' rows are fetched (normally already there),
+//   5. colour 0 on the first and last rows, and the red points of the two halo rows as
+//      their owners compute them (same arithmetic on the same values, same bits),
+//   6. colour 1 on every row,
+//   7. warp 0 completes the previous sweep's reduction from the prefetched words and
+//      decides; one barrier; thread 0 publishes this sweep's largest change.
+// The neighbours' boundary rows of the level system (deep->cS, deep->cN) must already be
+// in place (the caller exchanges them once per level). The team reduces max |t| (the change
+// over omega), so the tolerance comes as tol_w = tol / omega. Returns the sweep count (< 0
+// on abort).
+template <int NT, typename T>
+__device__ int level_sor_deep(const TeamCtl& c, Team& t, const Smem<T>& m, double omega, double tol_w, int* s_ok,
+                              const Deep<T>& deep) {
+    const int nx = t.nx;
+    const int half = (nx + 1) >> 1;            // points of one colour per row, at most
+    const int nrows = t.nrows;
+    const int last = (nrows - 1) * nx;
+    const T om = (T)omega;
+    const bool has_s = t.b > 0, has_n = t.b + 1 < t.G;
+    const int lane = threadIdx.x & 31;
+    double prev = -1.0, prev2 = -1.0;          // global max change of sweeps s-1 and s-2 (thread 0)
+    unsigned long long pending = 0;
+    bool have_pending = false;
+    int* s_flag = reinterpret_cast<int*>(m.red + 48);
+    unsigned long long* wred = reinterpret_cast<unsigned long long*>(m.red);
+    const T* const lo[2] = {m.x, m.x + nx};
+    const T* const hi[2] = {m.x + last, m.x + last - nx};
+    T* const fS[2] = {m.haloS, deep.xS2};
+    T* const fN[2] = {m.haloN, deep.xN2};
+    // one point of a colour: local row jl, qi-th point of that colour in the row
+    auto update = [&](int jl, int qi, int color, unsigned long long& key) {
+        const int i = ((t.r0 + jl + color) & 1) + 2 * qi;
+        if (i >= nx) return;
+        const int k = jl * nx + i;
+        const T xW = i > 0 ? m.x[k - 1] : T(0);
+        const T xE = i < nx - 1 ? m.x[k + 1] : T(0);
+        const T xS = jl > 0 ? m.x[k - nx] : m.haloS[i];
+        const T xN = jl < nrows - 1 ? m.x[k + nx] : m.haloN[i];
+        T tk;
+        m.x[k] = sor_point<T>(m.x[k], m.bs[k], m.cw[k], m.ce[k], m.cs[k], m.cn[k], xW, xE, xS, xN, om, tk);
+        const unsigned long long kk = mag_key(tk);
+        key = kk > key ? kk : key;
+    };
+    for (int sweep = 1;; ++sweep) {
+        unsigned long long key = 0;
+        // 1.
+        const unsigned long long seq = publish_rows_tagged<NT, T, 2>(t, deep.tpub, lo, hi);
+        // 2. (teams of up to 32 CTAs: one word pair per lane; wider teams poll in step 7)
+        unsigned long long pw0 = 0, pw1 = 0;
+        const bool prefetched = have_pending && t.G <= 32;
+        if (prefetched && threadIdx.x < 32 && lane < t.G) {
+            const unsigned long long* w = deep.tred + ((size_t)(pending & 3) * t.G + lane) * kTagRedWords;
+            pw0 = ld_relaxed_u64(w);
+            pw1 = ld_relaxed_u64(w + 1);
+        }
+        // 3.
+        for (int q = threadIdx.x; q < (nrows - 2) * half; q += NT) {
+            const int r = q / half;
+            update(1 + r, q - r * half, 0, key);
+        }
+        // 4.
+        if (!fetch_rows_tagged<NT, T, 2>(c, t, deep.tpub, seq, fS, fN)) {
+            *s_ok = 0;
+            return -1;
+        }
+        // 5.
+        const int r_s = t.r0 - 1, r_n = t.r0 + nrows;
+        for (int q = threadIdx.x; q < 4 * half; q += NT) {
+            if (q < 2 * half) {
+                if (q < half) update(0, q, 0, key);
+                else if (nrows > 1) update(nrows - 1, q - half, 0, key);
+            } else {
+                const int qh = q - 2 * half;
+                const bool south = qh < half;
+                if (south ? !has_s : !has_n) continue;
+                const int row = south ? r_s : r_n;
+                const int i = (row & 1) + 2 * (south ? qh : qh - half);
+                if (i >= nx) continue;
+                T* h = south ? m.haloS : m.haloN;
+                T* const* cc = south ? deep.cS : deep.cN;
+                const T xS = south ? deep.xS2[i] : m.x[last + i];
+                const T xN = south ? m.x[i] : deep.xN2[i];
+                const T xW = i > 0 ? h[i - 1] : T(0);
+                const T xE = i < nx - 1 ? h[i + 1] : T(0);
+                T unused;
+                h[i] = sor_point<T>(h[i], cc[4][i], cc[0][i], cc[1][i], cc[2][i], cc[3][i], xW, xE, xS, xN, om, unused);
+            }
+        }
+        __syncthreads();
+        // 6.
+        for (int q = threadIdx.x; q < nrows * half; q += NT) {
+            const int r = q / half;
+            update(r, q - r * half, 1, key);
+        }
+        // 7.
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long w = __shfl_xor_sync(0xffffffffu, key, o);
+            key = w > key ? w : key;
+        }
+        if (lane == 0) wred[threadIdx.x >> 5] = key;
+        if (have_pending && threadIdx.x < 32) {
+            const unsigned long long t0 = lane == 0 ? global_ns() : 0ull;
+            bool ok = true;
+            double d = 0.0;
+            bool nan = false;
+            if (prefetched) {
+                unsigned long long dk = 0ull;
+                if (lane < t.G) {
+                    const unsigned tag = (unsigned)(pending + 1);
+                    unsigned long long w[2] = {pw0, pw1};
+                    if ((unsigned)(w[0] >> 32) != tag || (unsigned)(w[1] >> 32) != tag) {
+                        const unsigned long long* base =
+                            deep.tred + ((size_t)(pending & 3) * t.G + lane) * kTagRedWords;
+                        const unsigned long long* src[2] = {base, base + 1};
+                        ok = wait_tagged<2>(c, src, w, tag);
+                    }
+                    dk = ((w[1] & 0xffffffffull) << 32) | (w[0] & 0xffffffffull);
                 }
+                ok = __all_sync(0xffffffffu, ok);
+                // non-negative values (or NaN): the maximum of the bit patterns, integer pipe
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long w = __shfl_xor_sync(0xffffffffu, dk, o);
+                    dk = w > dk ? w : dk;
+                }
+                d = key_val(dk);
+                nan = d != d;
+            } else {
+                double g1[1];
+                ok = tagged_finish<1, true>(c, t, deep.tred, pending, g1);
+                d = g1[0];
+                nan = d != d;
+            }
+            if (lane == 0) {
+                t.t_red += global_ns() - t0;
+                *s_flag = ok ? sor_decision(nan, d, omega, tol_w, sweep, c.max_iter, prev, prev2) : -1;
+            }
+        }
+        __syncthreads();
+        const unsigned long long use = t.tag_seq++;
+        if (threadIdx.x == 0) {
+            unsigned long long kmax = wred[0];
+            for (int w = 1; w < NT / 32; ++w) kmax = wred[w] > kmax ? wred[w] : kmax;
+            const double v1[1] = {mag_val<T>(kmax)};  // max |t|: the change is omega times it
+            tagged_arrive<1>(t, deep.tred, use, v1);
+        }
+        if (have_pending) {
+            // s_flag and wred are written again only after the next sweep's barriers
+            const int decision = *s_flag;
+            if (decision < 0) {
+                if (threadIdx.x == 0 && !ld_acquire_s32(c.abort_flag)) team_fail(c, ST_ETIMEOUT);
+                *s_ok = 0;
+                return -1;
+            }
+            if (decision) {
+                if (decision == 2 && threadIdx.x == 0) atomicCAS(c.status, 0, ST_EDIVERGED);
                 return sweep;
             }
         }
@@ -1067,6 +1216,18 @@ __device__ int level_bicgstab(const TeamCtl& c, Team& t, const Smem<T>& m, doubl
     return c.max_iter;
 }
 
+// Thread 0: SOR's omega for a level with Jacobi-scaled Gershgorin bound rho_g (< 1), in
+// FP32 (a few digits suffice, and GB300's FP32 square root and division are short):
+// omega = 2 / (1 + sqrt(1 - rho^2)) (Young), capped below 2 / (1 + rho) when some row has
+// opposite-signed couplings (see level_solve).
+__device__ __forceinline__ double sor_omega(double rho_g, bool nonsym) {
+    if (!(rho_g < 1.0)) return 1.0;
+    const float rc = (float)fmin(rho_g, 0.999999);
+    float w = 2.0f / (1.0f + sqrtf(1.0f - rc * rc));
+    if (nonsym) w = fmaxf(1.0f, fminf(w, 0.99f * 2.0f / (1.0f + (float)rho_g)));
+    return (double)w;
+}
+
 // Solve the scaled level system in m with the method chosen from the level's
 // Gershgorin bound rho_g; SOR's omega = 2/(1 + sqrt(1 - rho^2)) is formed by
 // thread 0. Returns iterations (< 0 on abort) and the method used (1 SOR, 2 BiCGStab).
@@ -1082,14 +1243,23 @@ __device__ __forceinline__ int level_solve(const TeamCtl& c, Team& t, const Smem
     *used = use_sor ? 1 : 2;
     if (use_sor) {
         double omega = 1.0;
-        if (threadIdx.x == 0 && rho_g < 1.0) {
-            const double rc = fmin(rho_g, 0.999999);
-            omega = 2.0 / (1.0 + sqrt(1.0 - rc * rc));
-            if (nonsym) omega = fmax(1.0, fmin(omega, 0.99 * 2.0 / (1.0 + rho_g)));
-        }
+        if (threadIdx.x == 0) omega = sor_omega(rho_g, nonsym);
         omega = bcast0(omega, m.red + 48);
-        return level_sor<NT, T>(c, t, m, omega, sor_tol, s_ok, deep);
+        return deep ? level_sor_deep<NT, T>(c, t, m, omega, sor_tol / omega, s_ok, *deep)
+                    : level_sor<NT, T>(c, t, m, omega, sor_tol, s_ok);
     }
+    return level_bicgstab<NT, T>(c, t, m, eta, atol, s_ok);
+}
+
+// level_solve for the wavefront kernel: the method, omega and the tolerances come decided
+// (thread 0 forms them with the forcing term and broadcasts them in one barrier).
+template <int NT, typename T>
+__device__ __forceinline__ int level_solve_decided(const TeamCtl& c, Team& t, const Smem<T>& m, bool use_sor,
+                                                   double omega, double sor_tol_w, double eta, double atol, int* s_ok,
+                                                   const Deep<T>* deep) {
+    if (use_sor)
+        return deep ? level_sor_deep<NT, T>(c, t, m, omega, sor_tol_w, s_ok, *deep)
+                    : level_sor<NT, T>(c, t, m, omega, sor_tol_w * omega, s_ok);
     return level_bicgstab<NT, T>(c, t, m, eta, atol, s_ok);
 }
 
@@ -1294,9 +1464,15 @@ struct WaveArgs {
     double* cell_prefix;                // [k_end][M] max_{j <= n} ||r^j_k||_inf (written by CTA 0 of the team)
     int* cell_iters;                    // [k_end][M] 1 + sweeps (SOR) or -(1 + iterations) (BiCGStab); 0 = not run
     double* cta_sumsq;                  // [k_end][G] sum of du_k^2 over the CTA's rows
-    unsigned long long* timers;         // [K][8] CTA 0 of each team: halo, reduction, predecessor waits, total,
-                                        // level setup, level solves, update (ns)
+    unsigned long long* timers;         // [K][kWaveTimers] CTA 0 of each team (see kWaveTimers)
 };
+
+// Phase timers of CTA 0 of every team of a wavefront launch, per team (ns unless noted):
+// 0 halo waits (flag protocol), 1 team-reduction waits, 2 waits for the previous Newton
+// iteration, 3 total, 4 level setup (all of it), 5 level solves, 6 updates and progress
+// publication, 7 setup: loading u^n_k, 8 setup: team reduction and boundary-row exchange,
+// 9 cells solved (count), 10 sweeps or iterations (count), 11 unused.
+constexpr int kWaveTimers = 12;
 
 // u^n_k with its halo rows ((cap + 2 nx) doubles) shares the BiCGStab scratch r..t
 // when it fits there; otherwise it follows uprev.
@@ -1324,6 +1500,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
     TeamCtl c{a.abort_flag, a.status, a.wait_budget, a.max_iter};
     const unsigned long long t_start = global_ns();
     unsigned long long t_pred = 0, t_setup = 0, t_solve = 0, t_upd = 0, t_mark = 0;
+    unsigned long long t_load = 0, t_sred = 0, n_cells = 0, n_sweeps = 0;
     const int nloc = t.nloc;
     const int cap = (a.rows_base + (a.rows_rem ? 1 : 0)) * nx;
     const Smem<T> m = smem_layout<T>(smem, cap, nx);
@@ -1342,6 +1519,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
     const double dconst = 1.0 / (1.0 + 2.0 * oc.mu_a * (oc.vx + oc.vy));
     // their folded constants: viscous mu_a tau / h^2, and the scaled couplings
     const double vmu_x = oc.mu_a * oc.vx, vmu_y = oc.mu_a * oc.vy;
+    const double kcen = 1.0 + 2.0 * (vmu_x + vmu_y);
     const double sjx = oc.jx * dconst, sjy = oc.jy * dconst, svx = vmu_x * dconst, svy = vmu_y * dconst;
     // neighbour rows for one-exchange SOR sweeps: in the BiCGStab scratch r..t (5 cap values),
     // which SOR leaves unused and u^n_k no longer needs once the level's system is formed.
@@ -1372,16 +1550,18 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
         __syncthreads();
         for (int n = 0; n < M; ++n) {
             // 1. wait until iteration k - 1 has finished level n on rows r0-1 .. r0+nrows and
-            //    on CTA 0 (which publishes its running residual max), then read that max
-            if (threadIdx.x == 0) {
+            //    on CTA 0 (which publishes its running residual max): lanes 0..3 of warp 0 poll
+            //    the progress words of CTAs b-1, b, b+1 and 0 at once (acquire)
+            const int pl = b == 0 ? 1 : (b == 1 ? 0 : 3);  // the lane that polls CTA 0
+            if (threadIdx.x < 32) {
+                const int lane = threadIdx.x;
                 bool stop_seen = false;
-                double pred_prefix = 1.0 / 0.0;
                 if (k > a.k_begin) {
                     const unsigned long long target = a.cell_base + (unsigned long long)(k - 1) * M + n + 1;
-                    const unsigned long long t0 = global_ns();
-                    for (int q = 0; q < 4 && !stop_seen; ++q) {
-                        const int nbr = q < 3 ? b - 1 + q : 0;
-                        if (nbr < 0 || nbr >= a.G || (q == 3 && b <= 1)) continue;
+                    const unsigned long long t0 = lane == 0 ? global_ns() : 0ull;
+                    int nbr = lane < 3 ? b - 1 + lane : (lane == 3 && b > 1 ? 0 : -1);
+                    if (nbr >= a.G) nbr = -1;
+                    if (nbr >= 0) {
                         long long spins = 0;
                         while (ld_acquire_u64(pred_prog + nbr) < target) {
                             if ((a.stop && ld_acquire_s32(a.stop)) || ld_acquire_s32(a.abort_flag)) {
@@ -1395,52 +1575,36 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                             }
                             if (spins > 4096) __nanosleep(64);
                         }
+                        __threadfence();
                     }
-                    __threadfence();
-                    t_pred += global_ns() - t0;
-                    if (!stop_seen) pred_prefix = __ldcg(a.cell_prefix + (size_t)(k - 1) * M + n);
+                    stop_seen = __any_sync(0xffffffffu, stop_seen);
+                    if (lane == 0) t_pred += global_ns() - t0;
                 }
-                s_ok = (stop_seen || (a.stop && ld_acquire_s32(a.stop)) || ld_acquire_s32(a.abort_flag)) ? 1 : 0;
-                slot[0] = pred_prefix;
+                if (lane == 0)
+                    s_ok = (stop_seen || (a.stop && ld_acquire_s32(a.stop)) || ld_acquire_s32(a.abort_flag)) ? 1 : 0;
             }
             __syncthreads();
             const int stop_local = s_ok;
-            const double pred_prefix = slot[0];
-            __syncthreads();
             // every later cell is a skip once the stop flag is up (or the launch aborts)
             if (stop_local) goto done;
-            if (pred_prefix <= a.tol_res) {
-                // levels 0..n converged in iteration k - 1: du^n_k = 0, nothing to solve
-                for (int i = threadIdx.x; i < nloc; i += NT) m.x[i] = T(0);
-                uprev_valid = false;
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    prefix = pred_prefix;
-                    __threadfence();
-                    if (b == 0) {
-                        __stcg(a.cell_prefix + (size_t)k * M + n, prefix);
-                        if (a.cell_iters) a.cell_iters[(size_t)k * M + n] = 1;
-                        __threadfence();
-                    }
-                    st_release_u64(my_prog + b, a.cell_base + (unsigned long long)k * M + n + 1);
-                }
-                continue;
-            }
-            if (!uprev_valid) {
-                // the previous level was skipped: u^{n-1}_k is the global (final) iterate
+            if (threadIdx.x == 0) t_mark = global_ns();
+            // 2. the previous iteration's running max (lane pl: it acquired CTA 0's progress), and
+            //    in the same round trip u^{n-1}_k when the previous level was skipped (the global,
+            //    final iterate) and u^n_k (below)
+            if (threadIdx.x == pl) slot[0] = k > a.k_begin ? __ldcg(a.cell_prefix + (size_t)(k - 1) * M + n) : 1.0 / 0.0;
+            const bool reload_prev = !uprev_valid;
+            if (reload_prev) {
                 const double* up = n == 0 ? a.u0 + off0 : a.U + (long long)(n - 1) * Ns + off0;
                 for (int i = threadIdx.x; i < nloc; i += NT) uprev[i] = __ldcg(up + i);
                 uprev_valid = true;
-                __syncthreads();
             }
-            if (threadIdx.x == 0) t_mark = global_ns();
-            // 2. u^n_k: own rows and one halo row each side (Dirichlet data off the domain)
+            // u^n_k: own rows and one halo row each side (Dirichlet data off the domain)
             const double* Un = a.U + (long long)n * Ns;
             const double* bnd = a.bc ? a.bc + (long long)n * nb : nullptr;
             // maxima as integer keys (abs_key), so the bookkeeping stays off the FP64 pipe
             unsigned long long krmax = 0, krs = 0, kbmax = 0;
             bool ns = false;
-            if (!stop_local) {
+            {
                 for (int i = threadIdx.x; i < (t.nrows + 2) * nx; i += NT) {
                     const int jr = i / nx, ii = i - jr * nx, j = t.r0 - 1 + jr;
                     double val;
@@ -1450,59 +1614,105 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                     u[i] = val;
                 }
                 __syncthreads();
+                if (threadIdx.x == 0) t_load += global_ns() - t_mark;
+                const double pred_prefix = slot[0];
+                if (pred_prefix <= a.tol_res) {
+                    // levels 0..n converged in iteration k - 1: du^n_k = 0, nothing to solve
+                    __syncthreads();  // slot[0] read by every thread
+                    for (int i = threadIdx.x; i < nloc; i += NT) m.x[i] = T(0);
+                    uprev_valid = false;
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        prefix = pred_prefix;
+                        __threadfence();
+                        if (b == 0) {
+                            __stcg(a.cell_prefix + (size_t)k * M + n, prefix);
+                            if (a.cell_iters) a.cell_iters[(size_t)k * M + n] = 1;
+                            __threadfence();
+                        }
+                        st_release_u64(my_prog + b, a.cell_base + (unsigned long long)k * M + n + 1);
+                    }
+                    continue;
+                }
                 // 3. residual r^n_k, scaled couplings, rhs; uprev <- u^n_k
                 const double* qn = a.q ? a.q + (long long)n * Ns + off0 : nullptr;
-#pragma unroll 2
-                for (int i = threadIdx.x; i < nloc; i += NT) {
+                struct NodeIn {
+                    double uC, uW, uE, uS, uN, up, x, q;
+                };
+                struct NodeOut {
+                    double r, aW, aE, aS, aN, bval, d;
+                };
+                auto load_node = [&](int i) {
                     const int jl = i / nx, ii = i - jl * nx, j = t.r0 + jl;
                     const int ku = (jl + 1) * nx + ii;
-                    const double uC = u[ku];
-                    const double uW = ii > 0 ? u[ku - 1] : (bnd ? bnd[2 * nx + j] : 0.0);
-                    const double uE = ii < nx - 1 ? u[ku + 1] : (bnd ? bnd[2 * nx + ny + j] : 0.0);
-                    const double uS = u[ku - nx];
-                    const double uN = u[ku + nx];
-                    double r, aW, aE, aS, aN, d;
+                    NodeIn v;
+                    v.uC = u[ku];
+                    v.uW = ii > 0 ? u[ku - 1] : (bnd ? bnd[2 * nx + j] : 0.0);
+                    v.uE = ii < nx - 1 ? u[ku + 1] : (bnd ? bnd[2 * nx + ny + j] : 0.0);
+                    v.uS = u[ku - nx];
+                    v.uN = u[ku + nx];
+                    v.up = uprev[i];
+                    v.x = (double)m.x[i];
+                    v.q = qn ? qn[i] : 0.0;
+                    return v;
+                };
+                auto form_node = [&](int i, const NodeIn& v) {
+                    const int jl = i / nx, ii = i - jl * nx, j = t.r0 + jl;
+                    NodeOut o;
                     if (CONV && !NLV) {
-                        // Burgers with constant viscosity: eq. 3 and its Jacobian with the constants
-                        // folded (the diagonal 1/d is constant), fewer FP64 operations
-                        const double sEW = uE + uW, sNS = uN + uS;
-                        const double cv = fma(oc.cy, (uN - uS) * sNS, oc.cx * ((uE - uW) * sEW));
-                        const double vs = fma(vmu_y, fma(-2.0, uC, sNS), vmu_x * fma(-2.0, uC, sEW));
-                        r = (uprev[i] - uC) - (cv - vs);
-                        d = dconst;
-                        aE = fma(sjx, uE, -svx);
-                        aW = fma(-sjx, uW, -svx);
-                        aN = fma(sjy, uN, -svy);
-                        aS = fma(-sjy, uS, -svy);
+                        // Burgers with constant viscosity: eq. 3-5 and the Jacobian with the
+                        // constants folded (the diagonal 1/d is constant). With mu tau/h^2 = vmu:
+                        //   r = u^{n-1} - kcen uC - uE (cx uE - vmu_x) + uW (cx uW + vmu_x)
+                        //                         - uN (cy uN - vmu_y) + uS (cy uS + vmu_y),
+                        // kcen = 1 + 2 (vmu_x + vmu_y): nine FP64 operations
+                        double r = fma(-kcen, v.uC, v.up);
+                        r = fma(-v.uE, fma(oc.cx, v.uE, -vmu_x), r);
+                        r = fma(v.uW, fma(oc.cx, v.uW, vmu_x), r);
+                        r = fma(-v.uN, fma(oc.cy, v.uN, -vmu_y), r);
+                        o.r = fma(v.uS, fma(oc.cy, v.uS, vmu_y), r);
+                        o.d = dconst;
+                        o.aE = fma(sjx, v.uE, -svx);
+                        o.aW = fma(-sjx, v.uW, -svx);
+                        o.aN = fma(sjy, v.uN, -svy);
+                        o.aS = fma(-sjy, v.uS, -svy);
                     } else {
-                        r = (uprev[i] - uC) - tau_F<CONV, NLV>(oc, uC, uW, uE, uS, uN);
+                        o.r = (v.up - v.uC) - tau_F<CONV, NLV>(oc, v.uC, v.uW, v.uE, v.uS, v.uN);
                         double aC;
-                        jac_row<CONV, NLV>(oc, uC, uW, uE, uS, uN, aC, aW, aE, aS, aN);
-                        d = NLV ? 1.0 / aC : dconst;
-                        aW *= d;
-                        aE *= d;
-                        aS *= d;
-                        aN *= d;
+                        jac_row<CONV, NLV>(oc, v.uC, v.uW, v.uE, v.uS, v.uN, aC, o.aW, o.aE, o.aS, o.aN);
+                        o.d = NLV ? 1.0 / aC : dconst;
+                        o.aW *= o.d;
+                        o.aE *= o.d;
+                        o.aS *= o.d;
+                        o.aN *= o.d;
                     }
-                    if (qn) r = fma(oc.dt, qn[i], r);
-                    if (ii == 0) aW = 0.0;
-                    if (ii == nx - 1) aE = 0.0;
-                    if (j == 0) aS = 0.0;
-                    if (j == ny - 1) aN = 0.0;
-                    m.cw[i] = (T)aW;
-                    m.ce[i] = (T)aE;
-                    m.cs[i] = (T)aS;
-                    m.cn[i] = (T)aN;
-                    const double bval = r + (double)m.x[i];  // r^n + du^{n-1}
-                    m.bs[i] = (T)(d * bval);
-                    m.x[i] = (T)bval;                        // SOR start
-                    uprev[i] = uC;                           // u^n_k for the next level's time difference
-                    const unsigned long long kr = abs_key(r), kg = abs_key(fabs(aW) + fabs(aE) + fabs(aS) + fabs(aN)),
-                                             kb = abs_key(bval);
+                    if (qn) o.r = fma(oc.dt, v.q, o.r);
+                    if (ii == 0) o.aW = 0.0;
+                    if (ii == nx - 1) o.aE = 0.0;
+                    if (j == 0) o.aS = 0.0;
+                    if (j == ny - 1) o.aN = 0.0;
+                    o.bval = o.r + v.x;  // r^n + du^{n-1}
+                    return o;
+                };
+                auto store_node = [&](int i, const NodeIn& v, const NodeOut& o) {
+                    m.cw[i] = (T)o.aW;
+                    m.ce[i] = (T)o.aE;
+                    m.cs[i] = (T)o.aS;
+                    m.cn[i] = (T)o.aN;
+                    m.bs[i] = (T)(o.d * o.bval);
+                    m.x[i] = (T)o.bval;  // SOR start
+                    uprev[i] = v.uC;     // u^n_k for the next level's time difference
+                    const unsigned long long kr = abs_key(o.r),
+                                             kg = abs_key(fabs(o.aW) + fabs(o.aE) + fabs(o.aS) + fabs(o.aN)),
+                                             kb = abs_key(o.bval);
                     krmax = kr > krmax ? kr : krmax;
                     krs = kg > krs ? kg : krs;
                     kbmax = kb > kbmax ? kb : kbmax;
-                    ns |= opposite_nonzero(aW, aE) || opposite_nonzero(aS, aN);
+                    ns |= opposite_nonzero(o.aW, o.aE) || opposite_nonzero(o.aS, o.aN);
+                };
+#pragma unroll 2
+                for (int i = threadIdx.x; i < nloc; i += NT) {
+                    const NodeIn v = load_node(i);
+                    store_node(i, v, form_node(i, v));
                 }
             }
             // 4. team reduction: max |r|, Gershgorin bound, 2 stop + nonsymmetric-row flag, max |rhs|
@@ -1513,6 +1723,16 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 unsigned long long kk[4] = {krmax, krs, abs_key((double)flags_local), kbmax};
                 block_max4_to0<NT>(kk, reinterpret_cast<unsigned long long*>(m.red));
                 for (int q = 0; q < 4; ++q) v3[q] = key_val(kk[q]);  // meaningful on thread 0 only
+            }
+            // deep rows: the neighbours' boundary rows of the level system travel while the
+            // team reduction does (publish now, fetch after it)
+            unsigned long long cseq = 0;
+            const unsigned long long t_sr0 = threadIdx.x == 0 ? global_ns() : 0ull;
+            if (deep) {
+                const int last = (t.nrows - 1) * nx;
+                const T* const lo[5] = {m.cw, m.ce, m.cs, m.cn, m.bs};
+                const T* const hi[5] = {m.cw + last, m.ce + last, m.cs + last, m.cn + last, m.bs + last};
+                cseq = publish_rows_tagged<NT, T, 5>(t, deep->tpub, lo, hi);
             }
             double g3[4];
             if (deep) {
@@ -1557,30 +1777,43 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 }
                 goto done;
             }
+            if (deep) {
+                T* const fS[5] = {deep->cS[0], deep->cS[1], deep->cS[2], deep->cS[3], deep->cS[4]};
+                T* const fN[5] = {deep->cN[0], deep->cN[1], deep->cN[2], deep->cN[3], deep->cN[4]};
+                if (!fetch_rows_tagged<NT, T, 5>(c, t, deep->tpub, cseq, fS, fN)) return;
+            }
+            if (threadIdx.x == 0) t_sred += global_ns() - t_sr0;
             {
-                // 5. forcing from the running max; SOR tolerance absolute, BiCGStab relative
-                double eta = 0.0, sor_tol = 0.0;
+                // 5. forcing from the running max; SOR tolerance absolute (as tol / omega, see
+                //    level_sor_deep), BiCGStab relative; method and omega from the level's bound.
+                //    Thread 0 forms them all, one barrier broadcasts them.
+                const bool use_sor = a.method == 1 || (a.method == 0 && g3[1] < a.sor_rho_max);
+                double* sc = m.red + 36;
                 if (threadIdx.x == 0) {
                     prefix = fmax(prefix, g3[0]);
-                    eta = fmax(fmin(a.eta_max, a.eta_gamma * prefix), 1e-300);
+                    const double eta = fmax(fmin(a.eta_max, a.eta_gamma * prefix), 1e-300);
                     // absolute, not below the level-solve precision's round-off of the rhs
-                    sor_tol = fmax(fmax(a.atol, eta * prefix), 16.0 * Eps<T>::value * g3[3]);
-                }
-                eta = bcast0(eta, slot);
-                sor_tol = bcast0(sor_tol, slot);
-                if (threadIdx.x == 0) {
+                    const double sor_tol = fmax(fmax(a.atol, eta * prefix), 16.0 * Eps<T>::value * g3[3]);
+                    const double omega = use_sor ? sor_omega(g3[1], g3[2] != 0.0) : 1.0;
+                    sc[0] = eta;
+                    sc[1] = omega;
+                    sc[2] = sor_tol / omega;
                     const unsigned long long now = global_ns();
                     t_setup += now - t_mark;
                     t_mark = now;
                 }
-                int used = 0;
-                const int iters = level_solve<NT, T>(c, t, m, a.method, a.sor_rho_max, g3[1], g3[2] != 0.0, sor_tol,
-                                                     eta, a.atol, &s_ok, &used, deep);
+                __syncthreads();
+                const double eta = sc[0], omega = sc[1], sor_tol_w = sc[2];
+                const int used = use_sor ? 1 : 2;
+                const int iters =
+                    level_solve_decided<NT, T>(c, t, m, use_sor, omega, sor_tol_w, eta, a.atol, &s_ok, deep);
                 if (iters < 0) return;  // aborted
                 if (threadIdx.x == 0) {
                     const unsigned long long now = global_ns();
                     t_solve += now - t_mark;
                     t_mark = now;
+                    n_cells += 1;
+                    n_sweeps += (unsigned long long)(iters > 0 ? iters : 0);
                 }
                 // 6. U^n += du^n; du^n stays in x for the next level
                 double* Uw = a.U + (long long)n * Ns + off0;
@@ -1627,7 +1860,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
     }
 done:
     if (b == 0 && threadIdx.x == 0 && a.timers) {
-        unsigned long long* tm = a.timers + (size_t)team * 8;
+        unsigned long long* tm = a.timers + (size_t)team * kWaveTimers;
         tm[0] = t.t_halo;
         tm[1] = t.t_red;
         tm[2] = t_pred;
@@ -1635,6 +1868,10 @@ done:
         tm[4] = t_setup;
         tm[5] = t_solve;
         tm[6] = t_upd;
+        tm[7] = t_load;
+        tm[8] = t_sred;
+        tm[9] = n_cells;
+        tm[10] = n_sweeps;
     }
     __syncthreads();
 }

@@ -33,7 +33,7 @@ EXPORTS = ("pit_default_options", "pit_create", "pit_set_data", "pit_fill_plain_
            "pit_net_create", "pit_net_get_params", "pit_net_set_params", "pit_net_guess", "pit_net_make_target",
            "pit_net_gradients", "pit_net_train_step", "pit_net_last_error", "pit_net_destroy",
            "pit_product_form_solve", "pit_solve_product", "pit_probe_fma_peak", "pit_conv3x3_forward",
-           "pit_conv3x3_backward")
+           "pit_conv3x3_backward", "pit_wave_timers")
 
 
 class pit_grid(ctypes.Structure):
@@ -168,6 +168,8 @@ def lib():
             L.pit_block_solve_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, V, V, V, ctypes.c_double,
                                                   ctypes.POINTER(pit_options), V, ctypes.c_char_p, ctypes.c_int]
             L.pit_block_solve_noalloc.restype = st
+            L.pit_wave_timers.argtypes = [P, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]
+            L.pit_wave_timers.restype = ctypes.c_int
             L.pit_probe_fma_peak.argtypes = [ctypes.c_int, V, D]
             L.pit_probe_fma_peak.restype = st
             L.pit_batch_create.argtypes = [ctypes.POINTER(pit_instance), ctypes.c_int, ctypes.POINTER(pit_options), V,
@@ -412,6 +414,19 @@ def pit_block_solve_noalloc(nx: int, ny: int, M: int, coef, R, dU, eta: float = 
     if check and s != PIT_OK:
         raise PitError(s, msg)
     return s, msg
+
+
+WAVE_TIMER_NAMES = ("halo_wait_ns", "reduce_wait_ns", "pred_wait_ns", "total_ns", "setup_ns", "solve_ns",
+                    "update_ns", "setup_load_ns", "setup_reduce_ns", "cells", "sweeps", "unused")
+
+
+def pit_wave_timers(ctx: "Context") -> list:
+    """Per-team phase timers of the last wavefront launch (list of dicts, one per team)."""
+    n = len(WAVE_TIMER_NAMES) * 64  # up to 64 teams
+    buf = (ctypes.c_ulonglong * n)()
+    have = lib().pit_wave_timers(ctx.handle, buf, n)
+    k = len(WAVE_TIMER_NAMES)
+    return [dict(zip(WAVE_TIMER_NAMES, buf[t * k:(t + 1) * k])) for t in range(max(have, 0) // k)]
 
 
 def pit_probe_fma_peak(precision: int = 0, stream=None) -> float:
