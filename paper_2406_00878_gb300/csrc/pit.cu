@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <vector>
 
@@ -668,6 +669,8 @@ static pit_status run_wave(pit_ctx* ctx, int s, int Mw, double* Uall, int k_begi
     a.rows_rem = ctx->w_rows_rem;
     a.k_begin = k_begin;
     a.k_end = k_end;
+    // bulk copies of the level strips need 16-byte aligned rows: nx even, U aligned
+    a.bulk_u = (ctx->grid.nx % 2 == 0) && (reinterpret_cast<uintptr_t>(U) % 16 == 0);
     a.tol_res = ctx->opt.tol_res;
     a.eta_max = ctx->opt.eta_max;
     a.eta_gamma = ctx->opt.eta_gamma;

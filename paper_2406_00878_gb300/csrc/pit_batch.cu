@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <map>
 #include <numeric>
@@ -303,6 +304,7 @@ static pit_status build_launch(pit_batch* b, const std::vector<pit_instance>& in
         bi[i].conv = I.params.equation == PIT_BURGERS;
         bi[i].nlv = I.params.mu_b != 0.0;
         bi[i].window = std::min(W, I.M);
+        bi[i].bulk_u = (I.grid.nx % 2 == 0) && (reinterpret_cast<uintptr_t>(I.U_dev) % 16 == 0);
         bi[i].u0 = I.u0_dev;
         bi[i].bc = I.bc_dev;
         bi[i].q = I.q_dev;

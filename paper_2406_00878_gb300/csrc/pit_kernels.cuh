@@ -53,6 +53,54 @@ __device__ __forceinline__ int ld_acquire_s32(const int* p) {
     return v;
 }
 
+// ---------------------------------------------- bulk copies (TMA) into shared memory
+// One thread copies a contiguous global range into shared memory with cp.async.bulk and
+// an mbarrier that counts the bytes; the CTA waits on the barrier's phase.
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Arrive (count one) and expect `bytes` of transactions in the current phase.
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+        "r"(bytes)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_test_parity(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Poll the phase with the given parity, at most `polls` times.
+__device__ __forceinline__ bool mbar_wait_parity(unsigned long long* bar, unsigned parity, long long polls) {
+    for (long long i = 0; i < polls; ++i)
+        if (mbar_test_parity(bar, parity)) return true;
+    return false;
+}
+// Generic-proxy accesses to shared memory before this point are ordered before later
+// async-proxy (TMA) writes (after a barrier that covers every thread's accesses).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Global -> shared bulk copy of `bytes` (multiple of 16; both addresses 16-byte aligned),
+// completing on bar's transaction count.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+constexpr long long kBulkWaitPolls = 1ll << 24;
+
 // |x| as an order-preserving key: non-negative doubles compare like their bits,
 // and NaN (sign cleared, 0x7ff8...) sorts above +Inf so it propagates through max.
 // The sign bit is masked on the integer pipe (GB300's FP64 pipe is the scarce one).
@@ -1433,6 +1481,14 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
 // no further update. The rule depends only on finished cells, so the result is
 // the same on every run. When an iteration ends with a running max <= tol_res,
 // every later cell is a skip; the team raises a stop flag so the others leave early.
+// The mbarrier of a CTA's bulk copies and the parity of its current phase. Initialised
+// once per launch (mbarrier.init on a live barrier is undefined), carried through every
+// wavefront body the CTA runs; every copy is waited for before the next is issued.
+struct BulkBar {
+    unsigned long long* bar;
+    unsigned phase;
+};
+
 struct WaveArgs {
     OpConst c;
     const double* u0;
@@ -1441,6 +1497,7 @@ struct WaveArgs {
     double* U;
     int K, G, rows_base, rows_rem;
     int k_begin, k_end;                 // iterations k_begin <= k < k_end may run
+    int bulk_u;                         // u^n_k strips by bulk copy (nx even, U 16-byte aligned)
     unsigned long long cell_base;       // added to every progress value (monotonic across calls)
     double tol_res, eta_max, eta_gamma, atol, sor_rho_max;
     int method;
@@ -1494,7 +1551,7 @@ __host__ __device__ inline size_t wave_smem_bytes(int cap, int nx) {
 // instance of a batched launch). t is the CTA's team state, already initialised
 // with the team's workspace; its sequence counters carry over between calls.
 template <int NT, bool CONV, bool NLV, typename T>
-__device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned char* smem, int& s_ok) {
+__device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned char* smem, int& s_ok, BulkBar& bb) {
     const OpConst& oc = a.c;
     const int nx = oc.nx, ny = oc.ny, M = oc.M;
     TeamCtl c{a.abort_flag, a.status, a.wait_budget, a.max_iter};
@@ -1539,6 +1596,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
         deep = &deep_rows;
     }
 
+    unsigned long long* const ubar = bb.bar;
     for (int k = a.k_begin + team; k < a.k_end; k += a.K) {
         for (int i = threadIdx.x; i < nloc; i += NT) {
             m.x[i] = T(0);              // du^{-1} = 0
@@ -1605,15 +1663,45 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
             unsigned long long krmax = 0, krs = 0, kbmax = 0;
             bool ns = false;
             {
-                for (int i = threadIdx.x; i < (t.nrows + 2) * nx; i += NT) {
-                    const int jr = i / nx, ii = i - jr * nx, j = t.r0 - 1 + jr;
-                    double val;
-                    if (j < 0) val = bnd ? bnd[ii] : 0.0;
-                    else if (j >= ny) val = bnd ? bnd[nx + ii] : 0.0;
-                    else val = __ldcg(Un + (long long)j * nx + ii);
-                    u[i] = val;
+                if (a.bulk_u) {
+                    // the strip's rows inside the domain are contiguous in U: one bulk copy
+                    // (TMA) issued by thread 0 -- every thread finished with this shared memory
+                    // at the barrier above; the rows off the domain take the Dirichlet data
+                    const int j0 = t.r0 > 0 ? t.r0 - 1 : 0;
+                    const int j1 = t.r0 + t.nrows < ny ? t.r0 + t.nrows : ny - 1;
+                    if (threadIdx.x == 0) {
+                        const unsigned bytes = (unsigned)((size_t)(j1 - j0 + 1) * nx * sizeof(double));
+                        fence_proxy_async_smem();
+                        mbar_arrive_expect_tx(ubar, bytes);
+                        bulk_copy_g2s(u + (size_t)(j0 - (t.r0 - 1)) * nx, Un + (long long)j0 * nx, bytes, ubar);
+                    }
+                    if (t.r0 == 0)
+                        for (int i = threadIdx.x; i < nx; i += NT) u[i] = bnd ? bnd[i] : 0.0;
+                    if (t.r0 + t.nrows == ny)
+                        for (int i = threadIdx.x; i < nx; i += NT) u[(size_t)(t.nrows + 1) * nx + i] = bnd ? bnd[nx + i] : 0.0;
+                    int landed = 1;
+                    if (threadIdx.x == 0) {
+                        landed = mbar_wait_parity(ubar, bb.phase, kBulkWaitPolls) ? 1 : 0;
+                        if (!landed) {
+                            // give up: raise the abort, and let the copy land before leaving
+                            team_fail(c, ST_ETIMEOUT);
+                            mbar_wait_parity(ubar, bb.phase, kBulkWaitPolls);
+                        }
+                    }
+                    bb.phase ^= 1u;
+                    if (!__syncthreads_and(landed)) return;
+                } else {
+#pragma unroll 4
+                    for (int i = threadIdx.x; i < (t.nrows + 2) * nx; i += NT) {
+                        const int jr = i / nx, ii = i - jr * nx, j = t.r0 - 1 + jr;
+                        double val;
+                        if (j < 0) val = bnd ? bnd[ii] : 0.0;
+                        else if (j >= ny) val = bnd ? bnd[nx + ii] : 0.0;
+                        else val = __ldcg(Un + (long long)j * nx + ii);
+                        u[i] = val;
+                    }
+                    __syncthreads();
                 }
-                __syncthreads();
                 if (threadIdx.x == 0) t_load += global_ns() - t_mark;
                 const double pred_prefix = slot[0];
                 if (pred_prefix <= a.tol_res) {
@@ -1885,7 +1973,11 @@ __global__ void __launch_bounds__(NT) wave_kernel(WaveArgs a) {
     Team t;
     team_init(t, b, a.G, a.c.nx, a.c.ny, a.rows_base, a.rows_rem, a.pub + (size_t)team * 2 * a.G * 2 * a.c.nx,
               a.flags + (size_t)team * a.G, a.red_part + (size_t)team * 4 * a.G * 4, a.red_cnt + (size_t)team * 4);
-    wave_body<NT, CONV, NLV, T>(a, team, b, t, smem, s_ok);
+    __shared__ __align__(8) unsigned long long s_ubar;
+    if (threadIdx.x == 0) mbar_init(&s_ubar, 1);
+    __syncthreads();
+    BulkBar bb{&s_ubar, 0u};
+    wave_body<NT, CONV, NLV, T>(a, team, b, t, smem, s_ok, bb);
 }
 
 // ------------------------------------------------ batched instances (one launch)
@@ -1895,6 +1987,7 @@ struct BatchInstance {
     OpConst c;                          // grid, all M levels, dt, closure
     int conv, nlv;                      // closure: Burgers convection, u-dependent viscosity
     int window;                         // levels per window
+    int bulk_u;                         // level strips by bulk copy (nx even, U 16-byte aligned)
     const double* u0;
     const double* bc;
     const double* q;
@@ -1984,19 +2077,19 @@ constexpr int kBatchThreads = 256;  // threads per CTA of every batched kernel
 
 template <int NT, int CLOSURES, typename T>
 __device__ __forceinline__ void wave_body_of(const WaveArgs& a, int bit, int team, int b, Team& t, unsigned char* smem,
-                                             int& s_ok) {
+                                             int& s_ok, BulkBar& bb) {
     if constexpr ((CLOSURES & closure_bit(true, true)) != 0)
-        if (bit == closure_bit(true, true)) return wave_body<NT, true, true, T>(a, team, b, t, smem, s_ok);
+        if (bit == closure_bit(true, true)) return wave_body<NT, true, true, T>(a, team, b, t, smem, s_ok, bb);
     if constexpr ((CLOSURES & closure_bit(true, false)) != 0)
-        if (bit == closure_bit(true, false)) return wave_body<NT, true, false, T>(a, team, b, t, smem, s_ok);
+        if (bit == closure_bit(true, false)) return wave_body<NT, true, false, T>(a, team, b, t, smem, s_ok, bb);
     if constexpr ((CLOSURES & closure_bit(false, true)) != 0)
-        if (bit == closure_bit(false, true)) return wave_body<NT, false, true, T>(a, team, b, t, smem, s_ok);
+        if (bit == closure_bit(false, true)) return wave_body<NT, false, true, T>(a, team, b, t, smem, s_ok, bb);
     if constexpr ((CLOSURES & closure_bit(false, false)) != 0)
-        if (bit == closure_bit(false, false)) return wave_body<NT, false, false, T>(a, team, b, t, smem, s_ok);
+        if (bit == closure_bit(false, false)) return wave_body<NT, false, false, T>(a, team, b, t, smem, s_ok, bb);
 }
 
 template <int NT, int CLOSURES, typename T>
-__device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigned char* smem, int& s_ok) {
+__device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigned char* smem, int& s_ok, BulkBar& bb) {
     const BatchInstance& in = ba.inst[job.inst];
     const BatchTeamWs& ws = ba.ws[job.team];
     const OpConst& oc = in.c;
@@ -2065,6 +2158,7 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
         a.rows_rem = rows_rem;
         a.k_begin = 0;
         a.k_end = ba.newton_max;
+        a.bulk_u = in.bulk_u;
         a.cell_base = base;
         a.tol_res = ba.tol_res;
         a.eta_max = ba.eta_max;
@@ -2098,7 +2192,7 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
         // first converged iteration
         a.kconv = (K > 1 || b == 0) ? ws.kconv : nullptr;
         // the host launches a kernel whose set holds every problem's closure
-        wave_body_of<NT, CLOSURES, T>(a, closure_bit(in.conv != 0, in.nlv != 0), tk, b, t, smem, s_ok);
+        wave_body_of<NT, CLOSURES, T>(a, closure_bit(in.conv != 0, in.nlv != 0), tk, b, t, smem, s_ok, bb);
         if (threadIdx.x == 0) {
             // a wait that gave up is the launch's failure; other codes are the window's
             if (ld_acquire_s32(ws.jstatus) == ST_ETIMEOUT) atomicCAS(ba.status, 0, ST_ETIMEOUT);
@@ -2221,10 +2315,14 @@ template <int NT, typename T, int CLOSURES>
 __global__ void __launch_bounds__(NT, 1) batch_kernel(BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_ok;
+    __shared__ __align__(8) unsigned long long s_ubar;
+    if (threadIdx.x == 0) mbar_init(&s_ubar, 1);
+    __syncthreads();
+    BulkBar bb{&s_ubar, 0u};
     const int c = blockIdx.x;
     for (int j = ba.job_off[c]; j < ba.job_off[c + 1]; ++j) {
         const BatchJob job = ba.jobs[j];
-        batch_instance<NT, CLOSURES, T>(ba, job, smem, s_ok);
+        batch_instance<NT, CLOSURES, T>(ba, job, smem, s_ok, bb);
         __syncthreads();
         if (threadIdx.x == 0) s_ok = ld_acquire_s32(ba.abort_flag);
         __syncthreads();
