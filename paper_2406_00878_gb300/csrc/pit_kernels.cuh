@@ -500,6 +500,14 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
     asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
+// Two adjacent tagged words (16-byte aligned) in one access: each 8-byte word is still
+// single-copy atomic, and each carries its own tag.
+__device__ __forceinline__ void st_relaxed_v2(unsigned long long* p, unsigned long long a, unsigned long long b) {
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+__device__ __forceinline__ void ld_relaxed_v2(const unsigned long long* p, unsigned long long& a, unsigned long long& b) {
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
 __device__ __forceinline__ unsigned long long tagged(unsigned tag, unsigned payload) {
     return ((unsigned long long)tag << 32) | payload;
 }
@@ -547,6 +555,29 @@ __device__ __forceinline__ bool wait_tagged(const TeamCtl& c, const unsigned lon
     }
 }
 
+// wait_tagged for N pairs of adjacent words (16-byte aligned), loaded two at a time.
+template <int N>
+__device__ __forceinline__ bool wait_tagged_pairs(const TeamCtl& c, const unsigned long long* const (&src)[N],
+                                                  unsigned long long (&w)[2 * N], unsigned tag) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        if (src[k]) ld_relaxed_v2(src[k], w[2 * k], w[2 * k + 1]);
+        else w[2 * k] = w[2 * k + 1] = tagged(tag, 0u);
+    }
+    for (long long spins = 0;; ++spins) {
+        bool all = true;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            if ((unsigned)(w[2 * k] >> 32) != tag || (unsigned)(w[2 * k + 1] >> 32) != tag) {
+                all = false;
+                ld_relaxed_v2(src[k], w[2 * k], w[2 * k + 1]);
+            }
+        if (all) return true;
+        if ((spins & 255) == 255 && ld_acquire_s32(c.abort_flag)) return false;
+        if (spins > c.wait_budget) return false;
+    }
+}
+
 // Publish H rows for each neighbour -- lo[h] (this CTA's first rows) for the CTA below and
 // hi[h] (its last rows) for the CTA above -- as sequence-tagged words. Returns the
 // publication's sequence number, which fetch_rows_tagged takes. No barrier: the caller
@@ -563,12 +594,18 @@ __device__ __forceinline__ unsigned long long publish_rows_tagged(Team& t, unsig
     unsigned long long* mine = tpub + ((size_t)(seq & 1) * t.G + t.b) * slot_w;
 #pragma unroll
     for (int h = 0; h < H; ++h)
-        for (int i = threadIdx.x; i < nx; i += NT)
-#pragma unroll
-            for (int k = 0; k < P; ++k) {
-                st_relaxed_u64(mine + h * row_w + (size_t)i * P + k, tagged(tag, Pieces<T>::get(lo[h][i], k)));
-                st_relaxed_u64(mine + (H + h) * row_w + (size_t)i * P + k, tagged(tag, Pieces<T>::get(hi[h][i], k)));
+        for (int i = threadIdx.x; i < nx; i += NT) {
+            if constexpr (P == 2) {
+                // both words of a double in one 16-byte store
+                st_relaxed_v2(mine + h * row_w + (size_t)i * 2, tagged(tag, Pieces<T>::get(lo[h][i], 0)),
+                              tagged(tag, Pieces<T>::get(lo[h][i], 1)));
+                st_relaxed_v2(mine + (H + h) * row_w + (size_t)i * 2, tagged(tag, Pieces<T>::get(hi[h][i], 0)),
+                              tagged(tag, Pieces<T>::get(hi[h][i], 1)));
+            } else {
+                st_relaxed_u64(mine + h * row_w + (size_t)i, tagged(tag, Pieces<T>::get(lo[h][i], 0)));
+                st_relaxed_u64(mine + (H + h) * row_w + (size_t)i, tagged(tag, Pieces<T>::get(hi[h][i], 0)));
             }
+        }
     return seq;
 }
 
@@ -589,16 +626,26 @@ __device__ bool fetch_rows_tagged(const TeamCtl& c, const Team& t, const unsigne
     for (int i0 = 0; i0 < nx && ok; i0 += NT) {
         const int i = i0 + threadIdx.x;
         if (i >= nx) continue;
-        const unsigned long long* src[2 * H * P];
         unsigned long long w[2 * H * P];
+        if constexpr (P == 2) {
+            const unsigned long long* src[2 * H];
 #pragma unroll
-        for (int h = 0; h < H; ++h)
-#pragma unroll
-            for (int k = 0; k < P; ++k) {
-                src[(h * P + k)] = srcS ? srcS + h * row_w + (size_t)i * P + k : nullptr;
-                src[(H + h) * P + k] = srcN ? srcN + h * row_w + (size_t)i * P + k : nullptr;
+            for (int h = 0; h < H; ++h) {
+                src[h] = srcS ? srcS + h * row_w + (size_t)i * 2 : nullptr;
+                src[H + h] = srcN ? srcN + h * row_w + (size_t)i * 2 : nullptr;
             }
-        ok = wait_tagged<2 * H * P>(c, src, w, tag);
+            ok = wait_tagged_pairs<2 * H>(c, src, w, tag);
+        } else {
+            const unsigned long long* src[2 * H * P];
+#pragma unroll
+            for (int h = 0; h < H; ++h)
+#pragma unroll
+                for (int k = 0; k < P; ++k) {
+                    src[(h * P + k)] = srcS ? srcS + h * row_w + (size_t)i * P + k : nullptr;
+                    src[(H + h) * P + k] = srcN ? srcN + h * row_w + (size_t)i * P + k : nullptr;
+                }
+            ok = wait_tagged<2 * H * P>(c, src, w, tag);
+        }
 #pragma unroll
         for (int h = 0; h < H; ++h) {
             unsigned pS[2] = {0u, 0u}, pN[2] = {0u, 0u};
@@ -640,10 +687,8 @@ __device__ __forceinline__ void tagged_arrive(Team& t, unsigned long long* tred,
     unsigned long long* w = tred + ((size_t)(use & 3) * t.G + t.b) * kTagRedWords;
     const unsigned tag = (unsigned)(use + 1);
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        st_relaxed_u64(w + 2 * k, tagged(tag, Pieces<double>::get(vals[k], 0)));
-        st_relaxed_u64(w + 2 * k + 1, tagged(tag, Pieces<double>::get(vals[k], 1)));
-    }
+    for (int k = 0; k < K; ++k)
+        st_relaxed_v2(w + 2 * k, tagged(tag, Pieces<double>::get(vals[k], 0)), tagged(tag, Pieces<double>::get(vals[k], 1)));
 }
 
 // Warp 0 only. Returns false when a wait timed out or the launch aborted. MAXOP is for
@@ -666,11 +711,11 @@ __device__ __forceinline__ bool tagged_finish(const TeamCtl& c, const Team& t, c
     }
     bool ok = true;
     for (int b = lane; b < t.G && ok; b += 32) {
-        const unsigned long long* src[2 * K];
+        const unsigned long long* src[K];
         unsigned long long w[2 * K];
 #pragma unroll
-        for (int k = 0; k < 2 * K; ++k) src[k] = base + (size_t)b * kTagRedWords + k;
-        ok = wait_tagged<2 * K>(c, src, w, tag);
+        for (int k = 0; k < K; ++k) src[k] = base + (size_t)b * kTagRedWords + 2 * k;
+        ok = wait_tagged_pairs<K>(c, src, w, tag);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             if (MAXOP) {
@@ -1002,6 +1047,10 @@ __device__ int level_sor(const TeamCtl& c, Team& t, const Smem<T>& m, double ome
 template <int NT, typename T>
 __device__ int level_sor_deep(const TeamCtl& c, Team& t, const Smem<T>& m, double omega, double tol_w, int* s_ok,
                               const Deep<T>& deep) {
+    // thread 0 adds each step's cycles to counters in shared memory (m.red[56..63]); the
+    // counter reads also keep the compiler from moving work across the steps, which measured
+    // faster than any schedule it picked on its own
+    unsigned long long* const cyc = reinterpret_cast<unsigned long long*>(m.red + 56);
     const int nx = t.nx;
     const int half = (nx + 1) >> 1;            // points of one colour per row, at most
     const int nrows = t.nrows;
@@ -1034,26 +1083,23 @@ __device__ int level_sor_deep(const TeamCtl& c, Team& t, const Smem<T>& m, doubl
     };
     for (int sweep = 1;; ++sweep) {
         unsigned long long key = 0;
+        const long long c0 = clock64();
         // 1.
         const unsigned long long seq = publish_rows_tagged<NT, T, 2>(t, deep.tpub, lo, hi);
-        // 2. (teams of up to 32 CTAs: one word pair per lane; wider teams poll in step 7)
-        unsigned long long pw0 = 0, pw1 = 0;
-        const bool prefetched = have_pending && t.G <= 32;
-        if (prefetched && threadIdx.x < 32 && lane < t.G) {
-            const unsigned long long* w = deep.tred + ((size_t)(pending & 3) * t.G + lane) * kTagRedWords;
-            pw0 = ld_relaxed_u64(w);
-            pw1 = ld_relaxed_u64(w + 1);
-        }
-        // 3.
-        for (int q = threadIdx.x; q < (nrows - 2) * half; q += NT) {
+        const long long c1 = clock64();
+        // 3. (the highest-numbered threads take the odd points out, so warp 0, which has the
+        //    serial work of steps 4 and 7, finishes its share first)
+        for (int q = NT - 1 - threadIdx.x; q < (nrows - 2) * half; q += NT) {
             const int r = q / half;
             update(1 + r, q - r * half, 0, key);
         }
+        const long long c2 = clock64();
         // 4.
         if (!fetch_rows_tagged<NT, T, 2>(c, t, deep.tpub, seq, fS, fN)) {
             *s_ok = 0;
             return -1;
         }
+        const long long c3 = clock64();
         // 5.
         const int r_s = t.r0 - 1, r_n = t.r0 + nrows;
         for (int q = threadIdx.x; q < 4 * half; q += NT) {
@@ -1077,12 +1123,21 @@ __device__ int level_sor_deep(const TeamCtl& c, Team& t, const Smem<T>& m, doubl
                 h[i] = sor_point<T>(h[i], cc[4][i], cc[0][i], cc[1][i], cc[2][i], cc[3][i], xW, xE, xS, xN, om, unused);
             }
         }
+        const long long c4a = clock64();
         __syncthreads();
+        const long long c4 = clock64();
+        // 2. (issued here: by now every CTA has arrived at the previous sweep's reduction;
+        //    teams of up to 32 CTAs, one word pair per lane; wider teams poll in step 7)
+        unsigned long long pw0 = 0, pw1 = 0;
+        const bool prefetched = have_pending && t.G <= 32;
+        if (prefetched && threadIdx.x < 32 && lane < t.G)
+            ld_relaxed_v2(deep.tred + ((size_t)(pending & 3) * t.G + lane) * kTagRedWords, pw0, pw1);
         // 6.
-        for (int q = threadIdx.x; q < nrows * half; q += NT) {
+        for (int q = NT - 1 - threadIdx.x; q < nrows * half; q += NT) {
             const int r = q / half;
             update(r, q - r * half, 1, key);
         }
+        const long long c5 = clock64();
         // 7.
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long w = __shfl_xor_sync(0xffffffffu, key, o);
@@ -1100,10 +1155,9 @@ __device__ int level_sor_deep(const TeamCtl& c, Team& t, const Smem<T>& m, doubl
                     const unsigned tag = (unsigned)(pending + 1);
                     unsigned long long w[2] = {pw0, pw1};
                     if ((unsigned)(w[0] >> 32) != tag || (unsigned)(w[1] >> 32) != tag) {
-                        const unsigned long long* base =
-                            deep.tred + ((size_t)(pending & 3) * t.G + lane) * kTagRedWords;
-                        const unsigned long long* src[2] = {base, base + 1};
-                        ok = wait_tagged<2>(c, src, w, tag);
+                        const unsigned long long* src[1] = {deep.tred + ((size_t)(pending & 3) * t.G + lane) *
+                                                                            kTagRedWords};
+                        ok = wait_tagged_pairs<1>(c, src, w, tag);
                     }
                     dk = ((w[1] & 0xffffffffull) << 32) | (w[0] & 0xffffffffull);
                 }
@@ -1126,7 +1180,19 @@ __device__ int level_sor_deep(const TeamCtl& c, Team& t, const Smem<T>& m, doubl
                 *s_flag = ok ? sor_decision(nan, d, omega, tol_w, sweep, c.max_iter, prev, prev2) : -1;
             }
         }
+        const long long c6a = clock64();
         __syncthreads();
+        const long long c6 = clock64();
+        if (threadIdx.x == 0) {
+            cyc[0] += c1 - c0;   // 1-2 publish
+            cyc[1] += c2 - c1;   // 3 interior colour 0
+            cyc[2] += c3 - c2;   // 4 fetch
+            cyc[3] += c4a - c3;  // 5 boundary rows and halo points
+            cyc[4] += c4 - c4a;  //   barrier
+            cyc[5] += c5 - c4;   // 6 colour 1
+            cyc[6] += c6a - c5;  // 7 reduction and decision
+            cyc[7] += c6 - c6a;  //   barrier
+        }
         const unsigned long long use = t.tag_seq++;
         if (threadIdx.x == 0) {
             unsigned long long kmax = wred[0];
@@ -1528,8 +1594,11 @@ struct WaveArgs {
 // 0 halo waits (flag protocol), 1 team-reduction waits, 2 waits for the previous Newton
 // iteration, 3 total, 4 level setup (all of it), 5 level solves, 6 updates and progress
 // publication, 7 setup: loading u^n_k, 8 setup: team reduction and boundary-row exchange,
-// 9 cells solved (count), 10 sweeps or iterations (count), 11 unused.
-constexpr int kWaveTimers = 12;
+// 9 cells solved (count), 10 sweeps or iterations (count), 11 unused, 12..19 cycles of
+// CTA 0's thread 0 in the steps of the deep SOR sweeps (see level_sor_deep): publish,
+// interior colour 0, fetch, boundary rows and halo points, barrier, colour 1, reduction and
+// decision, barrier.
+constexpr int kWaveTimers = 20;
 
 // u^n_k with its halo rows ((cap + 2 nx) doubles) shares the BiCGStab scratch r..t
 // when it fits there; otherwise it follows uprev.
@@ -1597,6 +1666,9 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
     }
 
     unsigned long long* const ubar = bb.bar;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 8; ++q) reinterpret_cast<unsigned long long*>(m.red + 56)[q] = 0ull;
+    __syncthreads();
     for (int k = a.k_begin + team; k < a.k_end; k += a.K) {
         for (int i = threadIdx.x; i < nloc; i += NT) {
             m.x[i] = T(0);              // du^{-1} = 0
@@ -1960,6 +2032,8 @@ done:
         tm[8] = t_sred;
         tm[9] = n_cells;
         tm[10] = n_sweeps;
+        const unsigned long long* cyc = reinterpret_cast<const unsigned long long*>(m.red + 56);
+        for (int q = 0; q < 8; ++q) tm[12 + q] = cyc[q];
     }
     __syncthreads();
 }
