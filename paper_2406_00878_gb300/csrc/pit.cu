@@ -371,6 +371,9 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
     c.vy = dt / (hy * hy);
     c.mu_a = params->mu_a;
     c.mu_b = params->mu_b;
+    c.vmx = c.mu_a * c.vx;
+    c.vmy = c.mu_a * c.vy;
+    c.kcen = 1.0 + 2.0 * (c.vmx + c.vmy);
 
     pit_status st = PIT_OK;
     auto setup = [&]() -> pit_status {

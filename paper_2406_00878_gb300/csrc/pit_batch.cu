@@ -301,6 +301,9 @@ static pit_status build_launch(pit_batch* b, const std::vector<pit_instance>& in
         c.vy = I.dt / (hy * hy);
         c.mu_a = I.params.mu_a;
         c.mu_b = I.params.mu_b;
+        c.vmx = c.mu_a * c.vx;
+        c.vmy = c.mu_a * c.vy;
+        c.kcen = 1.0 + 2.0 * (c.vmx + c.vmy);
         bi[i].conv = I.params.equation == PIT_BURGERS;
         bi[i].nlv = I.params.mu_b != 0.0;
         bi[i].window = std::min(W, I.M);

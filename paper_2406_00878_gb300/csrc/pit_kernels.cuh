@@ -29,6 +29,7 @@ struct OpConst {
     double jx, jy;    // dt / (2 h_x), dt / (2 h_y): tau * f'(u)/(2h)
     double vx, vy;    // dt / h_x^2, dt / h_y^2
     double mu_a, mu_b;
+    double vmx, vmy, kcen;  // mu_a dt / h_x^2, mu_a dt / h_y^2, 1 + 2 (vmx + vmy): constant-viscosity folds
 };
 
 // Status codes shared with the host (values of pit_status).
@@ -269,7 +270,18 @@ __global__ void __launch_bounds__(NT) residual_kernel(OpConst c, const double* _
         const double uE = node_value(u, bnd, c.nx, c.ny, j, i + 1);
         const double uS = node_value(u, bnd, c.nx, c.ny, j - 1, i);
         const double uN = node_value(u, bnd, c.nx, c.ny, j + 1, i);
-        double r = (up[k] - uC) - tau_F<CONV, NLV>(c, uC, uW, uE, uS, uN);
+        double r;
+        if (CONV && !NLV) {
+            // constant-viscosity Burgers with the constants folded (nine FP64 operations):
+            // r = u^{n-1} - kcen uC - uE (cx uE - vmx) + uW (cx uW + vmx) - (the same in y)
+            r = fma(-c.kcen, uC, up[k]);
+            r = fma(-uE, fma(c.cx, uE, -c.vmx), r);
+            r = fma(uW, fma(c.cx, uW, c.vmx), r);
+            r = fma(-uN, fma(c.cy, uN, -c.vmy), r);
+            r = fma(uS, fma(c.cy, uS, c.vmy), r);
+        } else {
+            r = (up[k] - uC) - tau_F<CONV, NLV>(c, uC, uW, uE, uS, uN);
+        }
         if (q) r = fma(c.dt, q[(long long)n * c.Ns + k], r);
         R[(long long)n * c.Ns + k] = r;
         key = abs_key(r);
@@ -1081,6 +1093,11 @@ __device__ int level_sor_deep(const TeamCtl& c, Team& t, const Smem<T>& m, doubl
         const unsigned long long kk = mag_key(tk);
         key = kk > key ? kk : key;
     };
+    // thread's first point (row, index in row) and the step of NT points, found once: the
+    // sweep loops then walk their points without an integer division per point
+    const int q_first = NT - 1 - (int)threadIdx.x;
+    const int r_first = q_first / half, qi_first = q_first - r_first * half;
+    const int dr = NT / half, dqi = NT - dr * half;
     for (int sweep = 1;; ++sweep) {
         unsigned long long key = 0;
         const long long c0 = clock64();
@@ -1089,9 +1106,17 @@ __device__ int level_sor_deep(const TeamCtl& c, Team& t, const Smem<T>& m, doubl
         const long long c1 = clock64();
         // 3. (the highest-numbered threads take the odd points out, so warp 0, which has the
         //    serial work of steps 4 and 7, finishes its share first)
-        for (int q = NT - 1 - threadIdx.x; q < (nrows - 2) * half; q += NT) {
-            const int r = q / half;
-            update(1 + r, q - r * half, 0, key);
+        {
+            int r = r_first, qi = qi_first;  // point NT - 1 - threadIdx.x, then NT points on
+            for (int q = NT - 1 - threadIdx.x; q < (nrows - 2) * half; q += NT) {
+                update(1 + r, qi, 0, key);
+                qi += dqi;
+                r += dr;
+                if (qi >= half) {
+                    qi -= half;
+                    ++r;
+                }
+            }
         }
         const long long c2 = clock64();
         // 4.
@@ -1133,9 +1158,17 @@ __device__ int level_sor_deep(const TeamCtl& c, Team& t, const Smem<T>& m, doubl
         if (prefetched && threadIdx.x < 32 && lane < t.G)
             ld_relaxed_v2(deep.tred + ((size_t)(pending & 3) * t.G + lane) * kTagRedWords, pw0, pw1);
         // 6.
-        for (int q = NT - 1 - threadIdx.x; q < nrows * half; q += NT) {
-            const int r = q / half;
-            update(r, q - r * half, 1, key);
+        {
+            int r = r_first, qi = qi_first;
+            for (int q = NT - 1 - threadIdx.x; q < nrows * half; q += NT) {
+                update(r, qi, 1, key);
+                qi += dqi;
+                r += dr;
+                if (qi >= half) {
+                    qi -= half;
+                    ++r;
+                }
+            }
         }
         const long long c5 = clock64();
         // 7.
@@ -1644,8 +1677,8 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
     // Burgers-type closures with constant viscosity have a constant diagonal 1 + 2 mu_a (vx + vy)
     const double dconst = 1.0 / (1.0 + 2.0 * oc.mu_a * (oc.vx + oc.vy));
     // their folded constants: viscous mu_a tau / h^2, and the scaled couplings
-    const double vmu_x = oc.mu_a * oc.vx, vmu_y = oc.mu_a * oc.vy;
-    const double kcen = 1.0 + 2.0 * (vmu_x + vmu_y);
+    const double vmu_x = oc.vmx, vmu_y = oc.vmy;
+    const double kcen = oc.kcen;
     const double sjx = oc.jx * dconst, sjy = oc.jy * dconst, svx = vmu_x * dconst, svy = vmu_y * dconst;
     // neighbour rows for one-exchange SOR sweeps: in the BiCGStab scratch r..t (5 cap values),
     // which SOR leaves unused and u^n_k no longer needs once the level's system is formed.
