@@ -117,6 +117,12 @@ __device__ __forceinline__ bool opposite_nonzero(double x, double y) {
     return ((bx ^ by) < 0) && (bx & mag) != 0 && (by & mag) != 0;
 }
 
+__device__ __forceinline__ bool opposite_nonzero(float x, float y) {
+    const int bx = __float_as_int(x), by = __float_as_int(y);
+    const int mag = 0x7fffffff;
+    return ((bx ^ by) < 0) && (bx & mag) != 0 && (by & mag) != 0;
+}
+
 // Maxima of four keys over the CTA, valid on thread 0 only (one barrier); red holds
 // NT/32 * 4 keys.
 template <int NT>
@@ -1680,6 +1686,8 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
     const double vmu_x = oc.vmx, vmu_y = oc.vmy;
     const double kcen = oc.kcen;
     const double sjx = oc.jx * dconst, sjy = oc.jy * dconst, svx = vmu_x * dconst, svy = vmu_y * dconst;
+    // the same in the level-solve precision (FP32 solves form their couplings in FP32)
+    const T sjx_t = (T)sjx, sjy_t = (T)sjy, svx_t = (T)svx, svy_t = (T)svy, dconst_t = (T)dconst;
     // neighbour rows for one-exchange SOR sweeps: in the BiCGStab scratch r..t (5 cap values),
     // which SOR leaves unused and u^n_k no longer needs once the level's system is formed.
     // The conditions are the same on every CTA of the team (cap and rows_base are team-wide).
@@ -1709,6 +1717,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
         }
         double prefix = 0.0;            // running max of ||r^j_k||_inf, j <= n (thread 0)
         double sumsq = 0.0;
+        float sumsq_f = 0.0f;
         bool uprev_valid = true;        // uprev holds u^{n-1}_k (false after a skipped level)
         __syncthreads();
         for (int n = 0; n < M; ++n) {
@@ -1829,14 +1838,16 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 }
                 // 3. residual r^n_k, scaled couplings, rhs; uprev <- u^n_k
                 const double* qn = a.q ? a.q + (long long)n * Ns + off0 : nullptr;
+                float gmax_f = 0.0f;  // FP32 solves: largest FP32 row sum of this thread's rows
                 struct NodeIn {
                     double uC, uW, uE, uS, uN, up, x, q;
                 };
                 struct NodeOut {
-                    double r, aW, aE, aS, aN, bval, d;
+                    double r, bval, d;
+                    T aW, aE, aS, aN;  // Jacobi-scaled couplings, in the level-solve precision
                 };
-                auto load_node = [&](int i) {
-                    const int jl = i / nx, ii = i - jl * nx, j = t.r0 + jl;
+                auto load_node = [&](int i, int jl, int ii) {
+                    const int j = t.r0 + jl;
                     const int ku = (jl + 1) * nx + ii;
                     NodeIn v;
                     v.uC = u[ku];
@@ -1849,8 +1860,8 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                     v.q = qn ? qn[i] : 0.0;
                     return v;
                 };
-                auto form_node = [&](int i, const NodeIn& v) {
-                    const int jl = i / nx, ii = i - jl * nx, j = t.r0 + jl;
+                auto form_node = [&](int jl, int ii, const NodeIn& v) {
+                    const int j = t.r0 + jl;
                     NodeOut o;
                     if (CONV && !NLV) {
                         // Burgers with constant viscosity: eq. 3-5 and the Jacobian with the
@@ -1864,49 +1875,78 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                         r = fma(-v.uN, fma(oc.cy, v.uN, -vmu_y), r);
                         o.r = fma(v.uS, fma(oc.cy, v.uS, vmu_y), r);
                         o.d = dconst;
-                        o.aE = fma(sjx, v.uE, -svx);
-                        o.aW = fma(-sjx, v.uW, -svx);
-                        o.aN = fma(sjy, v.uN, -svy);
-                        o.aS = fma(-sjy, v.uS, -svy);
+                        if constexpr (sizeof(T) == 4) {
+                            // FP32 level solves: the couplings are formed in FP32 from u in
+                            // FP32 (they are stored in FP32 anyway); only r and the rhs are FP64
+                            o.aE = fmaf(sjx_t, (float)v.uE, -svx_t);
+                            o.aW = fmaf(-sjx_t, (float)v.uW, -svx_t);
+                            o.aN = fmaf(sjy_t, (float)v.uN, -svy_t);
+                            o.aS = fmaf(-sjy_t, (float)v.uS, -svy_t);
+                        } else {
+                            o.aE = fma(sjx, v.uE, -svx);
+                            o.aW = fma(-sjx, v.uW, -svx);
+                            o.aN = fma(sjy, v.uN, -svy);
+                            o.aS = fma(-sjy, v.uS, -svy);
+                        }
                     } else {
                         o.r = (v.up - v.uC) - tau_F<CONV, NLV>(oc, v.uC, v.uW, v.uE, v.uS, v.uN);
-                        double aC;
-                        jac_row<CONV, NLV>(oc, v.uC, v.uW, v.uE, v.uS, v.uN, aC, o.aW, o.aE, o.aS, o.aN);
+                        double aC, aW, aE, aS, aN;
+                        jac_row<CONV, NLV>(oc, v.uC, v.uW, v.uE, v.uS, v.uN, aC, aW, aE, aS, aN);
                         o.d = NLV ? 1.0 / aC : dconst;
-                        o.aW *= o.d;
-                        o.aE *= o.d;
-                        o.aS *= o.d;
-                        o.aN *= o.d;
+                        o.aW = (T)(aW * o.d);
+                        o.aE = (T)(aE * o.d);
+                        o.aS = (T)(aS * o.d);
+                        o.aN = (T)(aN * o.d);
                     }
                     if (qn) o.r = fma(oc.dt, v.q, o.r);
-                    if (ii == 0) o.aW = 0.0;
-                    if (ii == nx - 1) o.aE = 0.0;
-                    if (j == 0) o.aS = 0.0;
-                    if (j == ny - 1) o.aN = 0.0;
+                    if (ii == 0) o.aW = T(0);
+                    if (ii == nx - 1) o.aE = T(0);
+                    if (j == 0) o.aS = T(0);
+                    if (j == ny - 1) o.aN = T(0);
                     o.bval = o.r + v.x;  // r^n + du^{n-1}
                     return o;
                 };
                 auto store_node = [&](int i, const NodeIn& v, const NodeOut& o) {
-                    m.cw[i] = (T)o.aW;
-                    m.ce[i] = (T)o.aE;
-                    m.cs[i] = (T)o.aS;
-                    m.cn[i] = (T)o.aN;
-                    m.bs[i] = (T)(o.d * o.bval);
-                    m.x[i] = (T)o.bval;  // SOR start
-                    uprev[i] = v.uC;     // u^n_k for the next level's time difference
-                    const unsigned long long kr = abs_key(o.r),
-                                             kg = abs_key(fabs(o.aW) + fabs(o.aE) + fabs(o.aS) + fabs(o.aN)),
-                                             kb = abs_key(o.bval);
+                    m.cw[i] = o.aW;
+                    m.ce[i] = o.aE;
+                    m.cs[i] = o.aS;
+                    m.cn[i] = o.aN;
+                    const T xt = (T)o.bval;
+                    if constexpr (sizeof(T) == 4 && CONV && !NLV) m.bs[i] = xt * dconst_t;  // FP32 product
+                    else m.bs[i] = (T)(o.d * o.bval);
+                    m.x[i] = xt;      // SOR start
+                    uprev[i] = v.uC;  // u^n_k for the next level's time difference
+                    const unsigned long long kr = abs_key(o.r), kb = abs_key(o.bval);
                     krmax = kr > krmax ? kr : krmax;
-                    krs = kg > krs ? kg : krs;
                     kbmax = kb > kbmax ? kb : kbmax;
+                    // Gershgorin row sum of the couplings as stored (FP32 sums for FP32 solves;
+                    // biased upward once per thread below so it stays an upper bound)
+                    if constexpr (sizeof(T) == 4) {
+                        gmax_f = fmaxf(gmax_f, fabsf(o.aW) + fabsf(o.aE) + fabsf(o.aS) + fabsf(o.aN));
+                    } else {
+                        const unsigned long long kg = abs_key(fabs(o.aW) + fabs(o.aE) + fabs(o.aS) + fabs(o.aN));
+                        krs = kg > krs ? kg : krs;
+                    }
                     ns |= opposite_nonzero(o.aW, o.aE) || opposite_nonzero(o.aS, o.aN);
                 };
+                // node i = (local row jl, column ii), stepped by NT without a division per node
+                int jl = (int)threadIdx.x / nx, ii = (int)threadIdx.x - jl * nx;
+                const int djl = NT / nx, dii = NT - djl * nx;
 #pragma unroll 2
                 for (int i = threadIdx.x; i < nloc; i += NT) {
-                    const NodeIn v = load_node(i);
-                    store_node(i, v, form_node(i, v));
+                    const NodeIn v = load_node(i, jl, ii);
+                    store_node(i, v, form_node(jl, ii, v));
+                    ii += dii;
+                    jl += djl;
+                    if (ii >= nx) {
+                        ii -= nx;
+                        ++jl;
+                    }
                 }
+                // four FP32 magnitudes summed in FP32 err by at most 3 units in 2^-24 of the sum:
+                // the bias 2^-20 keeps the bound above the exact sum of the stored couplings
+                // (a NaN in u shows in max |r|, which ends the window before any solve)
+                if constexpr (sizeof(T) == 4) krs = abs_key((double)gmax_f * (1.0 + 0x1p-20));
             }
             // 4. team reduction: max |r|, Gershgorin bound, 2 stop + nonsymmetric-row flag, max |rhs|
             //    (every CTA of the team takes the same decisions from these)
@@ -2011,9 +2051,13 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 // 6. U^n += du^n; du^n stays in x for the next level
                 double* Uw = a.U + (long long)n * Ns + off0;
                 for (int i = threadIdx.x; i < nloc; i += NT) {
-                    const double dx = (double)m.x[i];
+                    const T xt = m.x[i];
+                    const double dx = (double)xt;
                     __stcg(Uw + i, uprev[i] + dx);
-                    sumsq += dx * dx;
+                    // the update norm is a statistic: with FP32 level solves it is summed in
+                    // FP32, which leaves the scarce FP64 pipe to the arithmetic of the method
+                    if constexpr (sizeof(T) == 4) sumsq_f = fmaf(xt, xt, sumsq_f);
+                    else sumsq += dx * dx;
                 }
                 __syncthreads();
                 if (threadIdx.x == 0) {
@@ -2030,7 +2074,8 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
         }
         {
             // iteration k done on every level
-            double ss[1] = {sumsq};
+            double ss[1] = {sumsq + (double)sumsq_f};
+            sumsq_f = 0.0f;
             block_sum<NT, 1>(ss, m.red);
             if (threadIdx.x == 0) {
                 if (a.cta_sumsq) a.cta_sumsq[(size_t)k * a.G + b] = ss[0];
