@@ -108,9 +108,10 @@ typedef struct {
                                W, each starting from the plain guess u^n = u^{s-1} at its first
                                level s. The all-at-once system is block lower-triangular in time,
                                so the solution is the same. In both modes a window whose Newton
-                               diverges (residual not finite or above 1e10) or does not converge
-                               is halved and restarted from the plain guess, and grows back
-                               after a success */
+                               diverges (a residual that is not finite, above 1e10, or in an
+                               iteration k >= 1 above 1e3 times the first iteration's running
+                               residual at that level) or does not converge is halved and
+                               restarted from the plain guess, and grows back after a success */
     int batch_wave_nodes;   /* pit_batch_create: a problem with nx*ny >= batch_wave_nodes is a wavefront
                                job of the persistent launch (up to 6 teams, nearly every SM, several
                                Newton iterations of a window in flight), such jobs one after another;

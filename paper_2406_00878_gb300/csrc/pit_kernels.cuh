@@ -37,6 +37,12 @@ enum : int { ST_OK = 0, ST_ENOCONV = 4, ST_EDIVERGED = 5, ST_ETIMEOUT = 6 };
 
 // A Newton residual above this (or not finite) counts as divergence.
 constexpr double kDiverged = 1e10;
+// A Newton iteration k >= 1 whose residual at a level exceeds this many times the first
+// iteration's running residual there (or tol_res, if larger) counts as diverging too:
+// from a poor start Newton on these problems was seen to grow the residual up to ~70x
+// and still converge, while runs that grew it past ~1000x never did and burned capped
+// level solves; the window is then retried shorter (same solution, block triangular).
+constexpr double kGrowth = 1e3;
 
 // --------------------------------------------------------- memory primitives
 
@@ -1719,6 +1725,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
         double sumsq = 0.0;
         float sumsq_f = 0.0f;
         bool uprev_valid = true;        // uprev holds u^{n-1}_k (false after a skipped level)
+        double first_res = 1.0 / 0.0;   // iteration 0's running residual at the current level
         __syncthreads();
         for (int n = 0; n < M; ++n) {
             // 1. wait until iteration k - 1 has finished level n on rows r0-1 .. r0+nrows and
@@ -1763,7 +1770,11 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
             // 2. the previous iteration's running max (lane pl: it acquired CTA 0's progress), and
             //    in the same round trip u^{n-1}_k when the previous level was skipped (the global,
             //    final iterate) and u^n_k (below)
-            if (threadIdx.x == pl) slot[0] = k > a.k_begin ? __ldcg(a.cell_prefix + (size_t)(k - 1) * M + n) : 1.0 / 0.0;
+            if (threadIdx.x == pl) {
+                slot[0] = k > a.k_begin ? __ldcg(a.cell_prefix + (size_t)(k - 1) * M + n) : 1.0 / 0.0;
+                // the first iteration's running residual at this level (finished long before)
+                slot[1] = k > 0 ? __ldcg(a.cell_prefix + n) : 1.0 / 0.0;
+            }
             const bool reload_prev = !uprev_valid;
             if (reload_prev) {
                 const double* up = n == 0 ? a.u0 + off0 : a.U + (long long)(n - 1) * Ns + off0;
@@ -1818,6 +1829,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 }
                 if (threadIdx.x == 0) t_load += global_ns() - t_mark;
                 const double pred_prefix = slot[0];
+                first_res = slot[1];
                 if (pred_prefix <= a.tol_res) {
                     // levels 0..n converged in iteration k - 1: du^n_k = 0, nothing to solve
                     __syncthreads();  // slot[0] read by every thread
@@ -1990,7 +2002,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 return;
             }
             if (g3[2] >= 2.0) goto done;  // another iteration has converged (or the launch aborts)
-            if (!(g3[0] < kDiverged)) {
+            if (!(g3[0] < kDiverged) || g3[0] > kGrowth * fmax(first_res, a.tol_res)) {
                 // NaN/Inf or a runaway residual: Newton diverges on this range of levels. One
                 // team (a batch problem) ends its window and lets the caller retry a shorter
                 // one; several teams end the launch with PIT_EDIVERGED.

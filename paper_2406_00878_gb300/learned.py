@@ -41,6 +41,7 @@ class LearnedConfig:
     gen_window: int = 32          # windows for generating training solutions (robust Newton)
     solve_window: int = 0         # windows for the per-problem evaluation solves (0 = all levels at once)
     batch_window: int = 32        # windows of the batched evaluation forms
+    batch_wave_nodes: int = 65536  # batched forms: grids of at least this many nodes are wavefront jobs
     chunk: int = 512              # problems per generation batch
     extra: dict = field(default_factory=dict)
 
@@ -138,6 +139,7 @@ def evaluate(cfg: LearnedConfig, net, probs):
 
       plain     pit_solve per problem, FP64 level solves, plain guess u^n = u^0;
       learned   pit_solve per problem, FP64, from the network's guess (inference timed);
+      learned_fp32  the same with FP32 level solves inside FP64 Newton;
       batched   one pit_batch launch for all problems, FP32 level solves inside FP64 Newton,
                 windows of cfg.batch_window levels from the plain guess;
       combined  the network's guesses for all problems, then one pit_batch launch, FP32
@@ -149,7 +151,7 @@ def evaluate(cfg: LearnedConfig, net, probs):
     import torch
     S, dof = len(probs), cfg.M * cfg.n * cfg.n
     sol = {k: torch.empty((S, dof), dtype=torch.float64, device="cuda")
-           for k in ("plain", "learned", "batched", "combined")}
+           for k in ("plain", "learned", "learned_fp32", "batched", "combined")}
     guess = torch.empty((S, dof), dtype=torch.float64, device="cuda")
     infer(cfg, net, probs, guess)  # warm-up
     ms_net = infer(cfg, net, probs, guess)
@@ -169,6 +171,20 @@ def evaluate(cfg: LearnedConfig, net, probs):
                      "ms_learned": info_l["ms_total"] + ms_net / S, "ms_net": ms_net / S,
                      "res0_plain": info_p["res_inf"][0], "res0_learned": info_l["res_inf"][0]})
         ctx.close()
+    # the learned guess with FP32 level solves, problem by problem (no batching)
+    opt32 = pit.pit_default_options()
+    opt32.window = cfg.solve_window
+    opt32.precision = pit.PIT_FP32_INNER
+    ms32, it32, ok32 = 0.0, [], 0
+    for i, p in enumerate(probs):
+        ctx = pit.context_for(p, opt32)
+        U = sol["learned_fp32"][i]
+        U.copy_(guess[i])
+        st, info = pit.pit_solve(ctx, U, check=False)
+        ms32 += info["ms_total"] + ms_net / S
+        it32.append(info["newton_iters"])
+        ok32 += st == 0
+        ctx.close()
     ok = [r["plain_ok"] for r in rows]
     forms = {}
     n_ok = sum(ok)
@@ -177,9 +193,12 @@ def evaluate(cfg: LearnedConfig, net, probs):
     forms["learned"] = {"ms": sum(r["ms_learned"] for r in rows), "converged": sum(r["learned_ok"] for r in rows),
                         "newton_iters_mean": float(np.mean([r["it_learned"] for r in rows])), "ms_net": ms_net,
                         "max_rel_diff_vs_plain": _max_rel_diff(sol["learned"], sol["plain"], ok)}
+    forms["learned_fp32"] = {"ms": ms32, "converged": ok32, "newton_iters_mean": float(np.mean(it32)),
+                             "ms_net": ms_net, "max_rel_diff_vs_plain": _max_rel_diff(sol["learned_fp32"], sol["plain"], ok)}
     bopt = pit.pit_default_options()
     bopt.precision = pit.PIT_FP32_INNER
     bopt.window = cfg.batch_window
+    bopt.batch_wave_nodes = cfg.batch_wave_nodes
     for name, start in (("batched", pit.PIT_START_PLAIN), ("combined", pit.PIT_START_GIVEN)):
         bopt.window_start = start
         Ub = sol[name]
