@@ -56,7 +56,8 @@ typedef enum {
     PIT_ENOCONV = 4,      /* Newton or a level solve hit its iteration cap */
     PIT_EDIVERGED = 5,    /* NaN/Inf in the residual or the update */
     PIT_ETIMEOUT = 6,     /* a bounded device-side wait ran out of budget */
-    PIT_EUNSUPPORTED = 7  /* the problem does not fit the kernels' limits */
+    PIT_EUNSUPPORTED = 7, /* the problem does not fit the kernels' limits */
+    PIT_EBOUNDS = 8       /* bounds-checking build only: a kernel indexed an array out of range */
 } pit_status;
 
 typedef enum { PIT_HEAT = 0, PIT_BURGERS = 1 } pit_equation;
@@ -242,6 +243,24 @@ pit_status pit_newton_step(pit_ctx* ctx, double* U_dev, pit_step_info* info);
  * and halo points, a barrier, colour 1, the lagged reduction and stop decision, a barrier.
  * Copies up to n values and returns how many there are (20 K), or -1 for a NULL argument. */
 int pit_wave_timers(const pit_ctx* ctx, unsigned long long* out, int n);
+
+/* The bounds-checking build. Compiled with PIT_CHECK_BOUNDS, every indexed access of the
+ * residual, assembly, level-chain, wavefront and batched kernels to the problem's arrays
+ * (U, u0, boundary data, source, right-hand sides, coefficient planes), to the per-iteration
+ * records, and to the CTA's shared-memory arrays (couplings, rhs, iterate, solver vectors,
+ * halo rows, u^n_k strip, neighbour rows) is checked against the array's extent, and every
+ * bulk copy against its source and destination ranges and 16-byte alignment. An access out
+ * of range is skipped (a load reads a scratch word, a store writes it; a bad bulk copy is
+ * not issued), the array's id is recorded, and the kernel runs on: nothing traps. This call
+ * synchronises the device, sets *enabled = 1 in that build (0 in the ordinary build, where
+ * the checks are compiled out) and *first_id to the id of the first array found out of
+ * range since the previous call (0 = none), then clears the record. Returns PIT_EBOUNDS
+ * when an id was recorded, PIT_EINVAL for NULL arguments, PIT_ECUDA when the device
+ * cannot be read. Ids: 1 U, 2 u0, 3 boundary data, 4 source, 5 R, 6 coefficient planes,
+ * 7 dU; 16 + k the k-th shared array (cw ce cs cn bs x r rh p v t haloS haloN); 40 uprev,
+ * 41 u^n_k strip, 42 neighbour rows; 50 running-residual record, 51 cell iterations, 52
+ * update norms, 53 progress words, 58 per-level records; 60 a bulk copy. */
+pit_status pit_bounds_status(int* enabled, int* first_id);
 
 /* Row (a4): Newton from the iterate in U_dev until ||R||_inf <= tol_res or
  * newton_max updates (PIT_ENOCONV; U_dev holds the last iterate). By default all

@@ -11,6 +11,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libpit.so")
+# the bounds-checking build (-DPIT_CHECK_BOUNDS): every kernel array access checked
+CHECK_LIB = os.path.join(OUT_DIR, "libpit_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -45,16 +47,20 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libpit.so")
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, check_bounds: bool = False) -> str:
     """Compile every csrc/*.cu into paper_2406_00878_gb300/_build/libpit.so (skipped when up to date).
-    The compilations run in parallel (one nvcc each, at most one per CPU), then one nvcc call links."""
+    The compilations run in parallel (one nvcc each, at most one per CPU), then one nvcc call links.
+    check_bounds: the bounds-checking build, libpit_check.so (see pit_bounds_status)."""
     os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
+    lib_path = CHECK_LIB if check_bounds else LIB
+    if not force and os.path.exists(lib_path):
+        t = os.path.getmtime(lib_path)
         if all(os.path.getmtime(d) <= t for d in _deps()):
-            return LIB
-    tag = f"{os.getpid()}"
+            return lib_path
+    tag = f"{os.getpid()}{'c' if check_bounds else ''}"
     flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O2", f"-I{INCLUDE}", f"-I{CSRC}"]
+    if check_bounds:
+        flags.append("-DPIT_CHECK_BOUNDS")
     if verbose:
         flags.insert(0, "-Xptxas=-v")
     jobs = units()
@@ -71,16 +77,21 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for (src, extra, _), c in zip(jobs, codes):
             if c != 0:
                 raise subprocess.CalledProcessError(c, f"nvcc -c {src} {' '.join(extra)}")
-        tmp = LIB + f".{tag}.tmp"
+        tmp = lib_path + f".{tag}.tmp"
         subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs], check=True)
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib_path)
     finally:
         for o in objs:
             if os.path.exists(o):
                 os.remove(o)
-    return LIB
+    return lib_path
+
+
+def build_check(force: bool = False) -> str:
+    """The bounds-checking build, _build/libpit_check.so."""
+    return build(force=force, check_bounds=True)
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, check_bounds="--check-bounds" in sys.argv))

@@ -154,8 +154,44 @@ extern "C" const char* pit_status_string(pit_status s) {
         case PIT_EDIVERGED: return "PIT_EDIVERGED";
         case PIT_ETIMEOUT: return "PIT_ETIMEOUT";
         case PIT_EUNSUPPORTED: return "PIT_EUNSUPPORTED";
+        case PIT_EBOUNDS: return "PIT_EBOUNDS";
     }
     return "PIT_UNKNOWN";
+}
+
+// ------------------------------------------------------- bounds-checking build
+
+namespace {
+constexpr int kMaxBoundsReaders = 128;
+int (*g_bounds_readers[kMaxBoundsReaders])();
+int g_n_bounds_readers = 0;
+}  // namespace
+
+namespace pit {
+// Called from static initialisers of the check build's translation units (one thread, at
+// load time).
+void register_bounds_reader(int (*reader)()) {
+    if (g_n_bounds_readers < kMaxBoundsReaders) g_bounds_readers[g_n_bounds_readers++] = reader;
+}
+}  // namespace pit
+
+extern "C" pit_status pit_bounds_status(int* enabled, int* first_id) {
+    if (!enabled || !first_id) return PIT_EINVAL;
+#ifdef PIT_CHECK_BOUNDS
+    *enabled = 1;
+#else
+    *enabled = 0;
+#endif
+    *first_id = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return PIT_ECUDA;
+    bool failed = false;
+    for (int i = 0; i < g_n_bounds_readers; ++i) {
+        const int v = g_bounds_readers[i]();
+        if (v < 0) failed = true;
+        else if (v > 0 && *first_id == 0) *first_id = v;
+    }
+    if (failed) return PIT_ECUDA;
+    return *first_id ? PIT_EBOUNDS : PIT_OK;
 }
 
 extern "C" const char* pit_last_error(const pit_ctx* ctx) { return ctx ? ctx->err : "null context"; }

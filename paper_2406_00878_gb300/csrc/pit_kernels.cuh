@@ -17,6 +17,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "pit_check.cuh"
+
 namespace pit {
 
 // ------------------------------------------------------------------ constants
@@ -201,10 +203,10 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* red) {
 
 // Value of level vector u at (j, i), j in [-1, ny], i in [-1, nx]; off-interior
 // nodes read the level's Dirichlet data (zero when bnd == nullptr).
-__device__ __forceinline__ double node_value(const double* __restrict__ u, const double* __restrict__ bnd,
-                                             int nx, int ny, int j, int i) {
+template <typename PU, typename PB>
+__device__ __forceinline__ double node_value(const PU& u, const PB& bnd, int nx, int ny, int j, int i) {
     if (i >= 0 && i < nx && j >= 0 && j < ny) return u[(long long)j * nx + i];
-    if (bnd == nullptr) return 0.0;
+    if (!bnd) return 0.0;
     if (j < 0) return bnd[i];
     if (j >= ny) return bnd[nx + i];
     if (i < 0) return bnd[2 * nx + j];
@@ -272,11 +274,16 @@ __global__ void __launch_bounds__(NT) residual_kernel(OpConst c, const double* _
     const int n = blockIdx.y;  // level index 0..M-1 <-> u^{n+1}
     const long long k = (long long)blockIdx.x * NT + threadIdx.x;
     unsigned long long key = 0;
+    const long long nb = 2 * c.nx + 2 * c.ny, tot = (long long)c.M * c.Ns;
+    const auto Uc = chk(U, tot, kChkU);
+    const auto bcc = chk(bc, c.M * nb, kChkBc);
+    const auto qc = chk(q, tot, kChkQ);
+    const auto Rc = chk(R, tot, kChkR);
     if (k < c.Ns) {
         const int j = (int)(k / c.nx), i = (int)(k - (long long)j * c.nx);
-        const double* u = U + (long long)n * c.Ns;
-        const double* up = (n == 0) ? u0 : U + (long long)(n - 1) * c.Ns;
-        const double* bnd = bc ? bc + (long long)n * (2 * c.nx + 2 * c.ny) : nullptr;
+        const auto u = Uc + (long long)n * c.Ns;
+        const auto up = (n == 0) ? chk(u0, c.Ns, kChkU0) : Uc + (long long)(n - 1) * c.Ns;
+        const auto bnd = bc ? bcc + (long long)n * nb : bcc;
         const double uC = u[k];
         const double uW = node_value(u, bnd, c.nx, c.ny, j, i - 1);
         const double uE = node_value(u, bnd, c.nx, c.ny, j, i + 1);
@@ -294,8 +301,8 @@ __global__ void __launch_bounds__(NT) residual_kernel(OpConst c, const double* _
         } else {
             r = (up[k] - uC) - tau_F<CONV, NLV>(c, uC, uW, uE, uS, uN);
         }
-        if (q) r = fma(c.dt, q[(long long)n * c.Ns + k], r);
-        R[(long long)n * c.Ns + k] = r;
+        if (q) r = fma(c.dt, qc[(long long)n * c.Ns + k], r);
+        Rc[(long long)n * c.Ns + k] = r;
         key = abs_key(r);
     }
     key = block_max_u64<NT>(key, red);
@@ -318,10 +325,14 @@ __global__ void __launch_bounds__(NT) assemble_kernel(OpConst c, const double* _
     const long long k = (long long)blockIdx.x * NT + threadIdx.x;
     const long long plane = (long long)c.M * c.Ns;
     unsigned long long key = 0;
+    const long long nb = 2 * c.nx + 2 * c.ny;
+    const auto Uc = chk(U, plane, kChkU);
+    const auto bcc = chk(bc, c.M * nb, kChkBc);
+    const auto coefc = chk(coef, 5 * plane, kChkCoef);
     if (k < c.Ns) {
         const int j = (int)(k / c.nx), i = (int)(k - (long long)j * c.nx);
-        const double* u = U + (long long)n * c.Ns;
-        const double* bnd = bc ? bc + (long long)n * (2 * c.nx + 2 * c.ny) : nullptr;
+        const auto u = Uc + (long long)n * c.Ns;
+        const auto bnd = bc ? bcc + (long long)n * nb : bcc;
         const double uC = u[k];
         const double uW = node_value(u, bnd, c.nx, c.ny, j, i - 1);
         const double uE = node_value(u, bnd, c.nx, c.ny, j, i + 1);
@@ -333,7 +344,7 @@ __global__ void __launch_bounds__(NT) assemble_kernel(OpConst c, const double* _
         if (i == c.nx - 1) aE = 0.0;
         if (j == 0) aS = 0.0;
         if (j == c.ny - 1) aN = 0.0;
-        double* o = coef + (long long)n * c.Ns + k;
+        const auto o = coefc + ((long long)n * c.Ns + k);
         if (SCALED) {
             const double d = 1.0 / aC;
             aW *= d;
@@ -361,8 +372,10 @@ __global__ void __launch_bounds__(NT) assemble_kernel(OpConst c, const double* _
 
 static __global__ void plain_guess_kernel(const double* __restrict__ u0, double* __restrict__ U, long long Ns, int M) {
     const long long total = Ns * (long long)M;
+    const auto Uc = chk(U, total, kChkU);
+    const auto u0c = chk(u0, Ns, kChkU0);
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x)
-        U[t] = u0[t % Ns];
+        Uc[t] = u0c[t % Ns];
 }
 
 // ------------------------------------------------------ (a3) the level chain
@@ -462,7 +475,8 @@ __device__ __forceinline__ void publish_and_wait(const TeamCtl& c, Team& t, unsi
 // (row r0+nrows). Rows outside the domain are zero (the correction vanishes on
 // the Dirichlet boundary). Returns false when the launch aborted.
 template <int NT, typename T>
-__device__ bool exchange_halo(const TeamCtl& c, Team& t, const T* v, T* haloS, T* haloN, int* s_ok) {
+__device__ bool exchange_halo(const TeamCtl& c, Team& t, const sptr<const T> v, const sptr<T> haloS, const sptr<T> haloN,
+                              int* s_ok) {
     const int nx = t.nx;
     const unsigned long long seq = ++t.pub_seq;
     T* const pubT = reinterpret_cast<T*>(t.pub);
@@ -510,10 +524,10 @@ template <typename T>
 struct Deep {
     unsigned long long* tpub;
     unsigned long long* tred;
-    T* cS[5];
-    T* cN[5];
-    T* xS2;
-    T* xN2;
+    sptr<T> cS[5];
+    sptr<T> cN[5];
+    sptr<T> xS2;
+    sptr<T> xN2;
 };
 
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
@@ -608,7 +622,8 @@ __device__ __forceinline__ bool wait_tagged_pairs(const TeamCtl& c, const unsign
 // makes the rows final before (a __syncthreads) and may compute on until it fetches.
 template <int NT, typename T, int H>
 __device__ __forceinline__ unsigned long long publish_rows_tagged(Team& t, unsigned long long* tpub,
-                                                                  const T* const (&lo)[H], const T* const (&hi)[H]) {
+                                                                  const sptr<const T> (&lo)[H],
+                                                                  const sptr<const T> (&hi)[H]) {
     static_assert(2 * H <= kDeepSlotRows, "slot too small");
     constexpr int P = Pieces<T>::n;
     const int nx = t.nx;
@@ -638,7 +653,7 @@ __device__ __forceinline__ unsigned long long publish_rows_tagged(Team& t, unsig
 // out (the launch is then aborted) or the launch aborted.
 template <int NT, typename T, int H>
 __device__ bool fetch_rows_tagged(const TeamCtl& c, const Team& t, const unsigned long long* tpub,
-                                  unsigned long long seq, T* const (&fromS)[H], T* const (&fromN)[H]) {
+                                  unsigned long long seq, const sptr<T> (&fromS)[H], const sptr<T> (&fromN)[H]) {
     constexpr int P = Pieces<T>::n;
     const int nx = t.nx;
     const unsigned tag = (unsigned)seq;
@@ -692,8 +707,9 @@ __device__ bool fetch_rows_tagged(const TeamCtl& c, const Team& t, const unsigne
 
 // Publish, then fetch at once (no work in between).
 template <int NT, typename T, int H>
-__device__ bool exchange_rows_tagged(const TeamCtl& c, Team& t, unsigned long long* tpub, const T* const (&lo)[H],
-                                     const T* const (&hi)[H], T* const (&fromS)[H], T* const (&fromN)[H]) {
+__device__ bool exchange_rows_tagged(const TeamCtl& c, Team& t, unsigned long long* tpub,
+                                     const sptr<const T> (&lo)[H], const sptr<const T> (&hi)[H],
+                                     const sptr<T> (&fromS)[H], const sptr<T> (&fromN)[H]) {
     const unsigned long long seq = publish_rows_tagged<NT, T, H>(t, tpub, lo, hi);
     return fetch_rows_tagged<NT, T, H>(c, t, tpub, seq, fromS, fromN);
 }
@@ -840,10 +856,11 @@ template <> struct Eps<float> { static constexpr double value = 5.96046447753906
 // the precision of the level solve: double, or float for FP32 inner solves.
 template <typename T>
 struct Smem {
-    T *cw, *ce, *cs, *cn, *bs, *x;           // scaled couplings, scaled rhs, iterate
-    T *r, *rh, *p, *v, *t;                   // BiCGStab vectors (s shares r)
-    T *haloS, *haloN;                        // neighbour rows of the exchanged vector
+    sptr<T> cw, ce, cs, cn, bs, x;           // scaled couplings, scaled rhs, iterate
+    sptr<T> r, rh, p, v, t;                  // BiCGStab vectors (s shares r)
+    sptr<T> haloS, haloN;                    // neighbour rows of the exchanged vector
     double* red;                             // 64 doubles: block reductions [0,32), broadcast [32,48), flags [48,64)
+                                             // (addressed by constant offsets and warp numbers only)
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -859,26 +876,26 @@ template <typename T>
 __device__ __forceinline__ Smem<T> smem_layout(unsigned char* base, int cap, int nx) {
     Smem<T> m;
     T* b = reinterpret_cast<T*>(base);
-    m.cw = b;
-    m.ce = b + cap;
-    m.cs = b + 2 * cap;
-    m.cn = b + 3 * cap;
-    m.bs = b + 4 * cap;
-    m.x = b + 5 * cap;
-    m.r = b + 6 * cap;
-    m.rh = b + 7 * cap;
-    m.p = b + 8 * cap;
-    m.v = b + 9 * cap;
-    m.t = b + 10 * cap;
-    m.haloS = b + 11 * cap;
-    m.haloN = m.haloS + nx;
+    m.cw = chk(b, cap, kChkSmem + 0);
+    m.ce = chk(b + cap, cap, kChkSmem + 1);
+    m.cs = chk(b + 2 * cap, cap, kChkSmem + 2);
+    m.cn = chk(b + 3 * cap, cap, kChkSmem + 3);
+    m.bs = chk(b + 4 * cap, cap, kChkSmem + 4);
+    m.x = chk(b + 5 * cap, cap, kChkSmem + 5);
+    m.r = chk(b + 6 * cap, cap, kChkSmem + 6);
+    m.rh = chk(b + 7 * cap, cap, kChkSmem + 7);
+    m.p = chk(b + 8 * cap, cap, kChkSmem + 8);
+    m.v = chk(b + 9 * cap, cap, kChkSmem + 9);
+    m.t = chk(b + 10 * cap, cap, kChkSmem + 10);
+    m.haloS = chk(b + 11 * cap, nx, kChkSmem + 11);
+    m.haloN = chk(b + 11 * cap + nx, nx, kChkSmem + 12);
     m.red = reinterpret_cast<double*>(base + smem_red_offset<T>(cap, nx));
     return m;
 }
 
 // y = (D^{-1} A) v on the local rows (unit diagonal), halos of v in haloS/haloN.
 template <int NT, typename T>
-__device__ __forceinline__ void local_spmv(const Team& t, const Smem<T>& m, const T* v, T* y) {
+__device__ __forceinline__ void local_spmv(const Team& t, const Smem<T>& m, const sptr<const T> v, const sptr<T> y) {
     const int nx = t.nx;
     for (int k = threadIdx.x; k < t.nloc; k += NT) {
         const int jl = k / nx, i = k - jl * nx;
@@ -1087,10 +1104,10 @@ __device__ int level_sor_deep(const TeamCtl& c, Team& t, const Smem<T>& m, doubl
     bool have_pending = false;
     int* s_flag = reinterpret_cast<int*>(m.red + 48);
     unsigned long long* wred = reinterpret_cast<unsigned long long*>(m.red);
-    const T* const lo[2] = {m.x, m.x + nx};
-    const T* const hi[2] = {m.x + last, m.x + last - nx};
-    T* const fS[2] = {m.haloS, deep.xS2};
-    T* const fN[2] = {m.haloN, deep.xN2};
+    const sptr<const T> lo[2] = {m.x, m.x + nx};
+    const sptr<const T> hi[2] = {m.x + last, m.x + last - nx};
+    const sptr<T> fS[2] = {m.haloS, deep.xS2};
+    const sptr<T> fN[2] = {m.haloN, deep.xN2};
     // one point of a colour: local row jl, qi-th point of that colour in the row
     auto update = [&](int jl, int qi, int color, unsigned long long& key) {
         const int i = ((t.r0 + jl + color) & 1) + 2 * qi;
@@ -1150,8 +1167,8 @@ __device__ int level_sor_deep(const TeamCtl& c, Team& t, const Smem<T>& m, doubl
                 const int row = south ? r_s : r_n;
                 const int i = (row & 1) + 2 * (south ? qh : qh - half);
                 if (i >= nx) continue;
-                T* h = south ? m.haloS : m.haloN;
-                T* const* cc = south ? deep.cS : deep.cN;
+                const sptr<T> h = south ? m.haloS : m.haloN;
+                const sptr<T>* cc = south ? deep.cS : deep.cN;
                 const T xS = south ? deep.xS2[i] : m.x[last + i];
                 const T xN = south ? m.x[i] : deep.xN2[i];
                 const T xW = i > 0 ? h[i - 1] : T(0);
@@ -1480,6 +1497,11 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
     const long long plane = (long long)a.M * Ns;
     const long long off0 = (long long)t.r0 * a.nx;
     double sumsq = 0.0;
+    const auto coefg = chk(a.coef, 5 * plane, kChkCoef);
+    const auto Rg = chk(a.R, plane, kChkR);
+    const auto Ug = chk(a.U, plane, kChkU);
+    const auto dUg = chk(a.dU, plane, kChkDU);
+    const auto rho_keyg = chk(a.rho_key, 2 * (long long)a.M, kChkLevel);
 
     // du^0 = 0 lives in x
     for (int k = threadIdx.x; k < nloc; k += NT) m.x[k] = 0.0;
@@ -1487,7 +1509,7 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
 
     for (int n = 0; n < a.M; ++n) {
         const long long lo = (long long)n * Ns + off0;
-        const double* cd = a.coef + lo;
+        const auto cd = coefg + lo;
         // rhs b = r^n + du^{n-1}, scaled by 1/C; load the couplings
         double rho_g;
         bool nonsym;
@@ -1498,13 +1520,13 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
                 m.ce[k] = cd[2 * plane + k];
                 m.cs[k] = cd[3 * plane + k];
                 m.cn[k] = cd[4 * plane + k];
-                const double b = a.R[lo + k] + m.x[k];
+                const double b = Rg[lo + k] + m.x[k];
                 m.bs[k] = d * b;
                 m.x[k] = b;  // SOR start: unscaled rhs (exact for the smooth modes where A ~ I)
             }
             __syncthreads();
-            rho_g = key_val(a.rho_key[n]);
-            nonsym = a.rho_key[a.M + n] != 0ull;
+            rho_g = key_val(rho_keyg[n]);
+            nonsym = rho_keyg[a.M + n] != 0ull;
         } else {
             // row sums folded as order-preserving keys: a NaN entry gives a NaN bound
             // (above +Inf), so the level goes to BiCGStab, which reports it
@@ -1518,7 +1540,7 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
                 m.ce[k] = e;
                 m.cs[k] = sv;
                 m.cn[k] = nv;
-                const double b = a.R[lo + k] + m.x[k];
+                const double b = Rg[lo + k] + m.x[k];
                 m.bs[k] = d * b;
                 m.x[k] = b;
                 const unsigned long long kr = abs_key(fabs(w) + fabs(e) + fabs(sv) + fabs(nv));
@@ -1552,20 +1574,20 @@ __global__ void __launch_bounds__(NT) chain_kernel(ChainArgs a) {
         // du^n = x: update the iterate and keep x as du^{n-1} of the next level
         for (int k = threadIdx.x; k < nloc; k += NT) {
             const double dx = m.x[k];
-            if (a.update_U) a.U[lo + k] += dx;
-            if (a.dU) a.dU[lo + k] = dx;
+            if (a.update_U) Ug[lo + k] += dx;
+            if (a.dU) dUg[lo + k] = dx;
             sumsq += dx * dx;
         }
         if (t.b == 0 && threadIdx.x == 0) {
-            a.level_iters[n] = iters;
-            a.level_method[n] = used;
+            chk(a.level_iters, a.M, kChkLevel)[n] = iters;
+            chk(a.level_method, a.M, kChkLevel)[n] = used;
             if (iters >= a.max_iter) atomicCAS(a.status, 0, ST_ENOCONV);
         }
         __syncthreads();
     }
     double ss[1] = {sumsq};
     block_sum<NT, 1>(ss, m.red);
-    if (threadIdx.x == 0) a.cta_sumsq[t.b] = ss[0];
+    if (threadIdx.x == 0) chk(a.cta_sumsq, a.G, kChkSumsq)[t.b] = ss[0];
     if (t.b == 0 && threadIdx.x == 0) {
         a.timers[0] = t.t_halo;
         a.timers[1] = t.t_red;
@@ -1676,15 +1698,24 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
     const int cap = (a.rows_base + (a.rows_rem ? 1 : 0)) * nx;
     const Smem<T> m = smem_layout<T>(smem, cap, nx);
     // u^{n-1}_k, own rows (cap doubles), after the reduction area
-    double* uprev = reinterpret_cast<double*>(smem + smem_red_offset<T>(cap, nx) + 64 * sizeof(double));
+    double* const uprev_p = reinterpret_cast<double*>(smem + smem_red_offset<T>(cap, nx) + 64 * sizeof(double));
+    const sptr<double> uprev = chk(uprev_p, cap, kChkUprev);
     // u^n_k with one halo row each side: (nrows + 2) x nx doubles
-    double* u = wave_u_aliases<T>(cap, nx) ? reinterpret_cast<double*>(m.r) : uprev + cap;
+    const sptr<double> u = chk(wave_u_aliases<T>(cap, nx) ? reinterpret_cast<double*>(static_cast<T*>(m.r)) : uprev_p + cap,
+                               cap + 2 * nx, kChkUstrip);
     const long long Ns = t.Ns;
     const long long off0 = (long long)t.r0 * nx;
     const int nb = 2 * nx + 2 * ny;
+    // the problem's arrays (levels 0..M-1 of this call) and the per-iteration records
+    const auto Ug = chk(a.U, (long long)M * Ns, kChkU);
+    const auto u0g = chk(a.u0, Ns, kChkU0);
+    const auto bcg = chk(a.bc, (long long)M * nb, kChkBc);
+    const auto qg = chk(a.q, (long long)M * Ns, kChkQ);
+    const auto prefixg = chk(a.cell_prefix, (long long)a.k_end * M, kChkPrefix);
+    const auto itersg = chk(a.cell_iters, (long long)a.k_end * M, kChkCellIters);
     const int pred_team = (team + a.K - 1) % a.K;
-    unsigned long long* pred_prog = a.prog + (size_t)pred_team * a.G;
-    unsigned long long* my_prog = a.prog + (size_t)team * a.G;
+    const auto pred_prog = chk(a.prog, (long long)a.K * a.G, kChkProg) + (long long)pred_team * a.G;
+    const auto my_prog = chk(a.prog, (long long)a.K * a.G, kChkProg) + (long long)team * a.G;
     double* slot = m.red + 48;
     // Burgers-type closures with constant viscosity have a constant diagonal 1 + 2 mu_a (vx + vy)
     const double dconst = 1.0 / (1.0 + 2.0 * oc.mu_a * (oc.vx + oc.vy));
@@ -1700,13 +1731,13 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
     Deep<T> deep_rows;
     const Deep<T>* deep = nullptr;
     if (a.tpub && a.tred && a.G >= 2 && a.rows_base >= 2 && 12 * (size_t)nx <= 5 * (size_t)cap) {
-        T* d0 = m.r;
+        T* const d0 = static_cast<T*>(m.r);
         for (int h = 0; h < 5; ++h) {
-            deep_rows.cS[h] = d0 + (size_t)h * nx;
-            deep_rows.cN[h] = d0 + (size_t)(5 + h) * nx;
+            deep_rows.cS[h] = chk(d0 + (size_t)h * nx, nx, kChkDeep);
+            deep_rows.cN[h] = chk(d0 + (size_t)(5 + h) * nx, nx, kChkDeep);
         }
-        deep_rows.xS2 = d0 + (size_t)10 * nx;
-        deep_rows.xN2 = d0 + (size_t)11 * nx;
+        deep_rows.xS2 = chk(d0 + (size_t)10 * nx, nx, kChkDeep);
+        deep_rows.xN2 = chk(d0 + (size_t)11 * nx, nx, kChkDeep);
         deep_rows.tpub = a.tpub + (size_t)team * 2 * a.G * kDeepSlotRows * nx * 2;
         deep_rows.tred = a.tred + (size_t)team * 4 * a.G * kTagRedWords;
         deep = &deep_rows;
@@ -1719,7 +1750,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
     for (int k = a.k_begin + team; k < a.k_end; k += a.K) {
         for (int i = threadIdx.x; i < nloc; i += NT) {
             m.x[i] = T(0);              // du^{-1} = 0
-            uprev[i] = a.u0[off0 + i];  // u^0
+            uprev[i] = u0g[off0 + i];   // u^0
         }
         double prefix = 0.0;            // running max of ||r^j_k||_inf, j <= n (thread 0)
         double sumsq = 0.0;
@@ -1742,7 +1773,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                     if (nbr >= a.G) nbr = -1;
                     if (nbr >= 0) {
                         long long spins = 0;
-                        while (ld_acquire_u64(pred_prog + nbr) < target) {
+                        while (ld_acquire_u64(&pred_prog[nbr]) < target) {
                             if ((a.stop && ld_acquire_s32(a.stop)) || ld_acquire_s32(a.abort_flag)) {
                                 stop_seen = true;
                                 break;
@@ -1771,19 +1802,19 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
             //    in the same round trip u^{n-1}_k when the previous level was skipped (the global,
             //    final iterate) and u^n_k (below)
             if (threadIdx.x == pl) {
-                slot[0] = k > a.k_begin ? __ldcg(a.cell_prefix + (size_t)(k - 1) * M + n) : 1.0 / 0.0;
+                slot[0] = k > a.k_begin ? ldcg(prefixg + ((long long)(k - 1) * M + n)) : 1.0 / 0.0;
                 // the first iteration's running residual at this level (finished long before)
-                slot[1] = k > 0 ? __ldcg(a.cell_prefix + n) : 1.0 / 0.0;
+                slot[1] = k > 0 ? ldcg(prefixg + n) : 1.0 / 0.0;
             }
             const bool reload_prev = !uprev_valid;
             if (reload_prev) {
-                const double* up = n == 0 ? a.u0 + off0 : a.U + (long long)(n - 1) * Ns + off0;
-                for (int i = threadIdx.x; i < nloc; i += NT) uprev[i] = __ldcg(up + i);
+                const auto up = n == 0 ? u0g + off0 : Ug + ((long long)(n - 1) * Ns + off0);
+                for (int i = threadIdx.x; i < nloc; i += NT) uprev[i] = ldcg(up + i);
                 uprev_valid = true;
             }
             // u^n_k: own rows and one halo row each side (Dirichlet data off the domain)
-            const double* Un = a.U + (long long)n * Ns;
-            const double* bnd = a.bc ? a.bc + (long long)n * nb : nullptr;
+            const auto Un = Ug + (long long)n * Ns;
+            const auto bnd = a.bc ? bcg + (long long)n * nb : bcg;
             // maxima as integer keys (abs_key), so the bookkeeping stays off the FP64 pipe
             unsigned long long krmax = 0, krs = 0, kbmax = 0;
             bool ns = false;
@@ -1796,9 +1827,21 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                     const int j1 = t.r0 + t.nrows < ny ? t.r0 + t.nrows : ny - 1;
                     if (threadIdx.x == 0) {
                         const unsigned bytes = (unsigned)((size_t)(j1 - j0 + 1) * nx * sizeof(double));
+                        const auto dst = u + (long long)(j0 - (t.r0 - 1)) * nx;
+                        const auto src = Un + (long long)j0 * nx;
+                        bool issue = true;
+#ifdef PIT_CHECK_BOUNDS
+                        // the copy's ranges and alignment; a bad copy is not issued (the phase
+                        // then completes on the arrival alone)
+                        issue = dst.lo <= 0 && (long long)(j1 - j0 + 1) * nx <= dst.hi && src.lo <= 0 &&
+                                (long long)(j1 - j0 + 1) * nx <= src.hi && (bytes & 15u) == 0 &&
+                                ((size_t)static_cast<double*>(dst) & 15) == 0 &&
+                                ((size_t)static_cast<const double*>(src) & 15) == 0;
+                        if (!issue) bounds_fail(kChkBulk);
+#endif
                         fence_proxy_async_smem();
-                        mbar_arrive_expect_tx(ubar, bytes);
-                        bulk_copy_g2s(u + (size_t)(j0 - (t.r0 - 1)) * nx, Un + (long long)j0 * nx, bytes, ubar);
+                        mbar_arrive_expect_tx(ubar, issue ? bytes : 0u);
+                        if (issue) bulk_copy_g2s(dst, src, bytes, ubar);
                     }
                     if (t.r0 == 0)
                         for (int i = threadIdx.x; i < nx; i += NT) u[i] = bnd ? bnd[i] : 0.0;
@@ -1822,7 +1865,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                         double val;
                         if (j < 0) val = bnd ? bnd[ii] : 0.0;
                         else if (j >= ny) val = bnd ? bnd[nx + ii] : 0.0;
-                        else val = __ldcg(Un + (long long)j * nx + ii);
+                        else val = ldcg(Un + ((long long)j * nx + ii));
                         u[i] = val;
                     }
                     __syncthreads();
@@ -1840,16 +1883,16 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                         prefix = pred_prefix;
                         __threadfence();
                         if (b == 0) {
-                            __stcg(a.cell_prefix + (size_t)k * M + n, prefix);
-                            if (a.cell_iters) a.cell_iters[(size_t)k * M + n] = 1;
+                            stcg(prefixg + ((long long)k * M + n), prefix);
+                            if (a.cell_iters) itersg[(long long)k * M + n] = 1;
                             __threadfence();
                         }
-                        st_release_u64(my_prog + b, a.cell_base + (unsigned long long)k * M + n + 1);
+                        st_release_u64(&my_prog[b], a.cell_base + (unsigned long long)k * M + n + 1);
                     }
                     continue;
                 }
                 // 3. residual r^n_k, scaled couplings, rhs; uprev <- u^n_k
-                const double* qn = a.q ? a.q + (long long)n * Ns + off0 : nullptr;
+                const auto qn = a.q ? qg + ((long long)n * Ns + off0) : qg;
                 float gmax_f = 0.0f;  // FP32 solves: largest FP32 row sum of this thread's rows
                 struct NodeIn {
                     double uC, uW, uE, uS, uN, up, x, q;
@@ -1975,8 +2018,8 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
             const unsigned long long t_sr0 = threadIdx.x == 0 ? global_ns() : 0ull;
             if (deep) {
                 const int last = (t.nrows - 1) * nx;
-                const T* const lo[5] = {m.cw, m.ce, m.cs, m.cn, m.bs};
-                const T* const hi[5] = {m.cw + last, m.ce + last, m.cs + last, m.cn + last, m.bs + last};
+                const sptr<const T> lo[5] = {m.cw, m.ce, m.cs, m.cn, m.bs};
+                const sptr<const T> hi[5] = {m.cw + last, m.ce + last, m.cs + last, m.cn + last, m.bs + last};
                 cseq = publish_rows_tagged<NT, T, 5>(t, deep->tpub, lo, hi);
             }
             double g3[4];
@@ -2023,8 +2066,8 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 goto done;
             }
             if (deep) {
-                T* const fS[5] = {deep->cS[0], deep->cS[1], deep->cS[2], deep->cS[3], deep->cS[4]};
-                T* const fN[5] = {deep->cN[0], deep->cN[1], deep->cN[2], deep->cN[3], deep->cN[4]};
+                const sptr<T> fS[5] = {deep->cS[0], deep->cS[1], deep->cS[2], deep->cS[3], deep->cS[4]};
+                const sptr<T> fN[5] = {deep->cN[0], deep->cN[1], deep->cN[2], deep->cN[3], deep->cN[4]};
                 if (!fetch_rows_tagged<NT, T, 5>(c, t, deep->tpub, cseq, fS, fN)) return;
             }
             if (threadIdx.x == 0) t_sred += global_ns() - t_sr0;
@@ -2061,11 +2104,11 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                     n_sweeps += (unsigned long long)(iters > 0 ? iters : 0);
                 }
                 // 6. U^n += du^n; du^n stays in x for the next level
-                double* Uw = a.U + (long long)n * Ns + off0;
+                const auto Uw = Ug + ((long long)n * Ns + off0);
                 for (int i = threadIdx.x; i < nloc; i += NT) {
                     const T xt = m.x[i];
                     const double dx = (double)xt;
-                    __stcg(Uw + i, uprev[i] + dx);
+                    stcg(Uw + i, uprev[i] + dx);
                     // the update norm is a statistic: with FP32 level solves it is summed in
                     // FP32, which leaves the scarce FP64 pipe to the arithmetic of the method
                     if constexpr (sizeof(T) == 4) sumsq_f = fmaf(xt, xt, sumsq_f);
@@ -2074,11 +2117,11 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 __syncthreads();
                 if (threadIdx.x == 0) {
                     if (b == 0) {
-                        __stcg(a.cell_prefix + (size_t)k * M + n, prefix);
-                        if (a.cell_iters) a.cell_iters[(size_t)k * M + n] = used == 1 ? iters + 1 : -(iters + 1);
+                        stcg(prefixg + ((long long)k * M + n), prefix);
+                        if (a.cell_iters) itersg[(long long)k * M + n] = used == 1 ? iters + 1 : -(iters + 1);
                     }
                     __threadfence();
-                    st_release_u64(my_prog + b, a.cell_base + (unsigned long long)k * M + n + 1);
+                    st_release_u64(&my_prog[b], a.cell_base + (unsigned long long)k * M + n + 1);
                     if (iters >= c.max_iter) atomicCAS(a.status, 0, ST_ENOCONV);
                     t_upd += global_ns() - t_mark;
                 }
@@ -2090,9 +2133,9 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
             sumsq_f = 0.0f;
             block_sum<NT, 1>(ss, m.red);
             if (threadIdx.x == 0) {
-                if (a.cta_sumsq) a.cta_sumsq[(size_t)k * a.G + b] = ss[0];
+                if (a.cta_sumsq) chk(a.cta_sumsq, (long long)a.k_end * a.G, kChkSumsq)[(long long)k * a.G + b] = ss[0];
                 if (b == 0) {
-                    if (a.res_inf) a.res_inf[k] = prefix;
+                    if (a.res_inf) chk(a.res_inf, a.k_end, kChkLevel)[k] = prefix;
                     if (prefix <= a.tol_res && a.K > 1 && a.stop) {
                         atomicMin(a.stop + 1, k);
                         __threadfence();
@@ -2270,6 +2313,11 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
     const int cap = (rows_base + (rows_rem ? 1 : 0)) * nx;
     double* red = smem_layout<T>(smem, cap, nx).red;
     const int W = in.window > 0 ? in.window : M;
+    const int nb = 2 * nx + 2 * ny;
+    const auto Ug = chk(in.U, (long long)M * Ns, kChkU);
+    const auto u0g = chk(in.u0, Ns, kChkU0);
+    const auto bcg = chk(in.bc, (long long)M * nb, kChkBc);
+    const auto qg = chk(in.q, (long long)M * Ns, kChkQ);
     const bool lead = tk == 0 && b == 0;          // reports the results
     const unsigned long long job_ctas = (unsigned long long)K * G;
     unsigned long long jep = 0;                   // job-wide barriers passed (K > 1)
@@ -2283,14 +2331,14 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
     int clean_from = 0;                           // levels >= clean_from still hold the caller's iterate
     for (int s = 0; s < M;) {
         const int Mw = min(w, M - s);
-        const double* from = s == 0 ? in.u0 : in.U + (long long)(s - 1) * Ns;
+        const auto from = s == 0 ? u0g : Ug + (long long)(s - 1) * Ns;
         // the same decision on every CTA of the job (s and clean_from are job-wide)
         if (!(ba.start_given && s >= clean_from)) {
             // plain guess for the window from its previous level: own rows only, levels
             // tk, tk + K, ... by team tk
             for (int n = tk; n < Mw; n += K) {
-                double* dst = in.U + (long long)(s + n) * Ns + off0;
-                for (int i = threadIdx.x; i < nloc; i += NT) dst[i] = __ldcg(from + off0 + i);
+                const auto dst = Ug + ((long long)(s + n) * Ns + off0);
+                for (int i = threadIdx.x; i < nloc; i += NT) dst[i] = ldcg(from + (off0 + i));
             }
         }
         if (threadIdx.x == 0 && lead) {
@@ -2434,24 +2482,23 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
         return;
     }
     double rmax = 0.0;
-    const int nb = 2 * nx + 2 * ny;
     for (int n = tk; n < M; n += K) {
-        const double* Un = in.U + (long long)n * Ns;
-        const double* Up = n == 0 ? in.u0 : in.U + (long long)(n - 1) * Ns;
-        const double* bnd = in.bc ? in.bc + (long long)n * nb : nullptr;
+        const auto Un = Ug + (long long)n * Ns;
+        const auto Up = n == 0 ? u0g : Ug + (long long)(n - 1) * Ns;
+        const auto bnd = in.bc ? bcg + (long long)n * nb : bcg;
         for (int i = threadIdx.x; i < nloc; i += NT) {
             const int jl = i / nx, ii = i - jl * nx, j = t.r0 + jl;
             const long long k = (long long)j * nx + ii;
-            const double uC = __ldcg(Un + k);
-            const double uW = ii > 0 ? __ldcg(Un + k - 1) : (bnd ? bnd[2 * nx + j] : 0.0);
-            const double uE = ii < nx - 1 ? __ldcg(Un + k + 1) : (bnd ? bnd[2 * nx + ny + j] : 0.0);
-            const double uS = j > 0 ? __ldcg(Un + k - nx) : (bnd ? bnd[ii] : 0.0);
-            const double uN = j < ny - 1 ? __ldcg(Un + k + nx) : (bnd ? bnd[nx + ii] : 0.0);
+            const double uC = ldcg(Un + k);
+            const double uW = ii > 0 ? ldcg(Un + (k - 1)) : (bnd ? bnd[2 * nx + j] : 0.0);
+            const double uE = ii < nx - 1 ? ldcg(Un + (k + 1)) : (bnd ? bnd[2 * nx + ny + j] : 0.0);
+            const double uS = j > 0 ? ldcg(Un + (k - nx)) : (bnd ? bnd[ii] : 0.0);
+            const double uN = j < ny - 1 ? ldcg(Un + (k + nx)) : (bnd ? bnd[nx + ii] : 0.0);
             double tf;
             if (in.conv) tf = in.nlv ? tau_F<true, true>(oc, uC, uW, uE, uS, uN) : tau_F<true, false>(oc, uC, uW, uE, uS, uN);
             else tf = in.nlv ? tau_F<false, true>(oc, uC, uW, uE, uS, uN) : tau_F<false, false>(oc, uC, uW, uE, uS, uN);
-            double r = (__ldcg(Up + k) - uC) - tf;
-            if (in.q) r = fma(oc.dt, in.q[(long long)n * Ns + k], r);
+            double r = (ldcg(Up + k) - uC) - tf;
+            if (in.q) r = fma(oc.dt, qg[(long long)n * Ns + k], r);
             rmax = fmax(rmax, fabs(r));
             if (r != r) rmax = r;
         }

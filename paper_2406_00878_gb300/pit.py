@@ -17,7 +17,8 @@ import numpy as np
 
 from . import build as _build
 
-PIT_OK, PIT_EINVAL, PIT_ECUDA, PIT_ENOMEM, PIT_ENOCONV, PIT_EDIVERGED, PIT_ETIMEOUT, PIT_EUNSUPPORTED = range(8)
+(PIT_OK, PIT_EINVAL, PIT_ECUDA, PIT_ENOMEM, PIT_ENOCONV, PIT_EDIVERGED, PIT_ETIMEOUT, PIT_EUNSUPPORTED,
+ PIT_EBOUNDS) = range(9)
 PIT_HEAT, PIT_BURGERS = 0, 1
 PIT_LIN_AUTO, PIT_LIN_SOR, PIT_LIN_BICGSTAB = 0, 1, 2
 PIT_FP64, PIT_FP32_INNER = 0, 1
@@ -33,7 +34,7 @@ EXPORTS = ("pit_default_options", "pit_create", "pit_set_data", "pit_fill_plain_
            "pit_net_create", "pit_net_get_params", "pit_net_set_params", "pit_net_guess", "pit_net_make_target",
            "pit_net_gradients", "pit_net_train_step", "pit_net_last_error", "pit_net_destroy",
            "pit_product_form_solve", "pit_solve_product", "pit_probe_fma_peak", "pit_conv3x3_forward",
-           "pit_conv3x3_backward", "pit_wave_timers")
+           "pit_conv3x3_backward", "pit_wave_timers", "pit_bounds_status")
 
 
 class pit_grid(ctypes.Structure):
@@ -121,17 +122,29 @@ class PitError(RuntimeError):
 
 
 _lib = None
+_lib_path: Optional[str] = None
 _lock = threading.Lock()
+
+
+def use_library(path: str) -> None:
+    """Load the library from `path` instead of libpit.so (e.g. the bounds-checking build,
+    ``build.build_check()``). Must come before the first call into the library."""
+    global _lib_path
+    with _lock:
+        if _lib is not None and os.path.abspath(path) != os.path.abspath(_lib_path or _build.LIB):
+            raise RuntimeError("use_library: the library is already loaded from another path")
+        _lib_path = path
 
 
 def lib():
     """Load libpit.so (building it first if needed); raises if it cannot be built or loaded."""
-    global _lib
+    global _lib, _lib_path
     with _lock:
         if _lib is None:
-            path = _build.LIB
-            if not os.path.exists(path):
+            path = _lib_path or _build.LIB
+            if _lib_path is None and not os.path.exists(path):
                 path = _build.build()
+            _lib_path = path
             L = ctypes.CDLL(path)
             P, D, V = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p
             st = ctypes.c_int
@@ -172,6 +185,8 @@ def lib():
             L.pit_wave_timers.restype = ctypes.c_int
             L.pit_probe_fma_peak.argtypes = [ctypes.c_int, V, D]
             L.pit_probe_fma_peak.restype = st
+            L.pit_bounds_status.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+            L.pit_bounds_status.restype = st
             L.pit_batch_create.argtypes = [ctypes.POINTER(pit_instance), ctypes.c_int, ctypes.POINTER(pit_options), V,
                                            ctypes.POINTER(P)]
             L.pit_batch_create.restype = st
@@ -446,6 +461,17 @@ def pit_probe_fma_peak(precision: int = 0, stream=None) -> float:
 
 
 # ------------------------------------------------------------- convenience
+
+def pit_bounds_status() -> tuple:
+    """(enabled, first_id): whether this library is the bounds-checking build, and the id of
+    the first array a kernel indexed out of range since the last call (0 = none; cleared).
+    Synchronises the device. Raises PitError when the device cannot be read."""
+    en, fid = ctypes.c_int(0), ctypes.c_int(0)
+    s = lib().pit_bounds_status(ctypes.byref(en), ctypes.byref(fid))
+    if s not in (PIT_OK, PIT_EBOUNDS):
+        raise PitError(s, "pit_bounds_status failed")
+    return en.value, fid.value
+
 
 def context_for(problem, opt: Optional[pit_options] = None, stream=None) -> Context:
     """Create a context for a workloads.Problem and upload its data (device tensors)."""
