@@ -15,14 +15,17 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <random>
 #include <vector>
 
 #include "pit.h"
+#include "pit_conv_tma.cuh"
 #include "pit_tc.cuh"
 
 namespace {
@@ -253,11 +256,191 @@ extern "C" long long pit_net_param_count(const pit_net_shape* s) {
     return (C * 9 * 2 + C) + 2LL * s->blocks * (C * 9 * C + C) + (M * 9 * C + M);
 }
 
-// Y = act(conv3x3(X; Wt) + bias (+ res)) on the tcgen05 tensor cores (pit_tc.cuh).
+// ------------------------------------------------- TMA tensor maps (driver entry point)
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda);
+// null when the driver does not offer it.
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// Maps of the TMA convolution (pit_conv_tma.cuh): activations [B][H][W][Cin] as (8 channels,
+// W, Cin/8, H, B) with box (8, 130, Cin/8, 1, 1), weights [Cout][9][Cin] as (8 channels, Cout,
+// Cin/8, 9) with box (8, nco, Cin/8, 9). Off-tensor elements read as zero.
+static bool encode_conv_maps(CUtensorMap* xm, CUtensorMap* wm, const bf16* X, const bf16* Wt, int B, int H, int W,
+                             int Cin, int Cout, int nco, int sw) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    const cuuint64_t G = (cuuint64_t)(Cin / 8), cb = (cuuint64_t)Cin * 2;
+    const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
+    if (sw) {
+        // rows of 64 channels (128 bytes), contiguous in NHWC: 128-byte swizzle
+        const cuuint64_t xdim[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+        const cuuint64_t xstr[3] = {cb, cb * W, cb * W * H};
+        const cuuint32_t xbox[4] = {64, (cuuint32_t)pit_tc::kCols, 1, 1};
+        if (enc(xm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(X), xdim, xstr, xbox, ones,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    } else {
+        const cuuint64_t xdim[5] = {8, (cuuint64_t)W, G, (cuuint64_t)H, (cuuint64_t)B};
+        const cuuint64_t xstr[4] = {cb, 16, cb * W, cb * W * H};
+        const cuuint32_t xbox[5] = {8, (cuuint32_t)pit_tc::kCols, (cuuint32_t)G, 1, 1};
+        if (enc(xm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(X), xdim, xstr, xbox, ones,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    if (sw) {
+        // [Cout][9][Cin] as (Cin, 9, Cout): a box is 64 channels of one tap for nco outputs
+        const cuuint64_t wdim[3] = {(cuuint64_t)Cin, 9, (cuuint64_t)Cout};
+        const cuuint64_t wstr[2] = {cb, 9 * cb};
+        const cuuint32_t wbox[3] = {64, 1, (cuuint32_t)nco};
+        return enc(wm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(Wt), wdim, wstr, wbox, ones,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    const cuuint64_t wdim[4] = {8, (cuuint64_t)Cout, G, 9};
+    const cuuint64_t wstr[3] = {9 * cb, 16, cb};
+    const cuuint32_t wbox[4] = {8, (cuuint32_t)nco, (cuuint32_t)G, 9};
+    return enc(wm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(Wt), wdim, wstr, wbox, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+constexpr int kConvSmemLimit = 227 * 1024;
+
+// The row-stationary TMA convolution (Cin = 64 or 128, weights and two staged rows fit in
+// shared memory); false = not applicable.
+static bool launch_conv_rows(pit_net* net, const bf16* X, const bf16* Wt, const float* bias, const bf16* res,
+                             bf16* Y, int B, int H, int W, int Cin, int Cout, int relu, cudaError_t* cerr) {
+    *cerr = cudaSuccess;
+    if (Cin != 64 && Cin != 128) return false;
+    const int nco = Cout < 128 ? Cout : 128;
+    int ring = 3;
+    while (ring >= 2 && pit_tc::fwd_smem_bytes(Cin, nco, ring, 1) > kConvSmemLimit) --ring;
+    if (ring < 2 || (reinterpret_cast<uintptr_t>(X) & 15) || (reinterpret_cast<uintptr_t>(Wt) & 15)) return false;
+    CUtensorMap xm, wm;
+    if (!encode_conv_maps(&xm, &wm, X, Wt, B, H, W, Cin, Cout, nco, 1)) return false;
+    static int sms = 0;
+    static bool attr_set = false;  // the limit belongs to the kernel; raising it again is harmless
+    if (!attr_set) {
+        int dev = 0;
+        if ((*cerr = cudaGetDevice(&dev)) != cudaSuccess) return true;
+        if ((*cerr = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return true;
+        if ((*cerr = cudaFuncSetAttribute(pit_tc::conv3x3_fwd_rows_kernel<1>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmemLimit)) != cudaSuccess)
+            return true;
+        if ((*cerr = cudaFuncSetAttribute(pit_tc::conv3x3_fwd_rows_kernel<2>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmemLimit)) != cudaSuccess)
+            return true;
+        attr_set = true;
+    }
+    const int co_tiles = (Cout + nco - 1) / nco;
+    const long long rows = (long long)((W + pit_tc::kM - 1) / pit_tc::kM) * B * H;
+    const int per = (int)std::max(1LL, std::min((long long)std::max(1, sms / co_tiles), rows));
+    pit_tc::FwdTmaArgs a;
+    a.bias = bias;
+    a.residual = res;
+    a.Y = Y;
+    a.N = B;
+    a.H = H;
+    a.W = W;
+    a.Cin = Cin;
+    a.Cout = Cout;
+    a.relu = relu;
+    a.nco = nco;
+    a.ntp = 0;
+    a.ring = ring;
+    a.ctas_per_tile = per;
+    a.sw = 1;
+    a.err = net->tc_err;
+    const int smem = pit_tc::fwd_smem_bytes(Cin, nco, ring, 1);
+    if (Cin == 64)
+        pit_tc::conv3x3_fwd_rows_kernel<1><<<co_tiles * per, pit_tc::kRThreads, smem, net->stream>>>(xm, wm, a);
+    else
+        pit_tc::conv3x3_fwd_rows_kernel<2><<<co_tiles * per, pit_tc::kRThreads, smem, net->stream>>>(xm, wm, a);
+    *cerr = cudaGetLastError();
+    return true;
+}
+
+// The TMA convolution when the layer's weight tile and a ring of at least four input rows
+// fit in shared memory (and the maps encode); false = use the staged kernel.
+static bool launch_conv_tma(pit_net* net, const bf16* X, const bf16* Wt, const float* bias, const bf16* res, bf16* Y,
+                            int B, int H, int W, int Cin, int Cout, int relu, cudaError_t* cerr) {
+    *cerr = cudaSuccess;
+    if (launch_conv_rows(net, X, Wt, bias, res, Y, B, H, W, Cin, Cout, relu, cerr)) return true;
+    const int nco = Cout < pit_tc::kFNMax ? Cout : pit_tc::kFNMax;
+    const int sw = Cin % 64 == 0 ? 1 : 0;
+    int ring = pit_tc::kFRingMax;
+    while (ring >= 4 && pit_tc::fwd_smem_bytes(Cin, nco, ring, sw) > kConvSmemLimit) --ring;
+    if (ring < 4 || (reinterpret_cast<uintptr_t>(X) & 15) || (reinterpret_cast<uintptr_t>(Wt) & 15)) return false;
+    CUtensorMap xm, wm;
+    if (!encode_conv_maps(&xm, &wm, X, Wt, B, H, W, Cin, Cout, nco, sw)) return false;
+    static int sms = 0;
+    static bool attr_set = false;  // the limit belongs to the kernel; raising it again is harmless
+    if (!attr_set) {
+        int dev = 0;
+        if ((*cerr = cudaGetDevice(&dev)) != cudaSuccess) return true;
+        if ((*cerr = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return true;
+        if ((*cerr = cudaFuncSetAttribute(pit_tc::conv3x3_fwd_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          kConvSmemLimit)) != cudaSuccess)
+            return true;
+        attr_set = true;
+    }
+    const int co_tiles = (Cout + nco - 1) / nco;
+    const long long rows = (long long)((W + pit_tc::kM - 1) / pit_tc::kM) * B * H;
+    const int per = (int)std::max(1LL, std::min((long long)std::max(1, sms / co_tiles), rows));
+    pit_tc::FwdTmaArgs a;
+    a.bias = bias;
+    a.residual = res;
+    a.Y = Y;
+    a.N = B;
+    a.H = H;
+    a.W = W;
+    a.Cin = Cin;
+    a.Cout = Cout;
+    a.relu = relu;
+    a.nco = nco;
+    a.ntp = nco <= 32 ? 32 : (nco <= 64 ? 64 : (nco <= 128 ? 128 : 256));
+    a.ring = ring;
+    a.ctas_per_tile = per;
+    a.sw = sw;
+    a.err = net->tc_err;
+    pit_tc::conv3x3_fwd_tma_kernel<<<co_tiles * per, pit_tc::kFThreads, pit_tc::fwd_smem_bytes(Cin, nco, ring, sw),
+                                     net->stream>>>(xm, wm, a);
+    *cerr = cudaGetLastError();
+    return true;
+}
+
+// Y = act(conv3x3(X; Wt) + bias (+ res)) on the tcgen05 tensor cores: the TMA kernel
+// (pit_conv_tma.cuh) when the layer fits it, else the staged kernel (pit_tc.cuh).
 static pit_status launch_conv_tc(pit_net* net, const bf16* X, const bf16* Wt, const float* bias, const bf16* res,
                                  bf16* Y, int B, int Cin, int Cout, int relu) {
     const pit_net_shape& s = net->shape;
     if (Cin % 16 != 0 || Cout % 16 != 0) return nfail(net, PIT_EINVAL, "conv channels must be multiples of 16");
+    {
+        cudaError_t e = cudaSuccess;
+        if (launch_conv_tma(net, X, Wt, bias, res, Y, B, s.height, s.width, Cin, Cout, relu, &e)) {
+            NCK(e);
+            return PIT_OK;
+        }
+    }
     static bool attr_set = false;  // the limit belongs to the kernel; raising it again is harmless
     if (!attr_set) {
         NCK(cudaFuncSetAttribute(pit_tc::conv3x3_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

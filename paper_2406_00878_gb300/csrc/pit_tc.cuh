@@ -151,6 +151,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Store 16 consecutive FP32 columns of this thread's TMEM lane (completion: tcgen05.wait::st).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
 // Y[n][h][w][co] = act(bias[co] + sum_{tap, ci} X[n][h+r-1][w+s-1][ci] W[co][tap][ci] (+ residual)).
 // Grid: x = N * ceil(H / kRows) * ceil(W / 128) row-group segments, y = ceil(Cout / 128);
 // 128 threads; kSmemBytes of dynamic shared memory. Cin and Cout are multiples of 16.

@@ -29,8 +29,10 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 # (Cin, Cout): the network's lift (2 channels padded to 16 -> C), block (C -> C), head
-# (C -> M) at the benchmark's C = 64, M = 128, and tile-splitting shapes
-LAYERS = [(16, 64), (64, 64), (64, 128), (80, 144), (16, 32), (32, 16)]
+# (C -> M)
+# at the benchmark's C = 64, M = 128, tile-splitting shapes, and 64- and 128-channel inputs
+# with narrow and wide outputs (the TMA kernels' accumulator rings of 4 and 8 blocks)
+LAYERS = [(16, 64), (64, 64), (64, 128), (80, 144), (16, 32), (32, 16), (64, 16), (64, 96), (128, 64), (128, 32)]
 # (B, H, W): image rows longer than one 128-pixel segment with a ragged tail, row
 # counts that are not multiples of the 4-row CTA tile, and a tiny image
 IMAGES = [(2, 6, 130), (1, 5, 9), (3, 1, 17)]
