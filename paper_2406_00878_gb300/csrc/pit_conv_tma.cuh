@@ -623,4 +623,198 @@ __global__ void __launch_bounds__(kRThreads, 1) conv3x3_fwd_rows_kernel(const __
     if (warp == 0) tmem_dealloc(taddr, 512);
 }
 
+
+// ------------------------------------------------------------------ weight gradients
+//
+// dW[co][r][s][ci] = sum over images n, output rows h, pixels w of
+//                    dY[n][h][w][co] X[n][h + r - 1][w + s - 1][ci]       (zero off the image)
+// regrouped by input row j = h + r - 1: input row j meets output rows j + 1, j, j - 1 through
+// row taps r = 0, 1, 2. Per input row (a 128-pixel segment), the CTA stages with TMA the X row
+// (kCols pixels, w0-1 .. w0+128) and the three dY rows j-1, j+1, j (one 64-channel block of
+// dY: a tile of 64 output channels), all 128-byte swizzled, and the tensor cores read them as
+// MN-major operands -- the NHWC rows as they are, no transposition:
+//   A (M = 128, K = 16 pixels) = [dY row j+1 ; dY row j]   or   [dY row j-1 ; dY row j+1]
+//       (two 64-channel blocks, byte offset between them (LBO) = one dY slot)
+//   B (N = 192, K = 16 pixels) = the X row from pixel s, s = 0, 1, 2
+//       (three 64-channel blocks 128 bytes apart: block s starts s pixels later)
+// so D1[(r, co)][(s, ci)] (r = 0 in lanes 0-63, r = 1 in lanes 64-127) and D2 (r = 2 in lanes
+// 0-63; lanes 64-127 repeat r = 0 and are not read) accumulate every tap of the CTA's rows:
+// per 16 pixels two MMAs of N = 192. The epilogue writes the CTA's FP32 partial sums
+// part[split][co][tap][ci]; a second pass adds them over the splits in a fixed order.
+// The epilogue warps, idle until then, also sum each staged dY row j over its pixels (the
+// bias gradient; each output row is row j of exactly one input row).
+// Requires Cin = 64 and Cout a multiple of 64 (tiles of 64 output channels).
+constexpr int kWRThreads = 192;
+constexpr int kWRYBytes = kM * 128;                       // one staged dY row block (128 px x 64 ch)
+constexpr int kWRTile = kSwBlockBytes + 3 * kWRYBytes;    // X row + 3 dY rows
+__host__ __device__ constexpr int bwdw_rows_smem_bytes(int ring) { return 1024 + ring * kWRTile + 512 + 128 * 4; }
+
+struct BwdwArgs {
+    float* part;              // [splits][Cout][9][64] partial sums
+    float* bias_part;         // [splits][Cout] partial bias gradients
+    int N, H, W, Cout;
+    int ring;                 // staged row tiles (>= 2)
+    int ctas_per_tile;        // CTAs (splits) per 64-channel output tile
+    int* err;
+};
+
+__device__ __forceinline__ uint64_t smem_desc_sw128_mn(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo & 0x3FFFF) >> 4) << 16;
+    d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// X map: (64 channels, W, H, N), box (64, kCols, 1, 1); dY map: (Cout, W, H, N), box (64, 128, 1, 1);
+// both 128-byte swizzled. Grid: Cout/64 tiles x ctas_per_tile; kWRThreads threads.
+__global__ void __launch_bounds__(kWRThreads, 1) conv3x3_bwdw_rows_kernel(const __grid_constant__ CUtensorMap xmap,
+                                                                          const __grid_constant__ CUtensorMap ymap,
+                                                                          BwdwArgs a) {
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    unsigned char* sm = sm_raw + ((1024 - (smem_u32(sm_raw) & 1023)) & 1023);
+    const int ring = a.ring;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + ring * kWRTile);  // [kFRingMax]
+    uint64_t* empty = full + kFRingMax;                                 // [kFRingMax]
+    uint64_t* fin = empty + kFRingMax;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
+    volatile int* abort_word = reinterpret_cast<volatile int*>(tslot + 1);
+    float* s_bias = reinterpret_cast<float*>(sm + ring * kWRTile + 512);  // [128] bias halves
+
+    const int tile = blockIdx.x / a.ctas_per_tile, split = blockIdx.x - tile * a.ctas_per_tile;
+    const int co0 = tile * 64;
+    const int w_tiles = (a.W + kM - 1) / kM;
+    const long long T = (long long)w_tiles * a.N * a.H;
+    const long long q0 = T * split / a.ctas_per_tile, q1 = T * (split + 1) / a.ctas_per_tile;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (warp == 0) tmem_alloc(tslot, 512);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ring; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 5);  // the MMAs' commit and the four bias warps
+        }
+        mbar_init(fin, 1);
+        *abort_word = 0;
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = *tslot;
+    long long loads = 0;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (long long q = q0; q < q1 && !*abort_word; ++q) {
+                const FwdRow r = fwd_row(q, a.N, a.H);
+                const int s = (int)(loads % ring);
+                if (loads >= ring && !fwd_wait(&empty[s], (uint32_t)((loads / ring - 1) & 1), abort_word)) break;
+                mbar_arrive_tx(&full[s], (uint32_t)(fwd_row_bytes(64) + 3 * kWRYBytes));
+                unsigned char* t = sm + (size_t)s * kWRTile;
+                tma_load_4d(t, &xmap, 0, r.wt * kM - 1, r.h, r.n, &full[s]);
+                // dY slots in the order j-1, j+1, j (A pairs: [j+1 ; j] and [j-1 ; j+1])
+                tma_load_4d(t + kSwBlockBytes, &ymap, co0, r.wt * kM, r.h - 1, r.n, &full[s]);
+                tma_load_4d(t + kSwBlockBytes + kWRYBytes, &ymap, co0, r.wt * kM, r.h + 1, r.n, &full[s]);
+                tma_load_4d(t + kSwBlockBytes + 2 * kWRYBytes, &ymap, co0, r.wt * kM, r.h, r.n, &full[s]);
+                ++loads;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // F32 accumulate, BF16 A and B, both MN-major, N = 192, M = 128
+            const uint32_t idesc = idesc_bf16(kM, 192) | (1u << 15) | (1u << 16);
+            bool ok = true;
+            long long l = 0;
+            for (long long q = q0; q < q1 && ok; ++q, ++l) {
+                ok = fwd_wait(&full[l % ring], (uint32_t)((l / ring) & 1), abort_word);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t t = smem_u32(sm) + (uint32_t)((l % ring) * kWRTile);
+                const uint32_t xs = t, ys = t + kSwBlockBytes;
+#pragma unroll
+                for (int k = 0; k < kM / 16; ++k) {
+                    const uint64_t b = smem_desc_sw128_mn(xs + k * 2048, 128, 1024);
+                    const uint64_t a1 = smem_desc_sw128_mn(ys + kWRYBytes + k * 2048, kWRYBytes, 1024);
+                    const uint64_t a2 = smem_desc_sw128_mn(ys + k * 2048, kWRYBytes, 1024);
+                    const uint32_t acc = (q > q0 || k > 0) ? 1u : 0u;
+                    mma_bf16(taddr, a1, b, idesc, acc);
+                    mma_bf16(taddr + 192, a2, b, idesc, acc);
+                }
+                mma_commit(&empty[l % ring]);
+            }
+            if (!ok) atomicExch(a.err, 1);
+            mma_commit(fin);
+        }
+    } else {
+        // bias: thread t sums channel t & 63 of the staged dY row j over pixels 64 (t >> 6) .. +63
+        const int t = threadIdx.x - 64, c = t & 63, p0 = (t >> 6) * 64;
+        float bsum = 0.f;
+        long long l = 0;
+        bool ok = true;
+        for (long long q = q0; q < q1; ++q, ++l) {
+            ok = __all_sync(0xffffffffu, fwd_wait(&full[l % ring], (uint32_t)((l / ring) & 1), abort_word));
+            if (!ok) break;
+            const unsigned char* y = sm + (size_t)(l % ring) * kWRTile + kSwBlockBytes + 2 * kWRYBytes;
+#pragma unroll 8
+            for (int p = p0; p < p0 + 64; ++p) {
+                // 128-byte swizzle: 16-byte chunk (c / 8) of pixel row p sits at chunk (c / 8) ^ (p % 8)
+                const unsigned off = (unsigned)p * 128u + ((((unsigned)c >> 3) ^ ((unsigned)p & 7u)) << 4) + ((unsigned)c & 7u) * 2u;
+                bsum += __bfloat162float(*reinterpret_cast<const bf16*>(y + off));
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive1(&empty[l % ring]);
+        }
+        if (!ok && lane == 0) {
+            *abort_word = 1;
+            atomicExch(a.err, 1);
+        }
+        // the accumulators are final once every MMA has completed
+        const bool done = ok && __all_sync(0xffffffffu, fwd_wait(fin, 0, abort_word));
+        tc_fence_after();
+        const int quarter = warp & 3, row = quarter * 32 + lane;
+        const int co = co0 + (row & 63);
+        float* P = a.part + ((size_t)split * a.Cout + co) * 9 * 64;
+        // D1: lanes 0-63 tap row r = 0, 64-127 r = 1; D2: lanes 0-63 r = 2
+        for (int d = 0; d < 2; ++d) {
+            const int r = d == 0 ? (row >> 6) : 2;
+            for (int j0 = 0; j0 < 192; j0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(d * 192 + j0), v);
+                if (done && (d == 0 || row < 64)) {
+                    float4* o = reinterpret_cast<float4*>(P + r * 192 + j0);  // taps r*3 + s, s = j0 / 64
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        o[e] = make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
+                                           __uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3]));
+                }
+            }
+        }
+        s_bias[t] = bsum;
+        asm volatile("bar.sync 1, 128;" ::: "memory");  // the four bias warps
+        if (t < 64 && done) a.bias_part[(size_t)split * a.Cout + co0 + t] = s_bias[t] + s_bias[t + 64];
+        if (!done && lane == 0) atomicExch(a.err, 1);
+    }
+    __syncthreads();
+    if (warp == 1 && lane == 0) {
+        bool done = false;
+        for (long long k = 0; k < kWaitPolls && !done; ++k) done = mbar_try_wait(fin, 0);
+        if (!done) atomicExch(a.err, 1);
+    }
+    if (warp == 0 && lane == 0) {
+        const long long from = loads > ring ? loads - ring : 0;
+        for (long long l = from; l < loads; ++l) {
+            bool done = false;
+            for (long long k = 0; k < kWaitPolls && !done; ++k) done = mbar_try_wait(&full[l % ring], (uint32_t)((l / ring) & 1));
+            if (!done) atomicExch(a.err, 1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(taddr, 512);
+}
+
 }  // namespace pit_tc

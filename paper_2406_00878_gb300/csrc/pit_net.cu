@@ -325,6 +325,21 @@ static bool encode_conv_maps(CUtensorMap* xm, CUtensorMap* wm, const bf16* X, co
 
 constexpr int kConvSmemLimit = 227 * 1024;
 
+// An NHWC activation [B][H][W][C] as (C, W, H, B) with 128-byte-swizzled boxes of 64
+// channels x box_w pixels (one image row segment).
+static bool encode_rows_map(CUtensorMap* m, const bf16* base, int B, int H, int W, int C, int box_w) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+    const cuuint64_t cb = (cuuint64_t)C * 2;
+    const cuuint64_t dim[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t str[3] = {cb, cb * W, cb * W * H};
+    const cuuint32_t box[4] = {64, (cuuint32_t)box_w, 1, 1};
+    const cuuint32_t ones[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(base), dim, str, box, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // The row-stationary TMA convolution (Cin = 64 or 128, weights and two staged rows fit in
 // shared memory); false = not applicable.
 static bool launch_conv_rows(pit_net* net, const bf16* X, const bf16* Wt, const float* bias, const bf16* res,
@@ -477,6 +492,51 @@ static pit_status conv_bwd(pit_net* net, const bf16* X, const bf16* dY, const La
     const pit_net_shape& s = net->shape;
     // the data-gradient convolution reads L.cout input channels in chunks of 16
     if (L.cin % 16 != 0 || L.cout % 16 != 0) return nfail(net, PIT_EINVAL, "conv channels must be multiples of 16");
+    {
+        // the MN-major TMA kernel (pit_conv_tma.cuh) for 64 input channels and 64k outputs
+        CUtensorMap xm, ym;
+        if (L.cin == 64 && L.cout % 64 == 0 &&
+            encode_rows_map(&xm, X, B, s.height, s.width, 64, pit_tc::kCols) &&
+            encode_rows_map(&ym, dY, B, s.height, s.width, L.cout, pit_tc::kM)) {
+            static int sms = 0;
+            static bool rattr = false;  // the limit belongs to the kernel; raising it again is harmless
+            if (!rattr) {
+                int dev = 0;
+                NCK(cudaGetDevice(&dev));
+                NCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+                NCK(cudaFuncSetAttribute(pit_tc::conv3x3_bwdw_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kConvSmemLimit));
+                rattr = true;
+            }
+            const int co_tiles = L.cout / 64;
+            const long long T = (long long)((s.width + pit_tc::kM - 1) / pit_tc::kM) * B * s.height;
+            const int per = (int)std::max(1LL, std::min({(long long)std::max(1, sms / co_tiles), T, (long long)kMaxSplits}));
+            pit_tc::BwdwArgs ba;
+            ba.part = net->part;
+            ba.bias_part = net->bias_part;
+            ba.N = B;
+            ba.H = s.height;
+            ba.W = s.width;
+            ba.Cout = L.cout;
+            ba.ring = 3;
+            ba.ctas_per_tile = per;
+            ba.err = net->tc_err;
+            pit_tc::conv3x3_bwdw_rows_kernel<<<co_tiles * per, pit_tc::kWRThreads, pit_tc::bwdw_rows_smem_bytes(3),
+                                               net->stream>>>(xm, ym, ba);
+            NCK(cudaGetLastError());
+            const size_t nw = (size_t)L.cout * 9 * L.cin;
+            sum_partials_kernel<<<grid_for(nw), 256, 0, net->stream>>>(net->part, net->g + L.w_off, per, nw);
+            sum_rows_kernel<<<L.cout, 256, 0, net->stream>>>(net->bias_part, net->g + L.b_off, per, L.cout);
+            if (dX) {
+                flip_transpose_kernel<<<grid_for(nw), 256, 0, net->stream>>>(net->wb + L.w_off, net->wf, L.cout, L.cin);
+                if (pit_status st =
+                        launch_conv_tc(net, dY, net->wf, net->loss_part + 1024, nullptr, dX, B, L.cout, L.cin, 0))
+                    return st;
+            }
+            NCK(cudaGetLastError());
+            return PIT_OK;
+        }
+    }
     const int rows = B * s.height;
     // one CTA per split and channel tile pair, about one per SM
     const int tiles = ((L.cin + pit_tc::kWCi - 1) / pit_tc::kWCi) * ((L.cout + pit_tc::kWCo - 1) / pit_tc::kWCo);
