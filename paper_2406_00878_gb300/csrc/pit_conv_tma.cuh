@@ -60,6 +60,7 @@ __host__ __device__ constexpr int fwd_smem_bytes(int cin, int nco, int ring, int
 struct FwdTmaArgs {
     const float* bias;        // [Cout]
     const bf16* residual;     // [N][H][W][Cout] or null
+    const bf16* mask;         // [N][H][W][Cout] or null: outputs zeroed where mask <= 0
     bf16* Y;                  // [N][H][W][Cout]
     int N, H, W, Cin, Cout;
     int relu;
@@ -302,30 +303,8 @@ __global__ void __launch_bounds__(kFThreads, 1) conv3x3_fwd_tma_kernel(const __g
                     float v[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(v32[j]) + s_bias[j0 + j];
-                    if (a.residual) {
-                        const uint4* rs = reinterpret_cast<const uint4*>(a.residual + ybase + j0);
-#pragma unroll
-                        for (int e2 = 0; e2 < 2; ++e2) {
-                            const uint4 u = rs[e2];
-                            const unsigned uu[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                v[e2 * 8 + 2 * e] += __bfloat162float(__ushort_as_bfloat16((unsigned short)(uu[e] & 0xffff)));
-                                v[e2 * 8 + 2 * e + 1] += __bfloat162float(__ushort_as_bfloat16((unsigned short)(uu[e] >> 16)));
-                            }
-                        }
-                    }
-                    if (a.relu)
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
-                    uint32_t packed[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e)
-                        packed[e] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(v[2 * e])) |
-                                    ((uint32_t)__bfloat16_as_ushort(__float2bfloat16(v[2 * e + 1])) << 16);
-                    uint4* out = reinterpret_cast<uint4*>(a.Y + ybase + j0);
-                    out[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                    out[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                    epilogue16(v, a.residual ? a.residual + ybase + j0 : nullptr, a.mask ? a.mask + ybase + j0 : nullptr,
+                               a.relu, a.Y + ybase + j0);
                 }
             }
             tc_fence_before();
@@ -375,10 +354,14 @@ __global__ void __launch_bounds__(kFThreads, 1) conv3x3_fwd_tma_kernel(const __g
 // Per output row (steady state, 64 input channels): 3 shifts x 4 K steps = 12 MMAs of
 // N = 192 instead of 36 of N = 64.
 //
+// Warp roles (320 threads): warp 0 one lane, TMA producer (weights, then input rows);
+// warp 1 one lane, MMA issuer; warps 2..9 epilogue, two per TMEM lane quarter (warp w reads
+// quarter w % 4 and every other 16-column chunk), which also zero the blocks they read.
+//
 // Weights in shared memory: for shift s and channel block kb, the B tile holds rows
 // r * nco + co (r = 0, 1, 2) of 64 channels, 128-byte swizzled: 9 TMA boxes per block.
 // Input rows: as above (swizzled 64-channel blocks of kCols pixels).
-constexpr int kRThreads = 192;
+constexpr int kRThreads = 320;  // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue (two per lane quarter)
 
 template <int KB>
 __global__ void __launch_bounds__(kRThreads, 1) conv3x3_fwd_rows_kernel(const __grid_constant__ CUtensorMap xmap,
@@ -418,7 +401,7 @@ __global__ void __launch_bounds__(kRThreads, 1) conv3x3_fwd_rows_kernel(const __
         }
         for (int b = 0; b < NB; ++b) {
             mbar_init(&bfull[b], 1);
-            mbar_init(&bempty[b], 4);
+            mbar_init(&bempty[b], 8);
         }
         mbar_init(wfull, 1);
         mbar_init(fin, 1);
@@ -431,12 +414,13 @@ __global__ void __launch_bounds__(kRThreads, 1) conv3x3_fwd_rows_kernel(const __
     tc_fence_after();
     const uint32_t taddr = *tslot;
     if (warp >= 2) {
-        // every accumulator block starts at zero
-        const int quarter = warp & 3;
+        // every accumulator block starts at zero (the two warps of a lane quarter take
+        // alternate 16-column chunks)
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
         uint32_t z[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) z[k] = 0u;
-        for (int c = 0; c < 512; c += 16) tmem_st16(taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c, z);
+        for (int c = half * 16; c < 512; c += 32) tmem_st16(taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c, z);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
@@ -538,8 +522,9 @@ __global__ void __launch_bounds__(kRThreads, 1) conv3x3_fwd_rows_kernel(const __
             mma_commit(fin);
         }
     } else {
-        // epilogue: warps 2..5 cover the TMEM lane quarters 2, 3, 0, 1
-        const int quarter = warp & 3;
+        // epilogue: warps 2..9 -- warp w reads TMEM lane quarter w % 4 (32 pixels) and the
+        // 16-column chunks 16 h, 16 h + 32, ... with h = (w - 2) / 4
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
         int i = 0;
         for (long long q = q0; q < q1; ++q, ++i) {
             const int blk = i & (NB - 1);
@@ -558,7 +543,7 @@ __global__ void __launch_bounds__(kRThreads, 1) conv3x3_fwd_rows_kernel(const __
             uint32_t z[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) z[k] = 0u;
-            for (int j0 = 0; j0 < nco; j0 += 16) {
+            for (int j0 = half * 16; j0 < nco; j0 += 32) {
                 uint32_t v32[16];
                 tmem_ld16(tcol + (uint32_t)j0, v32);
                 tmem_st16(tcol + (uint32_t)j0, z);  // the block starts the next row at zero
@@ -566,30 +551,8 @@ __global__ void __launch_bounds__(kRThreads, 1) conv3x3_fwd_rows_kernel(const __
                     float v[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(v32[j]) + s_bias[j0 + j];
-                    if (a.residual) {
-                        const uint4* rs = reinterpret_cast<const uint4*>(a.residual + ybase + j0);
-#pragma unroll
-                        for (int e2 = 0; e2 < 2; ++e2) {
-                            const uint4 u = rs[e2];
-                            const unsigned uu[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                v[e2 * 8 + 2 * e] += __bfloat162float(__ushort_as_bfloat16((unsigned short)(uu[e] & 0xffff)));
-                                v[e2 * 8 + 2 * e + 1] += __bfloat162float(__ushort_as_bfloat16((unsigned short)(uu[e] >> 16)));
-                            }
-                        }
-                    }
-                    if (a.relu)
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
-                    uint32_t packed[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e)
-                        packed[e] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(v[2 * e])) |
-                                    ((uint32_t)__bfloat16_as_ushort(__float2bfloat16(v[2 * e + 1])) << 16);
-                    uint4* out = reinterpret_cast<uint4*>(a.Y + ybase + j0);
-                    out[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                    out[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                    epilogue16(v, a.residual ? a.residual + ybase + j0 : nullptr, a.mask ? a.mask + ybase + j0 : nullptr,
+                               a.relu, a.Y + ybase + j0);
                 }
             }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");

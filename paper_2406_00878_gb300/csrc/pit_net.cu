@@ -19,7 +19,6 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
-#include <cstdlib>
 #include <cstring>
 #include <random>
 #include <vector>
@@ -31,18 +30,26 @@
 namespace {
 
 typedef __nv_bfloat16 bf16;
-constexpr int kCinPad0 = 16;   // input channels padded for the K step
+constexpr int kCinPad0 = 64;   // input channels padded to one 64-channel block (the TMA convolutions' unit)
 constexpr int kMaxSplits = 160;  // pixel splits of the weight-gradient GEMMs, at most
 
-// Sum the split partials in split order (deterministic).
-__global__ void sum_partials_kernel(const float* __restrict__ part, float* __restrict__ out, int splits, size_t n) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        float s = 0.f;
+// Sum the split partials (deterministic): a CTA takes 64 outputs; thread group g (of four)
+// adds splits g, g + 4, ... in order, and the four sums are added in group order.
+__global__ void __launch_bounds__(256) sum_partials_kernel(const float* __restrict__ part, float* __restrict__ out,
+                                                           int splits, size_t n) {
+    __shared__ float red[4][64];
+    const int o = threadIdx.x & 63, g = threadIdx.x >> 6;
+    const size_t i = (size_t)blockIdx.x * 64 + o;
+    float s = 0.f;
+    if (i < n) {
 #pragma unroll 8
-        for (int k = 0; k < splits; ++k) s += __ldg(part + (size_t)k * n + i);  // loads batched, adds in order
-        out[i] = s;
+        for (int k = g; k < splits; k += 4) s += __ldg(part + (size_t)k * n + i);
     }
+    red[g][o] = s;
+    __syncthreads();
+    if (g == 0 && i < n) out[i] = ((red[0][o] + red[1][o]) + red[2][o]) + red[3][o];
 }
+static int sum_partials_grid(size_t n) { return (int)((n + 63) / 64); }
 
 // out[c] = sum over k of part[k][c] for few columns c and many rows k: one CTA per column,
 // threads take rows in a fixed stride and fold in a fixed tree (deterministic).
@@ -108,23 +115,20 @@ __global__ void relu_back_kernel(bf16* __restrict__ d, const bf16* __restrict__ 
         if (!(__bfloat162float(act[i]) > 0.f)) d[i] = __float2bfloat16(0.f);
 }
 
-// a += b (BF16 tensors, FP32 add).
-__global__ void add_kernel(bf16* __restrict__ a, const bf16* __restrict__ b, size_t n) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        a[i] = __float2bfloat16(__bfloat162float(a[i]) + __bfloat162float(b[i]));
-}
-
-// Network input: channel 0 = u0, channel 1 = log10 nu, channels 2..15 = 0.
+// Network input: channel 0 = u0, channel 1 = log10 nu, channels 2..kCinPad0-1 = 0; one
+// pixel's kCinPad0 channels written as 16-byte words.
 __global__ void input_kernel(const double* __restrict__ u0, const float* __restrict__ lognu, bf16* __restrict__ X,
                              int N, size_t Ns) {
+    static_assert(kCinPad0 % 8 == 0, "whole 16-byte words per pixel");
     const size_t n_total = (size_t)N * Ns;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_total; i += (size_t)gridDim.x * blockDim.x) {
         const int n = (int)(i / Ns);
-        bf16* x = X + i * kCinPad0;
-        x[0] = __float2bfloat16((float)u0[i]);
-        x[1] = __float2bfloat16(lognu[n]);
+        uint4* x = reinterpret_cast<uint4*>(X + i * kCinPad0);
+        const uint32_t w0 = (uint32_t)__bfloat16_as_ushort(__float2bfloat16((float)u0[i])) |
+                            ((uint32_t)__bfloat16_as_ushort(__float2bfloat16(lognu[n])) << 16);
+        x[0] = make_uint4(w0, 0u, 0u, 0u);
 #pragma unroll
-        for (int c = 2; c < kCinPad0; ++c) x[c] = __float2bfloat16(0.f);
+        for (int k = 1; k < kCinPad0 / 8; ++k) x[k] = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
@@ -153,10 +157,30 @@ __global__ void target_kernel(const double* __restrict__ U, const double* __rest
 
 // dout = 2 (out - target) / count and per-CTA partial sums of (out - target)^2.
 __global__ void mse_kernel(const bf16* __restrict__ out, const bf16* __restrict__ target, bf16* __restrict__ dout,
-                           float* __restrict__ partial, size_t n, float scale) {
+                           float* __restrict__ partial, size_t n, float scale, int vec) {
     __shared__ float red[256];
     float s = 0.f;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    // eight values (16 bytes) per step when every buffer is 16-byte aligned (vec); the rest
+    // one by one
+    const size_t n8 = vec ? n / 8 : 0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n8; k += stride) {
+        const uint4 uo = reinterpret_cast<const uint4*>(out)[k], ut = reinterpret_cast<const uint4*>(target)[k];
+        const unsigned wo[4] = {uo.x, uo.y, uo.z, uo.w}, wt[4] = {ut.x, ut.y, ut.z, ut.w};
+        unsigned wd[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float d0 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(wo[e] & 0xffff))) -
+                             __bfloat162float(__ushort_as_bfloat16((unsigned short)(wt[e] & 0xffff)));
+            const float d1 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(wo[e] >> 16))) -
+                             __bfloat162float(__ushort_as_bfloat16((unsigned short)(wt[e] >> 16)));
+            s += d0 * d0 + d1 * d1;
+            wd[e] = (unsigned)__bfloat16_as_ushort(__float2bfloat16(2.f * d0 * scale)) |
+                    ((unsigned)__bfloat16_as_ushort(__float2bfloat16(2.f * d1 * scale)) << 16);
+        }
+        reinterpret_cast<uint4*>(dout)[k] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    }
+    for (size_t i = n8 * 8 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float d = __bfloat162float(out[i]) - __bfloat162float(target[i]);
         s += d * d;
         dout[i] = __float2bfloat16(2.f * d * scale);
@@ -343,11 +367,14 @@ static bool encode_rows_map(CUtensorMap* m, const bf16* base, int B, int H, int 
 // The row-stationary TMA convolution (Cin = 64 or 128, weights and two staged rows fit in
 // shared memory); false = not applicable.
 static bool launch_conv_rows(pit_net* net, const bf16* X, const bf16* Wt, const float* bias, const bf16* res,
-                             bf16* Y, int B, int H, int W, int Cin, int Cout, int relu, cudaError_t* cerr) {
+                             const bf16* mask, bf16* Y, int B, int H, int W, int Cin, int Cout, int relu,
+                             cudaError_t* cerr) {
     *cerr = cudaSuccess;
     if (Cin != 64 && Cin != 128) return false;
     const int nco = Cout < 128 ? Cout : 128;
-    int ring = 3;
+    // four staged rows measured fastest (2: 1.346, 3: 1.336, 4: 1.331, 6: 1.351, 8: 1.376 ms
+    // per training step of the 64-channel network on 16 images of 128 x 128)
+    int ring = 4;
     while (ring >= 2 && pit_tc::fwd_smem_bytes(Cin, nco, ring, 1) > kConvSmemLimit) --ring;
     if (ring < 2 || (reinterpret_cast<uintptr_t>(X) & 15) || (reinterpret_cast<uintptr_t>(Wt) & 15)) return false;
     CUtensorMap xm, wm;
@@ -372,6 +399,7 @@ static bool launch_conv_rows(pit_net* net, const bf16* X, const bf16* Wt, const 
     pit_tc::FwdTmaArgs a;
     a.bias = bias;
     a.residual = res;
+    a.mask = mask;
     a.Y = Y;
     a.N = B;
     a.H = H;
@@ -396,10 +424,11 @@ static bool launch_conv_rows(pit_net* net, const bf16* X, const bf16* Wt, const 
 
 // The TMA convolution when the layer's weight tile and a ring of at least four input rows
 // fit in shared memory (and the maps encode); false = use the staged kernel.
-static bool launch_conv_tma(pit_net* net, const bf16* X, const bf16* Wt, const float* bias, const bf16* res, bf16* Y,
-                            int B, int H, int W, int Cin, int Cout, int relu, cudaError_t* cerr) {
+static bool launch_conv_tma(pit_net* net, const bf16* X, const bf16* Wt, const float* bias, const bf16* res,
+                            const bf16* mask, bf16* Y, int B, int H, int W, int Cin, int Cout, int relu,
+                            cudaError_t* cerr) {
     *cerr = cudaSuccess;
-    if (launch_conv_rows(net, X, Wt, bias, res, Y, B, H, W, Cin, Cout, relu, cerr)) return true;
+    if (launch_conv_rows(net, X, Wt, bias, res, mask, Y, B, H, W, Cin, Cout, relu, cerr)) return true;
     const int nco = Cout < pit_tc::kFNMax ? Cout : pit_tc::kFNMax;
     const int sw = Cin % 64 == 0 ? 1 : 0;
     int ring = pit_tc::kFRingMax;
@@ -424,6 +453,7 @@ static bool launch_conv_tma(pit_net* net, const bf16* X, const bf16* Wt, const f
     pit_tc::FwdTmaArgs a;
     a.bias = bias;
     a.residual = res;
+    a.mask = mask;
     a.Y = Y;
     a.N = B;
     a.H = H;
@@ -446,12 +476,12 @@ static bool launch_conv_tma(pit_net* net, const bf16* X, const bf16* Wt, const f
 // Y = act(conv3x3(X; Wt) + bias (+ res)) on the tcgen05 tensor cores: the TMA kernel
 // (pit_conv_tma.cuh) when the layer fits it, else the staged kernel (pit_tc.cuh).
 static pit_status launch_conv_tc(pit_net* net, const bf16* X, const bf16* Wt, const float* bias, const bf16* res,
-                                 bf16* Y, int B, int Cin, int Cout, int relu) {
+                                 bf16* Y, int B, int Cin, int Cout, int relu, const bf16* mask = nullptr) {
     const pit_net_shape& s = net->shape;
     if (Cin % 16 != 0 || Cout % 16 != 0) return nfail(net, PIT_EINVAL, "conv channels must be multiples of 16");
     {
         cudaError_t e = cudaSuccess;
-        if (launch_conv_tma(net, X, Wt, bias, res, Y, B, s.height, s.width, Cin, Cout, relu, &e)) {
+        if (launch_conv_tma(net, X, Wt, bias, res, mask, Y, B, s.height, s.width, Cin, Cout, relu, &e)) {
             NCK(e);
             return PIT_OK;
         }
@@ -466,7 +496,7 @@ static pit_status launch_conv_tc(pit_net* net, const bf16* X, const bf16* Wt, co
     dim3 grid((unsigned)(B * ((s.height + pit_tc::kRows - 1) / pit_tc::kRows) * ((s.width + pit_tc::kM - 1) / pit_tc::kM)),
               (unsigned)((Cout + pit_tc::kNMax - 1) / pit_tc::kNMax));
     pit_tc::conv3x3_fwd_tc_kernel<<<grid, pit_tc::kThreads, smem, net->stream>>>(
-        X, Wt, bias, res, Y, B, s.height, s.width, Cin, Cout, relu, net->tc_err);
+        X, Wt, bias, res, mask, Y, B, s.height, s.width, Cin, Cout, relu, net->tc_err);
     NCK(cudaGetLastError());
     return PIT_OK;
 }
@@ -487,8 +517,11 @@ static pit_status check_tc(pit_net* net) {
     return PIT_OK;
 }
 
-// dX = conv(dY, flipped W) without bias; dW, db into net->g.
-static pit_status conv_bwd(pit_net* net, const bf16* X, const bf16* dY, const Layer& L, bf16* dX, int B) {
+// dX = conv(dY, flipped W) without bias (+ dx_res, then zeroed where dx_mask <= 0: the
+// residual branch's gradient and the backward ReLU, fused into the epilogue; dx_res may be
+// dX itself); dW, db into net->g.
+static pit_status conv_bwd(pit_net* net, const bf16* X, const bf16* dY, const Layer& L, bf16* dX, int B,
+                           const bf16* dx_res = nullptr, const bf16* dx_mask = nullptr) {
     const pit_net_shape& s = net->shape;
     // the data-gradient convolution reads L.cout input channels in chunks of 16
     if (L.cin % 16 != 0 || L.cout % 16 != 0) return nfail(net, PIT_EINVAL, "conv channels must be multiples of 16");
@@ -525,12 +558,12 @@ static pit_status conv_bwd(pit_net* net, const bf16* X, const bf16* dY, const La
                                                net->stream>>>(xm, ym, ba);
             NCK(cudaGetLastError());
             const size_t nw = (size_t)L.cout * 9 * L.cin;
-            sum_partials_kernel<<<grid_for(nw), 256, 0, net->stream>>>(net->part, net->g + L.w_off, per, nw);
+            sum_partials_kernel<<<sum_partials_grid(nw), 256, 0, net->stream>>>(net->part, net->g + L.w_off, per, nw);
             sum_rows_kernel<<<L.cout, 256, 0, net->stream>>>(net->bias_part, net->g + L.b_off, per, L.cout);
             if (dX) {
                 flip_transpose_kernel<<<grid_for(nw), 256, 0, net->stream>>>(net->wb + L.w_off, net->wf, L.cout, L.cin);
-                if (pit_status st =
-                        launch_conv_tc(net, dY, net->wf, net->loss_part + 1024, nullptr, dX, B, L.cout, L.cin, 0))
+                if (pit_status st = launch_conv_tc(net, dY, net->wf, net->loss_part + 1024, dx_res, dX, B, L.cout,
+                                                   L.cin, 0, dx_mask))
                     return st;
             }
             NCK(cudaGetLastError());
@@ -555,7 +588,7 @@ static pit_status conv_bwd(pit_net* net, const bf16* X, const bf16* dY, const La
         X, dY, net->part, B, s.height, s.width, L.cin, L.cout, rows_per_split, net->tc_err);
     NCK(cudaGetLastError());
     const size_t nw = (size_t)L.cout * 9 * L.cin;
-    sum_partials_kernel<<<grid_for(nw), 256, 0, net->stream>>>(net->part, net->g + L.w_off, splits, nw);
+    sum_partials_kernel<<<sum_partials_grid(nw), 256, 0, net->stream>>>(net->part, net->g + L.w_off, splits, nw);
     {
         const size_t pixels = (size_t)B * s.height * s.width;
         const size_t per = (pixels + kBiasBlocks - 1) / kBiasBlocks;
@@ -566,7 +599,8 @@ static pit_status conv_bwd(pit_net* net, const bf16* X, const bf16* dY, const La
     if (dX) {
         flip_transpose_kernel<<<grid_for(nw), 256, 0, net->stream>>>(net->wb + L.w_off, net->wf, L.cout, L.cin);
         // zero bias for the data gradient: the zero tail of the loss buffer
-        if (pit_status st = launch_conv_tc(net, dY, net->wf, net->loss_part + 1024, nullptr, dX, B, L.cout, L.cin, 0))
+        if (pit_status st =
+                launch_conv_tc(net, dY, net->wf, net->loss_part + 1024, dx_res, dX, B, L.cout, L.cin, 0, dx_mask))
             return st;
     }
     NCK(cudaGetLastError());
@@ -793,24 +827,28 @@ static pit_status loss_grad(pit_net* net, const double* u0_dev, const float* log
     if (pit_status st = forward(net, u0_dev, net->lognu, B)) return st;
     const size_t nout = (size_t)B * Ns * s.levels;
     const int blocks = std::min(1024, grid_for(nout));
+    const int vec = (reinterpret_cast<uintptr_t>(target_dev) & 15) == 0 ? 1 : 0;
     mse_kernel<<<blocks, 256, 0, net->stream>>>(net->out, static_cast<const bf16*>(target_dev), net->dout,
-                                                net->loss_part, nout, 1.f / (float)nout);
+                                                net->loss_part, nout, 1.f / (float)nout, vec);
     NCK(cudaGetLastError());
     // backward: head, blocks in reverse, lift
     const int nb = s.blocks;
     bf16* dx = net->d0;
     if (pit_status st = conv_bwd(net, net->xs[nb], net->dout, net->layers.back(), dx, B)) return st;
     for (int k = nb - 1; k >= 0; --k) {
-        // x_{k+1} = x_k + conv2(h_k): gradient dx flows to conv2 and straight to x_k
+        // x_{k+1} = x_k + conv2(h_k): gradient dx flows to conv2 and straight to x_k.
+        // dh = (conv2's data gradient) zeroed where h_k <= 0 (h_k = relu(conv1(x_k)));
+        // dx += conv1's data gradient of dh, in place -- and for k = 0 zeroed where x_0 <= 0
+        // (x_0 = relu(lift(in))), the gradient the lift's weights need
         bf16* dh = net->d1;
-        if (pit_status st = conv_bwd(net, net->hs[k], dx, net->layers[2 + 2 * k], dh, B)) return st;
-        relu_back_kernel<<<grid_for(B * Ns * s.channels), 256, 0, net->stream>>>(dh, net->hs[k], B * Ns * s.channels);
-        bf16* dxi = net->d2;
-        if (pit_status st = conv_bwd(net, net->xs[k], dh, net->layers[1 + 2 * k], dxi, B)) return st;
-        add_kernel<<<grid_for(B * Ns * s.channels), 256, 0, net->stream>>>(dx, dxi, B * Ns * s.channels);
+        if (pit_status st = conv_bwd(net, net->hs[k], dx, net->layers[2 + 2 * k], dh, B, nullptr, net->hs[k]))
+            return st;
+        if (pit_status st = conv_bwd(net, net->xs[k], dh, net->layers[1 + 2 * k], dx, B, dx, k == 0 ? net->xs[0] : nullptr))
+            return st;
         NCK(cudaGetLastError());
     }
-    relu_back_kernel<<<grid_for(B * Ns * s.channels), 256, 0, net->stream>>>(dx, net->xs[0], B * Ns * s.channels);
+    if (nb == 0)
+        relu_back_kernel<<<grid_for(B * Ns * s.channels), 256, 0, net->stream>>>(dx, net->xs[0], B * Ns * s.channels);
     if (pit_status st = conv_bwd(net, net->in, dx, net->layers[0], nullptr, B)) return st;
     if (loss_out) {
         std::vector<float> part(blocks);

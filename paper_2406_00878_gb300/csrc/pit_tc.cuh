@@ -160,14 +160,60 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
         : "memory");
 }
 
+// Sixteen BF16 values from two 16-byte words.
+__device__ __forceinline__ void load_bf16x16(const bf16* p, float (&f)[16]) {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+    for (int e2 = 0; e2 < 2; ++e2) {
+        const uint4 u = q[e2];
+        const unsigned uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            f[e2 * 8 + 2 * e] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(uu[e] & 0xffff)));
+            f[e2 * 8 + 2 * e + 1] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(uu[e] >> 16)));
+        }
+    }
+}
+
+// Epilogue of 16 output channels of one pixel: v (accumulator + bias) + residual, then ReLU,
+// then the mask (zero where mask <= 0: back through a ReLU whose output was mask), rounded
+// to BF16 and stored as two 16-byte words. res and mask may be null.
+__device__ __forceinline__ void epilogue16(float (&v)[16], const bf16* res, const bf16* mask, int relu, bf16* out) {
+    if (res) {
+        float r[16];
+        load_bf16x16(res, r);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] += r[j];
+    }
+    if (relu)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
+    if (mask) {
+        float m[16];
+        load_bf16x16(mask, m);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (!(m[j] > 0.f)) v[j] = 0.f;
+    }
+    uint32_t packed[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+        packed[e] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(v[2 * e])) |
+                    ((uint32_t)__bfloat16_as_ushort(__float2bfloat16(v[2 * e + 1])) << 16);
+    uint4* o = reinterpret_cast<uint4*>(out);
+    o[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    o[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+}
+
 // Y[n][h][w][co] = act(bias[co] + sum_{tap, ci} X[n][h+r-1][w+s-1][ci] W[co][tap][ci] (+ residual)).
 // Grid: x = N * ceil(H / kRows) * ceil(W / 128) row-group segments, y = ceil(Cout / 128);
 // 128 threads; kSmemBytes of dynamic shared memory. Cin and Cout are multiples of 16.
 __global__ void __launch_bounds__(kThreads) conv3x3_fwd_tc_kernel(const bf16* __restrict__ X,
                                                                   const bf16* __restrict__ Wt,
                                                                   const float* __restrict__ bias,
-                                                                  const bf16* __restrict__ residual,
-                                                                  bf16* __restrict__ Y, int N, int H, int W, int Cin,
+                                                                  const bf16* residual, const bf16* mask,
+                                                                  bf16* Y,  // may alias residual (in place)
+                                                                  int N, int H, int W, int Cin,
                                                                   int Cout, int relu, int* err) {
     extern __shared__ __align__(128) unsigned char sm[];
     const int nb = Cout < kNMax ? Cout : kNMax;  // weight rows per staged plane
@@ -276,32 +322,8 @@ __global__ void __launch_bounds__(kThreads) conv3x3_fwd_tc_kernel(const bf16* __
                     float v[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]) + bias[co0 + j0 + j];
-                    if (residual) {
-                        const uint4* rs = reinterpret_cast<const uint4*>(residual + ybase + j0);
-#pragma unroll
-                        for (int e2 = 0; e2 < 2; ++e2) {
-                            const uint4 u = rs[e2];
-                            const unsigned uu[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                v[e2 * 8 + 2 * e] +=
-                                    __bfloat162float(__ushort_as_bfloat16((unsigned short)(uu[e] & 0xffff)));
-                                v[e2 * 8 + 2 * e + 1] +=
-                                    __bfloat162float(__ushort_as_bfloat16((unsigned short)(uu[e] >> 16)));
-                            }
-                        }
-                    }
-                    if (relu)
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
-                    uint32_t packed[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e)
-                        packed[e] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(v[2 * e])) |
-                                    ((uint32_t)__bfloat16_as_ushort(__float2bfloat16(v[2 * e + 1])) << 16);
-                    uint4* out = reinterpret_cast<uint4*>(Y + ybase + j0);
-                    out[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                    out[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                    epilogue16(v, residual ? residual + ybase + j0 : nullptr, mask ? mask + ybase + j0 : nullptr, relu,
+                               Y + ybase + j0);
                 }
             }
         }
