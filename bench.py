@@ -583,6 +583,8 @@ def learned_variant(args):
             "forms": forms,
             "combined_vs_plain_fp64": forms["combined"]["dof_per_s"] / plain if plain else None,
             "learned_vs_plain_fp64": forms["learned"]["dof_per_s"] / plain if plain else None,
+            "learned_fp32_vs_plain_fp64": forms["learned_fp32"]["dof_per_s"] / plain if plain else None,
+            "batched_vs_plain_fp64": forms["batched"]["dof_per_s"] / plain if plain else None,
             "newton_iters_plain": rep["newton_iters_plain_mean"],
             "newton_iters_learned": rep["newton_iters_learned_mean"],
             "train_tflops_bf16": rep["train_tflops"], "generation_dof_per_s": rep["generation_dof_per_s"],

@@ -528,6 +528,21 @@ __global__ void __launch_bounds__(kRThreads, 1) conv3x3_fwd_rows_kernel(const __
         int i = 0;
         for (long long q = q0; q < q1; ++q, ++i) {
             const int blk = i & (NB - 1);
+            const FwdRow r = fwd_row(q, a.N, a.H);
+            const int p = r.wt * kM + quarter * 32 + lane;  // this thread's pixel
+            const size_t ybase = (((size_t)r.n * a.H + r.h) * a.W + p) * a.Cout + co0;
+            // the residual and mask of this thread's first two chunks do not depend on the
+            // accumulator: load them before waiting for it
+            float rv[2][16], mv[2][16];
+            const bool pix = p < a.W;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int j0 = half * 16 + 32 * c;
+                if (pix && j0 < nt) {
+                    if (a.residual) load_bf16x16(a.residual + ybase + j0, rv[c]);
+                    if (a.mask) load_bf16x16(a.mask + ybase + j0, mv[c]);
+                }
+            }
             if (!__all_sync(0xffffffffu, fwd_wait(&bfull[blk], (uint32_t)((i / NB) & 1), abort_word))) {
                 if (lane == 0) {
                     *abort_word = 1;
@@ -536,18 +551,31 @@ __global__ void __launch_bounds__(kRThreads, 1) conv3x3_fwd_rows_kernel(const __
                 break;
             }
             tc_fence_after();
-            const FwdRow r = fwd_row(q, a.N, a.H);
-            const int p = r.wt * kM + quarter * 32 + lane;  // this thread's pixel
-            const size_t ybase = (((size_t)r.n * a.H + r.h) * a.W + p) * a.Cout + co0;
             const uint32_t tcol = taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((NB - 1 - blk) * nco);
             uint32_t z[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) z[k] = 0u;
-            for (int j0 = half * 16; j0 < nco; j0 += 32) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int j0 = half * 16 + 32 * c;
+                if (j0 < nco) {
+                    uint32_t v32[16];
+                    tmem_ld16(tcol + (uint32_t)j0, v32);
+                    tmem_st16(tcol + (uint32_t)j0, z);  // the block starts the next row at zero
+                    if (pix && j0 < nt) {
+                        float v[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(v32[j]) + s_bias[j0 + j];
+                        epilogue16_loaded(v, a.residual ? rv[c] : nullptr, a.mask ? mv[c] : nullptr, a.relu,
+                                          a.Y + ybase + j0);
+                    }
+                }
+            }
+            for (int j0 = half * 16 + 64; j0 < nco; j0 += 32) {
                 uint32_t v32[16];
                 tmem_ld16(tcol + (uint32_t)j0, v32);
-                tmem_st16(tcol + (uint32_t)j0, z);  // the block starts the next row at zero
-                if (p < a.W && j0 < nt) {
+                tmem_st16(tcol + (uint32_t)j0, z);
+                if (pix && j0 < nt) {
                     float v[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(v32[j]) + s_bias[j0 + j];

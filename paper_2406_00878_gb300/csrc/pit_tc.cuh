@@ -175,6 +175,29 @@ __device__ __forceinline__ void load_bf16x16(const bf16* p, float (&f)[16]) {
     }
 }
 
+// The epilogue with the residual and mask values already loaded (r, m; null when absent).
+__device__ __forceinline__ void epilogue16_loaded(float (&v)[16], const float* r, const float* m, int relu,
+                                                  bf16* out) {
+    if (r)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] += r[j];
+    if (relu)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
+    if (m)
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (!(m[j] > 0.f)) v[j] = 0.f;
+    uint32_t packed[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+        packed[e] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(v[2 * e])) |
+                    ((uint32_t)__bfloat16_as_ushort(__float2bfloat16(v[2 * e + 1])) << 16);
+    uint4* o = reinterpret_cast<uint4*>(out);
+    o[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    o[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+}
+
 // Epilogue of 16 output channels of one pixel: v (accumulator + bias) + residual, then ReLU,
 // then the mask (zero where mask <= 0: back through a ReLU whose output was mask), rounded
 // to BF16 and stored as two 16-byte words. res and mask may be null.
