@@ -74,6 +74,12 @@ struct pit_batch {
     double est_ms = 0.0, ms_tuning = 0.0;
     int min_team = 0, max_team = 0;
     bool calibrating = false;          // autotuner runs: plain starts on scratch iterates
+    // problems of several closures or kinds: one batch per closure and kind (wavefront job or
+    // single team), solved one after another (a kernel holding several closures' wave bodies
+    // ran each job 20-25 % slower than the kernel of its own closure); problem i is problem
+    // where[i].second of parts[where[i].first]
+    std::vector<pit_batch*> parts;
+    std::vector<std::pair<int, int>> where;
     char err[512] = "";
 };
 
@@ -101,19 +107,24 @@ static pit_status bfail(pit_batch* b, pit_status s, const char* fmt, ...) {
         if (s_ != PIT_OK) return s_; \
     } while (0)
 
-// The batched kernel of every precision and closure set, one per compilation of
-// pit_batch_kernels.cu: pit_batch_kernel_<fp32>_<set>().
-#define PIT_BK_SETS(X, f) \
-    X(f, 1) X(f, 2) X(f, 3) X(f, 4) X(f, 5) X(f, 6) X(f, 7) X(f, 8) X(f, 9) X(f, 10) X(f, 11) X(f, 12) X(f, 13) X(f, 14) X(f, 15)
+// The batched kernel of every precision and closure, one per compilation of
+// pit_batch_kernels.cu: pit_batch_kernel_<fp32>_<closure bit>(). A batch holds problems of
+// one closure (pit_batch_create splits mixed sets).
+#define PIT_BK_SETS(X, f) X(f, 1) X(f, 2) X(f, 4) X(f, 8)
 #define PIT_BK_DECL(f, c) __attribute__((visibility("hidden"))) const void* pit_batch_kernel_##f##_##c();
-#define PIT_BK_ENTRY(f, c) pit_batch_kernel_##f##_##c,
 PIT_BK_SETS(PIT_BK_DECL, 0)
 PIT_BK_SETS(PIT_BK_DECL, 1)
 
 static const void* batch_fn(bool fp32, int closures) {
-    using Getter = const void* (*)();
-    static const Getter table[2][16] = {{nullptr, PIT_BK_SETS(PIT_BK_ENTRY, 0)}, {nullptr, PIT_BK_SETS(PIT_BK_ENTRY, 1)}};
-    return closures >= 1 && closures <= 15 ? table[fp32 ? 1 : 0][closures]() : nullptr;
+    switch (closures) {
+#define PIT_BK_CASE(f, c) \
+    case c:               \
+        return fp32 ? pit_batch_kernel_1_##c() : pit_batch_kernel_0_##c();
+        PIT_BK_SETS(PIT_BK_CASE, 0)
+#undef PIT_BK_CASE
+        default:
+            return nullptr;
+    }
 }
 
 static size_t team_smem(bool fp32, int nx, int ny, int G) {
@@ -400,6 +411,55 @@ extern "C" pit_status pit_batch_create(const pit_instance* inst, int count, cons
     b->user_stream = static_cast<cudaStream_t>(stream);
     b->fp32 = b->opt.precision == PIT_FP32_INNER;
     b->in.assign(inst, inst + count);
+    {
+        // several closures, or wavefront jobs beside single teams: a batch per closure and
+        // kind, solved one after another (one launch mixing them measured slower than the
+        // separate launches together: 2019 against 1412 + 427 ms on the 64-problem workload)
+        auto key = [&](const pit_instance& I) {
+            const int bit = closure_bit(I.params.equation == PIT_BURGERS, I.params.mu_b != 0.0);
+            const bool wave = b->opt.batch_wave_nodes > 0 && (long long)I.grid.nx * I.grid.ny >= b->opt.batch_wave_nodes;
+            return 2 * bit + (wave ? 1 : 0);
+        };
+        unsigned long long keys = 0;  // bit 2 * closure_bit + wave: at most 2 * 8 + 1 = 17
+        for (int i = 0; i < count; ++i) {
+            const pit_instance& I = inst[i];
+            if (I.params.equation != PIT_HEAT && I.params.equation != PIT_BURGERS) {
+                delete b;
+                return PIT_EINVAL;
+            }
+            keys |= 1ull << key(I);
+        }
+        if (keys & (keys - 1)) {
+            b->where.resize(count);
+            for (int k = 0; k < 64; ++k) {
+                if (!(keys >> k & 1)) continue;
+                std::vector<pit_instance> sub;
+                for (int i = 0; i < count; ++i)
+                    if (key(inst[i]) == k) {
+                        b->where[i] = {(int)b->parts.size(), (int)sub.size()};
+                        sub.push_back(inst[i]);
+                    }
+                pit_batch* part = nullptr;
+                const pit_status st = pit_batch_create(sub.data(), (int)sub.size(), opt, stream, &part);
+                if (st != PIT_OK) {
+                    for (pit_batch* q : b->parts) pit_batch_destroy(q);
+                    delete b;
+                    return st;
+                }
+                b->parts.push_back(part);
+            }
+            for (pit_batch* q : b->parts) {
+                b->wave_jobs += q->wave_jobs;
+                b->ms_tuning += q->ms_tuning;
+                b->est_ms += q->est_ms;
+                b->ctas = std::max(b->ctas, q->ctas);
+                b->min_team = b->min_team ? std::min(b->min_team, q->min_team) : q->min_team;
+                b->max_team = std::max(b->max_team, q->max_team);
+            }
+            *out = b;
+            return PIT_OK;
+        }
+    }
     const auto t_start = std::chrono::steady_clock::now();
     auto setup = [&]() -> pit_status {
         if (b->opt.newton_max < 1 || b->opt.newton_max > PIT_MAX_NEWTON || b->opt.lin_max_iter < 1 ||
@@ -589,6 +649,39 @@ extern "C" pit_status pit_batch_create(const pit_instance* inst, int count, cons
 
 extern "C" pit_status pit_batch_solve(pit_batch* b, pit_batch_info* info) {
     if (!b) return PIT_EINVAL;
+    if (!b->parts.empty()) {
+        // one batch per closure, one after another; times and counts add up
+        pit_batch_info pi{}, sum{};
+        bool all_graph = true;
+        pit_status worst = PIT_OK;
+        for (pit_batch* q : b->parts) {
+            const pit_status st = pit_batch_solve(q, &pi);
+            if (st != PIT_OK && st != PIT_ENOCONV) {
+                snprintf(b->err, sizeof(b->err), "%s", q->err);
+                return st;
+            }
+            if (st == PIT_ENOCONV) worst = PIT_ENOCONV;
+            sum.ms += pi.ms;
+            sum.converged += pi.converged;
+            all_graph = all_graph && pi.graph;
+        }
+        if (info) {
+            info->count = b->count;
+            info->ctas = b->ctas;
+            info->teams = b->count;
+            info->min_team = b->min_team;
+            info->max_team = b->max_team;
+            info->converged = sum.converged;
+            info->graph = all_graph ? 1 : 0;
+            info->ms = sum.ms;
+            info->est_makespan_ms = b->est_ms;
+            info->ms_tuning = b->ms_tuning;
+            info->wave_jobs = b->wave_jobs;
+        }
+        if (worst != PIT_OK)
+            return bfail(b, worst, "%d of %d problems did not reach tol_res", b->count - sum.converged, b->count);
+        return PIT_OK;
+    }
     double ms = 0.0;
     bool used_graph = false;
     // the caller's stream may hold the producers of the problems' data
@@ -652,6 +745,9 @@ extern "C" pit_status pit_batch_solve(pit_batch* b, pit_batch_info* info) {
 extern "C" pit_status pit_batch_result(const pit_batch* b, int i, double* res_inf, int* newton_iters,
                                        int* windows_converged, int* team_ctas) {
     if (!b || i < 0 || i >= b->count) return PIT_EINVAL;
+    if (!b->parts.empty())
+        return pit_batch_result(b->parts[b->where[i].first], b->where[i].second, res_inf, newton_iters,
+                                windows_converged, team_ctas);
     if (res_inf) *res_inf = b->h_res[i];
     if (newton_iters) *newton_iters = b->h_iters[i];
     if (windows_converged) *windows_converged = b->h_iters[b->count + i];
@@ -661,6 +757,7 @@ extern "C" pit_status pit_batch_result(const pit_batch* b, int i, double* res_in
 
 extern "C" pit_status pit_batch_placement(const pit_batch* b, int i, int* teams, int* team_ctas) {
     if (!b || i < 0 || i >= b->count) return PIT_EINVAL;
+    if (!b->parts.empty()) return pit_batch_placement(b->parts[b->where[i].first], b->where[i].second, teams, team_ctas);
     if (teams) *teams = b->teams_of.empty() ? 0 : b->teams_of[i];
     if (team_ctas) *team_ctas = b->team_of.empty() ? 0 : b->team_of[i];
     return PIT_OK;
@@ -670,6 +767,7 @@ extern "C" const char* pit_batch_last_error(const pit_batch* b) { return b ? b->
 
 extern "C" void pit_batch_destroy(pit_batch* b) {
     if (!b) return;
+    for (pit_batch* q : b->parts) pit_batch_destroy(q);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     cudaFree(b->d_inst);

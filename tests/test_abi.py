@@ -105,12 +105,12 @@ def test_ctypes_structs_match_the_header_layout(tmp_path):
 
 def test_build_compiles_every_batched_kernel_instance_once():
     """The build compiles the batched-kernel source once per level-solve precision and
-    closure set (15 non-empty sets), and every other source once."""
+    closure (the four closure bits), and every other source once."""
     units = B.units()
     names = [u[2] for u in units]
     assert len(names) == len(set(names))
     bk = [u for u in units if os.path.basename(u[0]) == B.BATCH_KERNELS]
-    sets = {(f, c) for f in (0, 1) for c in range(1, 16)}
-    assert {(int(u[1][0].split("=")[1]), int(u[1][1].split("=")[1])) for u in bk} == sets and len(bk) == 30
+    sets = {(f, c) for f in (0, 1) for c in (1, 2, 4, 8)}
+    assert {(int(u[1][0].split("=")[1]), int(u[1][1].split("=")[1])) for u in bk} == sets and len(bk) == 8
     others = sorted(u[0] for u in units if os.path.basename(u[0]) != B.BATCH_KERNELS)
     assert others == sorted(B.sources()) and all(not u[1] for u in units if u not in bk)

@@ -155,10 +155,11 @@ def _closure_problem(bit, seed):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_every_closure_set_has_its_kernel(prec):
+def test_every_closure_set_is_solved(prec):
     """Each of the 15 non-empty sets of closures (Burgers/heat x constant/variable
-    viscosity) is solved by the batched kernel compiled for that set, per precision:
-    one problem of every closure in the set, each equal to the oracle's solution."""
+    viscosity), per precision: one problem of every closure in the set, each equal to the
+    oracle's solution. A batch of several closures runs one launch per closure, each with
+    the kernel compiled for that closure alone."""
     for closures in range(1, 16):
         probs = [_closure_problem(c, 100 + 4 * closures + c) for c in range(4) if closures >> c & 1]
         opt = pit.pit_default_options()
