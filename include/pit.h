@@ -387,6 +387,12 @@ void pit_net_destroy(pit_net* net);
  * accumulation, BF16 output; res (may be NULL) [B][H][W][Cout]; act = ReLU when relu != 0.
  * Backward, for the loss L = sum(dY * conv3x3(X, W)): dX [B][H][W][Cin] BF16 (may be NULL),
  * dW [Cout][3][3][Cin] FP32 and db [Cout] FP32 (device pointers).
+ * Kernels (tcgen05 MMAs, FP32 accumulators in tensor memory): for Cin = 64 or 128 the
+ * forward and data gradient run the row-stationary kernel, whose operands come from TMA
+ * tensor loads of 128-byte-swizzled NHWC rows and 64-channel weight blocks (X and W must be
+ * 16-byte aligned); for Cin = 64 and Cout a multiple of 64 the weight gradient reads the
+ * TMA-staged NHWC rows as MN-major operands. Other shapes take the general TMA or cp.async
+ * kernels; all give the same results up to FP32 summation order.
  * Both allocate their temporaries per call and synchronise `stream`. */
 pit_status pit_conv3x3_forward(const void* X_dev, const void* W_dev, const float* bias_dev, const void* res_dev,
                                void* Y_dev, int B, int H, int W, int Cin, int Cout, int relu, void* stream);
