@@ -389,7 +389,7 @@ void pit_net_destroy(pit_net* net);
  * dW [Cout][3][3][Cin] FP32 and db [Cout] FP32 (device pointers).
  * Kernels (tcgen05 MMAs, FP32 accumulators in tensor memory): for Cin = 64 or 128 the
  * forward and data gradient run the row-stationary kernel, whose operands come from TMA
- * tensor loads of 128-byte-swizzled NHWC rows and 64-channel weight blocks (X and W must be
+ * tensor loads of 128-byte-swizzled NHWC rows and 64-channel weight blocks (when X and W are
  * 16-byte aligned); for Cin = 64 and Cout a multiple of 64 the weight gradient reads the
  * TMA-staged NHWC rows as MN-major operands. Other shapes take the general TMA or cp.async
  * kernels; all give the same results up to FP32 summation order.
