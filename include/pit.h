@@ -233,15 +233,18 @@ pit_status pit_block_solve(pit_ctx* ctx, const double* U_dev, const double* R_de
 pit_status pit_newton_step(pit_ctx* ctx, double* U_dev, pit_step_info* info);
 
 /* Phase timers of the last wavefront launch of pit_solve, for performance analysis:
- * for every team t of the launch (Newton iterations t, t + K, ...), 20 values from its
- * first CTA, out[20 t + j]: 0 halo waits (flag protocol), 1 team-reduction waits,
+ * for every team t of the launch (Newton iterations t, t + K, ...), 25 values from its
+ * first CTA, out[25 t + j]: 0 halo waits (flag protocol), 1 team-reduction waits,
  * 2 waits for the previous Newton iteration, 3 total, 4 level setup, 5 level solves,
  * 6 updates, 7 setup: loading u^n_k, 8 setup: team reduction and boundary-row exchange
  * (nanoseconds), 9 cells solved, 10 sweeps or iterations (counts), 11 unused, 12..19 SM
  * cycles of its thread 0 in the steps of the SOR sweeps with deep rows: publishing the
  * boundary rows, interior rows of colour 0, fetching the neighbours' rows, boundary rows
- * and halo points, a barrier, colour 1, the lagged reduction and stop decision, a barrier.
- * Copies up to n values and returns how many there are (20 K), or -1 for a NULL argument. */
+ * and halo points, a barrier, colour 1, the lagged reduction and stop decision, a barrier;
+ * 20..24 SM cycles of its thread 0 in the steps of the level setup: the node loop
+ * (residual, couplings, rhs), the block reduction, publishing the level system's boundary
+ * rows, the team reduction, fetching the neighbours' boundary rows.
+ * Copies up to n values and returns how many there are (25 K), or -1 for a NULL argument. */
 int pit_wave_timers(const pit_ctx* ctx, unsigned long long* out, int n);
 
 /* The bounds-checking build. Compiled with PIT_CHECK_BOUNDS, every indexed access of the

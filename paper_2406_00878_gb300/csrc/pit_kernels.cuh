@@ -1664,8 +1664,11 @@ struct WaveArgs {
 // 9 cells solved (count), 10 sweeps or iterations (count), 11 unused, 12..19 cycles of
 // CTA 0's thread 0 in the steps of the deep SOR sweeps (see level_sor_deep): publish,
 // interior colour 0, fetch, boundary rows and halo points, barrier, colour 1, reduction and
-// decision, barrier.
-constexpr int kWaveTimers = 20;
+// decision, barrier; 20..24 cycles of CTA 0's thread 0 in the steps of the level setup: the
+// node loop (residual, couplings, rhs), the block reduction, publishing the boundary rows of
+// the level system, the team reduction (arrive, wait, broadcast), fetching the neighbours'
+// boundary rows.
+constexpr int kWaveTimers = 25;
 
 // u^n_k with its halo rows ((cap + 2 nx) doubles) shares the BiCGStab scratch r..t
 // when it fits there; otherwise it follows uprev.
@@ -1744,8 +1747,12 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
     }
 
     unsigned long long* const ubar = bb.bar;
-    if (threadIdx.x == 0)
+    // thread 0's cycle counters: the deep sweeps' steps in m.red[56..63], the setup's in m.red[50..54]
+    unsigned long long* const scyc = reinterpret_cast<unsigned long long*>(m.red + 50);
+    if (threadIdx.x == 0) {
         for (int q = 0; q < 8; ++q) reinterpret_cast<unsigned long long*>(m.red + 56)[q] = 0ull;
+        for (int q = 0; q < 5; ++q) scyc[q] = 0ull;
+    }
     __syncthreads();
     for (int k = a.k_begin + team; k < a.k_end; k += a.K) {
         for (int i = threadIdx.x; i < nloc; i += NT) {
@@ -1987,6 +1994,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 // node i = (local row jl, column ii), stepped by NT without a division per node
                 int jl = (int)threadIdx.x / nx, ii = (int)threadIdx.x - jl * nx;
                 const int djl = NT / nx, dii = NT - djl * nx;
+                const long long s0 = clock64();
 #pragma unroll 2
                 for (int i = threadIdx.x; i < nloc; i += NT) {
                     const NodeIn v = load_node(i, jl, ii);
@@ -2002,16 +2010,19 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 // the bias 2^-20 keeps the bound above the exact sum of the stored couplings
                 // (a NaN in u shows in max |r|, which ends the window before any solve)
                 if constexpr (sizeof(T) == 4) krs = abs_key((double)gmax_f * (1.0 + 0x1p-20));
+                if (threadIdx.x == 0) scyc[0] += clock64() - s0;
             }
             // 4. team reduction: max |r|, Gershgorin bound, 2 stop + nonsymmetric-row flag, max |rhs|
             //    (every CTA of the team takes the same decisions from these)
             const int flags_local = (stop_local ? 2 : 0) + (ns ? 1 : 0);
             double v3[4];
+            const long long s1 = clock64();
             {
                 unsigned long long kk[4] = {krmax, krs, abs_key((double)flags_local), kbmax};
                 block_max4_to0<NT>(kk, reinterpret_cast<unsigned long long*>(m.red));
                 for (int q = 0; q < 4; ++q) v3[q] = key_val(kk[q]);  // meaningful on thread 0 only
             }
+            const long long s2 = clock64();
             // deep rows: the neighbours' boundary rows of the level system travel while the
             // team reduction does (publish now, fetch after it)
             unsigned long long cseq = 0;
@@ -2022,6 +2033,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 const sptr<const T> hi[5] = {m.cw + last, m.ce + last, m.cs + last, m.cn + last, m.bs + last};
                 cseq = publish_rows_tagged<NT, T, 5>(t, deep->tpub, lo, hi);
             }
+            const long long s3 = clock64();
             double g3[4];
             if (deep) {
                 const unsigned long long use = t.tag_seq++;
@@ -2044,6 +2056,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
             } else if (!reduce_finish<4, true>(c, t, reduce_arrive<4>(t, v3), g3, m.red + 32, &s_ok)) {
                 return;
             }
+            const long long s4 = clock64();
             if (g3[2] >= 2.0) goto done;  // another iteration has converged (or the launch aborts)
             if (!(g3[0] < kDiverged) || g3[0] > kGrowth * fmax(first_res, a.tol_res)) {
                 // NaN/Inf or a runaway residual: Newton diverges on this range of levels. One
@@ -2069,6 +2082,12 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
                 const sptr<T> fS[5] = {deep->cS[0], deep->cS[1], deep->cS[2], deep->cS[3], deep->cS[4]};
                 const sptr<T> fN[5] = {deep->cN[0], deep->cN[1], deep->cN[2], deep->cN[3], deep->cN[4]};
                 if (!fetch_rows_tagged<NT, T, 5>(c, t, deep->tpub, cseq, fS, fN)) return;
+            }
+            if (threadIdx.x == 0) {
+                scyc[1] += s2 - s1;
+                scyc[2] += s3 - s2;
+                scyc[3] += s4 - s3;
+                scyc[4] += clock64() - s4;
             }
             if (threadIdx.x == 0) t_sred += global_ns() - t_sr0;
             {
@@ -2167,6 +2186,8 @@ done:
         tm[10] = n_sweeps;
         const unsigned long long* cyc = reinterpret_cast<const unsigned long long*>(m.red + 56);
         for (int q = 0; q < 8; ++q) tm[12 + q] = cyc[q];
+        const unsigned long long* sc5 = reinterpret_cast<const unsigned long long*>(m.red + 50);
+        for (int q = 0; q < 5; ++q) tm[20 + q] = sc5[q];
     }
     __syncthreads();
 }

@@ -434,7 +434,8 @@ def pit_block_solve_noalloc(nx: int, ny: int, M: int, coef, R, dU, eta: float = 
 WAVE_TIMER_NAMES = ("halo_wait_ns", "reduce_wait_ns", "pred_wait_ns", "total_ns", "setup_ns", "solve_ns",
                     "update_ns", "setup_load_ns", "setup_reduce_ns", "cells", "sweeps", "unused",
                     "sor_publish_cyc", "sor_interior_cyc", "sor_fetch_cyc", "sor_boundary_cyc", "sor_barrier5_cyc",
-                    "sor_colour1_cyc", "sor_decide_cyc", "sor_barrier7_cyc")
+                    "sor_colour1_cyc", "sor_decide_cyc", "sor_barrier7_cyc", "setup_nodes_cyc", "setup_blockmax_cyc",
+                    "setup_publish_cyc", "setup_teamreduce_cyc", "setup_fetch_cyc")
 
 
 def pit_wave_timers(ctx: "Context") -> list:

@@ -409,3 +409,23 @@ def test_fma_probe_measures_a_plausible_rate():
     f32 = pit.pit_probe_fma_peak(1)
     assert 0.3 < f64 < 3.0, f64
     assert 10.0 < f32 < 200.0 and f32 > 20 * f64, (f32, f64)
+
+
+def test_wave_timers_report_every_team():
+    # pit_wave_timers: 25 values per team of the last wavefront launch; the solved cells,
+    # their sweeps and the cycle counters of the deep sweeps and of the level setup are
+    # filled on the headline configuration (deep rows need teams of several CTAs)
+    p = W.truncated(W.burgers256(0), 16)
+    with pit.context_for(p) as ctx:
+        U = torch.empty(p.dof, dtype=torch.float64, device="cuda")
+        pit.pit_fill_plain_guess(ctx, U)
+        status, info = pit.pit_solve(ctx, U)
+        teams = pit.pit_wave_timers(ctx)
+    assert len(teams) == info["wave_teams"] >= 1 and len(pit.WAVE_TIMER_NAMES) == 25
+    assert all(t["total_ns"] > 0 for t in teams)
+    # a team whose iterations find every level converged skips all its cells
+    solved = [t for t in teams if t["cells"] > 0]
+    assert solved
+    for t in solved:
+        assert t["sweeps"] >= t["cells"]
+        assert t["setup_nodes_cyc"] > 0 and t["setup_teamreduce_cyc"] > 0 and t["sor_colour1_cyc"] > 0
