@@ -287,7 +287,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda);
-// null when the driver does not offer it.
+// null when the CUDA driver does not offer it.
 static EncodeTiledFn encode_tiled() {
     static EncodeTiledFn fn = nullptr;
     static bool tried = false;
