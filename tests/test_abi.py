@@ -32,6 +32,21 @@ def test_library_builds_and_exports_every_declared_symbol():
         assert hasattr(lib, name), name
 
 
+def test_bounds_checking_build_builds_and_exports_every_declared_symbol():
+    # the check build (-DPIT_CHECK_BOUNDS) compiles the same sources; its status query
+    # answers NULL arguments before any CUDA call, so it can be called without a GPU
+    path = B.build_check()
+    assert path.endswith("libpit_check.so") and path != B.LIB
+    lib = ctypes.CDLL(path)
+    for name in _declared():
+        assert hasattr(lib, name), name
+    lib.pit_bounds_status.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.pit_bounds_status.restype = ctypes.c_int
+    assert lib.pit_bounds_status(None, None) == pit.PIT_EINVAL
+    lib.pit_status_string.restype = ctypes.c_char_p
+    assert lib.pit_status_string(pit.PIT_EBOUNDS) == b"PIT_EBOUNDS"
+
+
 def test_default_options_and_status_strings():
     o = pit.pit_default_options()
     assert o.newton_max == 30 and o.tol_res == 1e-12 and o.lin_solver == pit.PIT_LIN_AUTO
