@@ -94,12 +94,15 @@ typedef struct {
     int lin_max_iter;       /* cap on sweeps / iterations per level solve (default 4000) */
     double sor_rho_max;     /* AUTO uses SOR below this Gershgorin bound (default 0.999; below 1 SOR
                                converges: symmetric levels are SPD, nonsymmetric ones get omega <= ~1) */
-    int team_ctas;          /* CTAs that share one level in the chain kernel (0 = auto) */
+    int team_ctas;          /* CTAs that share one level in the chain kernel; > 0 also caps the
+                               wavefront kernel's teams at this size, all equal (0 = auto) */
     long long wait_budget;  /* spin iterations before a device wait gives up (default 1<<26) */
     int wave_teams;         /* pit_solve: Newton iterations in flight in the wavefront kernel
                                (0 = auto: the most teams, up to 6, whose level strips fit in
                                shared memory; >= 1 that many; -1 = one launch per stage and
-                               Newton iteration, as pit_newton_step) */
+                               Newton iteration, as pit_newton_step). The SMs that K equal teams
+                               leave over go to the teams nearest the middle (a row less per
+                               strip), unless team_ctas > 0 fixes every team's size */
     int precision;          /* pit_solve level solves: PIT_FP64 (default) or PIT_FP32_INNER: the
                                Jacobian entries, right-hand sides and level-solve iterates are
                                held and updated in FP32, inside FP64 Newton (residual, update
@@ -151,7 +154,7 @@ typedef struct {
     pit_step_info steps[PIT_MAX_NEWTON];
     double ms_total;                       /* device time of the whole solve */
     int wave_teams;                        /* Newton iterations in flight (0: per-stage launches) */
-    int wave_team_ctas;                    /* CTAs per team */
+    int wave_team_ctas;                    /* CTAs per team (the smallest team's) */
     int wave_launches;                     /* wavefront launches (more than 1 after a restart) */
     float ms_wave;                         /* device time of the wavefront launches */
     float us_pred_wait;                    /* first CTA of team 0: waiting for the previous iteration */
@@ -162,6 +165,8 @@ typedef struct {
     float us_level_solve;                  /* first CTA of team 0: level solves (includes halo/reduction waits) */
     float us_update;                       /* first CTA of team 0: iterate updates and progress publication */
     int windows_converged;                 /* windows whose Newton reached tol_res (windows minus restarts) */
+    int wave_ctas;                         /* CTAs of the wavefront launch: SMs that K teams of
+                                              wave_team_ctas leave over go to the middle teams */
 } pit_solve_info;
 
 /* Fill *opt with the defaults listed above. */

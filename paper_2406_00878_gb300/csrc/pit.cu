@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -62,18 +63,20 @@ struct pit_ctx {
 
     // Newton wavefront (pit_solve): K teams of Gw CTAs
     int K = 0, Gw = 0, w_rows_base = 0, w_rows_rem = 0, kcap = 0;
+    int Gs = 0, w_ctas = 0;                 // CTAs of the largest team (workspace stride), of the launch
+    int* w_geom = nullptr;                  // [K][4] teams of different sizes (see WaveArgs::tgeom), or null
     size_t wave_smem = 0;
     double* w_pub = nullptr;
     unsigned long long* w_tpub = nullptr;   // tagged publication words: one-exchange SOR sweeps (rows_base >= 3)
     unsigned long long* w_tred = nullptr;   // tagged reduction words (with w_tpub)
     size_t w_tpub_n = 0, w_tred_n = 0;
     double* w_red = nullptr;
-    unsigned long long* w_sync = nullptr;  // flags[K*Gw], red_cnt[K*4], prog[K*Gw]
+    unsigned long long* w_sync = nullptr;  // flags[K*Gs], prog[K*Gs], red_cnt[K*4]
     int* w_ints = nullptr;                  // abort, status, stop[2]
     double* w_res = nullptr;                // [kcap]
     double* w_prefix = nullptr;             // [kcap][M]
     int* w_cell = nullptr;                  // [kcap][M]
-    double* w_sumsq = nullptr;              // [kcap][Gw]
+    double* w_sumsq = nullptr;              // [kcap][Gs]
     unsigned long long* w_timers = nullptr; // [K][kWaveTimers]
     std::vector<double> h_wres, h_wsumsq;
     std::vector<int> h_wcell;
@@ -483,33 +486,66 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
                     break;
                 }
             }
+            // SMs left over by K teams of Gw CTAs go to the middle teams, a row less per strip each
+            // where they suffice: under the forcing terms the middle Newton iterations take the
+            // most sweeps per level (burgers256, FP64: 5.6, 6.0, 7.5, 8.2, 5.7, 1.3), and the
+            // slowest iteration's level chain paces the ones after it. A fixed team size
+            // (o.team_ctas) keeps every team at Gw.
+            std::vector<int> geom;
+            if (ctx->K > 0) {
+                const int K = ctx->K, Gw = ctx->Gw;
+                const int rows = (ny + Gw - 1) / Gw;
+                const int G2 = rows > 2 ? (ny + rows - 2) / (rows - 1) : Gw;  // strips of rows - 1 rows
+                const int n_up = G2 > Gw && K >= 2 && o.team_ctas <= 0 ? std::min(K, (ctx->num_sms - K * Gw) / (G2 - Gw)) : 0;
+                std::vector<int> G(K, Gw);
+                if (n_up > 0) {
+                    std::vector<int> order(K);
+                    for (int t = 0; t < K; ++t) order[t] = t;
+                    // nearest the middle first (|2t - K| ascending, lower t on ties)
+                    std::stable_sort(order.begin(), order.end(),
+                                     [K](int x, int y) { return std::abs(2 * x - K) < std::abs(2 * y - K); });
+                    for (int i = 0; i < n_up; ++i) G[order[i]] = G2;
+                    int first = 0;
+                    for (int t = 0; t < K; ++t) {
+                        geom.insert(geom.end(), {first, G[t], ny / G[t], ny % G[t]});
+                        first += G[t];
+                    }
+                }
+                ctx->Gs = n_up > 0 ? G2 : Gw;
+                ctx->w_ctas = 0;
+                for (int t = 0; t < K; ++t) ctx->w_ctas += G[t];
+            }
             if (ctx->K > 0) {
                 CK(cudaFuncSetAttribute(wf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max));
                 int per = 0;
                 CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, wf, kNT, ctx->wave_smem));
-                if ((long long)per * ctx->num_sms < (long long)ctx->K * ctx->Gw) ctx->K = 0;  // fall back
+                if ((long long)per * ctx->num_sms < (long long)ctx->w_ctas) ctx->K = 0;  // fall back
             }
             if (ctx->K > 0) {
-                const int K = ctx->K, Gw = ctx->Gw;
+                const int K = ctx->K, Gw = ctx->Gw, Gs = ctx->Gs;
                 ctx->kcap = std::max(1, o.newton_max);
-                CK(dalloc(&ctx->w_pub, (size_t)K * 2 * Gw * 2 * nx));
+                if (!geom.empty()) {
+                    CK(cudaMalloc(&ctx->w_geom, sizeof(int) * geom.size()));
+                    CK(cudaMemcpy(ctx->w_geom, geom.data(), sizeof(int) * geom.size(), cudaMemcpyHostToDevice));
+                }
+                CK(dalloc(&ctx->w_pub, (size_t)K * 2 * Gs * 2 * nx));
                 if (ctx->w_rows_base >= 3 && Gw >= 2) {
-                    ctx->w_tpub_n = (size_t)K * 2 * Gw * kDeepSlotRows * nx * 2;
-                    ctx->w_tred_n = (size_t)K * 4 * Gw * kTagRedWords;
+                    ctx->w_tpub_n = (size_t)K * 2 * Gs * kDeepSlotRows * nx * 2;
+                    ctx->w_tred_n = (size_t)K * 4 * Gs * kTagRedWords;
                     CK(dalloc(&ctx->w_tpub, ctx->w_tpub_n));
                     CK(dalloc(&ctx->w_tred, ctx->w_tred_n));
                 }
-                CK(dalloc(&ctx->w_red, (size_t)K * 4 * Gw * 4));
-                CK(dalloc(&ctx->w_sync, (size_t)K * Gw * 2 + (size_t)K * 4));
+                CK(dalloc(&ctx->w_red, (size_t)K * 4 * Gs * 4));
+                CK(dalloc(&ctx->w_sync, (size_t)K * Gs * 2 + (size_t)K * 4));
                 CK(dalloc(&ctx->w_ints, 4));
                 CK(dalloc(&ctx->w_res, (size_t)ctx->kcap));
                 CK(dalloc(&ctx->w_prefix, (size_t)ctx->kcap * M));
                 CK(dalloc(&ctx->w_cell, (size_t)ctx->kcap * M));
-                CK(dalloc(&ctx->w_sumsq, (size_t)ctx->kcap * Gw));
+                CK(dalloc(&ctx->w_sumsq, (size_t)ctx->kcap * Gs));
                 CK(dalloc(&ctx->w_timers, (size_t)K * kWaveTimers));
                 ctx->h_wres.assign(ctx->kcap, 0.0);
                 ctx->h_wcell.assign((size_t)ctx->kcap * M, 0);
-                ctx->h_wsumsq.assign((size_t)ctx->kcap * Gw, 0.0);
+                ctx->h_wsumsq.assign((size_t)ctx->kcap * Gs, 0.0);
                 ctx->h_wtimers.assign((size_t)K * kWaveTimers, 0);
             }
         }
@@ -558,6 +594,7 @@ extern "C" void pit_destroy(pit_ctx* ctx) {
     cudaFree(ctx->cta_sumsq);
     cudaFree(ctx->timers);
     cudaFree(ctx->w_pub);
+    cudaFree(ctx->w_geom);
     cudaFree(ctx->w_tpub);
     cudaFree(ctx->w_tred);
     cudaFree(ctx->w_red);
@@ -683,14 +720,16 @@ extern "C" pit_status pit_newton_step(pit_ctx* ctx, double* U_dev, pit_step_info
 // raised the stop flag.
 static pit_status run_wave(pit_ctx* ctx, int s, int Mw, double* Uall, int k_begin, int k_end, pit_solve_info* inf,
                            int* k_done, bool* stopped) {
-    const int K = ctx->K, Gw = ctx->Gw, M = Mw;
+    const int K = ctx->K, Gs = ctx->Gs, M = Mw;
     double* U = Uall + (size_t)s * ctx->Ns;
-    const size_t nsync = (size_t)K * Gw * 2 + (size_t)K * 4;
+    const size_t nsync = (size_t)K * Gs * 2 + (size_t)K * 4;
     CK(cudaMemsetAsync(ctx->w_sync, 0, sizeof(unsigned long long) * nsync, ctx->stream));
     CK(cudaMemsetAsync(ctx->w_ints, 0, sizeof(int) * 3, ctx->stream));
     CK(cudaMemsetAsync(ctx->w_ints + 3, 0x7f, sizeof(int), ctx->stream));  // stop[1] = first converged k: large
     CK(cudaMemsetAsync(ctx->w_cell, 0, sizeof(int) * (size_t)ctx->kcap * M, ctx->stream));
     CK(cudaMemsetAsync(ctx->w_timers, 0, sizeof(unsigned long long) * K * kWaveTimers, ctx->stream));
+    // slots of CTAs a smaller team does not have stay zero
+    CK(cudaMemsetAsync(ctx->w_sumsq, 0, sizeof(double) * (size_t)ctx->kcap * Gs, ctx->stream));
     if (ctx->w_tpub) {  // tag 0 is never published: stale words of an earlier launch cannot match
         CK(cudaMemsetAsync(ctx->w_tpub, 0, sizeof(unsigned long long) * ctx->w_tpub_n, ctx->stream));
         CK(cudaMemsetAsync(ctx->w_tred, 0, sizeof(unsigned long long) * ctx->w_tred_n, ctx->stream));
@@ -703,9 +742,10 @@ static pit_status run_wave(pit_ctx* ctx, int s, int Mw, double* Uall, int k_begi
     a.q = ctx->has_q ? ctx->q + (size_t)s * ctx->Ns : nullptr;
     a.U = U;
     a.K = K;
-    a.G = Gw;
-    a.rows_base = ctx->w_rows_base;
+    a.G = Gs;
+    a.rows_base = ctx->w_rows_base;  // the largest strip (smallest team)
     a.rows_rem = ctx->w_rows_rem;
+    a.tgeom = ctx->w_geom;
     a.k_begin = k_begin;
     a.k_end = k_end;
     // bulk copies of the level strips need 16-byte aligned rows: nx even, U aligned
@@ -723,8 +763,8 @@ static pit_status run_wave(pit_ctx* ctx, int s, int Mw, double* Uall, int k_begi
     a.tred = ctx->w_tred;
     a.red_part = ctx->w_red;
     a.flags = ctx->w_sync;
-    a.prog = ctx->w_sync + (size_t)K * Gw;
-    a.red_cnt = ctx->w_sync + (size_t)K * Gw * 2;
+    a.prog = ctx->w_sync + (size_t)K * Gs;
+    a.red_cnt = ctx->w_sync + (size_t)K * Gs * 2;
     a.abort_flag = ctx->w_ints;
     a.status = ctx->w_ints + 1;
     a.stop = ctx->w_ints + 2;
@@ -737,7 +777,7 @@ static pit_status run_wave(pit_ctx* ctx, int s, int Mw, double* Uall, int k_begi
     void* args[] = {&a};
     const void* kf = wave_fn(ctx->conv, ctx->nlv, ctx->opt.precision == PIT_FP32_INNER);
     CK(cudaEventRecord(ctx->ev[2], ctx->stream));
-    CK(cudaLaunchCooperativeKernel(kf, dim3(K * Gw), dim3(kNT), args, ctx->wave_smem, ctx->stream));
+    CK(cudaLaunchCooperativeKernel(kf, dim3(ctx->w_ctas), dim3(kNT), args, ctx->wave_smem, ctx->stream));
     CK(cudaEventRecord(ctx->ev[3], ctx->stream));
     int hi[4];
     CK(cudaMemcpyAsync(hi, ctx->w_ints, sizeof(hi), cudaMemcpyDeviceToHost, ctx->stream));
@@ -745,7 +785,7 @@ static pit_status run_wave(pit_ctx* ctx, int s, int Mw, double* Uall, int k_begi
                        ctx->stream));
     CK(cudaMemcpyAsync(ctx->h_wcell.data(), ctx->w_cell, sizeof(int) * (size_t)ctx->kcap * M, cudaMemcpyDeviceToHost,
                        ctx->stream));
-    CK(cudaMemcpyAsync(ctx->h_wsumsq.data(), ctx->w_sumsq, sizeof(double) * (size_t)ctx->kcap * Gw,
+    CK(cudaMemcpyAsync(ctx->h_wsumsq.data(), ctx->w_sumsq, sizeof(double) * (size_t)ctx->kcap * Gs,
                        cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(ctx->h_wtimers.data(), ctx->w_timers, sizeof(unsigned long long) * K * kWaveTimers,
                        cudaMemcpyDeviceToHost, ctx->stream));
@@ -782,7 +822,7 @@ static pit_status run_wave(pit_ctx* ctx, int s, int Mw, double* Uall, int k_begi
             nsor += c > 0;
         }
         double ss = 0.0;
-        for (int b = 0; b < Gw; ++b) ss += ctx->h_wsumsq[(size_t)k * Gw + b];
+        for (int b = 0; b < Gs; ++b) ss += ctx->h_wsumsq[(size_t)k * Gs + b];
         st.upd_rms = std::sqrt(ss / (double)((size_t)Mw * ctx->Ns));
         st.lin_iters_mean = (double)tot / M;
         st.lin_iters_max = mx;
@@ -835,6 +875,7 @@ static pit_status fill_window_guess(pit_ctx* ctx, double* U_dev, int s, int Mw) 
 static pit_status solve_wave(pit_ctx* ctx, double* U_dev, pit_solve_info* inf) {
     inf->wave_teams = ctx->K;
     inf->wave_team_ctas = ctx->Gw;
+    inf->wave_ctas = ctx->K > 0 ? ctx->w_ctas : 0;
     const int M = ctx->M;
     const int Wn = ctx->opt.window > 0 ? std::min(ctx->opt.window, M) : M;
     int w = Wn;

@@ -402,6 +402,7 @@ struct TeamCtl {
 //   red_cnt  [4]           arrival counters of the slots
 struct Team {
     int b, G, nx;
+    int rows_base;                // the team's strips: rows_base rows, one more for the first ones
     int r0, nrows, nloc;
     long long Ns;
     double* pub;
@@ -421,6 +422,7 @@ __device__ __forceinline__ void team_init(Team& t, int b, int G, int nx, int ny,
     t.b = b;
     t.G = G;
     t.nx = nx;
+    t.rows_base = rows_base;
     t.nrows = rows_base + (b < rows_rem ? 1 : 0);
     t.r0 = b * rows_base + (b < rows_rem ? b : rows_rem);
     t.nloc = t.nrows * nx;
@@ -1628,7 +1630,11 @@ struct WaveArgs {
     const double* bc;
     const double* q;
     double* U;
-    int K, G, rows_base, rows_rem;
+    int K, G, rows_base, rows_rem;      // G: CTAs per team and stride of the team workspaces;
+                                        // rows_base/rows_rem: the strips of a G-CTA team
+    const int* tgeom;                   // [K][4] per team (first block, CTAs <= G, rows_base, rows_rem),
+                                        // or null: every team has G CTAs. Either way the largest
+                                        // strip has rows_base + (rows_rem > 0) rows.
     int k_begin, k_end;                 // iterations k_begin <= k < k_end may run
     int bulk_u;                         // u^n_k strips by bulk copy (nx even, U 16-byte aligned)
     unsigned long long cell_base;       // added to every progress value (monotonic across calls)
@@ -1718,6 +1724,16 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
     const auto itersg = chk(a.cell_iters, (long long)a.k_end * M, kChkCellIters);
     const int pred_team = (team + a.K - 1) % a.K;
     const auto pred_prog = chk(a.prog, (long long)a.K * a.G, kChkProg) + (long long)pred_team * a.G;
+    // the predecessor team's CTAs that own rows r0-1 .. r0+nrows (its strips may differ from ours)
+    int p_lo = b - 1, p_hi = b + 1;
+    if (a.tgeom) {
+        const int prb = a.tgeom[4 * pred_team + 2], prr = a.tgeom[4 * pred_team + 3];
+        const int big = prr * (prb + 1);  // rows of its longer strips, which come first
+        const int rlo = max(t.r0 - 1, 0), rhi = min(t.r0 + t.nrows, ny - 1);
+        p_lo = rlo < big ? rlo / (prb + 1) : prr + (rlo - big) / prb;
+        p_hi = rhi < big ? rhi / (prb + 1) : prr + (rhi - big) / prb;
+    }
+    const int p_cnt = a.tgeom ? a.tgeom[4 * pred_team + 1] : a.G;
     const auto my_prog = chk(a.prog, (long long)a.K * a.G, kChkProg) + (long long)team * a.G;
     double* slot = m.red + 48;
     // Burgers-type closures with constant viscosity have a constant diagonal 1 + 2 mu_a (vx + vy)
@@ -1733,7 +1749,7 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
     // The conditions are the same on every CTA of the team (cap and rows_base are team-wide).
     Deep<T> deep_rows;
     const Deep<T>* deep = nullptr;
-    if (a.tpub && a.tred && a.G >= 2 && a.rows_base >= 2 && 12 * (size_t)nx <= 5 * (size_t)cap) {
+    if (a.tpub && a.tred && t.G >= 2 && t.rows_base >= 2 && 12 * (size_t)nx <= 5 * (size_t)cap) {
         T* const d0 = static_cast<T*>(m.r);
         for (int h = 0; h < 5; ++h) {
             deep_rows.cS[h] = chk(d0 + (size_t)h * nx, nx, kChkDeep);
@@ -1767,17 +1783,18 @@ __device__ void wave_body(const WaveArgs& a, int team, int b, Team& t, unsigned 
         __syncthreads();
         for (int n = 0; n < M; ++n) {
             // 1. wait until iteration k - 1 has finished level n on rows r0-1 .. r0+nrows and
-            //    on CTA 0 (which publishes its running residual max): lanes 0..3 of warp 0 poll
-            //    the progress words of CTAs b-1, b, b+1 and 0 at once (acquire)
-            const int pl = b == 0 ? 1 : (b == 1 ? 0 : 3);  // the lane that polls CTA 0
+            //    on CTA 0 (which publishes its running residual max): lanes of warp 0 poll the
+            //    progress words of the predecessor's CTAs p_lo..p_hi (b-1, b, b+1 when the
+            //    teams' strips match) and lane 31 its CTA 0, at once (acquire)
+            const int pl = p_lo <= 0 ? -p_lo : 31;  // the lane that polls CTA 0
             if (threadIdx.x < 32) {
                 const int lane = threadIdx.x;
                 bool stop_seen = false;
                 if (k > a.k_begin) {
                     const unsigned long long target = a.cell_base + (unsigned long long)(k - 1) * M + n + 1;
                     const unsigned long long t0 = lane == 0 ? global_ns() : 0ull;
-                    int nbr = lane < 3 ? b - 1 + lane : (lane == 3 && b > 1 ? 0 : -1);
-                    if (nbr >= a.G) nbr = -1;
+                    int nbr = p_lo + lane <= p_hi ? p_lo + lane : (lane == 31 && p_lo > 0 ? 0 : -1);
+                    if (nbr >= p_cnt) nbr = -1;
                     if (nbr >= 0) {
                         long long spins = 0;
                         while (ld_acquire_u64(&pred_prog[nbr]) < target) {
@@ -2196,10 +2213,17 @@ template <int NT, bool CONV, bool NLV, typename T = double>
 __global__ void __launch_bounds__(NT) wave_kernel(WaveArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_ok;
-    const int team = blockIdx.x / a.G;
-    const int b = blockIdx.x - team * a.G;
+    int team = blockIdx.x / a.G, b = blockIdx.x - team * a.G, G = a.G, rb = a.rows_base, rr = a.rows_rem;
+    if (a.tgeom) {  // teams of their own sizes, in block order
+        team = 0;
+        while (team + 1 < a.K && (int)blockIdx.x >= a.tgeom[4 * (team + 1)]) ++team;
+        b = blockIdx.x - a.tgeom[4 * team];
+        G = a.tgeom[4 * team + 1];
+        rb = a.tgeom[4 * team + 2];
+        rr = a.tgeom[4 * team + 3];
+    }
     Team t;
-    team_init(t, b, a.G, a.c.nx, a.c.ny, a.rows_base, a.rows_rem, a.pub + (size_t)team * 2 * a.G * 2 * a.c.nx,
+    team_init(t, b, G, a.c.nx, a.c.ny, rb, rr, a.pub + (size_t)team * 2 * a.G * 2 * a.c.nx,
               a.flags + (size_t)team * a.G, a.red_part + (size_t)team * 4 * a.G * 4, a.red_cnt + (size_t)team * 4);
     __shared__ __align__(8) unsigned long long s_ubar;
     if (threadIdx.x == 0) mbar_init(&s_ubar, 1);

@@ -71,13 +71,14 @@ class pit_solve_info(ctypes.Structure):
                 ("wave_launches", ctypes.c_int), ("ms_wave", ctypes.c_float), ("us_pred_wait", ctypes.c_float),
                 ("us_halo_wait", ctypes.c_float), ("us_reduce_wait", ctypes.c_float), ("windows", ctypes.c_int),
                 ("newton_iters_total", ctypes.c_int), ("us_setup", ctypes.c_float), ("us_level_solve", ctypes.c_float),
-                ("us_update", ctypes.c_float), ("windows_converged", ctypes.c_int)]
+                ("us_update", ctypes.c_float), ("windows_converged", ctypes.c_int),
+                ("wave_ctas", ctypes.c_int)]
 
     def as_dict(self):
         k = self.newton_iters
         return {"newton_iters": k, "converged": bool(self.converged), "res_inf": list(self.res_inf[:k + 1]),
                 "steps": [self.steps[i].as_dict() for i in range(k)], "ms_total": self.ms_total,
-                "wave_teams": self.wave_teams, "wave_team_ctas": self.wave_team_ctas,
+                "wave_teams": self.wave_teams, "wave_team_ctas": self.wave_team_ctas, "wave_ctas": self.wave_ctas,
                 "wave_launches": self.wave_launches, "ms_wave": self.ms_wave, "us_pred_wait": self.us_pred_wait,
                 "us_halo_wait": self.us_halo_wait, "us_reduce_wait": self.us_reduce_wait, "windows": self.windows,
                 "newton_iters_total": self.newton_iters_total, "us_setup": self.us_setup,
