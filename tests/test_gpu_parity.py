@@ -272,6 +272,37 @@ def test_wavefront_iterates_equal_classic_newton_iterates():
     np.testing.assert_allclose(outs[1], outs[0], rtol=0, atol=1e-11 * np.abs(outs[0]).max())
 
 
+@pytest.mark.parametrize("prec", [pit.PIT_FP64, pit.PIT_FP32_INNER])
+def test_wavefront_teams_of_different_sizes_run_the_same_iterates(prec):
+    # The SMs that equal teams leave over go to the middle teams (shorter strips), and each
+    # CTA then waits on the predecessor team's CTAs that own its rows. 64 x 256 interior
+    # nodes: six teams of 24 CTAs (11-row strips) leave 8 of 152 SMs, which give four teams
+    # 26 CTAs (10-row strips). The iterates must be those of equal teams bit for bit (the
+    # red-black sweeps and the max-reductions do not depend on the strips), and the oracle's.
+    p = W.random_problem(5, 64, 256, 8, W.BURGERS, with_bc=True)
+    outs, infos = [], []
+    for fixed in (False, True):
+        opt = pit.pit_default_options()
+        opt.precision = prec
+        if fixed:
+            opt.team_ctas = infos[0]["wave_team_ctas"]
+        with pit.context_for(p, opt) as ctx:
+            U = torch.empty(p.dof, dtype=torch.float64, device="cuda")
+            pit.pit_fill_plain_guess(ctx, U)
+            status, info = pit.pit_solve(ctx, U)
+            outs.append(U.cpu().numpy())
+            infos.append(info)
+    auto, equal = infos
+    assert auto["converged"] and equal["converged"]
+    assert equal["wave_ctas"] == equal["wave_teams"] * equal["wave_team_ctas"]
+    if torch.cuda.get_device_properties(0).multi_processor_count == 152:
+        assert auto["wave_ctas"] > auto["wave_teams"] * auto["wave_team_ctas"]
+    assert auto["wave_ctas"] <= torch.cuda.get_device_properties(0).multi_processor_count
+    assert np.array_equal(outs[0], outs[1])
+    Uo, _, _, _ = oracle.solve(p, tol=1e-13)
+    assert np.abs(outs[0].reshape(p.M, -1) - Uo).max() <= 1e-10 * np.abs(Uo).max()
+
+
 def _window_residual(p, U, start, count):
     """Oracle residual of levels start..start+count-1 of U (level n depends only on U[n-1], U[n])."""
     u_prev = p.u0 if start == 0 else U[start - 1]
