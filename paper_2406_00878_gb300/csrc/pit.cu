@@ -61,7 +61,7 @@ struct pit_ctx {
     double* cta_sumsq = nullptr;               // [G]
     unsigned long long* timers = nullptr;      // [4] chain kernel, CTA 0
 
-    // Newton wavefront (pit_solve): K teams of Gw CTAs
+    // Newton wavefront (pit_solve): K teams of Gw CTAs, the middle ones larger where SMs are left over
     int K = 0, Gw = 0, w_rows_base = 0, w_rows_rem = 0, kcap = 0;
     int Gs = 0, w_ctas = 0;                 // CTAs of the largest team (workspace stride), of the launch
     int* w_geom = nullptr;                  // [K][4] teams of different sizes (see WaveArgs::tgeom), or null
