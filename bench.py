@@ -45,7 +45,7 @@ FLOPS_PER_BICGSTAB_ITER = 2 * 9 + 6 * 2 + 5 * 2
 # of the kernel sources whose SHA-256 digests are listed (null once they change).
 WAVE_TRAFFIC_BYTES = 579169024 + 293091072
 WAVE_TRAFFIC_SOURCES = {
-    "paper_2406_00878_gb300/csrc/pit_kernels.cuh": "d31928dcd2bc3c82ae47909c9296e1baf7c43759f9cf173efa00e59a78420bd9",
+    "paper_2406_00878_gb300/csrc/pit_kernels.cuh": "fd63019189123d130c4fe289b9eb5246bd131938853eac81834b01d5b218b414",
     "paper_2406_00878_gb300/csrc/pit.cu": "3907dee2bab4debf76d6c1e1d56edc21ffbc9bc9c8791798b2fd7f98438504ae",
 }
 

@@ -21,6 +21,7 @@
 #include <cstring>
 #include <map>
 #include <numeric>
+#include <cstdlib>
 #include <vector>
 
 #include "pit.h"
@@ -55,6 +56,7 @@ struct pit_batch {
     BatchJob* d_jobs = nullptr;
     int* d_job_off = nullptr;
     BatchTeamWs* d_ws = nullptr;
+    int* d_geom = nullptr;             // team sizes of the wavefront jobs whose teams differ (BatchTeamWs::tgeom)
     unsigned char* pool = nullptr;     // job workspaces
     size_t pool_bytes = 0, sync_bytes = 0;  // sync region (zeroed per launch) at the start of the pool
     double* d_res = nullptr;
@@ -172,8 +174,37 @@ static bool wave_shape(const pit_batch* b, const pit_instance& I, int* K_out, in
 struct Job {
     int inst, G, K;
     double start, dur;
-    std::vector<int> ctas;  // K * G CTAs: team tk, rank r -> ctas[tk * G + r]
+    std::vector<int> size, first;  // per team: CTAs (G, or more for the middle teams of a wavefront
+                                   // job where SMs are left over) and the first one's index
+    int width = 0, Gs = 0;         // CTAs of the job, the largest team's size
+    std::vector<int> ctas;         // team tk, rank r -> ctas[first[tk] + r]
 };
+
+// Team sizes of a job of K teams of G CTAs on P SMs: the SMs that the K teams leave over go to
+// the teams nearest the middle, a row less per strip each where they suffice (the middle
+// Newton iterations take the most sweeps per level, and the slowest one paces the rest; the
+// single-problem wavefront launch does the same). fixed > 0 keeps every team at G.
+static void team_sizes(Job& j, int ny, int P, int fixed) {
+    j.size.assign(j.K, j.G);
+    const int rows = (ny + j.G - 1) / j.G;
+    const int G2 = rows > 2 ? (ny + rows - 2) / (rows - 1) : j.G;  // strips of rows - 1 rows
+    if (j.K >= 2 && fixed <= 0 && G2 > j.G && G2 <= kMaxTeam && P > j.K * j.G) {
+        const int n_up = std::min(j.K, (P - j.K * j.G) / (G2 - j.G));
+        std::vector<int> order(j.K);
+        std::iota(order.begin(), order.end(), 0);
+        const int K = j.K;
+        std::stable_sort(order.begin(), order.end(), [K](int x, int y) { return std::abs(2 * x - K) < std::abs(2 * y - K); });
+        for (int i = 0; i < n_up; ++i) j.size[order[i]] = G2;
+    }
+    j.first.assign(j.K, 0);
+    j.width = 0;
+    j.Gs = 0;
+    for (int t = 0; t < j.K; ++t) {
+        j.first[t] = j.width;
+        j.width += j.size[t];
+        j.Gs = std::max(j.Gs, j.size[t]);
+    }
+}
 
 // Build jobs, workspace and device descriptors for problems `in` with K[i] teams of
 // G[i] CTAs each (K[i] > 1: a wavefront job, placed first on CTAs 0 .. K G - 1, one
@@ -208,7 +239,8 @@ static pit_status build_launch(pit_batch* b, const std::vector<pit_instance>& in
         j.inst = i;
         j.G = team[i];
         j.K = teams[i];
-        const int width = j.K * j.G;
+        team_sizes(j, in[i].grid.ny, P, b->opt.team_ctas);
+        const int width = j.width;
         if (j.K > 1) {
             j.ctas.resize(width);
             std::iota(j.ctas.begin(), j.ctas.end(), 0);
@@ -239,12 +271,23 @@ static pit_status build_launch(pit_batch* b, const std::vector<pit_instance>& in
     for (size_t q = 0; q < jobs.size(); ++q) {
         const Job& j = jobs[q];
         const pit_instance& I = in[j.inst];
-        wss[q] = ws_size(j.K, j.G, I.grid.nx, b->opt.newton_max, std::min(W, I.M));
+        wss[q] = ws_size(j.K, j.Gs, I.grid.nx, b->opt.newton_max, std::min(W, I.M));
         sync_total += wss[q].sync;
         data_total += wss[q].data;
         for (int tk = 0; tk < j.K; ++tk)
-            for (int r = 0; r < j.G; ++r)
-                per[j.ctas[(size_t)tk * j.G + r]].push_back(BatchJob{j.inst, r, j.G, (int)q, j.K, tk});
+            for (int r = 0; r < j.size[tk]; ++r)
+                per[j.ctas[(size_t)j.first[tk] + r]].push_back(
+                    BatchJob{j.inst, r, j.size[tk], (int)q, j.K, tk, j.first[tk], j.width, j.Gs});
+    }
+    // the geometry of the jobs whose teams differ in size (first CTA, CTAs, strips)
+    std::vector<int> geom;
+    std::vector<long long> geom_at(jobs.size(), -1);
+    for (size_t q = 0; q < jobs.size(); ++q) {
+        const Job& j = jobs[q];
+        if (j.K < 2 || j.width == j.K * j.G) continue;
+        const int ny = in[j.inst].grid.ny;
+        geom_at[q] = (long long)geom.size();
+        for (int t = 0; t < j.K; ++t) geom.insert(geom.end(), {j.first[t], j.size[t], ny / j.size[t], ny % j.size[t]});
     }
     // device buffers (freed and rebuilt for every build)
     cudaFree(b->pool);
@@ -252,18 +295,24 @@ static pit_status build_launch(pit_batch* b, const std::vector<pit_instance>& in
     cudaFree(b->d_job_off);
     cudaFree(b->d_ws);
     cudaFree(b->d_inst);
+    cudaFree(b->d_geom);
     b->pool = nullptr;
     b->d_jobs = nullptr;
     b->d_job_off = nullptr;
     b->d_ws = nullptr;
     b->d_inst = nullptr;
+    b->d_geom = nullptr;
+    if (!geom.empty()) {
+        BCK(cudaMalloc(&b->d_geom, sizeof(int) * geom.size()));
+        BCK(cudaMemcpy(b->d_geom, geom.data(), sizeof(int) * geom.size(), cudaMemcpyHostToDevice));
+    }
     b->pool_bytes = sync_total + data_total;
     b->sync_bytes = sync_total;
     BCK(cudaMalloc(&b->pool, b->pool_bytes));
     std::vector<BatchTeamWs> ws(jobs.size());
     size_t so = 0, dof = sync_total;
     for (size_t q = 0; q < jobs.size(); ++q) {
-        const int K = jobs[q].K, G = jobs[q].G, nx = in[jobs[q].inst].grid.nx;
+        const int K = jobs[q].K, G = jobs[q].Gs, nx = in[jobs[q].inst].grid.nx;  // G: the workspace stride
         unsigned long long* sw = reinterpret_cast<unsigned long long*>(b->pool + so);
         ws[q].jbar = sw;
         ws[q].jres = sw + 1;
@@ -284,6 +333,7 @@ static pit_status build_launch(pit_batch* b, const std::vector<pit_instance>& in
         ws[q].pub = dw;
         ws[q].red_part = dw + (size_t)K * 2 * G * 2 * nx;
         ws[q].cell_prefix = ws[q].red_part + (size_t)K * 4 * G * 4;
+        ws[q].tgeom = geom_at[q] >= 0 ? b->d_geom + geom_at[q] : nullptr;
         dof += wss[q].data;
     }
     std::vector<BatchJob> flat;
@@ -339,7 +389,8 @@ static pit_status build_launch(pit_batch* b, const std::vector<pit_instance>& in
     BCK(cudaMemcpy(b->d_job_off, off.data(), sizeof(int) * (used + 1), cudaMemcpyHostToDevice));
     BCK(cudaMemcpy(b->d_ws, ws.data(), sizeof(BatchTeamWs) * ws.size(), cudaMemcpyHostToDevice));
     b->min_team = *std::min_element(team.begin(), team.end());
-    b->max_team = *std::max_element(team.begin(), team.end());
+    b->max_team = 0;
+    for (const Job& j : jobs) b->max_team = std::max(b->max_team, j.Gs);
     return PIT_OK;
 }
 
@@ -774,6 +825,7 @@ extern "C" void pit_batch_destroy(pit_batch* b) {
     cudaFree(b->d_jobs);
     cudaFree(b->d_job_off);
     cudaFree(b->d_ws);
+    cudaFree(b->d_geom);
     cudaFree(b->pool);
     cudaFree(b->d_res);
     cudaFree(b->d_iters);

@@ -2256,9 +2256,12 @@ struct BatchInstance {
 // has all of its CTAs (no cyclic waits). The job's workspace is given by offsets
 // into the pools.
 struct BatchJob {
-    int inst, rank, G;
+    int inst, rank, G;                  // G: CTAs of this CTA's team
     int team;                           // index of the job's workspace
     int K, tk;
+    int first;                          // the team's first CTA among the job's CTAs
+    int jctas;                          // CTAs of the job (sum of its teams' sizes)
+    int Gs;                             // the largest team's size: stride of the team workspaces
 };
 
 struct BatchTeamWs {
@@ -2280,6 +2283,7 @@ struct BatchTeamWs {
     unsigned long long* tred;           // [K][4][G][kTagRedWords] tagged reduction words (zeroed per launch)
     unsigned long long* sync_words;     // flags, prog, red_cnt and the tagged words: zeroed again after a
     size_t sync_count;                  // window that ended on the job's abort word
+    const int* tgeom;                   // K > 1: [K][4] teams of different sizes (WaveArgs::tgeom), or null
 };
 
 struct BatchArgs {
@@ -2346,12 +2350,12 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
     const BatchTeamWs& ws = ba.ws[job.team];
     const OpConst& oc = in.c;
     const int nx = oc.nx, ny = oc.ny, M = oc.M;
-    const int G = job.G, b = job.rank, K = job.K, tk = job.tk;
+    const int G = job.G, b = job.rank, K = job.K, tk = job.tk, Gs = job.Gs;
     const int rows_base = ny / G, rows_rem = ny % G;
     TeamCtl c{ba.abort_flag, ba.status, ba.wait_budget, ba.max_iter};
     Team t;
-    team_init(t, b, G, nx, ny, rows_base, rows_rem, ws.pub + (size_t)tk * 2 * G * 2 * nx, ws.flags + (size_t)tk * G,
-              ws.red_part + (size_t)tk * 4 * G * 4, ws.red_cnt + (size_t)tk * 4);
+    team_init(t, b, G, nx, ny, rows_base, rows_rem, ws.pub + (size_t)tk * 2 * Gs * 2 * nx, ws.flags + (size_t)tk * Gs,
+              ws.red_part + (size_t)tk * 4 * Gs * 4, ws.red_cnt + (size_t)tk * 4);
     const long long Ns = t.Ns;
     const long long off0 = (long long)t.r0 * nx;
     const int nloc = t.nloc;
@@ -2364,7 +2368,7 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
     const auto bcg = chk(in.bc, (long long)M * nb, kChkBc);
     const auto qg = chk(in.q, (long long)M * Ns, kChkQ);
     const bool lead = tk == 0 && b == 0;          // reports the results
-    const unsigned long long job_ctas = (unsigned long long)K * G;
+    const unsigned long long job_ctas = (unsigned long long)job.jctas;
     unsigned long long jep = 0;                   // job-wide barriers passed (K > 1)
     unsigned long long base = 0;
     int iters_total = 0, conv_windows = 0;
@@ -2410,9 +2414,10 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
         a.q = in.q ? in.q + (long long)s * Ns : nullptr;
         a.U = in.U + (long long)s * Ns;
         a.K = K;
-        a.G = G;
-        a.rows_base = rows_base;
+        a.G = Gs;
+        a.rows_base = rows_base;  // this team's strips: the shared-memory layout above
         a.rows_rem = rows_rem;
+        a.tgeom = K > 1 ? ws.tgeom : nullptr;
         a.k_begin = 0;
         a.k_end = ba.newton_max;
         a.bulk_u = in.bulk_u;
@@ -2490,14 +2495,14 @@ __device__ void batch_instance(const BatchArgs& ba, const BatchJob& job, unsigne
                 // the teams left the window at different points: restart the job's
                 // synchronisation from a clean state (zeroed words, fresh counters)
                 const size_t per = (ws.sync_count + job_ctas - 1) / job_ctas;
-                const size_t r = (size_t)tk * G + b;
+                const size_t r = (size_t)job.first + b;
                 const size_t lo = r * per, hi = lo + per < ws.sync_count ? lo + per : ws.sync_count;
                 for (size_t i = lo + threadIdx.x; i < hi; i += NT) ws.sync_words[i] = 0ull;
             }
             if (!job_barrier(c, ws.jbar, job_ctas * ++jep, &s_ok)) return;
             if (reset)
-                team_init(t, b, G, nx, ny, rows_base, rows_rem, ws.pub + (size_t)tk * 2 * G * 2 * nx,
-                          ws.flags + (size_t)tk * G, ws.red_part + (size_t)tk * 4 * G * 4, ws.red_cnt + (size_t)tk * 4);
+                team_init(t, b, G, nx, ny, rows_base, rows_rem, ws.pub + (size_t)tk * 2 * Gs * 2 * nx,
+                          ws.flags + (size_t)tk * Gs, ws.red_part + (size_t)tk * 4 * Gs * 4, ws.red_cnt + (size_t)tk * 4);
         }
         base += (unsigned long long)ba.newton_max * Mw + 1;
         if (kdone < 0) clean_from = max(clean_from, s + Mw);  // the failed attempt overwrote these levels
