@@ -883,11 +883,13 @@ static pit_status solve_wave(pit_ctx* ctx, double* U_dev, pit_solve_info* inf) {
     // window with PIT_START_GIVEN, except on levels a failed attempt has overwritten
     const bool given = Wn == M || ctx->opt.window_start == PIT_START_GIVEN;
     int clean_from = 0;  // levels >= clean_from still hold the caller's iterate
+    bool whole = false;  // one window over all levels converged: its residual is the final one
     for (int s = 0; s < M;) {
         const int Mw = std::min(w, M - s);
         if (!(given && s >= clean_from)) CHECK_RET(fill_window_guess(ctx, U_dev, s, Mw));
         int iters = 0;
         const pit_status st = solve_window(ctx, U_dev, s, Mw, inf, &iters);
+        whole = st == PIT_OK && s == 0 && Mw == M;
         if (st != PIT_OK) clean_from = std::max(clean_from, s + Mw);
         inf->windows += 1;
         inf->newton_iters_total += iters;
@@ -902,7 +904,12 @@ static pit_status solve_wave(pit_ctx* ctx, double* U_dev, pit_solve_info* inf) {
             return st;
         }
     }
-    // the residual of the whole final iterate decides convergence
+    // the residual of the whole final iterate decides convergence (already computed, on the
+    // same iterate, when one window spanned every level)
+    if (whole) {
+        inf->converged = 1;
+        return PIT_OK;
+    }
     CHECK_RET(enqueue_residual(ctx, U_dev, ctx->R));
     double res = 0.0;
     CHECK_RET(read_res_inf(ctx, &res));
