@@ -495,7 +495,8 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
             if (ctx->K > 0) {
                 const int K = ctx->K, Gw = ctx->Gw;
                 const int rows = (ny + Gw - 1) / Gw;
-                const int G2 = rows > 2 ? (ny + rows - 2) / (rows - 1) : Gw;  // strips of rows - 1 rows
+                // strips of rows - 1 rows, still of at least kMinLocal unknowns
+                const int G2 = rows > 2 && rows - 1 >= rows_min ? (ny + rows - 2) / (rows - 1) : Gw;
                 const int n_up = G2 > Gw && K >= 2 && o.team_ctas <= 0 ? std::min(K, (ctx->num_sms - K * Gw) / (G2 - Gw)) : 0;
                 std::vector<int> G(K, Gw);
                 if (n_up > 0) {

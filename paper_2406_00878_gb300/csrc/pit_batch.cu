@@ -184,10 +184,12 @@ struct Job {
 // the teams nearest the middle, a row less per strip each where they suffice (the middle
 // Newton iterations take the most sweeps per level, and the slowest one paces the rest; the
 // single-problem wavefront launch does the same). fixed > 0 keeps every team at G.
-static void team_sizes(Job& j, int ny, int P, int fixed) {
+static void team_sizes(Job& j, int nx, int ny, int P, int fixed) {
     j.size.assign(j.K, j.G);
     const int rows = (ny + j.G - 1) / j.G;
-    const int G2 = rows > 2 ? (ny + rows - 2) / (rows - 1) : j.G;  // strips of rows - 1 rows
+    const int rows_min = (kMinLocal + nx - 1) / nx;
+    // strips of rows - 1 rows, still of at least kMinLocal unknowns
+    const int G2 = rows > 2 && rows - 1 >= rows_min ? (ny + rows - 2) / (rows - 1) : j.G;
     if (j.K >= 2 && fixed <= 0 && G2 > j.G && G2 <= kMaxTeam && P > j.K * j.G) {
         const int n_up = std::min(j.K, (P - j.K * j.G) / (G2 - j.G));
         std::vector<int> order(j.K);
@@ -239,7 +241,7 @@ static pit_status build_launch(pit_batch* b, const std::vector<pit_instance>& in
         j.inst = i;
         j.G = team[i];
         j.K = teams[i];
-        team_sizes(j, in[i].grid.ny, P, b->opt.team_ctas);
+        team_sizes(j, in[i].grid.nx, in[i].grid.ny, P, b->opt.team_ctas);
         const int width = j.width;
         if (j.K > 1) {
             j.ctas.resize(width);
