@@ -46,7 +46,7 @@ FLOPS_PER_BICGSTAB_ITER = 2 * 9 + 6 * 2 + 5 * 2
 WAVE_TRAFFIC_BYTES = 579169024 + 293091072
 WAVE_TRAFFIC_SOURCES = {
     "paper_2406_00878_gb300/csrc/pit_kernels.cuh": "fd63019189123d130c4fe289b9eb5246bd131938853eac81834b01d5b218b414",
-    "paper_2406_00878_gb300/csrc/pit.cu": "40e78dd8db27bd518a53580b4cc16aa21e51cc1e97325aff8be815e2ea64c4ea",
+    "paper_2406_00878_gb300/csrc/pit.cu": "f97dba1890ee46fe429a3ce32e51be68be3e33a6cafe4ffb5b5600e038ba9146",
 }
 
 

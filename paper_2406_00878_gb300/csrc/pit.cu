@@ -17,6 +17,7 @@
 
 #include "pit.h"
 #include "pit_internal.h"
+#include "pit_teams.h"
 #include "pit_kernels.cuh"
 
 using namespace pit;
@@ -486,35 +487,20 @@ extern "C" pit_status pit_create(const pit_grid* grid, int M, double dt, const p
                     break;
                 }
             }
-            // SMs left over by K teams of Gw CTAs go to the middle teams, a row less per strip each
-            // where they suffice: under the forcing terms the middle Newton iterations take the
-            // most sweeps per level (burgers256, FP64: 5.6, 6.0, 7.5, 8.2, 5.7, 1.3), and the
-            // slowest iteration's level chain paces the ones after it. A fixed team size
-            // (o.team_ctas) keeps every team at Gw.
+            // the SMs that K teams of Gw CTAs leave over go to the middle teams (pit_teams.h)
             std::vector<int> geom;
             if (ctx->K > 0) {
                 const int K = ctx->K, Gw = ctx->Gw;
-                const int rows = (ny + Gw - 1) / Gw;
-                // strips of rows - 1 rows, still of at least kMinLocal unknowns
-                const int G2 = rows > 2 && rows - 1 >= rows_min ? (ny + rows - 2) / (rows - 1) : Gw;
-                const int n_up = G2 > Gw && K >= 2 && o.team_ctas <= 0 ? std::min(K, (ctx->num_sms - K * Gw) / (G2 - Gw)) : 0;
                 std::vector<int> G(K, Gw);
-                if (n_up > 0) {
-                    std::vector<int> order(K);
-                    for (int t = 0; t < K; ++t) order[t] = t;
-                    // nearest the middle first (|2t - K| ascending, lower t on ties)
-                    std::stable_sort(order.begin(), order.end(),
-                                     [K](int x, int y) { return std::abs(2 * x - K) < std::abs(2 * y - K); });
-                    for (int i = 0; i < n_up; ++i) G[order[i]] = G2;
+                ctx->w_ctas = pit_wave_team_sizes(K, Gw, nx, ny, ctx->num_sms, kMinLocal, ny, o.team_ctas, G.data());
+                ctx->Gs = *std::max_element(G.begin(), G.end());
+                if (ctx->w_ctas != K * Gw) {
                     int first = 0;
                     for (int t = 0; t < K; ++t) {
                         geom.insert(geom.end(), {first, G[t], ny / G[t], ny % G[t]});
                         first += G[t];
                     }
                 }
-                ctx->Gs = n_up > 0 ? G2 : Gw;
-                ctx->w_ctas = 0;
-                for (int t = 0; t < K; ++t) ctx->w_ctas += G[t];
             }
             if (ctx->K > 0) {
                 CK(cudaFuncSetAttribute(wf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max));

@@ -26,6 +26,7 @@
 
 #include "pit.h"
 #include "pit_kernels.cuh"
+#include "pit_teams.h"
 
 using namespace pit;
 
@@ -180,30 +181,16 @@ struct Job {
     std::vector<int> ctas;         // team tk, rank r -> ctas[first[tk] + r]
 };
 
-// Team sizes of a job of K teams of G CTAs on P SMs: the SMs that the K teams leave over go to
-// the teams nearest the middle, a row less per strip each where they suffice (the middle
-// Newton iterations take the most sweeps per level, and the slowest one paces the rest; the
-// single-problem wavefront launch does the same). fixed > 0 keeps every team at G.
+// Team sizes of a job of K teams of G CTAs on P SMs: the SMs the teams leave over go to the
+// middle teams, as in the single-problem wavefront launch (pit_teams.h).
 static void team_sizes(Job& j, int nx, int ny, int P, int fixed) {
     j.size.assign(j.K, j.G);
-    const int rows = (ny + j.G - 1) / j.G;
-    const int rows_min = (kMinLocal + nx - 1) / nx;
-    // strips of rows - 1 rows, still of at least kMinLocal unknowns
-    const int G2 = rows > 2 && rows - 1 >= rows_min ? (ny + rows - 2) / (rows - 1) : j.G;
-    if (j.K >= 2 && fixed <= 0 && G2 > j.G && G2 <= kMaxTeam && P > j.K * j.G) {
-        const int n_up = std::min(j.K, (P - j.K * j.G) / (G2 - j.G));
-        std::vector<int> order(j.K);
-        std::iota(order.begin(), order.end(), 0);
-        const int K = j.K;
-        std::stable_sort(order.begin(), order.end(), [K](int x, int y) { return std::abs(2 * x - K) < std::abs(2 * y - K); });
-        for (int i = 0; i < n_up; ++i) j.size[order[i]] = G2;
-    }
+    j.width = pit_wave_team_sizes(j.K, j.G, nx, ny, P, kMinLocal, kMaxTeam, fixed, j.size.data());
     j.first.assign(j.K, 0);
-    j.width = 0;
     j.Gs = 0;
-    for (int t = 0; t < j.K; ++t) {
-        j.first[t] = j.width;
-        j.width += j.size[t];
+    for (int t = 0, f = 0; t < j.K; ++t) {
+        j.first[t] = f;
+        f += j.size[t];
         j.Gs = std::max(j.Gs, j.size[t]);
     }
 }
