@@ -291,8 +291,9 @@ pit_status pit_solve_host(pit_ctx* ctx, const double* u0_host, double* U_host, p
  * level chain of eq. 7 with Newton iterations until its residual is <= tol_res,
  * in windows of opt->window levels (default 32). A problem on a grid of at least
  * opt->batch_wave_nodes nodes is a wavefront job: K teams of G CTAs (K * G up to
- * the SM count) with K Newton iterations of a window in flight, as in pit_solve;
- * these jobs run first, one after another. Every other problem gets one team of
+ * the SM count, the SMs left over going to the middle teams) with K Newton
+ * iterations of a window in flight, as in pit_solve; these jobs run first, one
+ * after another. Every other problem gets one team of
  * CTAs, and teams of different sizes run side by side on the remaining SMs and
  * afterwards. pit_batch_create picks every such team's size with an autotuner
  * (short timed runs of each distinct grid size at candidate team sizes;
